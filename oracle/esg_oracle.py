@@ -1,0 +1,304 @@
+"""Float64 CPU oracle for ESG (arxiv 2504.04018). TEST INFRASTRUCTURE ONLY.
+
+Pure-Python/numpy parts: re-ranking, the elastic range decomposition of
+Algorithm 4, the exact range-filtered k-NN of Definitions 1-2, the merge of
+Algorithm 4, recall. Graph search (Algorithm 1) and the index build
+(Algorithm 3) run in ``esg_oracle.c`` (plain single-threaded C, float64),
+loaded through ctypes.
+
+Conventions: ranks are 0-based and ranges inclusive ([l, r] with
+0 <= l <= r <= N-1); the paper's ranks are 1-based (Definition 2). Row i of a
+re-ranked matrix holds the point of rank i. Squared Euclidean distance
+("l2") is sum (q - x)^2; inner-product distance ("ip") is -<q, x>. Orderings
+are lexicographic on (distance, rank).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "esg_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libesg_oracle.so")
+NONE = 0xFFFFFFFF
+METRICS = {"l2": 0, "ip": 1}
+
+__all__ = [
+    "build_c", "rerank", "is_leaf", "split", "Piece", "decompose", "graph_depths",
+    "bruteforce", "merge_topk", "OracleIndex", "build_index", "graph_search",
+    "search", "recall_at_k", "distances", "METRICS", "NONE",
+]
+
+
+# ------------------------------------------------------------------ C part
+
+def build_c(force: bool = False) -> str:
+    """Compile esg_oracle.c into oracle/_build/libesg_oracle.so (gcc -O2)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _c():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_c())
+        P = ctypes.c_void_p
+        lib.oracle_graph_search.restype = ctypes.c_int
+        lib.oracle_graph_search.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P,
+                                            ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
+                                            ctypes.c_int64, ctypes.c_int64, P, P, P]
+        lib.oracle_build.restype = ctypes.c_int
+        lib.oracle_build.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------- re-ranking
+
+def rerank(attr: np.ndarray) -> np.ndarray:
+    """Rank order of the points (Section 1 footnote): ``perm[i]`` is the
+    original row of the point with rank i, sorting by attribute value with
+    ties broken by original row."""
+    attr = np.asarray(attr, dtype=np.float64)
+    return np.lexsort((np.arange(attr.shape[0]), attr)).astype(np.int64)
+
+
+# ------------------------------------------------------------ segment tree
+
+def is_leaf(l: int, r: int, leaf_size: int) -> bool:
+    """A node [l, r] carries no graph when r - l < leaf_size (Algorithm 3
+    and Algorithm 4, first test)."""
+    return r - l < leaf_size
+
+
+def split(l: int, r: int) -> int:
+    """mid = floor((l + r) / 2); children are [l, mid] and [mid + 1, r]."""
+    return (l + r) // 2
+
+
+@dataclasses.dataclass(frozen=True)
+class Piece:
+    """One subrange chosen by Algorithm 4.
+
+    kind: "graph" (search the graph of node [node_l, node_r]) or "scan"
+    (linear scan). [pl, pr] is the part of the query range it answers.
+    heap: the node's heap number (root 0, children 2h+1 and 2h+2); depth:
+    its depth (root 0).
+    """
+    kind: str
+    node_l: int
+    node_r: int
+    pl: int
+    pr: int
+    heap: int
+    depth: int
+
+
+def decompose(n: int, leaf_size: int, lq: int, rq: int, fanout: int = 2) -> List[Piece]:
+    """Query-2D-Index (Algorithm 4) restricted to the choice of subranges.
+
+    Starting at the root [0, n-1]: a node with r - l < leaf_size is answered
+    by a linear scan of its part of the query; a node that contains the query
+    part with |[lq, rq]| / |[l, r]| >= c (c = 1/fanout, tested in integers as
+    fanout * |[lq, rq]| >= |[l, r]|) is answered by its graph; otherwise the
+    node is split at mid and the query part is clipped to each child it
+    overlaps (left first). Lemma 3 bounds the result to two pieces.
+    """
+    if not (0 <= lq <= rq <= n - 1):
+        raise ValueError("need 0 <= lq <= rq <= n-1")
+    out: List[Piece] = []
+
+    def rec(l, r, a, b, h, depth):
+        if is_leaf(l, r, leaf_size):
+            out.append(Piece("scan", l, r, a, b, h, depth))
+            return
+        if l <= a and b <= r and fanout * (b - a + 1) >= (r - l + 1):
+            out.append(Piece("graph", l, r, a, b, h, depth))
+            return
+        mid = split(l, r)
+        if a <= mid:
+            rec(l, mid, a, min(mid, b), 2 * h + 1, depth + 1)
+        if b > mid:
+            rec(mid + 1, r, max(mid + 1, a), b, 2 * h + 2, depth + 1)
+
+    rec(0, n - 1, lq, rq, 0, 0)
+    return out
+
+
+def graph_depths(n: int, leaf_size: int) -> int:
+    """Number of depths of the tree that hold at least one graph node."""
+    L = 0
+    frontier = [(0, n - 1)]
+    while frontier:
+        nxt = []
+        any_graph = False
+        for (l, r) in frontier:
+            if not is_leaf(l, r, leaf_size):
+                any_graph = True
+                m = split(l, r)
+                nxt += [(l, m), (m + 1, r)]
+        if not any_graph:
+            break
+        L += 1
+        frontier = nxt
+    return L
+
+
+# ------------------------------------------------------------ exact k-NN
+
+def distances(X: np.ndarray, q: np.ndarray, metric: str) -> np.ndarray:
+    """Float64 distances from q to every row of X: squared Euclidean
+    sum_j (q_j - x_j)^2, or negative inner product -sum_j q_j x_j."""
+    X = np.asarray(X, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    if metric == "l2":
+        diff = X - q[None, :]
+        return np.einsum("ij,ij->i", diff, diff)
+    if metric == "ip":
+        return -(X @ q)
+    raise ValueError(metric)
+
+
+def bruteforce(X: np.ndarray, q: np.ndarray, pl: int, pr: int, k: int, metric: str
+               ) -> Tuple[np.ndarray, np.ndarray]:
+    """Exact range-filtered k-NN (Definitions 1 and 2): the min(k, pr-pl+1)
+    rows of X with rank in [pl, pr] closest to q, ascending by (distance,
+    rank). Returns (ranks int64, distances float64)."""
+    if pr < pl:
+        return np.zeros(0, np.int64), np.zeros(0, np.float64)
+    dd = distances(X[pl:pr + 1], q, metric)
+    ranks = np.arange(pl, pr + 1, dtype=np.int64)
+    order = np.lexsort((ranks, dd))[:k]
+    return ranks[order], dd[order]
+
+
+def merge_topk(parts: Sequence[Tuple[np.ndarray, np.ndarray]], k: int
+               ) -> Tuple[np.ndarray, np.ndarray]:
+    """Merge of per-piece results (Algorithm 4, last step): the k best of
+    their union by (distance, rank). Pieces cover disjoint ranges, so no id
+    appears twice."""
+    if not parts:
+        return np.zeros(0, np.int64), np.zeros(0, np.float64)
+    ids = np.concatenate([p[0] for p in parts]).astype(np.int64)
+    dd = np.concatenate([p[1] for p in parts]).astype(np.float64)
+    order = np.lexsort((ids, dd))[:k]
+    return ids[order], dd[order]
+
+
+# ------------------------------------------------------------ index build
+
+@dataclasses.dataclass
+class OracleIndex:
+    """Graphs of the segment tree in the layout the GPU library imports.
+
+    X: float64 [n, d] in rank order. adj: uint32 [L, n, R]; row i of depth t
+    lists the neighbour ranks of point i in the graph of the depth-t node
+    that contains i (NONE-padded). entries: int32 [2^L - 1, E] entry ranks
+    per heap node (-1 padded; all -1 for leaves). perm: rank -> original row.
+    """
+    X: np.ndarray
+    perm: np.ndarray
+    adj: np.ndarray
+    entries: np.ndarray
+    leaf_size: int
+    M: int
+    metric: str
+
+    @property
+    def n(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def R(self) -> int:
+        return self.adj.shape[2]
+
+    @property
+    def L(self) -> int:
+        return self.adj.shape[0]
+
+
+def build_index(base: np.ndarray, attr: Optional[np.ndarray], metric: str, leaf_size: int,
+                M: int, efc: int = 200, n_entries: int = 16) -> OracleIndex:
+    """Re-rank the points, then Build-2D-Index (Algorithm 3) with HNSW-style
+    insertion into flat graphs (out-degree cap R = 2M, M neighbours chosen
+    per insertion by edge occlusion, efc = construction beam width)."""
+    n, d = base.shape
+    perm = rerank(attr) if attr is not None else np.arange(n, dtype=np.int64)
+    X = np.ascontiguousarray(base[perm].astype(np.float64))
+    L = graph_depths(n, leaf_size)
+    R = 2 * M
+    adj = np.empty((max(L, 0), n, R), dtype=np.uint32)
+    entries = np.empty(((1 << L) - 1 if L > 0 else 0, n_entries), dtype=np.int32)
+    rc = _c().oracle_build(_ptr(X), n, d, METRICS[metric], leaf_size, M, efc, n_entries, L,
+                           _ptr(adj), _ptr(entries) if entries.size else None)
+    if rc != 0:
+        raise RuntimeError("oracle_build failed")
+    return OracleIndex(X, perm, adj, entries, leaf_size, M, metric)
+
+
+# -------------------------------------------------------------- search
+
+def graph_search(index: OracleIndex, depth: int, heap: int, q: np.ndarray, ef: int,
+                 pl: int, pr: int, counters: Optional[np.ndarray] = None
+                 ) -> Tuple[np.ndarray, np.ndarray]:
+    """Algorithm 1 with POST filtering to [pl, pr] on the graph of heap node
+    `heap` (at `depth`), from that node's entry points. Returns up to ef
+    (ranks, distances) ascending."""
+    X = index.X
+    q64 = np.ascontiguousarray(q, dtype=np.float64)
+    ent = np.ascontiguousarray(index.entries[heap].astype(np.uint32))
+    ent_n = int(np.sum(index.entries[heap] >= 0))
+    adj = np.ascontiguousarray(index.adj[depth])
+    ids = np.empty(ef, dtype=np.uint32)
+    dd = np.empty(ef, dtype=np.float64)
+    cnt_arr = counters if counters is not None else np.zeros(2, dtype=np.int64)
+    cnt = _c().oracle_graph_search(_ptr(X), X.shape[0], X.shape[1], METRICS[index.metric],
+                                   _ptr(adj), index.R, _ptr(ent), ent_n, _ptr(q64), ef,
+                                   pl, pr, _ptr(ids), _ptr(dd), _ptr(cnt_arr))
+    return ids[:cnt].astype(np.int64), dd[:cnt].copy()
+
+
+def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
+           counters: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+    """Query-2D-Index (Algorithm 4): decompose [lq, rq]; answer scan pieces
+    exactly and graph pieces with Algorithm 1 + POST at beam width
+    max(ef, k); merge into the top k by (distance, rank). Returns ranks."""
+    parts = []
+    for p in decompose(index.n, index.leaf_size, lq, rq):
+        if p.kind == "scan":
+            parts.append(bruteforce(index.X, q, p.pl, p.pr, k, index.metric))
+        else:
+            ids, dd = graph_search(index, p.depth, p.heap, q, max(ef, k), p.pl, p.pr, counters)
+            parts.append((ids[:k], dd[:k]))
+    return merge_topk(parts, k)
+
+
+def recall_at_k(found: Sequence[np.ndarray], truth: Sequence[np.ndarray]) -> float:
+    """Mean over queries of |found ∩ truth| / |truth| (truth holds
+    min(k, range width) ids per query)."""
+    tot = 0.0
+    for f, t in zip(found, truth):
+        if len(t) == 0:
+            tot += 1.0
+            continue
+        tot += len(set(np.asarray(f).tolist()) & set(np.asarray(t).tolist())) / len(t)
+    return tot / max(1, len(truth))

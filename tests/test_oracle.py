@@ -1,0 +1,297 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself (hand traces, closed forms, brute force, textbook routines)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------- re-ranking
+
+def test_rerank_is_stable_sort_by_attribute():
+    attr = np.array([3.0, 1.0, 2.0, 1.0, -5.0, 2.0])
+    perm = O.rerank(attr)
+    # rank 0 = smallest attribute; ties keep original order
+    assert perm.tolist() == [4, 1, 3, 2, 5, 0]
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 20, size=500).astype(np.float64)
+    assert np.array_equal(O.rerank(a), np.argsort(a, kind="stable"))
+
+
+# ------------------------------------------------ decomposition (Alg 4)
+
+def _all_nodes(n, leaf):
+    """Every node of the segment tree as (l, r, depth, heap), by explicit
+    breadth-first enumeration."""
+    out, frontier, depth = [], [(0, n - 1, 0)], 0
+    while frontier:
+        nxt = []
+        for (l, r, h) in frontier:
+            out.append((l, r, depth, h))
+            if r - l >= leaf:
+                m = (l + r) // 2
+                nxt += [(l, m, 2 * h + 1), (m + 1, r, 2 * h + 2)]
+        frontier, depth = nxt, depth + 1
+    return out
+
+
+def _closed_form(nodes, leaf, lq, rq):
+    """Independent statement of the decomposition: along the chain of nodes
+    containing the query, take the shallowest that is a leaf or holds the query
+    with ratio >= 1/2; if none, split at the mid of the deepest containing
+    node and resolve each part the same way along its own chain."""
+    def chain(a, b):
+        return sorted([nd for nd in nodes if nd[0] <= a and b <= nd[1]], key=lambda t: t[2])
+
+    def accept(nd, a, b):
+        l, r = nd[0], nd[1]
+        return (r - l < leaf) or (2 * (b - a + 1) >= r - l + 1)
+
+    def resolve(a, b):
+        for nd in chain(a, b):
+            if accept(nd, a, b):
+                kind = "scan" if nd[1] - nd[0] < leaf else "graph"
+                return (kind, nd[0], nd[1], a, b, nd[3], nd[2])
+        raise AssertionError("a suffix/prefix part always reaches an accepting node")
+
+    ch = chain(lq, rq)
+    for nd in ch:
+        if accept(nd, lq, rq):
+            kind = "scan" if nd[1] - nd[0] < leaf else "graph"
+            return [(kind, nd[0], nd[1], lq, rq, nd[3], nd[2])]
+    deepest = ch[-1]
+    m = (deepest[0] + deepest[1]) // 2
+    return [resolve(lq, m), resolve(m + 1, rq)]
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 1), (2, 1), (3, 1), (7, 1), (7, 2), (64, 1), (64, 4),
+                                    (100, 3), (129, 8), (130, 16)])
+def test_decompose_matches_closed_form_exhaustive(n, leaf):
+    nodes = _all_nodes(n, leaf)
+    for lq in range(n):
+        for rq in range(lq, n):
+            got = [(p.kind, p.node_l, p.node_r, p.pl, p.pr, p.heap, p.depth)
+                   for p in O.decompose(n, leaf, lq, rq)]
+            assert got == _closed_form(nodes, leaf, lq, rq), (n, leaf, lq, rq)
+
+
+def _check_invariants(n, leaf, lq, rq, pieces):
+    assert 1 <= len(pieces) <= 2                                   # Lemma 3
+    # pieces partition [lq, rq] left to right
+    assert pieces[0].pl == lq and pieces[-1].pr == rq
+    for a, b in zip(pieces, pieces[1:]):
+        assert b.pl == a.pr + 1
+    for p in pieces:
+        assert p.node_l <= p.pl <= p.pr <= p.node_r                 # piece inside its node
+        size = p.node_r - p.node_l + 1
+        if p.kind == "graph":
+            assert size - 1 >= leaf
+            assert 2 * (p.pr - p.pl + 1) >= size                     # elastic factor >= 1/2
+        else:
+            assert size - 1 < leaf
+
+
+@pytest.mark.parametrize("n,leaf", [(1000, 16), (1023, 1), (257, 256), (256, 256)])
+def test_decompose_invariants_exhaustive(n, leaf):
+    for lq in range(n):
+        for rq in range(lq, n):
+            _check_invariants(n, leaf, lq, rq, O.decompose(n, leaf, lq, rq))
+
+
+@pytest.mark.parametrize("n,leaf", [(2049, 1), (10_000, 256), (1_000_000, 256), (10_000_000, 256)])
+def test_decompose_invariants_sampled(n, leaf):
+    rng = np.random.default_rng(n)
+    for _ in range(3000):
+        a, b = sorted(rng.integers(0, n, size=2).tolist())
+        _check_invariants(n, leaf, a, b, O.decompose(n, leaf, a, b))
+
+
+def test_decompose_special_cases():
+    # the full range is answered by the root graph alone
+    assert O.decompose(1000, 16, 0, 999) == [O.Piece("graph", 0, 999, 0, 999, 0, 0)]
+    # a single point inside a leaf is a scan of that point
+    p = O.decompose(1000, 16, 5, 5)
+    assert len(p) == 1 and p[0].kind == "scan" and (p[0].pl, p[0].pr) == (5, 5)
+    # exactly half of the root, straddling mid: 500 points of [0,999] with
+    # ratio 1/2 -> the root graph is accepted (the test is inclusive)
+    p = O.decompose(1000, 16, 250, 749)
+    assert p == [O.Piece("graph", 0, 999, 250, 749, 0, 0)]
+    # one point less than half -> split at the root's mid (499)
+    p = O.decompose(1000, 16, 251, 749)
+    assert [(q.pl, q.pr) for q in p] == [(251, 499), (500, 749)]
+    # whole tree is a leaf
+    assert O.decompose(10, 16, 2, 7)[0].kind == "scan"
+
+
+def test_graph_depths():
+    assert O.graph_depths(10, 16) == 0
+    assert O.graph_depths(17, 16) == 1
+    assert O.graph_depths(10_000, 256) == 6      # 10000, 5000, ..., 313 > 256 >= 157
+    assert O.graph_depths(1_000_000, 256) == 12
+
+
+# --------------------------------------------------------- exact k-NN
+
+def test_bruteforce_golden():
+    g = json.load(open(os.path.join(GOLDEN, "alg1_traces.json")))["bruteforce"]
+    X = np.array(g["points_1d"])[:, None]
+    for c in g["cases"]:
+        ranks, dd = O.bruteforce(X, np.array([c["q"]]), c["range"][0], c["range"][1], c["k"], c["metric"])
+        assert ranks.tolist() == c["ranks"]
+        assert np.allclose(dd, c["dist"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+def test_bruteforce_vs_expanded_form(metric):
+    """Against a differently-written distance (norm expansion) and argsort."""
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((400, 24))
+    for _ in range(20):
+        q = rng.standard_normal(24)
+        l, r = sorted(rng.integers(0, 400, size=2).tolist())
+        k = int(rng.integers(1, 30))
+        ids, dd = O.bruteforce(X, q, l, r, k, metric)
+        sub = X[l:r + 1]
+        if metric == "l2":
+            ref = (sub ** 2).sum(1) + (q ** 2).sum() - 2 * sub @ q
+        else:
+            ref = -np.array([sum(a * b for a, b in zip(row, q)) for row in sub])
+        order = np.argsort(ref, kind="stable")[:k] + l
+        assert ids.tolist() == order.tolist()
+        assert len(ids) == min(k, r - l + 1)
+        assert np.allclose(dd, ref[order - l], rtol=1e-9, atol=1e-9)
+
+
+def test_merge_topk():
+    a = (np.array([3, 9]), np.array([0.5, 2.0]))
+    b = (np.array([12, 14, 15]), np.array([0.1, 2.0, 3.0]))
+    ids, dd = O.merge_topk([a, b], 4)
+    assert ids.tolist() == [12, 3, 9, 14]          # tie at 2.0 broken by rank
+    assert dd.tolist() == [0.1, 0.5, 2.0, 2.0]
+
+
+# ---------------------------------------------------- Algorithm 1 traces
+
+def _path_index(points, adjacency, entries, metric):
+    n = len(points)
+    R = max(len(a) for a in adjacency)
+    adj = np.full((1, n, R), O.NONE, dtype=np.uint32)
+    for i, nb in enumerate(adjacency):
+        adj[0, i, :len(nb)] = nb
+    ent = np.full((1, len(entries)), -1, dtype=np.int32)
+    ent[0, :] = entries
+    X = np.array(points, dtype=np.float64)[:, None]
+    return O.OracleIndex(X, np.arange(n), adj, ent, 1, R // 2 or 1, metric)
+
+
+def test_graph_search_hand_traces():
+    g = json.load(open(os.path.join(GOLDEN, "alg1_traces.json")))
+    for c in g["cases"]:
+        idx = _path_index(g["points_1d"], g["adjacency"], c["entries"], g["metric"])
+        cnt = np.zeros(2, np.int64)
+        ids, dd = O.graph_search(idx, 0, 0, np.array([c["q"]]), c["ef"], c["range"][0],
+                                 c["range"][1], cnt)
+        assert ids.tolist() == c["result_ranks"], c["why"]
+        assert np.allclose(dd, c["result_dist"], atol=1e-12)
+        assert int(cnt[0]) == c["expansions"], c["why"]
+        assert int(cnt[1]) == c["distance_evals"], c["why"]
+
+
+# --------------------------------------- build (Alg 3) + search (Alg 4)
+
+@pytest.fixture(scope="module")
+def small_index():
+    w = synthetic.small_mixture(600, 16, 60, n_comp=8, seed=11, M=6, leaf_size=20)
+    idx = O.build_index(w.base, w.attr, w.metric, w.leaf_size, w.M, efc=40, n_entries=4)
+    return w, idx
+
+
+def test_build_invariants(small_index):
+    w, idx = small_index
+    n, R = idx.n, idx.R
+    assert idx.L == O.graph_depths(n, w.leaf_size)
+    nodes = [nd for nd in _all_nodes(n, w.leaf_size) if nd[1] - nd[0] >= w.leaf_size]
+    assert nodes and all(nd[2] < idx.L for nd in nodes)
+    for (l, r, depth, h) in nodes:
+        rows = idx.adj[depth, l:r + 1]
+        for i, row in zip(range(l, r + 1), rows):
+            nb = row[row != O.NONE].astype(np.int64)
+            assert len(nb) <= R
+            assert np.all(row[len(nb):] == O.NONE)          # packed to the left
+            assert i not in nb                               # no self loops
+            assert len(set(nb.tolist())) == len(nb)          # no duplicate edges
+            assert np.all((nb >= l) & (nb <= r))             # edges stay inside the node
+        ent = [e for e in idx.entries[h] if e >= 0]
+        assert ent and all(l <= e <= r for e in ent)
+        # almost every point is reachable from the entries; occlusion pruning
+        # of reverse edges can orphan a few points, as in HNSW
+        assert len(_reachable(idx, depth, h)) >= 0.99 * (r - l + 1)
+
+
+def _reachable(idx, depth, h):
+    ent = [int(e) for e in idx.entries[h] if e >= 0]
+    seen, stack = set(ent), list(ent)
+    while stack:
+        u = stack.pop()
+        for v in idx.adj[depth, u]:
+            if v != O.NONE and int(v) not in seen:
+                seen.add(int(v)); stack.append(int(v))
+    return seen
+
+
+def test_search_exact_when_ef_covers_node(small_index):
+    """With ef >= node size, Algorithm 1 + POST visits every point reachable
+    from the entries, so each graph piece returns the exact filtered k-NN of
+    its reachable points and scan pieces the exact k-NN of the piece."""
+    w, idx = small_index
+    for i in range(len(w.queries)):
+        l, r, k = int(w.l[i]), int(w.r[i]), 10
+        q = w.queries[i]
+        ids, dd = O.search(idx, q, l, r, k, ef=idx.n)
+        parts = []
+        for p in O.decompose(idx.n, idx.leaf_size, l, r):
+            cand = np.arange(p.pl, p.pr + 1)
+            if p.kind == "graph":
+                reach = _reachable(idx, p.depth, p.heap)
+                cand = np.array([c for c in cand if int(c) in reach], dtype=np.int64)
+            dist = O.distances(idx.X[cand], q, w.metric)
+            order = np.lexsort((cand, dist))[:k]
+            parts.append((cand[order], dist[order]))
+        gt, gd = O.merge_topk(parts, k)
+        assert ids.tolist() == gt.tolist()
+        assert np.allclose(dd, gd)
+
+
+def test_search_result_properties(small_index):
+    w, idx = small_index
+    for i in range(len(w.queries)):
+        l, r = int(w.l[i]), int(w.r[i])
+        ids, dd = O.search(idx, w.queries[i], l, r, 10, ef=8)
+        assert len(ids) >= min(10, r - l + 1) - 1
+        assert np.all((ids >= l) & (ids <= r))
+        assert len(set(ids.tolist())) == len(ids)
+        assert np.all(np.diff(dd) >= 0)
+
+
+def test_full_range_is_unfiltered_search(small_index):
+    """A full-range query is answered by the root graph with no filtering:
+    the same result as Algorithm 1 on the root from the root entries."""
+    w, idx = small_index
+    for i in range(10):
+        ids, _ = O.search(idx, w.queries[i], 0, idx.n - 1, 10, ef=16)
+        ids2, _ = O.graph_search(idx, 0, 0, w.queries[i], 16, 0, idx.n - 1)
+        assert ids.tolist() == ids2[:10].tolist()
+
+
+def test_leaf_range_is_exact_scan(small_index):
+    w, idx = small_index
+    for i in range(10):
+        ids, _ = O.search(idx, w.queries[i], 100, 100 + w.leaf_size - 5, 5, ef=1)
+        gt, _ = O.bruteforce(idx.X, w.queries[i], 100, 100 + w.leaf_size - 5, 5, w.metric)
+        assert ids.tolist() == gt.tolist()
