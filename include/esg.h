@@ -1,0 +1,253 @@
+/*
+ * esg.h — C ABI of the GB300 (sm_103a) implementation of ESG, elastic graphs
+ * for range-filtering approximate k-nearest-neighbour search (RFAKNN),
+ * arxiv 2504.04018.
+ *
+ * Problem (Definitions 1 and 2): points v_0..v_{N-1} in R^d carry a numeric
+ * attribute. After re-ranking (Section 1, footnote on re-ranking) the point
+ * of rank i is the i-th smallest attribute, so a value range becomes an
+ * inclusive rank range [l, r]. A query (q, [l, r], k) asks for the k points
+ * with rank in [l, r] closest to q.
+ *
+ * Method (Section 4.2): a segment tree over ranks holds one proximity graph
+ * per node wider than the leaf size (Algorithm 3). A query range is split
+ * into at most two elastic subranges (Algorithm 4, Lemma 3): a node is used
+ * when it contains the query part and the part covers at least half of it
+ * (elastic factor c = 1/2, Definition 3). Each graph piece is answered by a
+ * beam search (Algorithm 1) that walks out-of-range points but only admits
+ * in-range points to the result queue (the POST principle, Section 2.2);
+ * leaf pieces are scanned. The piece results are merged into the top k.
+ *
+ * Conventions for every call:
+ *  - ranks and ranges are 0-based and inclusive (the paper counts from 1);
+ *  - distances: ESG_L2SQ = sum_j (q_j - x_j)^2; ESG_IP = -sum_j q_j x_j;
+ *  - results are ordered by (distance, rank); unused result slots hold id -1
+ *    and distance +inf;
+ *  - "device" pointers are CUDA global memory of the current device, "host"
+ *    pointers are ordinary CPU memory; the caller owns every buffer it passes
+ *    and the library never frees caller memory;
+ *  - asynchronous calls enqueue work on the given stream and return; their
+ *    outputs are valid once the stream reaches that point;
+ *  - no C++ exception crosses this interface; every call returns an
+ *    esg_status and esg_last_error() describes the last failure on the
+ *    calling thread.
+ */
+#ifndef ESG_H
+#define ESG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *esg_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    ESG_OK = 0,
+    ESG_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+    ESG_ERR_OOM = 2,         /* device or host allocation failed */
+    ESG_ERR_CUDA = 3,        /* a CUDA runtime call failed (see esg_last_error) */
+    ESG_ERR_IO = 4,          /* file could not be read or written */
+    ESG_ERR_CORRUPT = 5,     /* file content is not a valid index */
+    ESG_ERR_TIMEOUT = 6,     /* a bounded device wait ran out */
+    ESG_ERR_UNSUPPORTED = 7  /* valid request this build does not implement */
+} esg_status;
+
+typedef enum { ESG_L2SQ = 0, ESG_IP = 1 } esg_metric;
+
+/* Storage type of the vectors used during graph traversal. */
+typedef enum { ESG_F32 = 0, ESG_BF16 = 1, ESG_FP8E4M3 = 2 } esg_dtype;
+
+/* Per-query status codes written by esg_search_batch. */
+enum {
+    ESG_Q_OK = 0,
+    ESG_Q_INVALID = 1,   /* l > r, r >= N, l < 0, k < 1 or k > k_max: count = 0 */
+    ESG_Q_TRUNCATED = 2, /* a beam search hit its expansion cap; results are partial */
+    ESG_Q_OVERFLOW = 4   /* the candidate list or visited set overflowed (results valid) */
+};
+
+/* Piece kinds of the elastic decomposition. */
+enum { ESG_PIECE_NONE = 0, ESG_PIECE_GRAPH = 1, ESG_PIECE_SCAN = 2 };
+
+/*
+ * One subrange chosen by Algorithm 4: the tree node [node_l, node_r] (heap
+ * number `heap`: root 0, children 2h+1 and 2h+2; `depth` from the root)
+ * answers the query part [pl, pr]. kind is ESG_PIECE_GRAPH (beam search on
+ * the node's graph) or ESG_PIECE_SCAN (linear scan of a leaf).
+ */
+typedef struct {
+    int64_t node_l, node_r, pl, pr;
+    int32_t heap, depth, kind, reserved;
+} esg_piece;
+
+typedef struct esg_index esg_index; /* opaque; owned by the library */
+
+/*
+ * Index build parameters. Defaults: esg_build_params_default().
+ *  M          graph degree parameter: each inserted point keeps up to M
+ *             neighbours chosen by edge occlusion and a row holds at most
+ *             R = 2M neighbours (Section 5.1 uses M = 16);
+ *  leaf_size  l: a tree node with r - l < leaf_size holds no graph and is
+ *             answered by a scan (Algorithm 3/4, first test);
+ *  n_entries  entry points per graph node (ranks evenly spaced over the
+ *             node), 1..32;
+ *  knn_k      exact nearest neighbours inside the node offered to edge
+ *             occlusion per point (construction candidate pool);
+ *  sample_k   nearest points of an evenly spaced sample of the node
+ *             (sample_size points) added to that pool for long-range edges;
+ *  storage    traversal precision kept on the device besides FP32.
+ */
+typedef struct {
+    int32_t M;
+    int32_t leaf_size;
+    int32_t n_entries;
+    int32_t knn_k;
+    int32_t sample_k;
+    int32_t sample_size;
+    esg_metric metric;
+    esg_dtype storage;
+} esg_build_params;
+
+/*
+ * Search parameters. Defaults: esg_search_params_default().
+ *  ef              beam width m of Algorithm 1 (>= k; raised to k if lower);
+ *  max_expansions  cap on expansions per graph piece (0 = 16 * ef + 256);
+ *                  reaching it sets ESG_Q_TRUNCATED;
+ *  rerank          with BF16/FP8 storage: recompute FP32 distances of the
+ *                  final candidates and re-sort (1) or not (0);
+ *  use_learned     1 = per-query beam width from the trained predictor
+ *                  (falls back to ef when no predictor is trained).
+ */
+typedef struct {
+    int32_t ef;
+    int32_t max_expansions;
+    int32_t rerank;
+    int32_t use_learned;
+} esg_search_params;
+
+esg_build_params esg_build_params_default(void);
+esg_search_params esg_search_params_default(void);
+
+/*
+ * Build an ESG index (Algorithm 3's segment tree of graphs) on the current
+ * CUDA device.
+ *  vectors  host, [n, d] row-major float32, original order;
+ *  attr     host, [n] float64 attribute values, or NULL (attribute = row);
+ *           ranks sort by attribute with ties broken by row;
+ *  n >= 1, 1 <= d <= 1024 with d % 8 == 0;
+ *  out      receives the new index; free it with esg_free.
+ * Synchronous: returns when the index is ready. The device copy of the
+ * vectors is FP32 (plus BF16 or FP8 if params->storage asks).
+ */
+esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *attr,
+                     const esg_build_params *params, esg_index **out);
+
+/*
+ * Create an index from graphs built elsewhere (for example by a CPU
+ * reference build), in the layout the library stores:
+ *  vectors  host [n, d] float32 in RANK order (row i = rank i);
+ *  perm     host [n] int64: original id of rank i (NULL = identity);
+ *  adj      host [L, n, R] uint32: row i of depth t lists the neighbour ranks
+ *           of point i in the graph of the depth-t node containing i, padded
+ *           with 0xFFFFFFFF; R <= 128;
+ *  entries  host [2^L - 1, n_entries] int32 entry ranks per heap node, -1
+ *           padded; n_entries <= 32.
+ * L must equal the number of depths holding graph nodes for (n, leaf_size).
+ */
+esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n, int32_t d,
+                            esg_metric metric, int32_t leaf_size, const uint32_t *adj,
+                            int32_t L, int32_t R, const int32_t *entries, int32_t n_entries,
+                            esg_dtype storage, esg_index **out);
+
+/* Shape of an index: any output pointer may be NULL. */
+esg_status esg_index_info(const esg_index *index, int64_t *n, int32_t *d, int32_t *L,
+                          int32_t *R, int32_t *n_entries, int32_t *leaf_size,
+                          int32_t *metric, int32_t *storage);
+
+/*
+ * Copy the index's graphs to host buffers of the esg_index_import layout:
+ * adj [L, n, R] uint32, entries [2^L - 1, n_entries] int32, perm [n] int64.
+ * Any pointer may be NULL to skip it. Synchronous.
+ */
+esg_status esg_index_export(const esg_index *index, uint32_t *adj, int32_t *entries,
+                            int64_t *perm);
+
+void esg_free(esg_index *index);
+
+/*
+ * Elastic decomposition (Algorithm 4's choice of subranges; at most two
+ * pieces by Lemma 3) of nq query ranges over the tree of n points with the
+ * given leaf size (fanout 2, elastic factor 1/2).
+ *  l, r         device [nq] int64 inclusive rank ranges;
+ *  out_pieces   device [nq, 2] esg_piece (unused slot: kind ESG_PIECE_NONE);
+ *  out_npieces  device [nq] int32: number of pieces, 0 for an invalid range.
+ * Asynchronous on `stream`. Integer-only and exact.
+ */
+esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
+                               int64_t nq, esg_piece *out_pieces, int32_t *out_npieces,
+                               esg_stream_t stream);
+
+/*
+ * Range-filtered approximate k-NN search (Algorithm 4 with Algorithm 1 +
+ * POST on each graph piece, exact scan of leaf pieces, merge).
+ *  queries     device [nq, d] float32;
+ *  l, r        device [nq] int64 inclusive rank ranges;
+ *  k           device [nq] int32 per-query k (1..k_max), or NULL for k_max;
+ *  k_max       1..1024, row stride of the outputs;
+ *  out_ids     device [nq, k_max] int64: original ids (via the re-ranking);
+ *  out_dist    device [nq, k_max] float32 distances;
+ *  out_count   device [nq] int32: results written, min(k, r - l + 1) when the
+ *              graphs reach enough in-range points;
+ *  out_status  device [nq] int32 (ESG_Q_* bits) or NULL;
+ *  out_stats   device [nq, 4] int64 (expansions, distance evaluations,
+ *              out-of-range evaluations, pieces) or NULL.
+ * Asynchronous on `stream`; temporary device memory is taken from and
+ * returned to the stream-ordered allocator of that stream.
+ */
+esg_status esg_search_batch(const esg_index *index, const float *queries, int64_t nq,
+                            const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
+                            const esg_search_params *params, int64_t *out_ids, float *out_dist,
+                            int32_t *out_count, int32_t *out_status, int64_t *out_stats,
+                            esg_stream_t stream);
+
+/*
+ * Exact range-filtered k-NN by brute force (Definitions 1 and 2): for each
+ * query the min(k, r - l + 1) rows of `base` with row index in [l, r] closest
+ * to q, ordered by (distance, row). Distances are evaluated in float32 in
+ * the direct form (sum of squared differences, or the negated dot product).
+ *  base      device [n, d] float32 row-major, d % 4 == 0;
+ *  queries   device [nq, d] float32;
+ *  l, r      device [nq] int64 inclusive row ranges (invalid range: count 0);
+ *  k         1..1024;
+ *  out_ids   device [nq, k] int64 row indices, out_dist device [nq, k] float32,
+ *  out_count device [nq] int32.
+ * Asynchronous on `stream`.
+ */
+esg_status esg_bruteforce_filtered_knn(const float *base, int64_t n, int32_t d, esg_metric metric,
+                                       const float *queries, int64_t nq, const int64_t *l,
+                                       const int64_t *r, int32_t k, int64_t *out_ids,
+                                       float *out_dist, int32_t *out_count, esg_stream_t stream);
+
+/*
+ * Map attribute value ranges [lo, hi] to inclusive rank ranges [l, r] on the
+ * host (binary search over the sorted attributes). A value range holding no
+ * point yields l = r + 1. Host pointers, [nq] each.
+ */
+esg_status esg_attr_to_rank_range(const esg_index *index, const double *lo, const double *hi,
+                                  int64_t nq, int64_t *l, int64_t *r);
+
+/* Save / load an index (graphs, vectors, permutation, parameters) with a
+ * versioned header and per-section CRC32. */
+esg_status esg_save(const esg_index *index, const char *path);
+esg_status esg_load(const char *path, esg_index **out);
+
+const char *esg_status_str(esg_status s);
+const char *esg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESG_H */

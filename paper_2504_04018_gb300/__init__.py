@@ -1,0 +1,296 @@
+"""Python binding of libesg, the GB300 (sm_103a) implementation of ESG
+range-filtered approximate k-NN search (arxiv 2504.04018).
+
+Argument marshalling only: every step of the search runs in the CUDA kernels
+of ``libesg.so`` behind the C ABI of ``include/esg.h``; the functions here
+keep its names. PyTorch provides device memory and streams. There is no CPU
+fallback: importing a compute function without the compiled library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _build_lib
+
+__all__ = [
+    "load_library", "Index", "esg_build", "esg_index_import", "esg_index_export", "esg_free",
+    "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
+    "esg_attr_to_rank_range", "esg_save", "esg_load", "EsgError", "METRIC", "STORAGE",
+    "PIECE_GRAPH", "PIECE_SCAN", "Q_INVALID", "Q_TRUNCATED", "Q_OVERFLOW",
+]
+
+METRIC = {"l2": 0, "ip": 1}
+STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
+PIECE_NONE, PIECE_GRAPH, PIECE_SCAN = 0, 1, 2
+Q_INVALID, Q_TRUNCATED, Q_OVERFLOW = 1, 2, 4
+
+EXPORTED = [
+    "esg_build_params_default", "esg_search_params_default", "esg_build", "esg_index_import",
+    "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
+    "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
+    "esg_status_str", "esg_last_error",
+]
+
+
+class EsgError(RuntimeError):
+    pass
+
+
+class _BuildParams(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("n_entries", ctypes.c_int32),
+                ("knn_k", ctypes.c_int32), ("sample_k", ctypes.c_int32),
+                ("sample_size", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
+
+
+class _SearchParams(ctypes.Structure):
+    _fields_ = [("ef", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
+                ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libesg.so (compiling it with nvcc first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build_lib.LIB
+    if build_if_missing:
+        path = _build_lib.build()
+    if not os.path.exists(path):
+        raise EsgError(f"libesg.so not built: {path}")
+    lib = ctypes.CDLL(path)
+    lib.esg_build_params_default.restype = _BuildParams
+    lib.esg_search_params_default.restype = _SearchParams
+    lib.esg_build.argtypes = [_P, _I64, _I32, _P, ctypes.POINTER(_BuildParams), ctypes.POINTER(_P)]
+    lib.esg_index_import.argtypes = [_P, _P, _I64, _I32, _I32, _I32, _P, _I32, _I32, _P, _I32, _I32,
+                                     ctypes.POINTER(_P)]
+    lib.esg_index_info.argtypes = [_P] + [_P] * 8
+    lib.esg_index_export.argtypes = [_P, _P, _P, _P]
+    lib.esg_free.argtypes = [_P]
+    lib.esg_free.restype = None
+    lib.esg_decompose_batch.argtypes = [_I64, _I32, _P, _P, _I64, _P, _P, _P]
+    lib.esg_search_batch.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, ctypes.POINTER(_SearchParams),
+                                     _P, _P, _P, _P, _P, _P]
+    lib.esg_bruteforce_filtered_knn.argtypes = [_P, _I64, _I32, _I32, _P, _I64, _P, _P, _I32, _P, _P,
+                                                _P, _P]
+    lib.esg_attr_to_rank_range.argtypes = [_P, _P, _P, _I64, _P, _P]
+    lib.esg_save.argtypes = [_P, ctypes.c_char_p]
+    lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
+    lib.esg_status_str.restype = ctypes.c_char_p
+    lib.esg_status_str.argtypes = [_I32]
+    lib.esg_last_error.restype = ctypes.c_char_p
+    for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
+                 "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
+                 "esg_attr_to_rank_range", "esg_save", "esg_load"]:
+        getattr(lib, name).restype = _I32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = load_library()
+        raise EsgError(f"{what}: {lib.esg_status_str(status).decode()} "
+                       f"({lib.esg_last_error().decode()})")
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_P)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "need a contiguous CUDA tensor"
+    return _P(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+class Index:
+    """Owner of an esg_index handle (freed with esg_free)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        lib = load_library()
+        n, d, L, R, E, leaf, metric, storage = (_I64(), _I32(), _I32(), _I32(), _I32(), _I32(),
+                                                _I32(), _I32())
+        _check(lib.esg_index_info(handle, *[ctypes.byref(x) for x in
+                                            (n, d, L, R, E, leaf, metric, storage)]), "esg_index_info")
+        self.n, self.d, self.L, self.R, self.E = n.value, d.value, L.value, R.value, E.value
+        self.leaf_size, self.metric, self.storage = leaf.value, metric.value, storage.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise EsgError("index already freed")
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            load_library().esg_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def esg_build(vectors: np.ndarray, attr: Optional[np.ndarray] = None, *, M: int = 16,
+              leaf_size: int = 256, n_entries: int = 16, knn_k: int = 64, sample_k: int = 16,
+              sample_size: int = 1024, metric: str = "l2", storage: str = "f32") -> Index:
+    """Build an index on the current CUDA device from host float32 vectors
+    [n, d] (original order) and optional float64 attributes [n]."""
+    lib = load_library()
+    v = np.ascontiguousarray(vectors, dtype=np.float32)
+    a = None if attr is None else np.ascontiguousarray(attr, dtype=np.float64)
+    p = _BuildParams(M, leaf_size, n_entries, knn_k, sample_k, sample_size, METRIC[metric],
+                     STORAGE[storage])
+    h = _P()
+    _check(lib.esg_build(_np_ptr(v), v.shape[0], v.shape[1], _np_ptr(a), ctypes.byref(p),
+                         ctypes.byref(h)), "esg_build")
+    return Index(h)
+
+
+def esg_index_import(vectors_ranked: np.ndarray, perm: Optional[np.ndarray], metric: str,
+                     leaf_size: int, adj: np.ndarray, entries: np.ndarray,
+                     storage: str = "f32") -> Index:
+    """Create an index from host graphs in the stored layout (vectors in rank
+    order, adj [L, n, R] uint32, entries [2^L - 1, E] int32)."""
+    lib = load_library()
+    v = np.ascontiguousarray(vectors_ranked, dtype=np.float32)
+    pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.uint32)
+    ent = np.ascontiguousarray(entries, dtype=np.int32)
+    L, _, R = adj.shape if adj.ndim == 3 else (0, 0, 1)
+    h = _P()
+    _check(lib.esg_index_import(_np_ptr(v), _np_ptr(pm), v.shape[0], v.shape[1], METRIC[metric],
+                                leaf_size, _np_ptr(adj) if L else None, L, R,
+                                _np_ptr(ent) if L else None, ent.shape[1] if ent.ndim == 2 else 1,
+                                STORAGE[storage], ctypes.byref(h)), "esg_index_import")
+    return Index(h)
+
+
+def esg_index_export(index: Index) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(adj [L, n, R] uint32, entries [2^L-1, E] int32, perm [n] int64)."""
+    lib = load_library()
+    adj = np.empty((index.L, index.n, index.R), dtype=np.uint32)
+    ent = np.empty(((1 << index.L) - 1, index.E), dtype=np.int32)
+    perm = np.empty(index.n, dtype=np.int64)
+    _check(lib.esg_index_export(index.handle, _np_ptr(adj) if adj.size else None,
+                                _np_ptr(ent) if ent.size else None, _np_ptr(perm)),
+           "esg_index_export")
+    return adj, ent, perm
+
+
+def esg_free(index: Index):
+    index.close()
+
+
+def esg_decompose_batch(n: int, leaf_size: int, l, r, stream=None):
+    """Elastic decomposition on the device. l, r: CUDA int64 [nq]. Returns
+    (pieces int64 [nq, 2, 6] raw esg_piece records, npieces int32 [nq])."""
+    import torch
+    lib = load_library()
+    nq = l.numel()
+    pieces = torch.empty((nq, 2, 6), dtype=torch.int64, device=l.device)
+    npieces = torch.empty(nq, dtype=torch.int32, device=l.device)
+    _check(lib.esg_decompose_batch(n, leaf_size, _dev_ptr(l), _dev_ptr(r), nq, _dev_ptr(pieces),
+                                   _dev_ptr(npieces), _stream_ptr(stream)), "esg_decompose_batch")
+    return pieces, npieces
+
+
+def unpack_pieces(pieces):
+    """Split raw esg_piece records into (node_l, node_r, pl, pr, heap, depth, kind)."""
+    p64 = pieces
+    p32 = pieces.view(dtype=__import__("torch").int32)
+    return (p64[..., 0], p64[..., 1], p64[..., 2], p64[..., 3], p32[..., 8], p32[..., 9], p32[..., 10])
+
+
+def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,
+                     max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
+                     out=None, want_status: bool = True, want_stats: bool = False, stream=None):
+    """Range-filtered search of CUDA float32 queries [nq, d] with CUDA int64
+    ranges [nq]. Returns (ids int64 [nq,k_max], dist f32, count int32,
+    status int32 or None, stats int64 [nq,4] or None)."""
+    import torch
+    lib = load_library()
+    nq = queries.shape[0]
+    dev = queries.device
+    if out is None:
+        ids = torch.empty((nq, k_max), dtype=torch.int64, device=dev)
+        dist = torch.empty((nq, k_max), dtype=torch.float32, device=dev)
+        count = torch.empty(nq, dtype=torch.int32, device=dev)
+        status = torch.empty(nq, dtype=torch.int32, device=dev) if want_status else None
+        stats = torch.empty((nq, 4), dtype=torch.int64, device=dev) if want_stats else None
+    else:
+        ids, dist, count, status, stats = out
+    p = _SearchParams(ef, max_expansions, rerank, use_learned)
+    _check(lib.esg_search_batch(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
+                                _dev_ptr(k), k_max, ctypes.byref(p), _dev_ptr(ids), _dev_ptr(dist),
+                                _dev_ptr(count), _dev_ptr(status), _dev_ptr(stats),
+                                _stream_ptr(stream)), "esg_search_batch")
+    return ids, dist, count, status, stats
+
+
+def esg_bruteforce_filtered_knn(base, queries, l, r, k: int, metric: str = "l2", out=None,
+                                stream=None):
+    """Exact filtered k-NN by brute force on CUDA tensors. Returns
+    (ids int64 [nq, k] row indices, dist f32 [nq, k], count int32 [nq])."""
+    import torch
+    lib = load_library()
+    nq = queries.shape[0]
+    dev = queries.device
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        count = torch.empty(nq, dtype=torch.int32, device=dev)
+    else:
+        ids, dist, count = out
+    _check(lib.esg_bruteforce_filtered_knn(_dev_ptr(base), base.shape[0], base.shape[1],
+                                           METRIC[metric], _dev_ptr(queries), nq, _dev_ptr(l),
+                                           _dev_ptr(r), k, _dev_ptr(ids), _dev_ptr(dist),
+                                           _dev_ptr(count), _stream_ptr(stream)),
+           "esg_bruteforce_filtered_knn")
+    return ids, dist, count
+
+
+def esg_attr_to_rank_range(index: Index, lo: np.ndarray, hi: np.ndarray):
+    lib = load_library()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    l = np.empty(lo.shape[0], dtype=np.int64)
+    r = np.empty(lo.shape[0], dtype=np.int64)
+    _check(lib.esg_attr_to_rank_range(index.handle, _np_ptr(lo), _np_ptr(hi), lo.shape[0],
+                                      _np_ptr(l), _np_ptr(r)), "esg_attr_to_rank_range")
+    return l, r
+
+
+def esg_save(index: Index, path: str):
+    _check(load_library().esg_save(index.handle, path.encode()), "esg_save")
+
+
+def esg_load(path: str) -> Index:
+    h = _P()
+    _check(load_library().esg_load(path.encode(), ctypes.byref(h)), "esg_load")
+    return Index(h)

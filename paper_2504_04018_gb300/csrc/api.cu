@@ -1,0 +1,424 @@
+// C ABI entry points of libesg (declared in include/esg.h): argument checks,
+// index lifetime, re-ranking, save/load, and dispatch to the kernels.
+#include "esg_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+namespace {
+thread_local std::string g_last_error;
+
+template <typename T>
+esg_status dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return ESG_OK;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        esg_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        *p = nullptr;
+        return ESG_ERR_OOM;
+    }
+    return ESG_OK;
+}
+
+void free_index_memory(esg_index *ix) {
+    if (!ix) return;
+    cudaFree(ix->X); cudaFree(ix->Xb); cudaFree(ix->X8); cudaFree(ix->scale8);
+    cudaFree(ix->adj); cudaFree(ix->entries); cudaFree(ix->perm); cudaFree(ix->mlp);
+    ix->X = nullptr; ix->Xb = nullptr; ix->X8 = nullptr; ix->scale8 = nullptr;
+    ix->adj = nullptr; ix->entries = nullptr; ix->perm = nullptr; ix->mlp = nullptr;
+}
+
+bool dim_ok(int32_t d) { return d >= 4 && d <= 1024 && d % 4 == 0; }
+
+// Common tail of build/import/load: allocate device arrays for the shape.
+esg_status alloc_index(esg_index *ix) {
+    esg_status s;
+    if ((s = dev_alloc(&ix->X, (size_t)ix->n * ix->d)) != ESG_OK) return s;
+    if ((s = dev_alloc(&ix->adj, (size_t)ix->L * ix->n * ix->R)) != ESG_OK) return s;
+    if ((s = dev_alloc(&ix->entries, (size_t)ix->n_heap * ix->E)) != ESG_OK) return s;
+    if ((s = dev_alloc(&ix->perm, (size_t)ix->n)) != ESG_OK) return s;
+    return ESG_OK;
+}
+
+uint32_t crc32_update(uint32_t crc, const void *data, size_t len) {
+    static uint32_t table[256];
+    static bool init = false;
+    if (!init) {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+        init = true;
+    }
+    const unsigned char *p = (const unsigned char *)data;
+    crc = ~crc;
+    for (size_t i = 0; i < len; ++i) crc = table[(crc ^ p[i]) & 0xFF] ^ (crc >> 8);
+    return ~crc;
+}
+}  // namespace
+
+void esg_set_error(const std::string &msg) { g_last_error = msg; }
+
+extern "C" {
+
+const char *esg_last_error(void) { return g_last_error.c_str(); }
+
+const char *esg_status_str(esg_status s) {
+    switch (s) {
+        case ESG_OK: return "ok";
+        case ESG_ERR_INVALID_ARG: return "invalid argument";
+        case ESG_ERR_OOM: return "out of memory";
+        case ESG_ERR_CUDA: return "CUDA error";
+        case ESG_ERR_IO: return "I/O error";
+        case ESG_ERR_CORRUPT: return "corrupt index file";
+        case ESG_ERR_TIMEOUT: return "timeout";
+        case ESG_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+esg_build_params esg_build_params_default(void) {
+    esg_build_params p;
+    p.M = 16;
+    p.leaf_size = 256;
+    p.n_entries = 16;
+    p.knn_k = 64;
+    p.sample_k = 16;
+    p.sample_size = 1024;
+    p.metric = ESG_L2SQ;
+    p.storage = ESG_F32;
+    return p;
+}
+
+esg_search_params esg_search_params_default(void) {
+    esg_search_params p;
+    p.ef = 64;
+    p.max_expansions = 0;
+    p.rerank = 1;
+    p.use_learned = 0;
+    return p;
+}
+
+esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *attr,
+                     const esg_build_params *params, esg_index **out) {
+    if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!vectors || n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) || d % 8 != 0) {
+        esg_set_error("esg_build: need vectors != NULL, 1 <= n < 2^31-1, 8 <= d <= 1024, d % 8 == 0");
+        return ESG_ERR_INVALID_ARG;
+    }
+    esg_build_params p = params ? *params : esg_build_params_default();
+    if (p.M < 1 || 2 * p.M > 128 || p.leaf_size < 1 || p.n_entries < 1 || p.n_entries > 32 ||
+        p.knn_k < 0 || p.sample_k < 0 || p.knn_k + p.sample_k < 1 || p.sample_size < 1 ||
+        (p.metric != ESG_L2SQ && p.metric != ESG_IP) ||
+        (p.storage != ESG_F32 && p.storage != ESG_BF16 && p.storage != ESG_FP8E4M3)) {
+        esg_set_error("esg_build: parameter out of range");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (attr) for (int64_t i = 0; i < n; ++i) if (std::isnan(attr[i])) {
+        esg_set_error("esg_build: NaN attribute");
+        return ESG_ERR_INVALID_ARG;
+    }
+    esg_index *ix = new (std::nothrow) esg_index();
+    if (!ix) return ESG_ERR_OOM;
+    ix->n = n; ix->d = d; ix->metric = p.metric; ix->storage = p.storage;
+    ix->leaf_size = p.leaf_size; ix->M = p.M; ix->R = 2 * p.M; ix->E = p.n_entries;
+    ix->L = esg_graph_depths(n, p.leaf_size);
+    if (ix->L > 30) { delete ix; esg_set_error("tree too deep (leaf_size too small)"); return ESG_ERR_UNSUPPORTED; }
+    ix->n_heap = ((int64_t)1 << ix->L) - 1;
+    cudaGetDevice(&ix->device);
+    // re-ranking: rank i = i-th smallest attribute, ties by row
+    ix->perm_host.resize(n);
+    std::iota(ix->perm_host.begin(), ix->perm_host.end(), (int64_t)0);
+    if (attr) {
+        std::stable_sort(ix->perm_host.begin(), ix->perm_host.end(),
+                         [attr](int64_t a, int64_t b) { return attr[a] < attr[b]; });
+        ix->attr_sorted.resize(n);
+        for (int64_t i = 0; i < n; ++i) ix->attr_sorted[i] = attr[ix->perm_host[i]];
+    }
+    esg_status s = alloc_index(ix);
+    cudaStream_t stream = nullptr;
+    std::vector<float> ranked;
+    if (s == ESG_OK && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+        esg_set_error("cudaStreamCreate failed"); s = ESG_ERR_CUDA;
+    }
+    if (s == ESG_OK) {
+        try {
+            ranked.resize((size_t)n * d);
+        } catch (...) { s = ESG_ERR_OOM; }
+    }
+    if (s == ESG_OK) {
+        for (int64_t i = 0; i < n; ++i)
+            std::memcpy(&ranked[(size_t)i * d], vectors + (size_t)ix->perm_host[i] * d, sizeof(float) * d);
+        cudaError_t e = cudaMemcpyAsync(ix->X, ranked.data(), sizeof(float) * n * d, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ix->perm, ix->perm_host.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess && ix->L > 0) e = cudaMemsetAsync(ix->adj, 0xFF, sizeof(uint32_t) * ix->L * n * ix->R, stream);
+        if (e == cudaSuccess && ix->n_heap > 0) e = cudaMemsetAsync(ix->entries, 0xFF, sizeof(int32_t) * ix->n_heap * ix->E, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); s = ESG_ERR_CUDA; }
+    }
+    if (s == ESG_OK) s = esg_build_graphs(ix, p, stream);
+    if (s == ESG_OK) s = esg_make_storage(ix, stream);
+    if (stream) cudaStreamDestroy(stream);
+    if (s != ESG_OK) { free_index_memory(ix); delete ix; return s; }
+    *out = ix;
+    return ESG_OK;
+}
+
+esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n, int32_t d,
+                            esg_metric metric, int32_t leaf_size, const uint32_t *adj, int32_t L,
+                            int32_t R, const int32_t *entries, int32_t n_entries, esg_dtype storage,
+                            esg_index **out) {
+    if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!vectors || n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) || leaf_size < 1 ||
+        R < 1 || R > 128 || n_entries < 1 || n_entries > 32 || (L > 0 && (!adj || !entries)) ||
+        (metric != ESG_L2SQ && metric != ESG_IP)) {
+        esg_set_error("esg_index_import: argument out of range");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (L != esg_graph_depths(n, leaf_size)) {
+        esg_set_error("esg_index_import: L does not match (n, leaf_size)");
+        return ESG_ERR_INVALID_ARG;
+    }
+    esg_index *ix = new (std::nothrow) esg_index();
+    if (!ix) return ESG_ERR_OOM;
+    ix->n = n; ix->d = d; ix->metric = metric; ix->storage = storage; ix->leaf_size = leaf_size;
+    ix->L = L; ix->R = R; ix->M = R / 2; ix->E = n_entries; ix->n_heap = ((int64_t)1 << L) - 1;
+    cudaGetDevice(&ix->device);
+    ix->perm_host.resize(n);
+    if (perm) std::memcpy(ix->perm_host.data(), perm, sizeof(int64_t) * n);
+    else std::iota(ix->perm_host.begin(), ix->perm_host.end(), (int64_t)0);
+    esg_status s = alloc_index(ix);
+    if (s == ESG_OK) {
+        cudaError_t e = cudaMemcpy(ix->X, vectors, sizeof(float) * n * d, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(ix->perm, ix->perm_host.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && L > 0) e = cudaMemcpy(ix->adj, adj, sizeof(uint32_t) * L * n * R, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && L > 0) e = cudaMemcpy(ix->entries, entries, sizeof(int32_t) * ix->n_heap * n_entries, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); s = ESG_ERR_CUDA; }
+    }
+    if (s == ESG_OK) s = esg_make_storage(ix, nullptr);
+    if (s == ESG_OK && cudaDeviceSynchronize() != cudaSuccess) s = ESG_ERR_CUDA;
+    if (s != ESG_OK) { free_index_memory(ix); delete ix; return s; }
+    *out = ix;
+    return ESG_OK;
+}
+
+esg_status esg_index_info(const esg_index *ix, int64_t *n, int32_t *d, int32_t *L, int32_t *R,
+                          int32_t *n_entries, int32_t *leaf_size, int32_t *metric, int32_t *storage) {
+    if (!ix) { esg_set_error("index is NULL"); return ESG_ERR_INVALID_ARG; }
+    if (n) *n = ix->n;
+    if (d) *d = ix->d;
+    if (L) *L = ix->L;
+    if (R) *R = ix->R;
+    if (n_entries) *n_entries = ix->E;
+    if (leaf_size) *leaf_size = ix->leaf_size;
+    if (metric) *metric = ix->metric;
+    if (storage) *storage = ix->storage;
+    return ESG_OK;
+}
+
+esg_status esg_index_export(const esg_index *ix, uint32_t *adj, int32_t *entries, int64_t *perm) {
+    if (!ix) { esg_set_error("index is NULL"); return ESG_ERR_INVALID_ARG; }
+    if (adj && ix->L > 0) ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj, sizeof(uint32_t) * ix->L * ix->n * ix->R, cudaMemcpyDeviceToHost));
+    if (entries && ix->n_heap > 0) ESG_CUDA_TRY(cudaMemcpy(entries, ix->entries, sizeof(int32_t) * ix->n_heap * ix->E, cudaMemcpyDeviceToHost));
+    if (perm) std::memcpy(perm, ix->perm_host.data(), sizeof(int64_t) * ix->n);
+    return ESG_OK;
+}
+
+void esg_free(esg_index *ix) {
+    if (!ix) return;
+    free_index_memory(ix);
+    delete ix;
+}
+
+esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
+                               int64_t nq, esg_piece *out_pieces, int32_t *out_npieces,
+                               esg_stream_t stream) {
+    if (n < 1 || leaf_size < 1 || nq < 0 || (nq > 0 && (!l || !r || !out_pieces || !out_npieces))) {
+        esg_set_error("esg_decompose_batch: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    return esg_launch_decompose(n, leaf_size, l, r, nq, out_pieces, out_npieces, (cudaStream_t)stream);
+}
+
+esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+                            const int64_t *r, const int32_t *k, int32_t k_max,
+                            const esg_search_params *params, int64_t *out_ids, float *out_dist,
+                            int32_t *out_count, int32_t *out_status, int64_t *out_stats,
+                            esg_stream_t stream) {
+    if (!ix || nq < 0 || k_max < 1 || k_max > 1024 ||
+        (nq > 0 && (!queries || !l || !r || !out_ids || !out_dist || !out_count))) {
+        esg_set_error("esg_search_batch: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)queries) % 16 != 0) {
+        esg_set_error("esg_search_batch: queries must be 16-byte aligned");
+        return ESG_ERR_INVALID_ARG;
+    }
+    SearchLaunch s;
+    s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max;
+    s.p = params ? *params : esg_search_params_default();
+    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0) {
+        esg_set_error("esg_search_batch: ef must be in 1..1024");
+        return ESG_ERR_INVALID_ARG;
+    }
+    s.out_ids = out_ids; s.out_dist = out_dist; s.out_count = out_count;
+    s.out_status = out_status; s.out_stats = out_stats;
+    return esg_launch_search(s, (cudaStream_t)stream);
+}
+
+esg_status esg_bruteforce_filtered_knn(const float *base, int64_t n, int32_t d, esg_metric metric,
+                                       const float *queries, int64_t nq, const int64_t *l,
+                                       const int64_t *r, int32_t k, int64_t *out_ids,
+                                       float *out_dist, int32_t *out_count, esg_stream_t stream) {
+    if (n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) || nq < 0 || k < 1 || k > 1024 ||
+        (metric != ESG_L2SQ && metric != ESG_IP) ||
+        (nq > 0 && (!base || !queries || !l || !r || !out_ids || !out_dist || !out_count))) {
+        esg_set_error("esg_bruteforce_filtered_knn: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)base) % 16 != 0 || ((uintptr_t)queries) % 16 != 0) {
+        esg_set_error("esg_bruteforce_filtered_knn: base and queries must be 16-byte aligned");
+        return ESG_ERR_INVALID_ARG;
+    }
+    return esg_launch_bruteforce(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist,
+                                 out_count, nullptr, 0, (cudaStream_t)stream);
+}
+
+esg_status esg_attr_to_rank_range(const esg_index *ix, const double *lo, const double *hi, int64_t nq,
+                                  int64_t *l, int64_t *r) {
+    if (!ix || nq < 0 || (nq > 0 && (!lo || !hi || !l || !r))) {
+        esg_set_error("esg_attr_to_rank_range: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < nq; ++i) {
+        if (ix->attr_sorted.empty()) {
+            // attribute = original row: ranks are rows
+            double a = std::ceil(lo[i]), b = std::floor(hi[i]);
+            int64_t la = (int64_t)std::max(0.0, a), rb = (int64_t)std::min((double)(ix->n - 1), b);
+            l[i] = la; r[i] = rb;
+            if (la > rb) { l[i] = rb + 1; }
+        } else {
+            const auto &A = ix->attr_sorted;
+            int64_t la = std::lower_bound(A.begin(), A.end(), lo[i]) - A.begin();
+            int64_t rb = (std::upper_bound(A.begin(), A.end(), hi[i]) - A.begin()) - 1;
+            l[i] = la; r[i] = rb;
+            if (la > rb) l[i] = rb + 1;
+        }
+    }
+    return ESG_OK;
+}
+
+// ------------------------------------------------------------ save / load
+
+namespace {
+const char kMagic[8] = {'E', 'S', 'G', 'G', 'B', '3', '0', '0'};
+const uint32_t kVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t d, metric, storage, leaf_size, L, R, E, M;
+    int64_t n;
+    int64_t n_heap;
+    uint64_t attr_count;
+};
+
+bool write_section(FILE *f, const void *data, size_t bytes) {
+    uint64_t len = bytes;
+    uint32_t crc = crc32_update(0, data, bytes);
+    return fwrite(&len, 8, 1, f) == 1 && (bytes == 0 || fwrite(data, 1, bytes, f) == bytes) &&
+           fwrite(&crc, 4, 1, f) == 1;
+}
+
+esg_status read_section(FILE *f, void *data, size_t bytes) {
+    uint64_t len = 0;
+    uint32_t crc = 0;
+    if (fread(&len, 8, 1, f) != 1) return ESG_ERR_CORRUPT;
+    if (len != bytes) return ESG_ERR_CORRUPT;
+    if (bytes && fread(data, 1, bytes, f) != bytes) return ESG_ERR_CORRUPT;
+    if (fread(&crc, 4, 1, f) != 1) return ESG_ERR_CORRUPT;
+    if (crc != crc32_update(0, data, bytes)) return ESG_ERR_CORRUPT;
+    return ESG_OK;
+}
+}  // namespace
+
+esg_status esg_save(const esg_index *ix, const char *path) {
+    if (!ix || !path) { esg_set_error("esg_save: bad argument"); return ESG_ERR_INVALID_ARG; }
+    std::vector<float> X((size_t)ix->n * ix->d);
+    std::vector<uint32_t> adj((size_t)ix->L * ix->n * ix->R);
+    std::vector<int32_t> ent((size_t)ix->n_heap * ix->E);
+    ESG_CUDA_TRY(cudaMemcpy(X.data(), ix->X, sizeof(float) * X.size(), cudaMemcpyDeviceToHost));
+    if (!adj.empty()) ESG_CUDA_TRY(cudaMemcpy(adj.data(), ix->adj, sizeof(uint32_t) * adj.size(), cudaMemcpyDeviceToHost));
+    if (!ent.empty()) ESG_CUDA_TRY(cudaMemcpy(ent.data(), ix->entries, sizeof(int32_t) * ent.size(), cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) { esg_set_error(std::string("esg_save: cannot open ") + path); return ESG_ERR_IO; }
+    FileHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = kVersion; h.d = ix->d; h.metric = ix->metric; h.storage = ix->storage;
+    h.leaf_size = ix->leaf_size; h.L = ix->L; h.R = ix->R; h.E = ix->E; h.M = ix->M; h.n = ix->n;
+    h.n_heap = ix->n_heap; h.attr_count = ix->attr_sorted.size();
+    bool ok = write_section(f, &h, sizeof(h)) && write_section(f, X.data(), sizeof(float) * X.size()) &&
+              write_section(f, ix->perm_host.data(), sizeof(int64_t) * ix->n) &&
+              write_section(f, adj.data(), sizeof(uint32_t) * adj.size()) &&
+              write_section(f, ent.data(), sizeof(int32_t) * ent.size()) &&
+              write_section(f, ix->attr_sorted.data(), sizeof(double) * ix->attr_sorted.size());
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) { esg_set_error("esg_save: write failed"); return ESG_ERR_IO; }
+    return ESG_OK;
+}
+
+esg_status esg_load(const char *path, esg_index **out) {
+    if (!path || !out) { esg_set_error("esg_load: bad argument"); return ESG_ERR_INVALID_ARG; }
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) { esg_set_error(std::string("esg_load: cannot open ") + path); return ESG_ERR_IO; }
+    FileHeader h;
+    esg_status s = read_section(f, &h, sizeof(h));
+    if (s == ESG_OK && (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion || h.n < 1 ||
+                        !dim_ok(h.d) || h.L < 0 || h.L > 30 || h.R < 1 || h.R > 128 || h.E < 1 ||
+                        h.E > 32 || h.n_heap != (((int64_t)1 << h.L) - 1) ||
+                        h.L != esg_graph_depths(h.n, h.leaf_size) ||
+                        (h.attr_count != 0 && h.attr_count != (uint64_t)h.n)))
+        s = ESG_ERR_CORRUPT;
+    std::vector<float> X;
+    std::vector<int64_t> perm;
+    std::vector<uint32_t> adj;
+    std::vector<int32_t> ent;
+    std::vector<double> attr;
+    if (s == ESG_OK) {
+        try {
+            X.resize((size_t)h.n * h.d); perm.resize(h.n); adj.resize((size_t)h.L * h.n * h.R);
+            ent.resize((size_t)h.n_heap * h.E); attr.resize(h.attr_count);
+        } catch (...) { s = ESG_ERR_OOM; }
+    }
+    if (s == ESG_OK) s = read_section(f, X.data(), sizeof(float) * X.size());
+    if (s == ESG_OK) s = read_section(f, perm.data(), sizeof(int64_t) * perm.size());
+    if (s == ESG_OK) s = read_section(f, adj.data(), sizeof(uint32_t) * adj.size());
+    if (s == ESG_OK) s = read_section(f, ent.data(), sizeof(int32_t) * ent.size());
+    if (s == ESG_OK) s = read_section(f, attr.data(), sizeof(double) * attr.size());
+    fclose(f);
+    if (s != ESG_OK) {
+        if (s == ESG_ERR_CORRUPT) esg_set_error("esg_load: file is not a valid index (header, size or CRC)");
+        return s;
+    }
+    esg_index *ix = nullptr;
+    s = esg_index_import(X.data(), perm.data(), h.n, h.d, (esg_metric)h.metric, h.leaf_size,
+                         adj.data(), h.L, h.R, ent.data(), h.E, (esg_dtype)h.storage, &ix);
+    if (s != ESG_OK) return s;
+    ix->M = h.M;
+    ix->attr_sorted.swap(attr);
+    *out = ix;
+    return ESG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Internal declarations shared by the translation units of libesg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/esg.h"
+
+#define ESG_NONE 0xFFFFFFFFu
+#define ESG_EXPANDED 0x80000000u
+#define ESG_ID_MASK 0x7FFFFFFFu
+
+// ----------------------------------------------------------------- errors
+
+void esg_set_error(const std::string &msg);
+
+#define ESG_CUDA_TRY(expr)                                                                 \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            esg_set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));            \
+            return _e == cudaErrorMemoryAllocation ? ESG_ERR_OOM : ESG_ERR_CUDA;           \
+        }                                                                                  \
+    } while (0)
+
+// ------------------------------------------------------------------ index
+
+struct esg_index {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t metric = 0;
+    int32_t storage = 0;
+    int32_t leaf_size = 0;
+    int32_t L = 0;           // depths holding graph nodes
+    int32_t R = 0;           // row width of the adjacency
+    int32_t E = 0;           // entry points per node
+    int32_t M = 0;
+    int64_t n_heap = 0;      // 2^L - 1 heap slots with entries
+    int device = 0;
+    float *X = nullptr;              // [n, d] fp32, rank order
+    __nv_bfloat16 *Xb = nullptr;     // [n, d] bf16 (storage BF16)
+    __nv_fp8_e4m3 *X8 = nullptr;     // [n, d] fp8 (storage FP8)
+    float *scale8 = nullptr;         // [n] per-row fp8 scale
+    uint32_t *adj = nullptr;         // [L, n, R]
+    int32_t *entries = nullptr;      // [n_heap, E]
+    int64_t *perm = nullptr;         // [n] rank -> original id (device)
+    std::vector<int64_t> perm_host;  // same on the host
+    std::vector<double> attr_sorted; // sorted attribute values (host), may be empty
+    // learned beam-width predictor (device weights), null when untrained
+    float *mlp = nullptr;
+    int32_t mlp_ready = 0;
+};
+
+// Number of depths that hold at least one graph node.
+int esg_graph_depths(int64_t n, int32_t leaf_size);
+
+// --------------------------------------------------------- launch helpers
+
+struct SearchLaunch {
+    const esg_index *ix;
+    const float *queries;
+    int64_t nq;
+    const int64_t *l, *r;
+    const int32_t *k;
+    int32_t k_max;
+    esg_search_params p;
+    int64_t *out_ids;
+    float *out_dist;
+    int32_t *out_count;
+    int32_t *out_status;
+    int64_t *out_stats;
+};
+
+esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
+                                int64_t nq, esg_piece *pieces, int32_t *npieces,
+                                cudaStream_t stream);
+esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream);
+esg_status esg_launch_bruteforce(const float *base, int64_t n, int32_t d, int metric,
+                                 const float *queries, int64_t nq, const int64_t *l,
+                                 const int64_t *r, int32_t k, int64_t *out_ids, float *out_dist,
+                                 int32_t *out_count, const int64_t *id_map, int32_t exclude_self,
+                                 cudaStream_t stream);
+esg_status esg_build_graphs(esg_index *ix, const esg_build_params &p, cudaStream_t stream);
+esg_status esg_make_storage(esg_index *ix, cudaStream_t stream);
+
+// --------------------------------------------------------- device helpers
+
+struct Cand {
+    float d;
+    uint32_t id;  // bit 31: expanded flag (search lists only)
+};
+
+__device__ __forceinline__ bool cand_less(float da, uint32_t ia, float db, uint32_t ib) {
+    return da < db || (da == db && (ia & ESG_ID_MASK) < (ib & ESG_ID_MASK));
+}
+__device__ __forceinline__ bool cand_less(const Cand &a, const Cand &b) {
+    return cand_less(a.d, a.id, b.d, b.id);
+}
+__device__ __forceinline__ bool cand_eq(const Cand &a, const Cand &b) {
+    return a.d == b.d && (a.id & ESG_ID_MASK) == (b.id & ESG_ID_MASK);
+}
+
+// Bitonic sort of 64 candidates in shared memory by one warp (ascending).
+__device__ __forceinline__ void warp_sort64(Cand *v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            // each lane owns one compare-exchange pair of the 32 pairs
+            int i = 2 * stride * (lane / stride) + (lane % stride);
+            int j = i + stride;
+            bool up = ((i & size) == 0);
+            Cand a = v[i], b = v[j];
+            bool swap = up ? cand_less(b, a) : cand_less(a, b);
+            __syncwarp();
+            if (swap) { v[i] = b; v[j] = a; }
+            __syncwarp();
+        }
+    }
+}
+
+// Bitonic sort of P (a power of two, <= 1024) candidates in shared memory by
+// one warp (ascending); pad unused slots with {+inf, ESG_NONE} first.
+__device__ __forceinline__ void warp_sort_pow2(Cand *v, int P) {
+    const int lane = threadIdx.x & 31;
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int p = lane; p < P / 2; p += 32) {
+                int i = 2 * stride * (p / stride) + (p % stride);
+                int j = i + stride;
+                bool up = ((i & size) == 0);
+                Cand a = v[i], b = v[j];
+                bool swap = up ? cand_less(b, a) : cand_less(a, b);
+                if (swap) { v[i] = b; v[j] = a; }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__device__ __forceinline__ int next_pow2_int(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Number of items of sorted list `v[0..n)` strictly less than `x`.
+__device__ __forceinline__ int lower_rank(const Cand *v, int n, const Cand &x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cand_less(v[mid], x)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float warp_sum_group(float v, int group) {
+    for (int off = group >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+static inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

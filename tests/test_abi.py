@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every function include/esg.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2504_04018_gb300 as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "esg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(esg_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["esg_build", "esg_search_batch", "esg_bruteforce_filtered_knn",
+                     "esg_decompose_batch", "esg_index_import", "esg_free"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = E.load_library()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(E.EXPORTED) <= set(_declared())
+
+
+def test_defaults_and_status_strings():
+    lib = E.load_library()
+    b = lib.esg_build_params_default()
+    assert (b.M, b.leaf_size, b.n_entries) == (16, 256, 16)
+    s = lib.esg_search_params_default()
+    assert s.ef == 64 and s.use_learned == 0
+    assert lib.esg_status_str(0) == b"ok"
+    assert lib.esg_status_str(7) == b"unsupported"
+
+
+def test_invalid_arguments_rejected_on_host():
+    lib = E.load_library()
+    h = ctypes.c_void_p()
+    assert lib.esg_build(None, 10, 16, None, None, ctypes.byref(h)) == 1
+    assert b"esg_build" in lib.esg_last_error()
+    # d not a multiple of 8
+    import numpy as np
+    v = np.zeros((4, 12), np.float32)
+    assert lib.esg_build(v.ctypes.data_as(ctypes.c_void_p), 4, 12, None, None, ctypes.byref(h)) == 1
+    assert lib.esg_decompose_batch(0, 16, None, None, 1, None, None, None) == 1
+    assert lib.esg_search_batch(None, None, 1, None, None, None, 10, None, None, None, None, None,
+                                None, None) == 1
+    assert lib.esg_bruteforce_filtered_knn(None, 10, 16, 0, None, 1, None, None, 0, None, None,
+                                           None, None) == 1
+
+
+def test_load_missing_and_corrupt_files(tmp_path):
+    lib = E.load_library()
+    h = ctypes.c_void_p()
+    assert lib.esg_load(str(tmp_path / "nope.esg").encode(), ctypes.byref(h)) == 4   # IO
+    bad = tmp_path / "bad.esg"
+    bad.write_bytes(b"\x00" * 64)
+    assert lib.esg_load(str(bad).encode(), ctypes.byref(h)) == 5                     # CORRUPT
