@@ -86,26 +86,25 @@ typedef struct esg_index esg_index; /* opaque; owned by the library */
 
 /*
  * Index build parameters. Defaults: esg_build_params_default().
- *  M          graph degree parameter: each inserted point keeps up to M
- *             neighbours chosen by edge occlusion and a row holds at most
- *             R = 2M neighbours (Section 5.1 uses M = 16);
- *  leaf_size  l: a tree node with r - l < leaf_size holds no graph and is
- *             answered by a scan (Algorithm 3/4, first test);
- *  n_entries  entry points per graph node (ranks evenly spaced over the
- *             node), 1..32;
- *  knn_k      exact nearest neighbours inside the node offered to edge
- *             occlusion per point (construction candidate pool);
- *  sample_k   nearest points of an evenly spaced sample of the node
- *             (sample_size points) added to that pool for long-range edges;
- *  storage    traversal precision kept on the device besides FP32.
+ *  M                graph degree parameter: an inserted point links to at most
+ *                   M neighbours chosen by edge occlusion and a row holds at
+ *                   most R = 2M neighbours (Section 5.1 uses M = 16);
+ *  leaf_size        l: a tree node with r - l < leaf_size holds no graph and
+ *                   is answered by a scan (Algorithms 3 and 4, first test);
+ *  n_entries        query entry points per graph node (ranks evenly spaced
+ *                   over the node), 1..32;
+ *  ef_construction  beam width of the insertion searches (Section 5.1: 200);
+ *  batch_div        points inserted concurrently per node and round are at
+ *                   most 1/batch_div of the points already in its graph;
+ *  storage          traversal precision kept on the device besides FP32.
  */
 typedef struct {
     int32_t M;
     int32_t leaf_size;
     int32_t n_entries;
-    int32_t knn_k;
-    int32_t sample_k;
-    int32_t sample_size;
+    int32_t ef_construction;
+    int32_t batch_div;
+    int32_t reserved;
     esg_metric metric;
     esg_dtype storage;
 } esg_build_params;

@@ -42,8 +42,8 @@ class EsgError(RuntimeError):
 
 class _BuildParams(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("n_entries", ctypes.c_int32),
-                ("knn_k", ctypes.c_int32), ("sample_k", ctypes.c_int32),
-                ("sample_size", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("ef_construction", ctypes.c_int32), ("batch_div", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("storage", ctypes.c_int32)]
 
 
@@ -157,14 +157,14 @@ class Index:
 
 
 def esg_build(vectors: np.ndarray, attr: Optional[np.ndarray] = None, *, M: int = 16,
-              leaf_size: int = 256, n_entries: int = 16, knn_k: int = 64, sample_k: int = 16,
-              sample_size: int = 1024, metric: str = "l2", storage: str = "f32") -> Index:
+              leaf_size: int = 256, n_entries: int = 16, ef_construction: int = 200,
+              batch_div: int = 8, metric: str = "l2", storage: str = "f32") -> Index:
     """Build an index on the current CUDA device from host float32 vectors
     [n, d] (original order) and optional float64 attributes [n]."""
     lib = load_library()
     v = np.ascontiguousarray(vectors, dtype=np.float32)
     a = None if attr is None else np.ascontiguousarray(attr, dtype=np.float64)
-    p = _BuildParams(M, leaf_size, n_entries, knn_k, sample_k, sample_size, METRIC[metric],
+    p = _BuildParams(M, leaf_size, n_entries, ef_construction, batch_div, 0, METRIC[metric],
                      STORAGE[storage])
     h = _P()
     _check(lib.esg_build(_np_ptr(v), v.shape[0], v.shape[1], _np_ptr(a), ctypes.byref(p),

@@ -89,9 +89,9 @@ esg_build_params esg_build_params_default(void) {
     p.M = 16;
     p.leaf_size = 256;
     p.n_entries = 16;
-    p.knn_k = 64;
-    p.sample_k = 16;
-    p.sample_size = 1024;
+    p.ef_construction = 200;
+    p.batch_div = 8;
+    p.reserved = 0;
     p.metric = ESG_L2SQ;
     p.storage = ESG_F32;
     return p;
@@ -116,7 +116,7 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
     }
     esg_build_params p = params ? *params : esg_build_params_default();
     if (p.M < 1 || 2 * p.M > 128 || p.leaf_size < 1 || p.n_entries < 1 || p.n_entries > 32 ||
-        p.knn_k < 0 || p.sample_k < 0 || p.knn_k + p.sample_k < 1 || p.sample_size < 1 ||
+        p.ef_construction < 1 || p.ef_construction > 1024 || p.batch_div < 1 ||
         (p.metric != ESG_L2SQ && p.metric != ESG_IP) ||
         (p.storage != ESG_F32 && p.storage != ESG_BF16 && p.storage != ESG_FP8E4M3)) {
         esg_set_error("esg_build: parameter out of range");

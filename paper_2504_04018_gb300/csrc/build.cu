@@ -1,18 +1,23 @@
-// GPU construction of the segment tree's graphs (the index of Section 4.2,
-// Algorithm 3's tree: root [0, N-1], split at mid, no graph when
-// r - l < leaf_size).
+// GPU construction of the ESG index: Build-2D-Index (Algorithm 3).
 //
-// Each graph node gets a flat proximity graph over its points. Instead of
-// inserting points one by one with a beam search per insertion, every point
-// of a node is "inserted" at once with a candidate pool made of
-//   - its knn_k exact nearest neighbours inside the node (tiled brute force),
-//   - its sample_k nearest points among an evenly spaced sample of the node
-//     (long-range candidates, the role early insertions play in incremental
-//     construction),
-// from which edge occlusion (HNSW's neighbour-selection heuristic: keep c
-// unless an already kept s has d(c, s) < d(c, u)) keeps at most M forward
-// edges; reverse edges are then added and rows longer than R = 2M are
-// re-selected with the same rule over the R * 2 closest candidates.
+// The tree: root [0, N-1], children [l, mid] and [mid+1, r] with
+// mid = floor((l + r) / 2), no graph when r - l < leaf_size. A graph node's
+// graph is the left child's graph (copied: the child keeps its own) with the
+// points mid+1..r inserted in increasing rank order; when the left child is a
+// leaf the graph is first built from scratch over [l, mid] by insertion.
+// Insertion follows HNSW's flat layer: a beam search (ef = ef_construction)
+// from the node's first point finds candidates, edge occlusion keeps at most
+// M of them (keep c unless an already kept s has d(c, s) < d(c, u)), and each
+// chosen neighbour gets the reverse edge, re-selecting its row by occlusion
+// when it would exceed R = 2M.
+//
+// GPU schedule: depths are processed bottom-up; within a depth all nodes
+// advance together. Points are inserted in rounds: a round inserts, for every
+// node, the next max(1, inserted / batch_div) points of its rank order as one
+// batch of independent searches (the warp beam-search kernel) over the graph
+// as it stood before the round, then applies their forward edges and the
+// reverse-edge updates. A batch never exceeds 1/batch_div of the graph it is
+// inserted into, so points of a round miss only each other as candidates.
 #include "esg_internal.cuh"
 
 #include <algorithm>
@@ -20,56 +25,16 @@
 
 #include <cub/cub.cuh>
 
-esg_status esg_launch_bruteforce_mode(int mode, const float *base, int64_t n, int32_t d,
-                                      const float *queries, int64_t nq, const int64_t *l,
-                                      const int64_t *r, int32_t k, int64_t *out_ids,
-                                      float *out_dist, int32_t *out_count, const int64_t *id_map,
-                                      int32_t exclude_self, const float *xnorm,
-                                      const float *qnorm, cudaStream_t stream);
-__global__ void row_norms_kernel(const float *X, int64_t n, int d, float *out);
+esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, const uint32_t *adj,
+                                int R, const int32_t *entries, int E, const int64_t *qidx,
+                                const esg_piece *pieces, int64_t n_items, int ef, int k,
+                                int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
+                                int64_t *res_stats, cudaStream_t stream);
 
 namespace {
 
-constexpr int kMaxPool = 256;   // candidate pool per point (knn_k + sample_k)
+constexpr int kMaxPool = 256;   // candidates considered when re-selecting a row
 constexpr int kMaxRow = 128;    // R
-
-// Node of `depth` that contains point i: its range, or an empty range when
-// the node is a leaf (no graph). Also the node's index within the depth.
-__global__ void point_node_kernel(int64_t n, int32_t leaf, int depth, int64_t *lo, int64_t *hi,
-                                  int32_t *node_idx) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t l = 0, r = n - 1;
-    int32_t idx = 0;
-    bool ok = true;
-    for (int t = 0; t < depth; ++t) {
-        if (r - l < leaf) { ok = false; break; }
-        int64_t mid = l + (r - l) / 2;
-        if (i <= mid) { r = mid; idx = 2 * idx; } else { l = mid + 1; idx = 2 * idx + 1; }
-    }
-    if (ok && r - l < leaf) ok = false;
-    lo[i] = ok ? l : 1;
-    hi[i] = ok ? r : 0;
-    node_idx[i] = ok ? idx : -1;
-}
-
-__global__ void gather_rows_kernel(const float *X, int d, const int64_t *rows, int64_t m, float *out) {
-    int64_t i = blockIdx.x;
-    if (i >= m) return;
-    const float *src = X + rows[i] * d;
-    float *dst = out + i * d;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) dst[j] = src[j];
-}
-
-__global__ void sample_range_kernel(int64_t n, const int32_t *node_idx, const int64_t *s_off,
-                                    const int64_t *s_cnt, int64_t *lo, int64_t *hi) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t j = node_idx[i];
-    if (j < 0) { lo[i] = 1; hi[i] = 0; return; }
-    lo[i] = s_off[j];
-    hi[i] = s_off[j] + s_cnt[j] - 1;
-}
 
 // Warp-cooperative distance between rows a and b.
 __device__ __forceinline__ float row_dist(const float *X, int d, int metric, uint32_t a, uint32_t b) {
@@ -85,18 +50,18 @@ __device__ __forceinline__ float row_dist(const float *X, int d, int metric, uin
     return metric == ESG_L2SQ ? acc : -acc;
 }
 
-// Edge occlusion over pool[0..m) (sorted ascending by distance to u, no
-// duplicates, u excluded): keep c unless some kept s has d(c, s) < d(c, u).
-// Returns the number kept (<= max_keep) in keep[].
+// Edge occlusion over pool[0..m) (ascending by distance to the base point,
+// no duplicates, base excluded): keep c unless some kept s has
+// d(c, s) < d(c, base). Returns the number kept (<= max_keep) in keep[].
 __device__ int occlusion_select(const float *X, int d, int metric, const Cand *pool, int m,
                                 int max_keep, uint32_t *keep) {
     int kept = 0;
     for (int i = 0; i < m && kept < max_keep; ++i) {
-        const uint32_t c = pool[i].id;
-        const float dcu = pool[i].d;
+        const uint32_t c = pool[i].id & ESG_ID_MASK;
+        const float dcb = pool[i].d;
         bool good = true;
         for (int s = 0; s < kept; ++s) {
-            if (row_dist(X, d, metric, c, keep[s]) < dcu) { good = false; break; }
+            if (row_dist(X, d, metric, c, keep[s]) < dcb) { good = false; break; }
         }
         if (good) {
             if ((threadIdx.x & 31) == 0) keep[kept] = c;
@@ -107,167 +72,102 @@ __device__ int occlusion_select(const float *X, int d, int metric, const Cand *p
     return kept;
 }
 
-// Forward edges: merge the two candidate lists of point i, drop self and
-// repeats, recompute exact distances, select by occlusion.
-__global__ void forward_kernel(const float *X, int64_t n, int d, int metric, const int32_t *node_idx,
-                               const int64_t *knn_ids, int K, const int64_t *smp_ids, int Ks,
-                               int M, uint32_t *fwd, int32_t *indeg) {
-    __shared__ Cand pool_s[4][kMaxPool];  // m <= kMaxPool, a power of two
+// Forward edges of the inserted points: occlusion over each point's search
+// result (already ascending), at most M; the point's row becomes those
+// edges, padded with NONE. Counts the reverse edges each target receives.
+__global__ void forward_kernel(const float *X, int d, int metric, int64_t n_items, const int64_t *pts,
+                               const Cand *res, const int32_t *res_cnt, int efc, int M, int R,
+                               uint32_t *adj_depth, int32_t *indeg) {
     __shared__ uint32_t keep_s[4][kMaxRow];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
-    if (i >= n) return;
-    uint32_t *out = fwd + i * (int64_t)M;
-    if (node_idx[i] < 0) {
-        for (int j = lane; j < M; j += 32) out[j] = ESG_NONE;
-        return;
-    }
-    Cand *pool = pool_s[w];
-    int m = 0;
-    // gather candidate ids (knn first, then sample), skipping self / invalid / repeats
-    for (int src = 0; src < 2; ++src) {
-        const int64_t *ids = src == 0 ? knn_ids + i * (int64_t)K : smp_ids + i * (int64_t)Ks;
-        const int cnt = src == 0 ? K : Ks;
-        for (int b0 = 0; b0 < cnt; b0 += 32) {
-            int j = b0 + lane;
-            int64_t id = j < cnt ? ids[j] : -1;
-            bool ok = id >= 0 && id != i;
-            if (ok) {
-                for (int t = 0; t < m; ++t) if (pool[t].id == (uint32_t)id) { ok = false; break; }
-            }
-            // repeats within this chunk
-            unsigned bal = __ballot_sync(0xffffffffu, ok);
-            for (int o = 0; o < 32; ++o) {
-                int64_t other = __shfl_sync(0xffffffffu, id, o);
-                if (o < lane && ((bal >> o) & 1) && other == id) ok = false;
-            }
-            bal = __ballot_sync(0xffffffffu, ok);
-            if (ok && m + __popc(bal & ((1u << lane) - 1)) < kMaxPool)
-                pool[m + __popc(bal & ((1u << lane) - 1))] = Cand{0.f, (uint32_t)id};
-            m = min(m + __popc(bal), kMaxPool);
-            __syncwarp();
-        }
-    }
-    // exact distances to u = i
-    for (int t = 0; t < m; ++t) {
-        float dd = row_dist(X, d, metric, (uint32_t)i, pool[t].id);
-        if (lane == 0) pool[t].d = dd;
-    }
-    __syncwarp();
-    // sort pool ascending
-    {
-        const int P = next_pow2_int(max(m, 2));
-        for (int j = m + lane; j < P; j += 32) pool[j] = Cand{INFINITY, ESG_NONE};
-        __syncwarp();
-        warp_sort_pow2(pool, P);
-    }
+    const int64_t it = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
+    if (it >= n_items) return;
+    const int64_t p = pts[it];
+    const Cand *pool = res + it * (int64_t)efc;
+    const int m = res_cnt[it];
     int kept = occlusion_select(X, d, metric, pool, m, M, keep_s[w]);
-    for (int j = lane; j < M; j += 32) {
+    uint32_t *row = adj_depth + p * (int64_t)R;
+    for (int j = lane; j < R; j += 32) {
         uint32_t v = j < kept ? keep_s[w][j] : ESG_NONE;
-        out[j] = v;
+        row[j] = v;
         if (v != ESG_NONE) atomicAdd(&indeg[v], 1);
     }
 }
 
-__global__ void scatter_reverse_kernel(int64_t n, int M, const uint32_t *fwd, const int64_t *off,
+__global__ void scatter_reverse_kernel(int64_t n_items, const int64_t *pts, int M, int R,
+                                       const uint32_t *adj_depth, const int64_t *off,
                                        int32_t *cursor, uint32_t *rev) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (it >= n_items) return;
+    const int64_t p = pts[it];
+    const uint32_t *row = adj_depth + p * (int64_t)R;
     for (int j = 0; j < M; ++j) {
-        uint32_t v = fwd[i * (int64_t)M + j];
+        uint32_t v = row[j];
         if (v == ESG_NONE) break;
         int pos = atomicAdd(&cursor[v], 1);
-        rev[off[v] + pos] = (uint32_t)i;
+        rev[off[v] + pos] = (uint32_t)p;
     }
 }
 
-// Final row of point u: forward edges plus reverse edges; when more than R,
-// re-select by occlusion among the 2R closest.
-__global__ void final_row_kernel(const float *X, int64_t n, int d, int metric, const int32_t *node_idx,
-                                 int M, int R, const uint32_t *fwd, const int64_t *off,
-                                 const int32_t *indeg, const uint32_t *rev, uint32_t *adj_depth) {
-    __shared__ Cand pool_s[4][2 * kMaxPool];  // cap + 32 rounded up to a power of two
+// Reverse edges into point v: append the new sources to v's row; when the
+// row would exceed R, re-select it by occlusion among the (at most
+// kMaxPool) closest of old row + new sources.
+__global__ void reverse_update_kernel(const float *X, int64_t n, int d, int metric, int R,
+                                      const int64_t *off, const int32_t *indeg, const uint32_t *rev,
+                                      uint32_t *adj_depth) {
+    __shared__ Cand pool_s[4][2 * kMaxPool];
     __shared__ uint32_t keep_s[4][kMaxRow];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
-    if (u >= n) return;
-    uint32_t *row = adj_depth + u * (int64_t)R;
-    if (node_idx[u] < 0) {
-        for (int j = lane; j < R; j += 32) row[j] = ESG_NONE;
+    const int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + w;
+    if (v >= n) return;
+    const int nr = indeg[v];
+    if (nr == 0) return;
+    uint32_t *row = adj_depth + v * (int64_t)R;
+    int deg = 0;
+    for (int b0 = 0; b0 < R; b0 += 32) {
+        bool has = b0 + lane < R && row[b0 + lane] != ESG_NONE;
+        deg += __popc(__ballot_sync(0xffffffffu, has));
+    }
+    const uint32_t *src = rev + off[v];
+    if (deg + nr <= R) {
+        for (int j = lane; j < nr; j += 32) row[deg + j] = src[j];
         return;
     }
     Cand *pool = pool_s[w];
-    const int cap = 2 * R <= kMaxPool ? 2 * R : kMaxPool;
-    int m = 0;  // sorted, unique, at most cap
-    const int nf = M;
-    const int64_t nr = indeg[u];
-    const int64_t total = nf + nr;
-    for (int64_t b0 = 0; b0 < total; b0 += 32) {
-        int64_t j = b0 + lane;
+    const int cap = kMaxPool;
+    int m = 0;
+    const int total = deg + nr;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int j = b0 + lane;
         uint32_t id = ESG_NONE;
-        if (j < nf) id = fwd[u * (int64_t)M + j];
-        else if (j < total) id = rev[off[u] + (j - nf)];
+        if (j < deg) id = row[j];
+        else if (j < total) id = src[j - deg];
         float dd = INFINITY;
-        // distances: one warp-wide reduction per candidate of the chunk
         for (int o = 0; o < 32; ++o) {
             uint32_t c = __shfl_sync(0xffffffffu, id, o);
             if (c == ESG_NONE) continue;
-            float t = row_dist(X, d, metric, (uint32_t)u, c);
+            float t = row_dist(X, d, metric, (uint32_t)v, c);
             if (lane == o) dd = t;
         }
-        // drop ids already pooled
-        bool ok = id != ESG_NONE;
-        if (ok) for (int t = 0; t < m; ++t) if (pool[t].id == id) { ok = false; break; }
-        unsigned bal = __ballot_sync(0xffffffffu, ok);
-        for (int o = 0; o < 32; ++o) {
-            uint32_t other = __shfl_sync(0xffffffffu, id, o);
-            if (o < lane && ((bal >> o) & 1) && other == id) ok = false;
-        }
-        bal = __ballot_sync(0xffffffffu, ok);
-        int c = __popc(bal);
-        if (c == 0) continue;
-        // append, sort, then keep the `cap` closest
+        const bool ok = id != ESG_NONE;
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        const int c = __popc(bal);
         if (ok) pool[m + __popc(bal & ((1u << lane) - 1))] = Cand{dd, id};
         __syncwarp();
-        {
-            const int mm = m + c;
-            const int P = next_pow2_int(max(mm, 2));
-            for (int j = mm + lane; j < P; j += 32) pool[j] = Cand{INFINITY, ESG_NONE};
-            __syncwarp();
-            warp_sort_pow2(pool, P);
-        }
-        m = min(m + c, cap);
-    }
-    int kept;
-    if (m <= R) {
-        kept = m;
-        for (int j = lane; j < m; j += 32) keep_s[w][j] = pool[j].id;
+        const int mm = m + c;
+        const int P = next_pow2_int(max(mm, 2));
+        for (int t = mm + lane; t < P; t += 32) pool[t] = Cand{INFINITY, ESG_NONE};
         __syncwarp();
-    } else {
-        kept = occlusion_select(X, d, metric, pool, m, R, keep_s[w]);
+        warp_sort_pow2(pool, P);
+        m = min(mm, cap);
     }
+    const int kept = occlusion_select(X, d, metric, pool, m, R, keep_s[w]);
     for (int j = lane; j < R; j += 32) row[j] = j < kept ? keep_s[w][j] : ESG_NONE;
 }
 
-}  // namespace
-
-int esg_graph_depths(int64_t n, int32_t leaf_size) {
-    // every node of a depth has size floor or ceil of n / 2^t; the depth
-    // holds a graph node iff its largest node is wider than the leaf size
-    int L = 0;
-    int64_t big = n;  // size of the largest node at depth L
-    while (big - 1 >= leaf_size) {
-        ++L;
-        big = (big + 1) / 2;
-    }
-    return L;
-}
-
-namespace {
 struct HostNode { int64_t l, r; int32_t heap; };
 
 void nodes_at_depth(int64_t n, int32_t leaf, int depth, std::vector<HostNode> &out) {
-    out.clear();
     std::vector<HostNode> cur{{0, n - 1, 0}};
     for (int t = 0; t < depth; ++t) {
         std::vector<HostNode> nxt;
@@ -279,125 +179,134 @@ void nodes_at_depth(int64_t n, int32_t leaf, int depth, std::vector<HostNode> &o
         }
         cur.swap(nxt);
     }
-    for (auto &nd : cur) out.push_back(nd);
+    out.clear();
+    for (auto &nd : cur) if (nd.r - nd.l >= leaf) out.push_back(nd);
 }
+
 }  // namespace
+
+int esg_graph_depths(int64_t n, int32_t leaf_size) {
+    // every node of a depth has size floor or ceil of n / 2^t; the depth
+    // holds a graph node iff its largest node is wider than the leaf size
+    int L = 0;
+    int64_t big = n;
+    while (big - 1 >= leaf_size) {
+        ++L;
+        big = (big + 1) / 2;
+    }
+    return L;
+}
 
 esg_status esg_build_graphs(esg_index *ix, const esg_build_params &p, cudaStream_t stream) {
     const int64_t n = ix->n;
     const int d = ix->d;
     const int L = ix->L, R = ix->R, M = p.M, E = ix->E;
-    const int K = std::min(p.knn_k, kMaxPool);
-    const int Ks = std::min(p.sample_k, kMaxPool - K);
-    const int S = std::max(1, p.sample_size);
+    const int efc = std::max(p.ef_construction, M);
+    const int div = std::max(1, p.batch_div);
     if (L == 0) return ESG_OK;
 
     std::vector<int32_t> entries_h((size_t)ix->n_heap * E, -1);
-    int64_t *lo = nullptr, *hi = nullptr, *knn = nullptr, *smp = nullptr, *s_rows = nullptr;
-    int64_t *s_off_d = nullptr, *s_cnt_d = nullptr, *off = nullptr;
-    int32_t *node_idx = nullptr, *cnt = nullptr, *indeg = nullptr, *cursor = nullptr;
-    float *dist = nullptr, *xnorm = nullptr, *S_mat = nullptr, *snorm = nullptr;
-    uint32_t *fwd = nullptr, *rev = nullptr;
+    std::vector<int32_t> build_entry((size_t)ix->n_heap, -1);
+    int64_t *pts = nullptr, *off = nullptr, *stats = nullptr;
+    esg_piece *pieces = nullptr;
+    Cand *res = nullptr;
+    int32_t *res_cnt = nullptr, *indeg = nullptr, *cursor = nullptr, *bentry = nullptr;
+    uint32_t *rev = nullptr;
     void *cub_tmp = nullptr;
     size_t cub_bytes = 0;
+    int64_t cap_items = 0;
     esg_status st = ESG_OK;
+    std::vector<HostNode> nodes;
+    std::vector<int64_t> h_pts;
+    std::vector<esg_piece> h_pieces;
 #define B_TRY(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) { esg_set_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); st = _e == cudaErrorMemoryAllocation ? ESG_ERR_OOM : ESG_ERR_CUDA; goto done; } } while (0)
-    {
-    B_TRY(cudaMalloc(&lo, sizeof(int64_t) * n));
-    B_TRY(cudaMalloc(&hi, sizeof(int64_t) * n));
-    B_TRY(cudaMalloc(&node_idx, sizeof(int32_t) * n));
-    B_TRY(cudaMalloc(&knn, sizeof(int64_t) * n * std::max(K, 1)));
-    B_TRY(cudaMalloc(&smp, sizeof(int64_t) * n * std::max(Ks, 1)));
-    B_TRY(cudaMalloc(&dist, sizeof(float) * n * std::max(std::max(K, Ks), 1)));
-    B_TRY(cudaMalloc(&cnt, sizeof(int32_t) * n));
-    B_TRY(cudaMalloc(&xnorm, sizeof(float) * n));
-    B_TRY(cudaMalloc(&fwd, sizeof(uint32_t) * n * M));
+    // largest round: one batch per node, at most size / div + 1 points each
+    cap_items = n / div + ((int64_t)1 << (L - 1)) + 64;
+    cap_items = std::min<int64_t>(cap_items, n);
+    B_TRY(cudaMalloc(&pts, sizeof(int64_t) * cap_items));
+    B_TRY(cudaMalloc(&pieces, sizeof(esg_piece) * cap_items));
+    B_TRY(cudaMalloc(&res, sizeof(Cand) * cap_items * efc));
+    B_TRY(cudaMalloc(&res_cnt, sizeof(int32_t) * cap_items * 2));
+    B_TRY(cudaMalloc(&stats, sizeof(int64_t) * cap_items * 3));
     B_TRY(cudaMalloc(&indeg, sizeof(int32_t) * (n + 1)));
     B_TRY(cudaMalloc(&cursor, sizeof(int32_t) * n));
     B_TRY(cudaMalloc(&off, sizeof(int64_t) * (n + 1)));
-    B_TRY(cudaMalloc(&rev, sizeof(uint32_t) * n * M));
-    row_norms_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(ix->X, n, d, xnorm);
-    B_TRY(cudaGetLastError());
+    B_TRY(cudaMalloc(&rev, sizeof(uint32_t) * cap_items * M));
+    B_TRY(cudaMalloc(&bentry, sizeof(int32_t) * ix->n_heap));
     B_TRY(cub::DeviceScan::ExclusiveSum(nullptr, cub_bytes, (int32_t *)nullptr, (int64_t *)nullptr, (int)(n + 1)));
     B_TRY(cudaMalloc(&cub_tmp, cub_bytes));
-    const int mode = ix->metric == ESG_IP ? 1 : 2;
-    std::vector<HostNode> nodes;
-    for (int t = 0; t < L; ++t) {
-        point_node_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(n, ix->leaf_size, t, lo, hi, node_idx);
-        B_TRY(cudaGetLastError());
-        // exact knn_k nearest inside the node
-        if (K > 0) {
-            st = esg_launch_bruteforce_mode(mode, ix->X, n, d, ix->X, n, lo, hi, K, knn, dist, cnt,
-                                            nullptr, 1, xnorm, xnorm, stream);
-            if (st != ESG_OK) goto done;
-        }
-        // sample of each graph node at this depth
+    B_TRY(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n + 1), stream));
+    for (int t = L - 1; t >= 0; --t) {
         nodes_at_depth(n, ix->leaf_size, t, nodes);
-        std::vector<int64_t> s_off(nodes.size(), 0), s_cnt(nodes.size(), 0), rows;
+        uint32_t *adj_t = ix->adj + (size_t)t * (size_t)n * (size_t)R;
+        std::vector<int64_t> inserted(nodes.size(), 0);
         for (size_t j = 0; j < nodes.size(); ++j) {
             const HostNode &nd = nodes[j];
+            const int64_t mid = nd.l + (nd.r - nd.l) / 2;
             const int64_t size = nd.r - nd.l + 1;
-            // entry points of this node: E ranks evenly spaced
-            if (nd.r - nd.l >= ix->leaf_size) {
-                int ce = (int)std::min<int64_t>(E, size);
-                for (int e = 0; e < ce; ++e)
-                    entries_h[(size_t)nd.heap * E + e] = (int32_t)(nd.l + (int64_t)e * size / ce);
-                int64_t cs = std::min<int64_t>(S, size);
-                s_off[j] = (int64_t)rows.size();
-                s_cnt[j] = cs;
-                for (int64_t e = 0; e < cs; ++e) rows.push_back(nd.l + e * size / cs);
+            build_entry[nd.heap] = (int32_t)nd.l;  // insertion searches start at the first point
+            int ce = (int)std::min<int64_t>(E, size);
+            for (int e = 0; e < ce; ++e)
+                entries_h[(size_t)nd.heap * E + e] = (int32_t)(nd.l + (int64_t)e * size / ce);
+            if (mid - nd.l >= ix->leaf_size) {
+                // the left child holds a graph: copy its rows (Algorithm 3, line 7 reading)
+                B_TRY(cudaMemcpyAsync(adj_t + nd.l * (size_t)R, ix->adj + ((size_t)(t + 1) * n + nd.l) * R,
+                                      sizeof(uint32_t) * (size_t)(mid - nd.l + 1) * R,
+                                      cudaMemcpyDeviceToDevice, stream));
+                inserted[j] = mid - nd.l + 1;
+            } else {
+                inserted[j] = 1;  // first point of a fresh graph: no edges
             }
         }
-        if (Ks > 0 && !rows.empty()) {
-            int64_t ns = (int64_t)rows.size();
-            B_TRY(cudaMalloc(&s_rows, sizeof(int64_t) * ns));
-            B_TRY(cudaMalloc(&S_mat, sizeof(float) * ns * d));
-            B_TRY(cudaMalloc(&snorm, sizeof(float) * ns));
-            B_TRY(cudaMalloc(&s_off_d, sizeof(int64_t) * nodes.size()));
-            B_TRY(cudaMalloc(&s_cnt_d, sizeof(int64_t) * nodes.size()));
-            B_TRY(cudaMemcpyAsync(s_rows, rows.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, stream));
-            B_TRY(cudaMemcpyAsync(s_off_d, s_off.data(), sizeof(int64_t) * nodes.size(), cudaMemcpyHostToDevice, stream));
-            B_TRY(cudaMemcpyAsync(s_cnt_d, s_cnt.data(), sizeof(int64_t) * nodes.size(), cudaMemcpyHostToDevice, stream));
-            gather_rows_kernel<<<(unsigned)ns, 128, 0, stream>>>(ix->X, d, s_rows, ns, S_mat);
-            B_TRY(cudaGetLastError());
-            row_norms_kernel<<<ceil_div_i(ns, 256), 256, 0, stream>>>(S_mat, ns, d, snorm);
-            B_TRY(cudaGetLastError());
-            // per-point range = its node's sample block (node index at this depth)
-            sample_range_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(n, node_idx, s_off_d, s_cnt_d, lo, hi);
-            B_TRY(cudaGetLastError());
-            st = esg_launch_bruteforce_mode(mode, S_mat, ns, d, ix->X, n, lo, hi, Ks, smp, dist, cnt,
-                                            s_rows, 0, snorm, xnorm, stream);
+        B_TRY(cudaMemcpyAsync(bentry, build_entry.data(), sizeof(int32_t) * ix->n_heap,
+                              cudaMemcpyHostToDevice, stream));
+        for (;;) {
+            h_pts.clear();
+            h_pieces.clear();
+            for (size_t j = 0; j < nodes.size(); ++j) {
+                const HostNode &nd = nodes[j];
+                const int64_t size = nd.r - nd.l + 1;
+                if (inserted[j] >= size) continue;
+                int64_t b = std::max<int64_t>(1, inserted[j] / div);
+                b = std::min(b, size - inserted[j]);
+                for (int64_t q = 0; q < b; ++q) {
+                    h_pts.push_back(nd.l + inserted[j] + q);
+                    esg_piece pc;
+                    pc.node_l = nd.l; pc.node_r = nd.r; pc.pl = nd.l; pc.pr = nd.r;
+                    pc.heap = nd.heap; pc.depth = t; pc.kind = ESG_PIECE_GRAPH; pc.reserved = 0;
+                    h_pieces.push_back(pc);
+                }
+                inserted[j] += b;
+            }
+            const int64_t ni = (int64_t)h_pts.size();
+            if (ni == 0) break;
+            if (ni > cap_items) { esg_set_error("build: round larger than its buffers"); st = ESG_ERR_CUDA; goto done; }
+            B_TRY(cudaMemcpyAsync(pts, h_pts.data(), sizeof(int64_t) * ni, cudaMemcpyHostToDevice, stream));
+            B_TRY(cudaMemcpyAsync(pieces, h_pieces.data(), sizeof(esg_piece) * ni, cudaMemcpyHostToDevice, stream));
+            st = esg_run_search_items(ix->X, n, d, ix->metric, ix->adj, R, bentry, 1, pts, pieces, ni,
+                                      efc, efc, 0, res, res_cnt, res_cnt + cap_items, stats, stream);
             if (st != ESG_OK) goto done;
+            B_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, stream));
+            forward_kernel<<<ceil_div_i(ni, 4), 128, 0, stream>>>(ix->X, d, ix->metric, ni, pts, res, res_cnt,
+                                                                 efc, M, R, adj_t, indeg);
+            B_TRY(cudaGetLastError());
+            B_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, indeg, off, (int)(n + 1), stream));
+            scatter_reverse_kernel<<<ceil_div_i(ni, 256), 256, 0, stream>>>(ni, pts, M, R, adj_t, off, cursor, rev);
+            B_TRY(cudaGetLastError());
+            reverse_update_kernel<<<ceil_div_i(n, 4), 128, 0, stream>>>(ix->X, n, d, ix->metric, R, off,
+                                                                        indeg, rev, adj_t);
+            B_TRY(cudaGetLastError());
+            B_TRY(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n + 1), stream));
             B_TRY(cudaStreamSynchronize(stream));
-            cudaFree(s_rows); cudaFree(S_mat); cudaFree(snorm); cudaFree(s_off_d); cudaFree(s_cnt_d);
-            s_rows = nullptr; S_mat = nullptr; snorm = nullptr; s_off_d = nullptr; s_cnt_d = nullptr;
-        } else {
-            B_TRY(cudaMemsetAsync(smp, 0xFF, sizeof(int64_t) * n * std::max(Ks, 1), stream));
         }
-        // forward edges by occlusion, then reverse edges
-        B_TRY(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n + 1), stream));
-        B_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, stream));
-        forward_kernel<<<ceil_div_i(n, 4), 128, 0, stream>>>(ix->X, n, d, ix->metric, node_idx, knn, K,
-                                                               smp, Ks, M, fwd, indeg);
-        B_TRY(cudaGetLastError());
-        B_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, indeg, off, (int)(n + 1), stream));
-        scatter_reverse_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(n, M, fwd, off, cursor, rev);
-        B_TRY(cudaGetLastError());
-        final_row_kernel<<<ceil_div_i(n, 4), 128, 0, stream>>>(
-            ix->X, n, d, ix->metric, node_idx, M, R, fwd, off, indeg, rev,
-            ix->adj + (size_t)t * (size_t)n * (size_t)R);
-        B_TRY(cudaGetLastError());
-        B_TRY(cudaStreamSynchronize(stream));
     }
     B_TRY(cudaMemcpyAsync(ix->entries, entries_h.data(), sizeof(int32_t) * entries_h.size(),
                           cudaMemcpyHostToDevice, stream));
     B_TRY(cudaStreamSynchronize(stream));
-    }
 done:
 #undef B_TRY
-    cudaFree(lo); cudaFree(hi); cudaFree(node_idx); cudaFree(knn); cudaFree(smp); cudaFree(dist);
-    cudaFree(cnt); cudaFree(xnorm); cudaFree(fwd); cudaFree(indeg); cudaFree(cursor); cudaFree(off);
-    cudaFree(rev); cudaFree(cub_tmp); cudaFree(s_rows); cudaFree(S_mat); cudaFree(snorm);
-    cudaFree(s_off_d); cudaFree(s_cnt_d);
+    cudaFree(pts); cudaFree(pieces); cudaFree(res); cudaFree(res_cnt); cudaFree(stats);
+    cudaFree(indeg); cudaFree(cursor); cudaFree(off); cudaFree(rev); cudaFree(bentry);
+    cudaFree(cub_tmp);
     return st;
 }

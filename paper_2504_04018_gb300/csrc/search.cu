@@ -176,8 +176,11 @@ struct SearchArgs {
     const uint32_t *adj;
     const int32_t *entries;
     const float *queries;
+    const int64_t *qidx;   // optional: query row of an item (build: the inserted point)
     const esg_piece *pieces;
-    const int32_t *kq;     // per-query k (validated), 0 = invalid
+    const int32_t *kq;     // per-query k (validated), 0 = invalid; null = kconst
+    int kconst;
+    int qshift;            // query of item i = i >> qshift (2 pieces per query: 1)
     int64_t n;
     int64_t n_items;
     int d, nvec, LPR, R, E, metric;
@@ -220,9 +223,9 @@ search_kernel(SearchArgs a) {
         if (lane == 0) item = (int64_t)atomicAdd(a.queue, 1ULL);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
-        const int64_t qi = item >> 1;
+        const int64_t qi = item >> a.qshift;
         const esg_piece pc = a.pieces[item];
-        const int kq = a.kq[qi];
+        const int kq = a.kq ? a.kq[qi] : a.kconst;
         int64_t n_exp = 0, n_eval = 0, n_oor = 0;
         int status = 0;
         if (pc.kind == ESG_PIECE_NONE || kq <= 0) {
@@ -237,7 +240,8 @@ search_kernel(SearchArgs a) {
         // query slice in registers
         float4 qv[VPL];
         {
-            const float4 *q4 = reinterpret_cast<const float4 *>(a.queries + qi * (int64_t)a.d);
+            const int64_t qrow = a.qidx ? a.qidx[item] : qi;
+            const float4 *q4 = reinterpret_cast<const float4 *>(a.queries + qrow * (int64_t)a.d);
             const int s = lane & (a.LPR - 1);
 #pragma unroll
             for (int v = 0; v < VPL; ++v) qv[v] = __ldg(q4 + s + v * a.LPR);
@@ -583,6 +587,7 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     if (st == ESG_OK) {
         SearchArgs a;
         a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
+        a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
         a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
         a.d = ix->d; a.nvec = ix->d / 4; a.LPR = lpr; a.R = ix->R; a.E = ix->E;
         a.metric = ix->metric; a.ef = ef;
@@ -600,6 +605,61 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
         ce = cudaGetLastError();
         if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     }
+    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }
+    return st;
+}
+
+// Beam search over prepared work items (graph construction): item i searches
+// the piece pieces[i] for the row qidx[i] of X, keeping the best k results in
+// res[i * k ..]. Entry points come from `entries` (E per heap node).
+esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, const uint32_t *adj,
+                                int R, const int32_t *entries, int E, const int64_t *qidx,
+                                const esg_piece *pieces, int64_t n_items, int ef, int k,
+                                int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
+                                int64_t *res_stats, cudaStream_t stream) {
+    if (n_items == 0) return ESG_OK;
+    int lpr = 0;
+    int vpl = esg_pick_vpl(d, &lpr);
+    if (vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
+    const int efk = std::max(ef, k);
+    int C = ((std::max(2 * efk, efk + 64) + 31) / 32) * 32;
+    int H = 1024;
+    const int hash_per_ef = env_int("ESG_BUILD_HASH_PER_EF", 48);
+    while (H < hash_per_ef * efk && H < (1 << 22)) H <<= 1;
+    while (H < 4 * R) H <<= 1;
+    const int wpb = 2;
+    const bool smem_hash = (size_t)H * 4 <= (size_t)env_int("ESG_SMEM_HASH_BYTES", 65536);
+    size_t per_warp = (smem_hash ? (size_t)H * 4 : 0) + (size_t)C * 16 + kBatch * 12 + 16;
+    size_t smem = per_warp * wpb;
+    SearchFn fn = pick_search(vpl);
+    int dev = 0, sms = 0, per_sm = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ESG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem));
+    if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
+    int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + wpb - 1) / wpb);
+    if (grid < 1) grid = 1;
+    size_t bytes_hash = smem_hash ? 0 : (size_t)grid * wpb * H * 4;
+    unsigned char *scratch = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes_hash + 256, stream));
+    unsigned long long *queue = (unsigned long long *)scratch;
+    uint32_t *ghash = smem_hash ? nullptr : (uint32_t *)(scratch + 256);
+    esg_status st = ESG_OK;
+    cudaError_t ce = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
+    if (ce == cudaSuccess) {
+        SearchArgs a;
+        a.X = X; a.adj = adj; a.entries = entries; a.queries = X; a.qidx = qidx;
+        a.pieces = pieces; a.kq = nullptr; a.kconst = k; a.qshift = 0;
+        a.n = n; a.n_items = n_items; a.d = d; a.nvec = d / 4; a.LPR = lpr; a.R = R; a.E = E;
+        a.metric = metric; a.ef = ef; a.max_exp = max_exp > 0 ? max_exp : 16 * ef + 256;
+        a.k_max = k; a.H = H; a.C = C; a.ghash = ghash; a.queue = queue;
+        a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
+        fn<<<(unsigned)grid, wpb * 32, smem, stream>>>(a);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     cudaError_t fe = cudaFreeAsync(scratch, stream);
     if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }
     return st;
