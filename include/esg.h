@@ -242,6 +242,19 @@ esg_status esg_attr_to_rank_range(const esg_index *index, const double *lo, cons
 esg_status esg_save(const esg_index *index, const char *path);
 esg_status esg_load(const char *path, esg_index **out);
 
+/*
+ * Benchmark timing (library-specific; no counterpart in the paper). While
+ * enabled, every esg_search_batch records a CUDA event pair around its beam
+ * search kernel on the call's stream and counts the kernels it launches.
+ * esg_profile_read waits for the recorded events and returns the summed
+ * kernel milliseconds, the number of kernels launched and the number of
+ * timed kernel launches since the last reset (reset != 0 clears them).
+ * Enabling resets the counters. Host pointers; any may be NULL.
+ */
+esg_status esg_profile_enable(int32_t on);
+esg_status esg_profile_read(double *kernel_ms, int64_t *kernel_launches, int64_t *timed_launches,
+                            int32_t reset);
+
 const char *esg_status_str(esg_status s);
 const char *esg_last_error(void);
 

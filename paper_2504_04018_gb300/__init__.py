@@ -32,7 +32,7 @@ EXPORTED = [
     "esg_build_params_default", "esg_search_params_default", "esg_build", "esg_index_import",
     "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
     "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
-    "esg_status_str", "esg_last_error",
+    "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
 ]
 
 
@@ -86,12 +86,15 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_attr_to_rank_range.argtypes = [_P, _P, _P, _I64, _P, _P]
     lib.esg_save.argtypes = [_P, ctypes.c_char_p]
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
+    lib.esg_profile_enable.argtypes = [_I32]
+    lib.esg_profile_read.argtypes = [_P, _P, _P, _I32]
     lib.esg_status_str.restype = ctypes.c_char_p
     lib.esg_status_str.argtypes = [_I32]
     lib.esg_last_error.restype = ctypes.c_char_p
     for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
-                 "esg_attr_to_rank_range", "esg_save", "esg_load"]:
+                 "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
+                 "esg_profile_read"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -294,3 +297,20 @@ def esg_load(path: str) -> Index:
     h = _P()
     _check(load_library().esg_load(path.encode(), ctypes.byref(h)), "esg_load")
     return Index(h)
+
+
+def esg_profile_enable(on: bool = True):
+    """Record CUDA events around each search kernel (benchmark timing)."""
+    _check(load_library().esg_profile_enable(1 if on else 0), "esg_profile_enable")
+
+
+def esg_profile_read(reset: bool = True):
+    """(summed search-kernel ms, kernels launched, timed launches) since the
+    last reset; waits for the recorded events."""
+    ms = ctypes.c_double()
+    launches = _I64()
+    timed = _I64()
+    _check(load_library().esg_profile_read(ctypes.byref(ms), ctypes.byref(launches),
+                                           ctypes.byref(timed), 1 if reset else 0),
+           "esg_profile_read")
+    return ms.value, launches.value, timed.value

@@ -87,6 +87,12 @@ esg_status esg_launch_bruteforce(const float *base, int64_t n, int32_t d, int me
 esg_status esg_build_graphs(esg_index *ix, const esg_build_params &p, cudaStream_t stream);
 esg_status esg_make_storage(esg_index *ix, cudaStream_t stream);
 
+// benchmark timing hooks (profile.cu)
+bool esg_prof_on();
+void esg_prof_count(int64_t launches);
+int esg_prof_begin(cudaStream_t stream);
+void esg_prof_end(int idx, cudaStream_t stream);
+
 // --------------------------------------------------------- device helpers
 
 struct Cand {

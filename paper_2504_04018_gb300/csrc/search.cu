@@ -531,12 +531,12 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     int C = ((std::max(4 * efk, efk + 64) + 31) / 32) * 32;
     if (C > 4096) C = 4096;
     // visited set: open addressing, power of two, sized from the beam width
-    int H = 1024;
-    const int hash_per_ef = env_int("ESG_HASH_PER_EF", 128);
+    int H = 4096;
+    const int hash_per_ef = env_int("ESG_HASH_PER_EF", 64);
     while (H < hash_per_ef * efk && H < (1 << 22)) H <<= 1;
     while (H < 4 * ix->R) H <<= 1;
     const int wpb = 2;
-    const bool smem_hash = (size_t)H * 4 <= (size_t)env_int("ESG_SMEM_HASH_BYTES", 65536);
+    const bool smem_hash = (size_t)H * 4 <= (size_t)env_int("ESG_SMEM_HASH_BYTES", 32768);
     size_t per_warp = (smem_hash ? (size_t)H * 4 : 0) + (size_t)C * 16 + kBatch * 12 + 16;
     size_t smem = per_warp * wpb;
     int64_t n_items = 2 * s.nq;
@@ -594,11 +594,14 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
         a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * ef + 256;
         a.k_max = s.k_max; a.H = H; a.C = C; a.ghash = ghash; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
+        const int pidx = esg_prof_begin(stream);
         fn<<<(unsigned)grid, wpb * 32, smem, stream>>>(a);
         ce = cudaGetLastError();
+        esg_prof_end(pidx, stream);
         if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     }
     if (st == ESG_OK) {
+        esg_prof_count(3);  // prep, search, merge
         merge_kernel<<<ceil_div_i(s.nq, 128), 128, 0, stream>>>(
             s.nq, s.k_max, kq, res, res_cnt, res_status, res_stats, qs, ix->perm, pieces,
             s.out_ids, s.out_dist, s.out_count, s.out_status, s.out_stats);
