@@ -284,8 +284,10 @@ def run_ours(args, rank, world, local):
     time.sleep(0.4)
     E.esg_profile_enable(True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     evs = [one_step() for _ in range(args.steps)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     kernel_ms, launches, timed = E.esg_profile_read(reset=True)
     E.esg_profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
