@@ -130,6 +130,25 @@ __device__ __forceinline__ void warp_sort64(Cand *v) {
     }
 }
 
+// Bitonic sort of one candidate per lane across the warp (ascending by lane),
+// in registers with shuffles.
+__device__ __forceinline__ void warp_sort32_reg(float &d, uint32_t &id) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, d, stride);
+            const uint32_t oid = __shfl_xor_sync(0xffffffffu, id, stride);
+            const bool lower = (lane & stride) == 0;        // I keep the smaller if ascending
+            const bool up = (lane & size) == 0;
+            const bool other_less = cand_less(od, oid, d, id);
+            const bool take = (lower == up) ? other_less : !other_less && !(od == d && oid == id);
+            if (take) { d = od; id = oid; }
+        }
+    }
+}
+
 // Bitonic sort of P (a power of two, <= 1024) candidates in shared memory by
 // one warp (ascending); pad unused slots with {+inf, ESG_NONE} first.
 __device__ __forceinline__ void warp_sort_pow2(Cand *v, int P) {

@@ -42,20 +42,46 @@ __device__ __forceinline__ uint32_t hash_mix(uint32_t x) {
     return x;
 }
 
-// Returns false iff `id` is already in the visited set. When the set has
-// reached its load limit the id is reported as new without being stored
-// (the caller's list de-duplication then catches repeats still listed).
-__device__ __forceinline__ bool visit(uint32_t *hash, uint32_t hmask, int *hcount, int hlimit,
-                                      uint32_t id, bool *saturated) {
-    uint32_t h = hash_mix(id) & hmask;
-    for (uint32_t probe = 0; probe <= hmask; ++probe) {
-        uint32_t slot = (h + probe) & hmask;
-        uint32_t cur = hash[slot];
+// Visited set of one beam search: an open-addressing table in shared memory
+// backed, once it reaches its load limit, by a larger table in a per-warp
+// global-memory slot. visit() returns false iff `id` was already visited.
+// Only when both tables are at their limits is an id reported as new without
+// being stored (`saturated`; the list de-duplication then catches repeats).
+struct Visited {
+    uint32_t *hs;   // shared table, hmask + 1 slots
+    uint32_t hmask;
+    int *hcount;
+    int hlimit;
+    uint32_t *hg;   // global overflow table, gmask + 1 slots (all ESG_NONE when unused)
+    uint32_t gmask;
+    int *gcount;
+    int glimit;
+};
+
+__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated, bool *used_g) {
+    uint32_t h = hash_mix(id) & v.hmask;
+    for (uint32_t probe = 0; probe <= v.hmask; ++probe) {
+        const uint32_t slot = (h + probe) & v.hmask;
+        const uint32_t cur = v.hs[slot];
         if (cur == id) return false;
         if (cur == ESG_NONE) {
-            if (*(volatile int *)hcount >= hlimit) { *saturated = true; return true; }
-            uint32_t prev = atomicCAS(&hash[slot], ESG_NONE, id);
-            if (prev == ESG_NONE) { atomicAdd(hcount, 1); return true; }
+            if (*(volatile int *)v.hcount >= v.hlimit) break;   // continue in the global table
+            const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
+            if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return true; }
+            if (prev == id) return false;
+        }
+    }
+    if (v.hg == nullptr) { *saturated = true; return true; }
+    *used_g = true;
+    h = hash_mix(id ^ 0x9e3779b9u) & v.gmask;
+    for (uint32_t probe = 0; probe <= v.gmask; ++probe) {
+        const uint32_t slot = (h + probe) & v.gmask;
+        const uint32_t cur = *(volatile uint32_t *)&v.hg[slot];
+        if (cur == id) return false;
+        if (cur == ESG_NONE) {
+            if (*(volatile int *)v.gcount >= v.glimit) { *saturated = true; return true; }
+            const uint32_t prev = atomicCAS(&v.hg[slot], ESG_NONE, id);
+            if (prev == ESG_NONE) { atomicAdd(v.gcount, 1); return true; }
             if (prev == id) return false;
         }
     }
@@ -73,7 +99,9 @@ __device__ __forceinline__ void eval_rows(const float4 *__restrict__ X4, int nve
     const int s = lane & (LPR - 1);
     const int g = lane / LPR;
     const int rows_per_pass = 32 / LPR;
-    constexpr int U = (VPL <= 2) ? 4 : 2;
+    // all loads of U passes are issued before any reduction: U * VPL float4
+    // (at most 16, 64 registers) per lane in flight
+    constexpr int U = (VPL <= 2) ? 8 : (VPL <= 4 ? 4 : 2);
     for (int base = 0; base < m; base += rows_per_pass * U) {
         float4 xv[U][VPL];
         uint32_t id[U];
@@ -139,6 +167,7 @@ struct ListState {
     int len;       // items in the list
     int qn;        // in-range items kept (<= ef)
     Cand qworst;   // the ef-th in-range item when qn == ef, else +inf
+    int first;     // position of the best unexpanded item, -1 if none
 };
 
 // Cut the list after its ef-th in-range item (Q keeps the best ef; nothing
@@ -149,26 +178,67 @@ __device__ __forceinline__ void truncate_list(const Cand *list, ListState &st, i
     int seen = 0;
     st.qn = 0;
     st.qworst = Cand{INFINITY, ESG_NONE};
+    st.first = -1;
     for (int base = 0; base < st.len; base += 32) {
-        int i = base + lane;
-        uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
-        bool inr = i < st.len && id >= pl && id <= pr;
-        unsigned bal = __ballot_sync(0xffffffffu, inr);
-        int c = __popc(bal);
+        const int i = base + lane;
+        const uint32_t raw = i < st.len ? list[i].id : ESG_NONE;
+        const uint32_t id = raw & ESG_ID_MASK;
+        const bool inr = i < st.len && id >= pl && id <= pr;
+        const unsigned bal = __ballot_sync(0xffffffffu, inr);
+        const unsigned unexp = __ballot_sync(0xffffffffu, i < st.len && !(raw & ESG_EXPANDED));
+        const int c = __popc(bal);
         if (seen + c >= ef) {
             // position of the (ef - seen)-th set bit of bal
-            int need = ef - seen;
+            const int need = ef - seen;
             unsigned b = bal;
             for (int t = 1; t < need; ++t) b &= b - 1;
-            int pos = base + __ffs(b) - 1;
+            const int pos = base + __ffs(b) - 1;
             st.len = pos + 1;
             st.qn = ef;
             st.qworst = list[pos];
+            const unsigned keep_unexp = unexp & (pos - base == 31 ? 0xffffffffu : ((1u << (pos - base + 1)) - 1));
+            if (st.first < 0 && keep_unexp) st.first = base + __ffs(keep_unexp) - 1;
             return;
         }
+        if (st.first < 0 && unexp) st.first = base + __ffs(unexp) - 1;
         seen += c;
     }
     st.qn = seen;
+}
+
+// Admitted candidates sit in batch[0..64) (rejected slots hold +inf). Sort
+// them and merge them into `list`, returning the merged list (list or list2)
+// after truncation. Batches of at most 32 are sorted in registers.
+__device__ __forceinline__ Cand *admit_batch(Cand *batch, Cand *cbuf, Cand *list, Cand *list2,
+                                             ListState &st, int ef, int C, uint32_t pl, uint32_t pr,
+                                             int &status) {
+    const int lane = threadIdx.x & 31;
+    const Cand x0 = batch[lane], x1 = batch[lane + 32];
+    const bool k0 = x0.id != ESG_NONE, k1 = x1.id != ESG_NONE;
+    const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+    const int b = __popc(b0) + __popc(b1);
+    if (b == 0) return list;
+    const Cand *B;
+    if (b <= 32) {
+        const unsigned below = (1u << lane) - 1;
+        if (k0) cbuf[__popc(b0 & below)] = x0;
+        if (k1) cbuf[__popc(b0) + __popc(b1 & below)] = x1;
+        __syncwarp();
+        float d = lane < b ? cbuf[lane].d : INFINITY;
+        uint32_t id = lane < b ? cbuf[lane].id : ESG_NONE;
+        __syncwarp();
+        warp_sort32_reg(d, id);
+        cbuf[lane] = Cand{d, id};
+        __syncwarp();
+        B = cbuf;
+    } else {
+        warp_sort64(batch);
+        B = batch;
+    }
+    if (st.len + b > C) status |= ESG_Q_OVERFLOW;
+    st.len = warp_merge(list, st.len, B, b, list2, C);
+    truncate_list(list2, st, ef, pl, pr);
+    return list2;
 }
 
 struct SearchArgs {
@@ -186,7 +256,8 @@ struct SearchArgs {
     int d, nvec, LPR, R, E, metric;
     int ef, max_exp, k_max;
     int H, C;
-    uint32_t *ghash;       // global visited sets, one H-slot per warp, or null
+    uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
+    int G;
     unsigned long long *queue;  // atomic work counter
     Cand *res;             // [n_items, k_max]
     int32_t *res_cnt;      // [n_items]
@@ -195,27 +266,34 @@ struct SearchArgs {
 };
 
 template <int VPL>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(64, 8)
 search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const bool smem_hash = a.ghash == nullptr;
-    size_t per_warp = (smem_hash ? (size_t)a.H * 4 : 0) + (size_t)a.C * 8 * 2 + kBatch * 8 +
-                      kBatch * 4 + 16;
+    const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 * 2 + kBatch * 8 + 32 * 8 +
+                            kBatch * 4 + 16;
     unsigned char *base = smem_raw + per_warp * wib;
     WarpSmem w;
     size_t off = 0;
     w.list = (Cand *)(base + off); off += (size_t)a.C * 8;
     w.list2 = (Cand *)(base + off); off += (size_t)a.C * 8;
     w.batch = (Cand *)(base + off); off += kBatch * 8;
+    Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
     w.nbuf = (uint32_t *)(base + off); off += kBatch * 4;
     w.hcount = (int *)(base + off); off += 16;
     const int gwarp = blockIdx.x * wpb + wib;
-    w.hash = smem_hash ? (uint32_t *)(base + off) : a.ghash + (size_t)gwarp * a.H;
-    const uint32_t hmask = (uint32_t)a.H - 1;
-    const int hlimit = (a.H * 3) / 4;
+    w.hash = (uint32_t *)(base + off);
+    Visited vis;
+    vis.hs = w.hash;
+    vis.hmask = (uint32_t)a.H - 1;
+    vis.hcount = w.hcount;
+    vis.hlimit = (a.H * 3) / 4;
+    vis.hg = a.ghash ? a.ghash + (size_t)gwarp * a.G : nullptr;
+    vis.gmask = (uint32_t)a.G - 1;
+    vis.gcount = w.hcount + 1;
+    vis.glimit = (a.G * 3) / 4;
     const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
 
     for (;;) {
@@ -246,48 +324,44 @@ search_kernel(SearchArgs a) {
 #pragma unroll
             for (int v = 0; v < VPL; ++v) qv[v] = __ldg(q4 + s + v * a.LPR);
         }
-        ListState st{0, 0, Cand{INFINITY, ESG_NONE}};
+        ListState st{0, 0, Cand{INFINITY, ESG_NONE}, -1};
         Cand *list = w.list, *list2 = w.list2;
         bool saturated = false;
 
         if (!is_graph) {
             // Leaf piece: exact scan of [pl, pr] (Algorithm 4, first branch).
             for (int64_t c0 = pl; c0 <= (int64_t)pr; c0 += kBatch) {
-                int m = (int)(((int64_t)pr - c0 + 1) < kBatch ? ((int64_t)pr - c0 + 1) : kBatch);
+                const int m = (int)(((int64_t)pr - c0 + 1) < kBatch ? ((int64_t)pr - c0 + 1) : kBatch);
                 for (int j = lane; j < m; j += 32) w.nbuf[j] = (uint32_t)(c0 + j);
                 __syncwarp();
                 eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
                 n_eval += m;
                 for (int j = lane; j < kBatch; j += 32) {
-                    bool keep = j < m && (st.qn < ef || cand_less(w.batch[j], st.qworst));
+                    const bool keep = j < m && (st.qn < ef || cand_less(w.batch[j], st.qworst));
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                warp_sort64(w.batch);
-                int b = 0;
-                for (int j = lane; j < kBatch; j += 32) b += w.batch[j].id != ESG_NONE;
-                for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-                st.len = warp_merge(list, st.len, w.batch, b, list2, a.C);
-                Cand *t = list; list = list2; list2 = t;
-                truncate_list(list, st, ef, pl, pr);
+                Cand *nl = admit_batch(w.batch, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                if (nl != list) { list2 = list; list = nl; }
             }
         } else {
             // Graph piece: Algorithm 1 with POST filtering to [pl, pr].
             for (int i = lane; i < a.H; i += 32) w.hash[i] = ESG_NONE;
-            if (lane == 0) *w.hcount = 0;
+            if (lane == 0) { w.hcount[0] = 0; w.hcount[1] = 0; }
             __syncwarp();
+            bool used_g = false;
             const uint32_t *adj = a.adj + (size_t)pc.depth * (size_t)a.n * a.R;
             // entry points: into P, and into Q when in range
             {
                 uint32_t e = ESG_NONE;
                 if (lane < a.E) {
-                    int32_t v = a.entries[(size_t)pc.heap * a.E + lane];
+                    const int32_t v = a.entries[(size_t)pc.heap * a.E + lane];
                     if (v >= 0 && v < a.n) e = (uint32_t)v;
                 }
-                bool nw = e != ESG_NONE && visit(w.hash, hmask, w.hcount, hlimit, e, &saturated);
-                unsigned bal = __ballot_sync(0xffffffffu, nw);
+                const bool nw = e != ESG_NONE && visit(vis, e, &saturated, &used_g);
+                const unsigned bal = __ballot_sync(0xffffffffu, nw);
                 if (nw) w.nbuf[__popc(bal & ((1u << lane) - 1))] = e;
-                int m = __popc(bal);
+                const int m = __popc(bal);
                 __syncwarp();
                 eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
                 n_eval += m;
@@ -296,18 +370,18 @@ search_kernel(SearchArgs a) {
                     else n_oor += (w.batch[j].id < pl || w.batch[j].id > pr);
                 }
                 __syncwarp();
-                warp_sort64(w.batch);
-                st.len = warp_merge(list, 0, w.batch, m, list2, a.C);
-                Cand *t = list; list = list2; list2 = t;
-                truncate_list(list, st, ef, pl, pr);
+                Cand *nl = admit_batch(w.batch, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                if (nl != list) { list2 = list; list = nl; }
             }
+            // all items before `hint` are expanded
+            int hint = st.first < 0 ? st.len : st.first;
             for (;;) {
                 // best unexpanded candidate
                 int pos = -1;
-                for (int b0 = 0; b0 < st.len; b0 += 32) {
-                    int i = b0 + lane;
-                    bool f = i < st.len && !(list[i].id & ESG_EXPANDED);
-                    unsigned bal = __ballot_sync(0xffffffffu, f);
+                for (int b0 = hint & ~31; b0 < st.len; b0 += 32) {
+                    const int i = b0 + lane;
+                    const bool f = i >= hint && i < st.len && !(list[i].id & ESG_EXPANDED);
+                    const unsigned bal = __ballot_sync(0xffffffffu, f);
                     if (bal) { pos = b0 + __ffs(bal) - 1; break; }
                 }
                 if (pos < 0) break;
@@ -317,6 +391,7 @@ search_kernel(SearchArgs a) {
                 __syncwarp();
                 if (u_in) {
                     if (lane == 0) list[pos].id = u | ESG_EXPANDED;
+                    hint = pos + 1;
                 } else {
                     // an expanded out-of-range point is neither in Q nor in P
                     const int cnt = st.len - 1 - pos;
@@ -329,71 +404,76 @@ search_kernel(SearchArgs a) {
                         __syncwarp();
                     }
                     st.len -= 1;
+                    hint = pos;
                 }
                 __syncwarp();
                 ++n_exp;
                 // neighbours of u, in chunks of 64
                 const uint32_t *row = adj + (size_t)u * a.R;
                 for (int c64 = 0; c64 < a.R; c64 += 64) {
-                uint32_t v0 = c64 + lane < a.R ? __ldg(row + c64 + lane) : ESG_NONE;
-                uint32_t v1 = c64 + lane + 32 < a.R ? __ldg(row + c64 + lane + 32) : ESG_NONE;
-                if (v0 >= (uint64_t)a.n) v0 = ESG_NONE;   // malformed imported graph: ignore
-                if (v1 >= (uint64_t)a.n) v1 = ESG_NONE;
-                bool n0 = v0 != ESG_NONE && visit(w.hash, hmask, w.hcount, hlimit, v0, &saturated);
-                bool n1 = v1 != ESG_NONE && visit(w.hash, hmask, w.hcount, hlimit, v1, &saturated);
-                unsigned b0 = __ballot_sync(0xffffffffu, n0);
-                unsigned b1 = __ballot_sync(0xffffffffu, n1);
-                int c0 = __popc(b0);
-                if (n0) w.nbuf[__popc(b0 & ((1u << lane) - 1))] = v0;
-                if (n1) w.nbuf[c0 + __popc(b1 & ((1u << lane) - 1))] = v1;
-                int m = c0 + __popc(b1);
-                __syncwarp();
-                if (m == 0) continue;  // next chunk
-                eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
-                n_eval += m;
-                // Algorithm 1's admission test, then de-duplication against
-                // the list (only needed once the visited set saturates)
-                for (int j = lane; j < kBatch; j += 32) {
-                    bool keep = false;
-                    if (j < m) {
-                        Cand x = w.batch[j];
-                        n_oor += (x.id < pl || x.id > pr);
-                        keep = st.qn < ef || cand_less(x, st.qworst);
-                        if (keep && saturated) {
-                            int p = lower_rank(list, st.len, x);
-                            if (p < st.len && cand_eq(list[p], x)) keep = false;
+                    uint32_t v0 = c64 + lane < a.R ? __ldg(row + c64 + lane) : ESG_NONE;
+                    uint32_t v1 = c64 + lane + 32 < a.R ? __ldg(row + c64 + lane + 32) : ESG_NONE;
+                    if (v0 >= (uint64_t)a.n) v0 = ESG_NONE;   // malformed imported graph: ignore
+                    if (v1 >= (uint64_t)a.n) v1 = ESG_NONE;
+                    const bool n0 = v0 != ESG_NONE && visit(vis, v0, &saturated, &used_g);
+                    const bool n1 = v1 != ESG_NONE && visit(vis, v1, &saturated, &used_g);
+                    const unsigned b0 = __ballot_sync(0xffffffffu, n0);
+                    const unsigned b1 = __ballot_sync(0xffffffffu, n1);
+                    const int c0 = __popc(b0);
+                    if (n0) w.nbuf[__popc(b0 & ((1u << lane) - 1))] = v0;
+                    if (n1) w.nbuf[c0 + __popc(b1 & ((1u << lane) - 1))] = v1;
+                    const int m = c0 + __popc(b1);
+                    __syncwarp();
+                    if (m == 0) continue;
+                    eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
+                    n_eval += m;
+                    // Algorithm 1's admission test, then de-duplication against
+                    // the list (only needed once the visited set saturates)
+                    const bool sat = __any_sync(0xffffffffu, saturated);
+                    for (int j = lane; j < kBatch; j += 32) {
+                        bool keep = false;
+                        if (j < m) {
+                            const Cand x = w.batch[j];
+                            n_oor += (x.id < pl || x.id > pr);
+                            keep = st.qn < ef || cand_less(x, st.qworst);
+                            if (keep && sat) {
+                                const int p = lower_rank(list, st.len, x);
+                                if (p < st.len && cand_eq(list[p], x)) keep = false;
+                            }
                         }
+                        if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                     }
-                    if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
-                }
-                __syncwarp();
-                warp_sort64(w.batch);
-                int b = 0;
-                for (int j = lane; j < kBatch; j += 32) b += w.batch[j].id != ESG_NONE;
-                for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-                if (b == 0) continue;  // next chunk
-                if (st.len + b > a.C) status |= ESG_Q_OVERFLOW;
-                st.len = warp_merge(list, st.len, w.batch, b, list2, a.C);
-                Cand *t = list; list = list2; list2 = t;
-                truncate_list(list, st, ef, pl, pr);
+                    __syncwarp();
+                    Cand *nl = admit_batch(w.batch, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                    if (nl != list) {
+                        list2 = list; list = nl;
+                        hint = st.first < 0 ? st.len : st.first;
+                    }
                 }  // neighbour chunk
             }
-            if (saturated) status |= ESG_Q_OVERFLOW;
+            if (__any_sync(0xffffffffu, saturated)) status |= ESG_Q_OVERFLOW;
+            if (__any_sync(0xffffffffu, used_g)) {
+                // leave the overflow table clean for the warp's next item
+                for (int i = lane; i < a.G; i += 32) vis.hg[i] = ESG_NONE;
+                __syncwarp();
+            }
         }
         // emit the first min(k, |Q|) in-range items
         {
             int written = 0;
             Cand *out = a.res + item * (int64_t)a.k_max;
             for (int b0 = 0; b0 < st.len && written < kq; b0 += 32) {
-                int i = b0 + lane;
-                uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
-                bool inr = i < st.len && id >= pl && id <= pr;
-                unsigned bal = __ballot_sync(0xffffffffu, inr);
-                int pos = written + __popc(bal & ((1u << lane) - 1));
+                const int i = b0 + lane;
+                const uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
+                const bool inr = i < st.len && id >= pl && id <= pr;
+                const unsigned bal = __ballot_sync(0xffffffffu, inr);
+                const int pos = written + __popc(bal & ((1u << lane) - 1));
                 if (inr && pos < kq) out[pos] = Cand{list[i].d, id};
                 written += __popc(bal);
             }
             written = min(written, kq);
+            n_exp = __shfl_sync(0xffffffffu, n_exp, 0);
+            for (int o = 16; o > 0; o >>= 1) n_oor += __shfl_xor_sync(0xffffffffu, n_oor, o);
             if (lane == 0) {
                 a.res_cnt[item] = written;
                 a.res_status[item] = status;
@@ -497,15 +577,60 @@ int env_int(const char *name, int dflt) {
     return v && *v ? atoi(v) : dflt;
 }
 
+// Launch shape and shared-memory plan of the beam-search kernel.
+struct SearchPlan {
+    SearchFn fn;
+    int vpl, lpr, C, H, G, wpb;
+    size_t smem;
+    int64_t grid;
+};
+
+}  // namespace
+int esg_pick_vpl(int d, int *lpr);
+namespace {
+
+esg_status make_plan(int d, int R, int efk, int64_t n_items, SearchPlan &pl) {
+    pl.vpl = esg_pick_vpl(d, &pl.lpr);
+    if (pl.vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
+    if (R > 128) { esg_set_error("R > 128"); return ESG_ERR_UNSUPPORTED; }
+    pl.fn = pick_search(pl.vpl);
+    pl.C = ((std::max(8 * efk, 256) + 31) / 32) * 32;
+    if (pl.C > 4096) pl.C = 4096;
+    // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
+    // the global overflow table takes what does not fit
+    const int per_ef = env_int("ESG_HASH_PER_EF", 64);
+    const int hmax = env_int("ESG_HASH_MAX", 8192);
+    pl.H = 2048;
+    while (pl.H < per_ef * efk && pl.H < hmax) pl.H <<= 1;
+    while (pl.H < 4 * R) pl.H <<= 1;
+    pl.G = 16384;
+    while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
+    pl.wpb = 2;
+    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 16 + kBatch * 12 + 32 * 8 + 16) * pl.wpb;
+    int dev = 0, sms = 0, per_sm = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ESG_CUDA_TRY(cudaFuncSetAttribute(pl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.fn, pl.wpb * 32, pl.smem));
+    if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
+    pl.grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + pl.wpb - 1) / pl.wpb);
+    if (pl.grid < 1) pl.grid = 1;
+    return ESG_OK;
+}
+
 }  // namespace
 
+// Lanes per row (LPR) and float4 per lane (VPL) for rows of d floats: prefer
+// 8 lanes per row (4 rows per warp instruction, short shuffle reductions);
+// wider rows use 16 or 32 lanes.
 int esg_pick_vpl(int d, int *lpr) {
-    int nvec = d / 4;
-    const int vpls[] = {1, 2, 3, 4, 6, 8};
-    for (int v : vpls) {
-        if (nvec % v) continue;
-        int L = nvec / v;
-        if (L == 1 || L == 2 || L == 4 || L == 8 || L == 16 || L == 32) { *lpr = L; return v; }
+    if (d % 4) return 0;
+    const int nvec = d / 4;
+    const int lprs[] = {8, 4, 2, 1, 16, 32};
+    for (int L : lprs) {
+        if (nvec % L) continue;
+        const int v = nvec / L;
+        if (v == 1 || v == 2 || v == 3 || v == 4 || v == 6 || v == 8) { *lpr = L; return v; }
     }
     return 0;
 }
@@ -523,32 +648,13 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     if (s.nq == 0) return ESG_OK;
     int ef = std::max(s.p.ef, 1);
     if (ef > 1024) { esg_set_error("ef > 1024"); return ESG_ERR_INVALID_ARG; }
-    int efk = std::max(ef, s.k_max);
-    int lpr = 0;
-    int vpl = esg_pick_vpl(ix->d, &lpr);
-    if (vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
-    if (ix->R > 128) { esg_set_error("R > 128"); return ESG_ERR_UNSUPPORTED; }
-    int C = ((std::max(4 * efk, efk + 64) + 31) / 32) * 32;
-    if (C > 4096) C = 4096;
-    // visited set: open addressing, power of two, sized from the beam width
-    int H = 4096;
-    const int hash_per_ef = env_int("ESG_HASH_PER_EF", 64);
-    while (H < hash_per_ef * efk && H < (1 << 22)) H <<= 1;
-    while (H < 4 * ix->R) H <<= 1;
-    const int wpb = 2;
-    const bool smem_hash = (size_t)H * 4 <= (size_t)env_int("ESG_SMEM_HASH_BYTES", 32768);
-    size_t per_warp = (smem_hash ? (size_t)H * 4 : 0) + (size_t)C * 16 + kBatch * 12 + 16;
-    size_t smem = per_warp * wpb;
-    int64_t n_items = 2 * s.nq;
-    SearchFn fn = pick_search(vpl);
-    int dev = 0, sms = 0, per_sm = 0;
-    ESG_CUDA_TRY(cudaGetDevice(&dev));
-    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ESG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem));
-    if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
-    int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + wpb - 1) / wpb);
-    if (grid < 1) grid = 1;
+    const int efk = std::max(ef, s.k_max);
+    const int64_t n_items = 2 * s.nq;
+    SearchPlan plan;
+    esg_status pst = make_plan(ix->d, ix->R, efk, n_items, plan);
+    if (pst != ESG_OK) return pst;
+    const int wpb = plan.wpb;
+    const int64_t grid = plan.grid;
 
     // scratch: pieces, k, status, per-item results, global visited sets
     size_t bytes_pieces = sizeof(esg_piece) * n_items;
@@ -557,7 +663,7 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     size_t bytes_res = sizeof(Cand) * n_items * s.k_max;
     size_t bytes_cnt = sizeof(int32_t) * n_items * 2;
     size_t bytes_stats = sizeof(int64_t) * n_items * 3;
-    size_t bytes_hash = smem_hash ? 0 : (size_t)grid * wpb * H * 4;
+    size_t bytes_hash = (size_t)grid * wpb * plan.G * 4;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = al(bytes_pieces) + al(bytes_kq) + al(bytes_qs) + al(bytes_res) + al(bytes_cnt) +
                    al(bytes_stats) + al(bytes_hash) + 256;
@@ -572,11 +678,12 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     int32_t *res_status = res_cnt + n_items;
     p += al(bytes_cnt);
     int64_t *res_stats = (int64_t *)p; p += al(bytes_stats);
-    uint32_t *ghash = smem_hash ? nullptr : (uint32_t *)p; p += al(bytes_hash);
+    uint32_t *ghash = (uint32_t *)p; p += al(bytes_hash);
     unsigned long long *queue = (unsigned long long *)p;
 
     esg_status st = ESG_OK;
     cudaError_t ce = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream);
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     if (st == ESG_OK) {
         prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(ix->n, ix->leaf_size, s.l, s.r, s.k,
@@ -589,13 +696,13 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
         a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
         a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
         a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
-        a.d = ix->d; a.nvec = ix->d / 4; a.LPR = lpr; a.R = ix->R; a.E = ix->E;
-        a.metric = ix->metric; a.ef = ef;
+        a.d = ix->d; a.nvec = ix->d / 4; a.R = ix->R; a.E = ix->E;
+        a.metric = ix->metric; a.ef = ef; a.LPR = plan.lpr;
         a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * ef + 256;
-        a.k_max = s.k_max; a.H = H; a.C = C; a.ghash = ghash; a.queue = queue;
+        a.k_max = s.k_max; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
         const int pidx = esg_prof_begin(stream);
-        fn<<<(unsigned)grid, wpb * 32, smem, stream>>>(a);
+        plan.fn<<<(unsigned)grid, wpb * 32, plan.smem, stream>>>(a);
         ce = cudaGetLastError();
         esg_prof_end(pidx, stream);
         if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
@@ -622,44 +729,26 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
                                 int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
-    int lpr = 0;
-    int vpl = esg_pick_vpl(d, &lpr);
-    if (vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
-    const int efk = std::max(ef, k);
-    int C = ((std::max(2 * efk, efk + 64) + 31) / 32) * 32;
-    int H = 1024;
-    const int hash_per_ef = env_int("ESG_BUILD_HASH_PER_EF", 48);
-    while (H < hash_per_ef * efk && H < (1 << 22)) H <<= 1;
-    while (H < 4 * R) H <<= 1;
-    const int wpb = 2;
-    const bool smem_hash = (size_t)H * 4 <= (size_t)env_int("ESG_SMEM_HASH_BYTES", 65536);
-    size_t per_warp = (smem_hash ? (size_t)H * 4 : 0) + (size_t)C * 16 + kBatch * 12 + 16;
-    size_t smem = per_warp * wpb;
-    SearchFn fn = pick_search(vpl);
-    int dev = 0, sms = 0, per_sm = 0;
-    ESG_CUDA_TRY(cudaGetDevice(&dev));
-    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ESG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem));
-    if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
-    int64_t grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + wpb - 1) / wpb);
-    if (grid < 1) grid = 1;
-    size_t bytes_hash = smem_hash ? 0 : (size_t)grid * wpb * H * 4;
+    SearchPlan plan;
+    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, plan);
+    if (pst != ESG_OK) return pst;
+    const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
     unsigned char *scratch = nullptr;
     ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes_hash + 256, stream));
     unsigned long long *queue = (unsigned long long *)scratch;
-    uint32_t *ghash = smem_hash ? nullptr : (uint32_t *)(scratch + 256);
+    uint32_t *ghash = (uint32_t *)(scratch + 256);
     esg_status st = ESG_OK;
     cudaError_t ce = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream);
     if (ce == cudaSuccess) {
         SearchArgs a;
         a.X = X; a.adj = adj; a.entries = entries; a.queries = X; a.qidx = qidx;
         a.pieces = pieces; a.kq = nullptr; a.kconst = k; a.qshift = 0;
-        a.n = n; a.n_items = n_items; a.d = d; a.nvec = d / 4; a.LPR = lpr; a.R = R; a.E = E;
+        a.n = n; a.n_items = n_items; a.d = d; a.nvec = d / 4; a.LPR = plan.lpr; a.R = R; a.E = E;
         a.metric = metric; a.ef = ef; a.max_exp = max_exp > 0 ? max_exp : 16 * ef + 256;
-        a.k_max = k; a.H = H; a.C = C; a.ghash = ghash; a.queue = queue;
+        a.k_max = k; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
-        fn<<<(unsigned)grid, wpb * 32, smem, stream>>>(a);
+        plan.fn<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
