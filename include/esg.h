@@ -117,13 +117,18 @@ typedef struct {
  *  rerank          with BF16/FP8 storage: recompute FP32 distances of the
  *                  final candidates and re-sort (1) or not (0);
  *  use_learned     1 = per-query beam width from the trained predictor
- *                  (falls back to ef when no predictor is trained).
+ *                  (falls back to ef when no predictor is trained);
+ *  traversal       row type used for traversal distances: ESG_F32, or
+ *                  ESG_BF16 / ESG_FP8E4M3 when the index was built with that
+ *                  storage (FP32 accumulation in every case).
  */
 typedef struct {
     int32_t ef;
     int32_t max_expansions;
     int32_t rerank;
     int32_t use_learned;
+    esg_dtype traversal;
+    int32_t reserved;
 } esg_search_params;
 
 esg_build_params esg_build_params_default(void);
@@ -173,6 +178,23 @@ esg_status esg_index_info(const esg_index *index, int64_t *n, int32_t *d, int32_
 esg_status esg_index_export(const esg_index *index, uint32_t *adj, int32_t *entries,
                             int64_t *perm);
 
+/*
+ * Copy the index's low-precision traversal rows of type `dtype` to host
+ * buffers (rank order): ESG_BF16: rows = [n, d] uint16 bit patterns;
+ * ESG_FP8E4M3: rows = [n, d] uint8 E4M3 codes and scale = [n] float32 per-row
+ * scales (x ~= scale * code). ESG_ERR_INVALID_ARG when the index holds no such
+ * copy. Synchronous.
+ */
+esg_status esg_index_export_storage(const esg_index *index, esg_dtype dtype, void *rows,
+                                    float *scale);
+
+/*
+ * Add a low-precision copy of the rows (ESG_BF16 or ESG_FP8E4M3) to an index
+ * so that searches can traverse with it; a copy that exists is kept.
+ * Synchronous.
+ */
+esg_status esg_index_add_storage(esg_index *index, esg_dtype dtype);
+
 void esg_free(esg_index *index);
 
 /*
@@ -200,8 +222,9 @@ esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, c
  *  out_count   device [nq] int32: results written, min(k, r - l + 1) when the
  *              graphs reach enough in-range points;
  *  out_status  device [nq] int32 (ESG_Q_* bits) or NULL;
- *  out_stats   device [nq, 4] int64 (expansions, distance evaluations,
- *              out-of-range evaluations, pieces) or NULL.
+ *  out_stats   device [nq, 5] int64 (expansions, distance evaluations on
+ *              traversal rows, out-of-range evaluations, FP32 re-rank rows,
+ *              pieces) or NULL.
  * Asynchronous on `stream`; temporary device memory is taken from and
  * returned to the stream-ordered allocator of that stream.
  */

@@ -32,7 +32,8 @@ METRICS = {"l2": 0, "ip": 1}
 __all__ = [
     "build_c", "rerank", "is_leaf", "split", "Piece", "decompose", "graph_depths",
     "bruteforce", "merge_topk", "OracleIndex", "build_index", "graph_search",
-    "search", "recall_at_k", "distances", "METRICS", "NONE",
+    "search", "recall_at_k", "distances", "METRICS", "NONE", "bf16_round", "bf16_to_float",
+    "fp8_e4m3_grid", "fp8_quantize_rows", "fp8_to_float", "traversal_rows",
 ]
 
 
@@ -204,6 +205,82 @@ def merge_topk(parts: Sequence[Tuple[np.ndarray, np.ndarray]], k: int
     return ids[order], dd[order]
 
 
+# ------------------------------------------------- low-precision storage
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns of float32 values, rounding to nearest, ties to
+    even (the upper 16 bits of the float32 pattern after adding 0x7FFF plus
+    the lowest kept bit). NaN stays NaN."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    nan = np.isnan(np.asarray(x, dtype=np.float32))
+    return np.where(nan, np.uint16(0x7FC0), rounded)
+
+
+def bf16_to_float(b: np.ndarray) -> np.ndarray:
+    return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32)
+
+
+def fp8_e4m3_grid() -> np.ndarray:
+    """The 127 non-negative finite FP8-E4M3 values in code order 0..126:
+    code = (e << 3) | m, value = m/8 * 2^-6 for e = 0 (subnormal), else
+    (1 + m/8) * 2^(e - 7); code 127 (e = 15, m = 7) is NaN, so 448 is the
+    largest finite value."""
+    vals = []
+    for code in range(127):
+        e, m = code >> 3, code & 7
+        vals.append((m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(vals, dtype=np.float64)
+
+
+_FP8_GRID = fp8_e4m3_grid()
+
+
+def _fp8_code(v: np.ndarray) -> np.ndarray:
+    """Saturating round-to-nearest-even of float32 values to E4M3 codes."""
+    v = np.asarray(v, dtype=np.float32).astype(np.float64)
+    a = np.minimum(np.abs(v), 448.0)
+    hi = np.clip(np.searchsorted(_FP8_GRID, a, side="left"), 0, 126)
+    lo = np.clip(hi - 1, 0, 126)
+    dlo = a - _FP8_GRID[lo]
+    dhi = _FP8_GRID[hi] - a
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (hi % 2 == 0))
+    code = np.where(pick_hi, hi, lo).astype(np.uint8)
+    code = np.where(a == _FP8_GRID[hi], hi, code).astype(np.uint8)
+    return np.where(np.signbit(v), code | 0x80, code).astype(np.uint8)
+
+
+def fp8_quantize_rows(X: np.ndarray):
+    """Per-row FP8-E4M3 storage: s_i = max_j |x_ij| / 448 and
+    code_ij = satfinite RNE(x_ij / s_i), both divisions in float32 (code 0
+    for an all-zero row). Returns (codes uint8 [n, d], scales float32 [n])."""
+    X = np.asarray(X, dtype=np.float32)
+    m = np.abs(X).max(axis=1)
+    s = (m / np.float32(448.0)).astype(np.float32)
+    safe = np.where(s > 0, s, np.float32(1.0)).astype(np.float32)
+    v = (X / safe[:, None]).astype(np.float32)
+    v = np.where(s[:, None] > 0, v, np.float32(0.0))
+    return _fp8_code(v), s
+
+
+def fp8_to_float(codes: np.ndarray) -> np.ndarray:
+    codes = np.asarray(codes, dtype=np.uint8)
+    mag = _FP8_GRID[np.minimum(codes & 0x7F, 126)]
+    return np.where(codes & 0x80, -mag, mag)
+
+
+def traversal_rows(X32: np.ndarray, dtype: str) -> np.ndarray:
+    """Float64 values the traversal distances use for rows stored in `dtype`
+    ("f32", "bf16" or "fp8")."""
+    X32 = np.asarray(X32, dtype=np.float32)
+    if dtype == "f32":
+        return X32.astype(np.float64)
+    if dtype == "bf16":
+        return bf16_to_float(bf16_round(X32)).astype(np.float64)
+    codes, s = fp8_quantize_rows(X32)
+    return fp8_to_float(codes) * s.astype(np.float64)[:, None]
+
+
 # ------------------------------------------------------------ index build
 
 @dataclasses.dataclass
@@ -258,12 +335,13 @@ def build_index(base: np.ndarray, attr: Optional[np.ndarray], metric: str, leaf_
 # -------------------------------------------------------------- search
 
 def graph_search(index: OracleIndex, depth: int, heap: int, q: np.ndarray, ef: int,
-                 pl: int, pr: int, counters: Optional[np.ndarray] = None
-                 ) -> Tuple[np.ndarray, np.ndarray]:
+                 pl: int, pr: int, counters: Optional[np.ndarray] = None,
+                 X: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
     """Algorithm 1 with POST filtering to [pl, pr] on the graph of heap node
-    `heap` (at `depth`), from that node's entry points. Returns up to ef
-    (ranks, distances) ascending."""
-    X = index.X
+    `heap` (at `depth`), from that node's entry points, over the rows X
+    (default: the index's float64 rows). Returns up to ef (ranks, distances)
+    ascending."""
+    X = index.X if X is None else np.ascontiguousarray(X, dtype=np.float64)
     q64 = np.ascontiguousarray(q, dtype=np.float64)
     ent = np.ascontiguousarray(index.entries[heap].astype(np.uint32))
     ent_n = int(np.sum(index.entries[heap] >= 0))
@@ -278,17 +356,33 @@ def graph_search(index: OracleIndex, depth: int, heap: int, q: np.ndarray, ef: i
 
 
 def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
-           counters: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+           counters: Optional[np.ndarray] = None, trav_X: Optional[np.ndarray] = None
+           ) -> Tuple[np.ndarray, np.ndarray]:
     """Query-2D-Index (Algorithm 4): decompose [lq, rq]; answer scan pieces
     exactly and graph pieces with Algorithm 1 + POST at beam width
-    max(ef, k); merge into the top k by (distance, rank). Returns ranks."""
+    max(ef, k); merge into the top k by (distance, rank). Returns ranks.
+
+    With `trav_X` (rows as stored in low precision, see traversal_rows) the
+    traversal and scans use those rows, each piece keeps its best max(ef, k)
+    in-range candidates, and these are re-ranked with the exact rows before
+    the merge."""
     parts = []
+    w = max(ef, k)
     for p in decompose(index.n, index.leaf_size, lq, rq):
+        if trav_X is None:
+            if p.kind == "scan":
+                parts.append(bruteforce(index.X, q, p.pl, p.pr, k, index.metric))
+            else:
+                ids, dd = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters)
+                parts.append((ids[:k], dd[:k]))
+            continue
         if p.kind == "scan":
-            parts.append(bruteforce(index.X, q, p.pl, p.pr, k, index.metric))
+            ids, _ = bruteforce(trav_X, q, p.pl, p.pr, w, index.metric)
         else:
-            ids, dd = graph_search(index, p.depth, p.heap, q, max(ef, k), p.pl, p.pr, counters)
-            parts.append((ids[:k], dd[:k]))
+            ids, _ = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters, X=trav_X)
+        exact = distances(index.X[ids], q, index.metric)
+        order = np.lexsort((ids, exact))[:k]
+        parts.append((ids[order], exact[order]))
     return merge_topk(parts, k)
 
 

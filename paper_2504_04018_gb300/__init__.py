@@ -33,6 +33,7 @@ EXPORTED = [
     "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
     "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
+    "esg_index_export_storage", "esg_index_add_storage",
 ]
 
 
@@ -49,7 +50,8 @@ class _BuildParams(ctypes.Structure):
 
 class _SearchParams(ctypes.Structure):
     _fields_ = [("ef", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
-                ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32)]
+                ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32),
+                ("traversal", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -76,6 +78,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                      ctypes.POINTER(_P)]
     lib.esg_index_info.argtypes = [_P] + [_P] * 8
     lib.esg_index_export.argtypes = [_P, _P, _P, _P]
+    lib.esg_index_export_storage.argtypes = [_P, _I32, _P, _P]
+    lib.esg_index_add_storage.argtypes = [_P, _I32]
     lib.esg_free.argtypes = [_P]
     lib.esg_free.restype = None
     lib.esg_decompose_batch.argtypes = [_I64, _I32, _P, _P, _I64, _P, _P, _P]
@@ -94,7 +98,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
-                 "esg_profile_read"]:
+                 "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -206,6 +210,27 @@ def esg_index_export(index: Index) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     return adj, ent, perm
 
 
+def esg_index_export_storage(index: Index, dtype: str):
+    """Low-precision traversal rows in rank order: (uint16 [n, d] BF16 bits,
+    None) or (uint8 [n, d] E4M3 codes, float32 [n] scales)."""
+    lib = load_library()
+    if dtype == "bf16":
+        rows = np.empty((index.n, index.d), dtype=np.uint16)
+        _check(lib.esg_index_export_storage(index.handle, STORAGE[dtype], _np_ptr(rows), None),
+               "esg_index_export_storage")
+        return rows, None
+    rows = np.empty((index.n, index.d), dtype=np.uint8)
+    scale = np.empty(index.n, dtype=np.float32)
+    _check(lib.esg_index_export_storage(index.handle, STORAGE[dtype], _np_ptr(rows), _np_ptr(scale)),
+           "esg_index_export_storage")
+    return rows, scale
+
+
+def esg_index_add_storage(index: Index, dtype: str):
+    """Add a BF16 or FP8 copy of the rows for low-precision traversal."""
+    _check(load_library().esg_index_add_storage(index.handle, STORAGE[dtype]), "esg_index_add_storage")
+
+
 def esg_free(index: Index):
     index.close()
 
@@ -232,10 +257,11 @@ def unpack_pieces(pieces):
 
 def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,
                      max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
-                     out=None, want_status: bool = True, want_stats: bool = False, stream=None):
+                     traversal: str = "f32", out=None, want_status: bool = True,
+                     want_stats: bool = False, stream=None):
     """Range-filtered search of CUDA float32 queries [nq, d] with CUDA int64
     ranges [nq]. Returns (ids int64 [nq,k_max], dist f32, count int32,
-    status int32 or None, stats int64 [nq,4] or None)."""
+    status int32 or None, stats int64 [nq,5] or None)."""
     import torch
     lib = load_library()
     nq = queries.shape[0]
@@ -245,10 +271,10 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
         dist = torch.empty((nq, k_max), dtype=torch.float32, device=dev)
         count = torch.empty(nq, dtype=torch.int32, device=dev)
         status = torch.empty(nq, dtype=torch.int32, device=dev) if want_status else None
-        stats = torch.empty((nq, 4), dtype=torch.int64, device=dev) if want_stats else None
+        stats = torch.empty((nq, 5), dtype=torch.int64, device=dev) if want_stats else None
     else:
         ids, dist, count, status, stats = out
-    p = _SearchParams(ef, max_expansions, rerank, use_learned)
+    p = _SearchParams(ef, max_expansions, rerank, use_learned, STORAGE[traversal], 0)
     _check(lib.esg_search_batch(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
                                 _dev_ptr(k), k_max, ctypes.byref(p), _dev_ptr(ids), _dev_ptr(dist),
                                 _dev_ptr(count), _dev_ptr(status), _dev_ptr(stats),

@@ -103,6 +103,8 @@ esg_search_params esg_search_params_default(void) {
     p.max_expansions = 0;
     p.rerank = 1;
     p.use_learned = 0;
+    p.traversal = ESG_F32;
+    p.reserved = 0;
     return p;
 }
 
@@ -231,6 +233,34 @@ esg_status esg_index_export(const esg_index *ix, uint32_t *adj, int32_t *entries
     if (entries && ix->n_heap > 0) ESG_CUDA_TRY(cudaMemcpy(entries, ix->entries, sizeof(int32_t) * ix->n_heap * ix->E, cudaMemcpyDeviceToHost));
     if (perm) std::memcpy(perm, ix->perm_host.data(), sizeof(int64_t) * ix->n);
     return ESG_OK;
+}
+
+esg_status esg_index_export_storage(const esg_index *ix, esg_dtype dtype, void *rows, float *scale) {
+    if (!ix || !rows) { esg_set_error("esg_index_export_storage: bad argument"); return ESG_ERR_INVALID_ARG; }
+    const size_t count = (size_t)ix->n * ix->d;
+    if (dtype == ESG_BF16 && ix->Xb) {
+        ESG_CUDA_TRY(cudaMemcpy(rows, ix->Xb, 2 * count, cudaMemcpyDeviceToHost));
+    } else if (dtype == ESG_FP8E4M3 && ix->X8) {
+        ESG_CUDA_TRY(cudaMemcpy(rows, ix->X8, count, cudaMemcpyDeviceToHost));
+        if (scale) ESG_CUDA_TRY(cudaMemcpy(scale, ix->scale8, sizeof(float) * ix->n, cudaMemcpyDeviceToHost));
+    } else {
+        esg_set_error("esg_index_export_storage: index holds no rows of that type");
+        return ESG_ERR_INVALID_ARG;
+    }
+    return ESG_OK;
+}
+
+esg_status esg_index_add_storage(esg_index *ix, esg_dtype dtype) {
+    if (!ix || (dtype != ESG_BF16 && dtype != ESG_FP8E4M3)) {
+        esg_set_error("esg_index_add_storage: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if ((dtype == ESG_BF16 && ix->Xb) || (dtype == ESG_FP8E4M3 && ix->X8)) return ESG_OK;
+    const int32_t keep = ix->storage;
+    ix->storage = dtype;
+    esg_status s = esg_make_storage(ix, nullptr);
+    ix->storage = keep == ESG_F32 ? dtype : keep;
+    return s;
 }
 
 void esg_free(esg_index *ix) {

@@ -89,57 +89,136 @@ __device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *satur
     return true;
 }
 
-// Distances from the query (held in registers as VPL float4 per lane, LPR
-// lanes per row) to the rows listed in nbuf[0..m); written to batch[0..m).
-template <int VPL>
-__device__ __forceinline__ void eval_rows(const float4 *__restrict__ X4, int nvec, int LPR,
-                                          const float4 (&qv)[VPL], const uint32_t *nbuf, int m,
-                                          Cand *batch, int metric) {
+// Storage types of the traversal rows (esg_dtype): elements per 16-byte vector.
+template <int ST> struct Store;
+template <> struct Store<ESG_F32> { static constexpr int EPV = 4; };
+template <> struct Store<ESG_BF16> { static constexpr int EPV = 8; };
+template <> struct Store<ESG_FP8E4M3> { static constexpr int EPV = 16; };
+
+// Accumulate the distance terms of one 16-byte vector of a row against the
+// query slice qs[0..EPV) (FP32 accumulation; FP8 codes times the row scale).
+template <int ST>
+__device__ __forceinline__ float accum_vec(const uint4 &raw, const float *qs, float scale, int metric,
+                                           float acc) {
+    float x[Store<ST>::EPV];
+    if (ST == ESG_F32) {
+        x[0] = __uint_as_float(raw.x); x[1] = __uint_as_float(raw.y);
+        x[2] = __uint_as_float(raw.z); x[3] = __uint_as_float(raw.w);
+    } else if (ST == ESG_BF16) {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            x[2 * t] = __uint_as_float(w4[t] << 16);
+            x[2 * t + 1] = __uint_as_float(w4[t] & 0xFFFF0000u);
+        }
+    } else {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w4[t] >> (16 * h)) & 0xFFFFu);
+                __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&hr));
+                x[4 * t + 2 * h] = f.x * scale;
+                x[4 * t + 2 * h + 1] = f.y * scale;
+            }
+        }
+    }
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+#pragma unroll
+    for (int e = 0; e < Store<ST>::EPV; e += 4) {
+        const float4 q = q4[e / 4];
+        if (metric == ESG_L2SQ) {
+            float a = q.x - x[e], b = q.y - x[e + 1], c = q.z - x[e + 2], d = q.w - x[e + 3];
+            acc = fmaf(a, a, acc); acc = fmaf(b, b, acc); acc = fmaf(c, c, acc); acc = fmaf(d, d, acc);
+        } else {
+            acc = fmaf(q.x, x[e], acc); acc = fmaf(q.y, x[e + 1], acc);
+            acc = fmaf(q.z, x[e + 2], acc); acc = fmaf(q.w, x[e + 3], acc);
+        }
+    }
+    return acc;
+}
+
+// Distances from the query (FP32, staged in shared memory `qs`) to the rows
+// listed in nbuf[0..m), written to batch[0..m). Rows are nvec 16-byte
+// vectors; LPR lanes share a row, each loading VPL vectors, and the loads of
+// U passes are all issued before any reduction.
+template <int ST, int VPL>
+__device__ __forceinline__ void eval_rows(const uint4 *__restrict__ Xv, const float *__restrict__ scale8,
+                                          int nvec, int LPR, const float *qs, const uint32_t *nbuf,
+                                          int m, Cand *batch, int metric) {
+    constexpr int EPV = Store<ST>::EPV;
     const int lane = threadIdx.x & 31;
     const int s = lane & (LPR - 1);
     const int g = lane / LPR;
     const int rows_per_pass = 32 / LPR;
-    // all loads of U passes are issued before any reduction: U * VPL float4
-    // (at most 16, 64 registers) per lane in flight
-    constexpr int U = (VPL <= 2) ? 8 : (VPL <= 4 ? 4 : 2);
+    // vectors in flight per lane scaled so that at most ~16 FP32-equivalent
+    // vectors are decoded per pass
+    constexpr int W = ST == ESG_F32 ? 1 : (ST == ESG_BF16 ? 2 : 4);
+    constexpr int U0 = 16 / (VPL * W);
+    constexpr int U = U0 < 1 ? 1 : (U0 > 8 ? 8 : U0);
     for (int base = 0; base < m; base += rows_per_pass * U) {
-        float4 xv[U][VPL];
+        uint4 xv[U][VPL];
         uint32_t id[U];
+        float sc[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            int row = base + u * rows_per_pass + g;
+            const int row = base + u * rows_per_pass + g;
             id[u] = row < m ? nbuf[row] : ESG_NONE;
+            sc[u] = 1.f;
             if (id[u] != ESG_NONE) {
-                const float4 *p = X4 + (size_t)id[u] * nvec + s;
+                const uint4 *p = Xv + (size_t)id[u] * nvec + s;
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) xv[u][v] = __ldg(p + v * LPR);
+                if (ST == ESG_FP8E4M3) sc[u] = __ldg(scale8 + id[u]);
             } else {
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) xv[u][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int v = 0; v < VPL; ++v) xv[u][v] = make_uint4(0, 0, 0, 0);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             float acc = 0.f;
-            if (metric == ESG_L2SQ) {
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    float a = qv[v].x - xv[u][v].x, b = qv[v].y - xv[u][v].y;
-                    float c = qv[v].z - xv[u][v].z, e = qv[v].w - xv[u][v].w;
-                    acc = fmaf(a, a, acc); acc = fmaf(b, b, acc);
-                    acc = fmaf(c, c, acc); acc = fmaf(e, e, acc);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    acc = fmaf(qv[v].x, xv[u][v].x, acc); acc = fmaf(qv[v].y, xv[u][v].y, acc);
-                    acc = fmaf(qv[v].z, xv[u][v].z, acc); acc = fmaf(qv[v].w, xv[u][v].w, acc);
-                }
-            }
+            for (int v = 0; v < VPL; ++v)
+                acc = accum_vec<ST>(xv[u][v], qs + (s + v * LPR) * EPV, sc[u], metric, acc);
             acc = warp_sum_group(acc, LPR);
-            int row = base + u * rows_per_pass + g;
+            const int row = base + u * rows_per_pass + g;
             if (s == 0 && row < m) batch[row] = Cand{metric == ESG_L2SQ ? acc : -acc, id[u]};
         }
+    }
+    __syncwarp();
+}
+
+// Exact FP32 distances of the rows in nbuf[0..m) (re-rank of candidates
+// found with low-precision rows): 8 lanes per row.
+__device__ __forceinline__ void eval_rows_fp32(const float *__restrict__ X, int d, const float *qs,
+                                               const uint32_t *nbuf, int m, Cand *out, int metric) {
+    const int lane = threadIdx.x & 31;
+    const int s = lane & 7, g = lane >> 3;
+    const int nv = d / 4;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    for (int base = 0; base < m; base += 4) {
+        const int row = base + g;
+        const uint32_t id = row < m ? nbuf[row] : ESG_NONE;
+        float acc = 0.f;
+        if (id != ESG_NONE) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(X + (size_t)id * d);
+#pragma unroll 4
+            for (int v = s; v < nv; v += 8) {
+                const float4 x = __ldg(x4 + v), q = q4[v];
+                if (metric == ESG_L2SQ) {
+                    float a = q.x - x.x, b = q.y - x.y, c = q.z - x.z, e = q.w - x.w;
+                    acc = fmaf(a, a, acc); acc = fmaf(b, b, acc); acc = fmaf(c, c, acc); acc = fmaf(e, e, acc);
+                } else {
+                    acc = fmaf(q.x, x.x, acc); acc = fmaf(q.y, x.y, acc);
+                    acc = fmaf(q.z, x.z, acc); acc = fmaf(q.w, x.w, acc);
+                }
+            }
+        }
+        acc = warp_sum_group(acc, 8);
+        if (s == 0 && row < m) out[row] = Cand{metric == ESG_L2SQ ? acc : -acc, id};
     }
     __syncwarp();
 }
@@ -242,7 +321,10 @@ __device__ __forceinline__ Cand *admit_batch(Cand *batch, Cand *cbuf, Cand *list
 }
 
 struct SearchArgs {
-    const float *X;
+    const float *X;        // FP32 rows (re-rank, and traversal when st == F32)
+    const uint4 *Xv;       // traversal rows (FP32, BF16 or FP8) as 16-byte vectors
+    const float *scale8;   // FP8 per-row scales
+    int rerank;
     const uint32_t *adj;
     const int32_t *entries;
     const float *queries;
@@ -262,18 +344,19 @@ struct SearchArgs {
     Cand *res;             // [n_items, k_max]
     int32_t *res_cnt;      // [n_items]
     int32_t *res_status;   // [n_items]
-    int64_t *res_stats;    // [n_items, 3]
+    int64_t *res_stats;    // [n_items, 4]
 };
 
-template <int VPL>
+template <int ST, int VPL>
 __global__ void __launch_bounds__(64, 8)
 search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    const size_t qbytes = ((size_t)a.d * 4 + 15) & ~(size_t)15;
     const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 * 2 + kBatch * 8 + 32 * 8 +
-                            kBatch * 4 + 16;
+                            kBatch * 4 + 16 + qbytes;
     unsigned char *base = smem_raw + per_warp * wib;
     WarpSmem w;
     size_t off = 0;
@@ -283,6 +366,7 @@ search_kernel(SearchArgs a) {
     Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
     w.nbuf = (uint32_t *)(base + off); off += kBatch * 4;
     w.hcount = (int *)(base + off); off += 16;
+    float *qs = (float *)(base + off); off += qbytes;
     const int gwarp = blockIdx.x * wpb + wib;
     w.hash = (uint32_t *)(base + off);
     Visited vis;
@@ -294,7 +378,6 @@ search_kernel(SearchArgs a) {
     vis.gmask = (uint32_t)a.G - 1;
     vis.gcount = w.hcount + 1;
     vis.glimit = (a.G * 3) / 4;
-    const float4 *X4 = reinterpret_cast<const float4 *>(a.X);
 
     for (;;) {
         int64_t item = 0;
@@ -304,25 +387,25 @@ search_kernel(SearchArgs a) {
         const int64_t qi = item >> a.qshift;
         const esg_piece pc = a.pieces[item];
         const int kq = a.kq ? a.kq[qi] : a.kconst;
-        int64_t n_exp = 0, n_eval = 0, n_oor = 0;
+        int64_t n_exp = 0, n_eval = 0, n_oor = 0, n_rr = 0;
         int status = 0;
         if (pc.kind == ESG_PIECE_NONE || kq <= 0) {
             if (lane == 0) { a.res_cnt[item] = 0; a.res_status[item] = 0; }
-            if (lane < 3) a.res_stats[item * 3 + lane] = 0;
+            if (lane < 4) a.res_stats[item * 4 + lane] = 0;
             continue;
         }
         const uint32_t pl = (uint32_t)pc.pl, pr = (uint32_t)pc.pr;
         const bool is_graph = pc.kind == ESG_PIECE_GRAPH;
-        const int ef = is_graph ? max(a.ef, kq) : kq;
+        // low-precision scans keep ef candidates for the FP32 re-rank
+        const bool do_rerank = ST != ESG_F32 && a.rerank;
+        const int ef = (is_graph || do_rerank) ? max(a.ef, kq) : kq;
 
-        // query slice in registers
-        float4 qv[VPL];
+        // query in shared memory (FP32)
         {
             const int64_t qrow = a.qidx ? a.qidx[item] : qi;
             const float4 *q4 = reinterpret_cast<const float4 *>(a.queries + qrow * (int64_t)a.d);
-            const int s = lane & (a.LPR - 1);
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) qv[v] = __ldg(q4 + s + v * a.LPR);
+            for (int v = lane; v < a.d / 4; v += 32) reinterpret_cast<float4 *>(qs)[v] = __ldg(q4 + v);
+            __syncwarp();
         }
         ListState st{0, 0, Cand{INFINITY, ESG_NONE}, -1};
         Cand *list = w.list, *list2 = w.list2;
@@ -334,7 +417,7 @@ search_kernel(SearchArgs a) {
                 const int m = (int)(((int64_t)pr - c0 + 1) < kBatch ? ((int64_t)pr - c0 + 1) : kBatch);
                 for (int j = lane; j < m; j += 32) w.nbuf[j] = (uint32_t)(c0 + j);
                 __syncwarp();
-                eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
                 n_eval += m;
                 for (int j = lane; j < kBatch; j += 32) {
                     const bool keep = j < m && (st.qn < ef || cand_less(w.batch[j], st.qworst));
@@ -363,7 +446,7 @@ search_kernel(SearchArgs a) {
                 if (nw) w.nbuf[__popc(bal & ((1u << lane) - 1))] = e;
                 const int m = __popc(bal);
                 __syncwarp();
-                eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
                 n_eval += m;
                 for (int j = lane; j < kBatch; j += 32) {
                     if (j >= m) w.batch[j] = Cand{INFINITY, ESG_NONE};
@@ -425,7 +508,7 @@ search_kernel(SearchArgs a) {
                     const int m = c0 + __popc(b1);
                     __syncwarp();
                     if (m == 0) continue;
-                    eval_rows<VPL>(X4, a.nvec, a.LPR, qv, w.nbuf, m, w.batch, a.metric);
+                    eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
                     n_eval += m;
                     // Algorithm 1's admission test, then de-duplication against
                     // the list (only needed once the visited set saturates)
@@ -458,6 +541,35 @@ search_kernel(SearchArgs a) {
                 __syncwarp();
             }
         }
+        // FP32 re-rank of the final in-range candidates found on low-precision rows
+        if (do_rerank && st.len > 0) {
+            int cnt = 0;
+            for (int b0 = 0; b0 < st.len; b0 += 32) {
+                const int i = b0 + lane;
+                const uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
+                const bool inr = i < st.len && id >= pl && id <= pr;
+                const unsigned bal = __ballot_sync(0xffffffffu, inr);
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1));
+                if (inr && pos < ef) list2[pos] = Cand{0.f, id};
+                cnt += __popc(bal);
+                if (cnt >= ef) break;
+            }
+            cnt = min(cnt, ef);
+            __syncwarp();
+            for (int c0 = 0; c0 < cnt; c0 += kBatch) {
+                const int m = min(kBatch, cnt - c0);
+                for (int j = lane; j < m; j += 32) w.nbuf[j] = list2[c0 + j].id;
+                __syncwarp();
+                eval_rows_fp32(a.X, a.d, qs, w.nbuf, m, list2 + c0, a.metric);
+            }
+            n_rr += cnt;
+            const int P = next_pow2_int(max(cnt, 2));
+            for (int j = cnt + lane; j < P; j += 32) list2[j] = Cand{INFINITY, ESG_NONE};
+            __syncwarp();
+            warp_sort_pow2(list2, P);
+            Cand *t = list; list = list2; list2 = t;
+            st.len = cnt;
+        }
         // emit the first min(k, |Q|) in-range items
         {
             int written = 0;
@@ -477,9 +589,10 @@ search_kernel(SearchArgs a) {
             if (lane == 0) {
                 a.res_cnt[item] = written;
                 a.res_status[item] = status;
-                a.res_stats[item * 3 + 0] = n_exp;
-                a.res_stats[item * 3 + 1] = n_eval;
-                a.res_stats[item * 3 + 2] = n_oor;
+                a.res_stats[item * 4 + 0] = n_exp;
+                a.res_stats[item * 4 + 1] = n_eval;
+                a.res_stats[item * 4 + 2] = n_oor;
+                a.res_stats[item * 4 + 3] = n_rr;
             }
         }
         __syncwarp();
@@ -541,9 +654,9 @@ __global__ void merge_kernel(int64_t nq, int32_t k_max, const int32_t *kq, const
     }
     if (out_stats) {
         int64_t np = (pieces[2 * i].kind != ESG_PIECE_NONE) + (pieces[2 * i + 1].kind != ESG_PIECE_NONE);
-        for (int c = 0; c < 3; ++c)
-            out_stats[i * 4 + c] = k > 0 ? res_stats[2 * i * 3 + c] + res_stats[(2 * i + 1) * 3 + c] : 0;
-        out_stats[i * 4 + 3] = np;
+        for (int c = 0; c < 4; ++c)
+            out_stats[i * 5 + c] = k > 0 ? res_stats[2 * i * 4 + c] + res_stats[(2 * i + 1) * 4 + c] : 0;
+        out_stats[i * 5 + 4] = np;
     }
 }
 
@@ -560,16 +673,32 @@ __global__ void decompose_kernel(int64_t n, int32_t leaf, const int64_t *l, cons
 
 typedef void (*SearchFn)(SearchArgs);
 
-SearchFn pick_search(int vpl) {
-    switch (vpl) {
-        case 1: return search_kernel<1>;
-        case 2: return search_kernel<2>;
-        case 3: return search_kernel<3>;
-        case 4: return search_kernel<4>;
-        case 6: return search_kernel<6>;
-        case 8: return search_kernel<8>;
-        default: return nullptr;
+SearchFn pick_search(int st, int vpl) {
+    if (st == ESG_F32) {
+        switch (vpl) {
+            case 1: return search_kernel<ESG_F32, 1>;
+            case 2: return search_kernel<ESG_F32, 2>;
+            case 3: return search_kernel<ESG_F32, 3>;
+            case 4: return search_kernel<ESG_F32, 4>;
+            case 6: return search_kernel<ESG_F32, 6>;
+            case 8: return search_kernel<ESG_F32, 8>;
+        }
+    } else if (st == ESG_BF16) {
+        switch (vpl) {
+            case 1: return search_kernel<ESG_BF16, 1>;
+            case 2: return search_kernel<ESG_BF16, 2>;
+            case 3: return search_kernel<ESG_BF16, 3>;
+            case 4: return search_kernel<ESG_BF16, 4>;
+            case 6: return search_kernel<ESG_BF16, 6>;
+        }
+    } else if (st == ESG_FP8E4M3) {
+        switch (vpl) {
+            case 1: return search_kernel<ESG_FP8E4M3, 1>;
+            case 2: return search_kernel<ESG_FP8E4M3, 2>;
+            case 3: return search_kernel<ESG_FP8E4M3, 3>;
+        }
     }
+    return nullptr;
 }
 
 int env_int(const char *name, int dflt) {
@@ -580,7 +709,7 @@ int env_int(const char *name, int dflt) {
 // Launch shape and shared-memory plan of the beam-search kernel.
 struct SearchPlan {
     SearchFn fn;
-    int vpl, lpr, C, H, G, wpb;
+    int vpl, lpr, C, H, G, wpb, nvec;
     size_t smem;
     int64_t grid;
 };
@@ -589,11 +718,15 @@ struct SearchPlan {
 int esg_pick_vpl(int d, int *lpr);
 namespace {
 
-esg_status make_plan(int d, int R, int efk, int64_t n_items, SearchPlan &pl) {
-    pl.vpl = esg_pick_vpl(d, &pl.lpr);
+esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, SearchPlan &pl) {
+    const int esize = st == ESG_BF16 ? 2 : (st == ESG_FP8E4M3 ? 1 : 4);
+    if ((d * esize) % 16 != 0 || d % 4 != 0) { esg_set_error("row size not a multiple of 16 bytes"); return ESG_ERR_UNSUPPORTED; }
+    pl.nvec = d * esize / 16;
+    pl.vpl = esg_pick_vpl(pl.nvec * 4, &pl.lpr);
     if (pl.vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
     if (R > 128) { esg_set_error("R > 128"); return ESG_ERR_UNSUPPORTED; }
-    pl.fn = pick_search(pl.vpl);
+    pl.fn = pick_search(st, pl.vpl);
+    if (pl.fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
     pl.C = ((std::max(8 * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
     // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
@@ -606,7 +739,8 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, SearchPlan &pl) {
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
     pl.wpb = 2;
-    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 16 + kBatch * 12 + 32 * 8 + 16) * pl.wpb;
+    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 16 + kBatch * 12 + 32 * 8 + 16 +
+               (((size_t)d * 4 + 15) & ~(size_t)15)) * pl.wpb;
     int dev = 0, sms = 0, per_sm = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -651,7 +785,13 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     const int efk = std::max(ef, s.k_max);
     const int64_t n_items = 2 * s.nq;
     SearchPlan plan;
-    esg_status pst = make_plan(ix->d, ix->R, efk, n_items, plan);
+    const int st_trav = s.p.traversal;
+    const void *Xt = ix->X;
+    if (st_trav == ESG_BF16) Xt = ix->Xb;
+    else if (st_trav == ESG_FP8E4M3) Xt = ix->X8;
+    else if (st_trav != ESG_F32) { esg_set_error("unknown traversal type"); return ESG_ERR_INVALID_ARG; }
+    if (Xt == nullptr) { esg_set_error("index has no rows of the requested traversal type (build with that storage)"); return ESG_ERR_INVALID_ARG; }
+    esg_status pst = make_plan(ix->d, ix->R, efk, n_items, st_trav, plan);
     if (pst != ESG_OK) return pst;
     const int wpb = plan.wpb;
     const int64_t grid = plan.grid;
@@ -662,7 +802,7 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     size_t bytes_qs = sizeof(int32_t) * s.nq;
     size_t bytes_res = sizeof(Cand) * n_items * s.k_max;
     size_t bytes_cnt = sizeof(int32_t) * n_items * 2;
-    size_t bytes_stats = sizeof(int64_t) * n_items * 3;
+    size_t bytes_stats = sizeof(int64_t) * n_items * 4;
     size_t bytes_hash = (size_t)grid * wpb * plan.G * 4;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = al(bytes_pieces) + al(bytes_kq) + al(bytes_qs) + al(bytes_res) + al(bytes_cnt) +
@@ -696,7 +836,8 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
         a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
         a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
         a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
-        a.d = ix->d; a.nvec = ix->d / 4; a.R = ix->R; a.E = ix->E;
+        a.d = ix->d; a.nvec = plan.nvec; a.R = ix->R; a.E = ix->E;
+        a.Xv = reinterpret_cast<const uint4 *>(Xt); a.scale8 = ix->scale8; a.rerank = s.p.rerank;
         a.metric = ix->metric; a.ef = ef; a.LPR = plan.lpr;
         a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * ef + 256;
         a.k_max = s.k_max; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
@@ -730,7 +871,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
     SearchPlan plan;
-    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, plan);
+    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, plan);
     if (pst != ESG_OK) return pst;
     const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
     unsigned char *scratch = nullptr;
@@ -744,7 +885,8 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
         SearchArgs a;
         a.X = X; a.adj = adj; a.entries = entries; a.queries = X; a.qidx = qidx;
         a.pieces = pieces; a.kq = nullptr; a.kconst = k; a.qshift = 0;
-        a.n = n; a.n_items = n_items; a.d = d; a.nvec = d / 4; a.LPR = plan.lpr; a.R = R; a.E = E;
+        a.n = n; a.n_items = n_items; a.d = d; a.nvec = plan.nvec; a.LPR = plan.lpr; a.R = R; a.E = E;
+        a.Xv = reinterpret_cast<const uint4 *>(X); a.scale8 = nullptr; a.rerank = 0;
         a.metric = metric; a.ef = ef; a.max_exp = max_exp > 0 ? max_exp : 16 * ef + 256;
         a.k_max = k; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;

@@ -295,3 +295,57 @@ def test_leaf_range_is_exact_scan(small_index):
         ids, _ = O.search(idx, w.queries[i], 100, 100 + w.leaf_size - 5, 5, ef=1)
         gt, _ = O.bruteforce(idx.X, w.queries[i], 100, 100 + w.leaf_size - 5, 5, w.metric)
         assert ids.tolist() == gt.tolist()
+
+
+# ------------------------------------------------- low-precision storage
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(50_000) * rng.choice([1e-3, 1.0, 1e2, 1e5], 50_000)).astype(np.float32)
+    x = np.concatenate([x, np.float32([0.0, -0.0, 1.0, 1.00390625, 1.01171875])])  # exact ties
+    ref = torch.tensor(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(O.bf16_round(x), ref)
+
+
+def test_fp8_grid_and_codes():
+    from oracle import esg_oracle as EO
+    g = O.fp8_e4m3_grid()
+    assert g[0] == 0.0 and g[1] == 2.0 ** -9 and g[8] == 2.0 ** -6 and g[126] == 448.0
+    assert np.all(np.diff(g) > 0)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    v = (rng.standard_normal(100_000) * rng.choice([1e-4, 1e-2, 1.0, 50.0, 300.0], 100_000)).astype(np.float32)
+    mids = ((g[1:] + g[:-1]) / 2).astype(np.float32)                 # exact ties -> even code
+    v = np.concatenate([v, mids, -mids])
+    v = v[np.abs(v) <= 448]
+    ref = torch.tensor(v).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(EO._fp8_code(v), ref)
+    # saturation (satfinite) beyond the largest finite value
+    assert EO._fp8_code(np.float32([1e9, -1e9, 449.0])).tolist() == [126, 254, 126]
+
+
+def test_fp8_rows_reconstruct_within_half_ulp():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((200, 24)).astype(np.float32)
+    X[3] = 0.0
+    codes, s = O.fp8_quantize_rows(X)
+    assert s[3] == 0 and np.all(codes[3] == 0)
+    rec = O.fp8_to_float(codes) * s[:, None]
+    # relative step of E4M3 is 2^-3; the row maximum maps to 448 exactly
+    err = np.abs(rec - X)
+    assert np.all(err <= np.maximum(2.0 ** -4 * np.abs(X), 2.0 ** -10 * s[:, None]) + 1e-12)
+    assert np.all(np.abs(O.fp8_to_float(codes).max(1)[s > 0]) <= 448)
+
+
+def test_lowprec_search_reranks_exactly(small_index):
+    """With traversal rows equal to the exact rows the re-ranked search is the
+    plain search; with bf16 rows every returned distance is exact."""
+    w, idx = small_index
+    for i in range(10):
+        a, _ = O.search(idx, w.queries[i], int(w.l[i]), int(w.r[i]), 10, 16)
+        b, bd = O.search(idx, w.queries[i], int(w.l[i]), int(w.r[i]), 10, 16, trav_X=idx.X)
+        assert a.tolist() == b.tolist()
+        c, cd = O.search(idx, w.queries[i], int(w.l[i]), int(w.r[i]), 10, 16,
+                         trav_X=O.traversal_rows(idx.X.astype(np.float32), "bf16"))
+        assert np.allclose(cd, O.distances(idx.X[c], w.queries[i], w.metric))
