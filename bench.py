@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--ef", type=int, default=0, help="fixed beam width (skip the sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
     return ap.parse_args()
 
 
@@ -207,7 +208,9 @@ def cpu_baseline(ix, w, ef, seconds):
                       f"Algorithm 4 + Algorithm 1 in C float64 on the same graph, ef={ef}"}
 
 
-VARIANTS = [("plain", "f32"), ("mixed-bf16", "bf16"), ("mixed-fp8", "fp8")]
+# (name, traversal rows, search width); "plain" is Algorithm 1's order on FP32 rows
+VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16", "fp8")
+                                    for wd in (1, 2, 4) if not (t == "f32" and wd == 1)]
 ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
 
 
@@ -251,12 +254,15 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     results = {}
-    for name, trav in VARIANTS:
+    chosen_variants = [v for v in VARIANTS if not args.variants or v[0] in args.variants.split(",")]
+    if not any(v[0] == "plain" for v in chosen_variants):
+        chosen_variants = [VARIANTS[0]] + chosen_variants
+    for name, trav, width in chosen_variants:
         sweep = []
         chosen = args.ef
         for ef in ([args.ef] if args.ef else EF_SWEEP):
             ids, dist, cnt, st, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=ef,
-                                                           traversal=trav)
+                                                           traversal=trav, width=width)
             torch.cuda.synchronize()
             rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
             sweep.append({"ef": ef, "recall": round(rec, 5)})
@@ -267,7 +273,7 @@ def run_ours(args, rank, world, local):
             chosen = EF_SWEEP[-1]
         # per-step algorithmic bytes from the search's own counters
         _, _, _, _, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=chosen, traversal=trav,
-                                               want_stats=True)
+                                               width=width, want_stats=True)
         torch.cuda.synchronize()
         stats = stats.cpu().numpy()
         alg_bytes = float(stats[:, 1].sum() * ix.d * ESIZE[trav] + stats[:, 0].sum() * ix.R * 4
@@ -278,7 +284,8 @@ def run_ours(args, rank, world, local):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=chosen, traversal=trav, out=out)
+            E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=chosen, traversal=trav, width=width,
+                               out=out)
             ev1.record(stream)
             return ev0, ev1
 
@@ -301,7 +308,7 @@ def run_ours(args, rank, world, local):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
             torch.distributed.barrier()
-        results[name] = {"trav": trav, "ef": chosen, "recall": sweep[-1]["recall"], "sweep": sweep,
+        results[name] = {"trav": trav, "width": width, "ef": chosen, "recall": sweep[-1]["recall"], "sweep": sweep,
                          "qps": world * nq * args.steps / (total_ms / 1e3),
                          "ms_per_step": total_ms / args.steps, "kernel_ms": kernel_ms / max(1, timed),
                          "alg_bytes": alg_bytes, "launches": launches,
@@ -330,7 +337,8 @@ def run_ours(args, rank, world, local):
         Qd.copy_(Qh, non_blocking=True)
         Ld.copy_(Lh, non_blocking=True)
         Rd.copy_(Rh, non_blocking=True)
-        E.esg_search_batch(ix, Qd, Ld, Rd, None, 10, ef=head["ef"], traversal=head["trav"], out=out)
+        E.esg_search_batch(ix, Qd, Ld, Rd, None, 10, ef=head["ef"], traversal=head["trav"],
+                           width=head["width"], out=out)
         ids_h.copy_(out[0], non_blocking=True)
         dist_h.copy_(out[1], non_blocking=True)
         cnt_h.copy_(out[2], non_blocking=True)

@@ -119,8 +119,13 @@ typedef struct {
  *  use_learned     1 = per-query beam width from the trained predictor
  *                  (falls back to ef when no predictor is trained);
  *  traversal       row type used for traversal distances: ESG_F32, or
- *                  ESG_BF16 / ESG_FP8E4M3 when the index was built with that
- *                  storage (FP32 accumulation in every case).
+ *                  ESG_BF16 / ESG_FP8E4M3 when the index holds that copy
+ *                  (FP32 accumulation in every case);
+ *  width           candidates expanded per iteration, 1..4. 1 (or 0) is
+ *                  Algorithm 1's order (one best candidate at a time); larger
+ *                  values expand the `width` best unexpanded candidates
+ *                  together (more memory parallelism, slightly different
+ *                  visit order).
  */
 typedef struct {
     int32_t ef;
@@ -128,7 +133,7 @@ typedef struct {
     int32_t rerank;
     int32_t use_learned;
     esg_dtype traversal;
-    int32_t reserved;
+    int32_t width;
 } esg_search_params;
 
 esg_build_params esg_build_params_default(void);

@@ -51,7 +51,7 @@ class _BuildParams(ctypes.Structure):
 class _SearchParams(ctypes.Structure):
     _fields_ = [("ef", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
                 ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32),
-                ("traversal", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("traversal", ctypes.c_int32), ("width", ctypes.c_int32)]
 
 
 _lib = None
@@ -257,7 +257,7 @@ def unpack_pieces(pieces):
 
 def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,
                      max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
-                     traversal: str = "f32", out=None, want_status: bool = True,
+                     traversal: str = "f32", width: int = 1, out=None, want_status: bool = True,
                      want_stats: bool = False, stream=None):
     """Range-filtered search of CUDA float32 queries [nq, d] with CUDA int64
     ranges [nq]. Returns (ids int64 [nq,k_max], dist f32, count int32,
@@ -274,7 +274,7 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
         stats = torch.empty((nq, 5), dtype=torch.int64, device=dev) if want_stats else None
     else:
         ids, dist, count, status, stats = out
-    p = _SearchParams(ef, max_expansions, rerank, use_learned, STORAGE[traversal], 0)
+    p = _SearchParams(ef, max_expansions, rerank, use_learned, STORAGE[traversal], width)
     _check(lib.esg_search_batch(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
                                 _dev_ptr(k), k_max, ctypes.byref(p), _dev_ptr(ids), _dev_ptr(dist),
                                 _dev_ptr(count), _dev_ptr(status), _dev_ptr(stats),

@@ -104,7 +104,7 @@ esg_search_params esg_search_params_default(void) {
     p.rerank = 1;
     p.use_learned = 0;
     p.traversal = ESG_F32;
-    p.reserved = 0;
+    p.width = 1;
     return p;
 }
 
@@ -296,8 +296,8 @@ esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t n
     SearchLaunch s;
     s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max;
     s.p = params ? *params : esg_search_params_default();
-    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0) {
-        esg_set_error("esg_search_batch: ef must be in 1..1024");
+    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0 || s.p.width < 0 || s.p.width > 4) {
+        esg_set_error("esg_search_batch: need 1 <= ef <= 1024 and 0 <= width <= 4");
         return ESG_ERR_INVALID_ARG;
     }
     s.out_ids = out_ids; s.out_dist = out_dist; s.out_count = out_count;

@@ -1,0 +1,18 @@
+// Beam-search kernels over BF16 traversal rows (instantiations of
+// search_kernel.cuh, one translation unit per row type for parallel builds).
+#include "search_kernel.cuh"
+
+namespace esg_sk {
+
+SearchFn pick_bf16(int vpl) {
+    switch (vpl) {
+        case 1: return search_kernel<ESG_BF16, 1>;
+        case 2: return search_kernel<ESG_BF16, 2>;
+        case 3: return search_kernel<ESG_BF16, 3>;
+        case 4: return search_kernel<ESG_BF16, 4>;
+        case 6: return search_kernel<ESG_BF16, 6>;
+    }
+    return nullptr;
+}
+
+}  // namespace esg_sk

@@ -1,0 +1,604 @@
+// Beam-search kernel shared by the per-row-type translation units
+// (search_f32.cu, search_bf16.cu, search_fp8.cu); host launch code lives in
+// search.cu. See search.cu for the design.
+#pragma once
+#include "esg_internal.cuh"
+
+namespace esg_sk {
+
+constexpr int kBatch = 64;  // neighbours handled per expansion (R <= 64 per pass)
+
+struct WarpSmem {
+    uint32_t *hash;
+    Cand *list;
+    Cand *list2;
+    Cand *batch;
+    uint32_t *nbuf;
+    int *hcount;
+};
+
+__device__ __forceinline__ uint32_t hash_mix(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+
+// Visited set of one beam search: an open-addressing table in shared memory
+// backed, once it reaches its load limit, by a larger table in a per-warp
+// global-memory slot. visit() returns false iff `id` was already visited.
+// Only when both tables are at their limits is an id reported as new without
+// being stored (`saturated`; the list de-duplication then catches repeats).
+struct Visited {
+    uint32_t *hs;   // shared table, hmask + 1 slots
+    uint32_t hmask;
+    int *hcount;
+    int hlimit;
+    uint32_t *hg;   // global overflow table, gmask + 1 slots (all ESG_NONE when unused)
+    uint32_t gmask;
+    int *gcount;
+    int glimit;
+};
+
+__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated, bool *used_g) {
+    uint32_t h = hash_mix(id) & v.hmask;
+    for (uint32_t probe = 0; probe <= v.hmask; ++probe) {
+        const uint32_t slot = (h + probe) & v.hmask;
+        const uint32_t cur = v.hs[slot];
+        if (cur == id) return false;
+        if (cur == ESG_NONE) {
+            if (*(volatile int *)v.hcount >= v.hlimit) break;   // continue in the global table
+            const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
+            if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return true; }
+            if (prev == id) return false;
+        }
+    }
+    if (v.hg == nullptr) { *saturated = true; return true; }
+    *used_g = true;
+    h = hash_mix(id ^ 0x9e3779b9u) & v.gmask;
+    for (uint32_t probe = 0; probe <= v.gmask; ++probe) {
+        const uint32_t slot = (h + probe) & v.gmask;
+        const uint32_t cur = *(volatile uint32_t *)&v.hg[slot];
+        if (cur == id) return false;
+        if (cur == ESG_NONE) {
+            if (*(volatile int *)v.gcount >= v.glimit) { *saturated = true; return true; }
+            const uint32_t prev = atomicCAS(&v.hg[slot], ESG_NONE, id);
+            if (prev == ESG_NONE) { atomicAdd(v.gcount, 1); return true; }
+            if (prev == id) return false;
+        }
+    }
+    *saturated = true;
+    return true;
+}
+
+// Storage types of the traversal rows (esg_dtype): elements per 16-byte vector.
+template <int ST> struct Store;
+template <> struct Store<ESG_F32> { static constexpr int EPV = 4; };
+template <> struct Store<ESG_BF16> { static constexpr int EPV = 8; };
+template <> struct Store<ESG_FP8E4M3> { static constexpr int EPV = 16; };
+
+// Accumulate the distance terms of one 16-byte vector of a row against the
+// query slice qs[0..EPV) (FP32 accumulation; FP8 codes times the row scale).
+template <int ST>
+__device__ __forceinline__ float accum_vec(const uint4 &raw, const float *qs, float scale, int metric,
+                                           float acc) {
+    float x[Store<ST>::EPV];
+    if (ST == ESG_F32) {
+        x[0] = __uint_as_float(raw.x); x[1] = __uint_as_float(raw.y);
+        x[2] = __uint_as_float(raw.z); x[3] = __uint_as_float(raw.w);
+    } else if (ST == ESG_BF16) {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            x[2 * t] = __uint_as_float(w4[t] << 16);
+            x[2 * t + 1] = __uint_as_float(w4[t] & 0xFFFF0000u);
+        }
+    } else {
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w4[t] >> (16 * h)) & 0xFFFFu);
+                __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&hr));
+                x[4 * t + 2 * h] = f.x * scale;
+                x[4 * t + 2 * h + 1] = f.y * scale;
+            }
+        }
+    }
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+#pragma unroll
+    for (int e = 0; e < Store<ST>::EPV; e += 4) {
+        const float4 q = q4[e / 4];
+        if (metric == ESG_L2SQ) {
+            float a = q.x - x[e], b = q.y - x[e + 1], c = q.z - x[e + 2], d = q.w - x[e + 3];
+            acc = fmaf(a, a, acc); acc = fmaf(b, b, acc); acc = fmaf(c, c, acc); acc = fmaf(d, d, acc);
+        } else {
+            acc = fmaf(q.x, x[e], acc); acc = fmaf(q.y, x[e + 1], acc);
+            acc = fmaf(q.z, x[e + 2], acc); acc = fmaf(q.w, x[e + 3], acc);
+        }
+    }
+    return acc;
+}
+
+// Distances from the query (FP32, staged in shared memory `qs`) to the rows
+// listed in nbuf[0..m), written to batch[0..m). Rows are nvec 16-byte
+// vectors; LPR lanes share a row, each loading VPL vectors, and the loads of
+// U passes are all issued before any reduction.
+template <int ST, int VPL>
+__device__ __forceinline__ void eval_rows(const uint4 *__restrict__ Xv, const float *__restrict__ scale8,
+                                          int nvec, int LPR, const float *qs, const uint32_t *nbuf,
+                                          int m, Cand *batch, int metric) {
+    constexpr int EPV = Store<ST>::EPV;
+    const int lane = threadIdx.x & 31;
+    const int s = lane & (LPR - 1);
+    const int g = lane / LPR;
+    const int rows_per_pass = 32 / LPR;
+    // vectors in flight per lane scaled so that at most ~16 FP32-equivalent
+    // vectors are decoded per pass (more would spill registers)
+    constexpr int W = ST == ESG_F32 ? 1 : (ST == ESG_BF16 ? 2 : 4);
+    constexpr int U0 = 16 / (VPL * W);
+    constexpr int U = U0 < 1 ? 1 : (U0 > 8 ? 8 : U0);
+    for (int base = 0; base < m; base += rows_per_pass * U) {
+        uint4 xv[U][VPL];
+        uint32_t id[U];
+        float sc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int row = base + u * rows_per_pass + g;
+            id[u] = row < m ? nbuf[row] : ESG_NONE;
+            sc[u] = 1.f;
+            if (id[u] != ESG_NONE) {
+                const uint4 *p = Xv + (size_t)id[u] * nvec + s;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) xv[u][v] = __ldg(p + v * LPR);
+                if (ST == ESG_FP8E4M3) sc[u] = __ldg(scale8 + id[u]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) xv[u][v] = make_uint4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float acc = 0.f;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+                acc = accum_vec<ST>(xv[u][v], qs + (s + v * LPR) * EPV, sc[u], metric, acc);
+            acc = warp_sum_group(acc, LPR);
+            const int row = base + u * rows_per_pass + g;
+            if (s == 0 && row < m) batch[row] = Cand{metric == ESG_L2SQ ? acc : -acc, id[u]};
+        }
+    }
+    __syncwarp();
+}
+
+// Exact FP32 distances of the rows in nbuf[0..m) (re-rank of candidates
+// found with low-precision rows): 8 lanes per row.
+__device__ __forceinline__ void eval_rows_fp32(const float *__restrict__ X, int d, const float *qs,
+                                               const uint32_t *nbuf, int m, Cand *out, int metric) {
+    const int lane = threadIdx.x & 31;
+    const int s = lane & 7, g = lane >> 3;
+    const int nv = d / 4;
+    const float4 *q4 = reinterpret_cast<const float4 *>(qs);
+    for (int base = 0; base < m; base += 4) {
+        const int row = base + g;
+        const uint32_t id = row < m ? nbuf[row] : ESG_NONE;
+        float acc = 0.f;
+        if (id != ESG_NONE) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(X + (size_t)id * d);
+#pragma unroll 4
+            for (int v = s; v < nv; v += 8) {
+                const float4 x = __ldg(x4 + v), q = q4[v];
+                if (metric == ESG_L2SQ) {
+                    float a = q.x - x.x, b = q.y - x.y, c = q.z - x.z, e = q.w - x.w;
+                    acc = fmaf(a, a, acc); acc = fmaf(b, b, acc); acc = fmaf(c, c, acc); acc = fmaf(e, e, acc);
+                } else {
+                    acc = fmaf(q.x, x.x, acc); acc = fmaf(q.y, x.y, acc);
+                    acc = fmaf(q.z, x.z, acc); acc = fmaf(q.w, x.w, acc);
+                }
+            }
+        }
+        acc = warp_sum_group(acc, 8);
+        if (s == 0 && row < m) out[row] = Cand{metric == ESG_L2SQ ? acc : -acc, id};
+    }
+    __syncwarp();
+}
+
+// Merge the sorted, duplicate-free batch B[0..b) into the sorted list
+// A[0..a), writing O (capacity C). Returns the new length min(a + b, C).
+__device__ __forceinline__ int warp_merge(const Cand *A, int a, const Cand *B, int b, Cand *O, int C) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < a; i += 32) {
+        Cand x = A[i];
+        int pos = i + lower_rank(B, b, x);
+        if (pos < C) O[pos] = x;
+    }
+    for (int j = lane; j < b; j += 32) {
+        Cand x = B[j];
+        int pos = j + lower_rank(A, a, x);
+        if (pos < C) O[pos] = x;
+    }
+    __syncwarp();
+    return min(a + b, C);
+}
+
+// List state of one beam search.
+struct ListState {
+    int len;       // items in the list
+    int qn;        // in-range items kept (<= ef)
+    Cand qworst;   // the ef-th in-range item when qn == ef, else +inf
+    int first;     // position of the best unexpanded item, -1 if none
+};
+
+// Cut the list after its ef-th in-range item (Q keeps the best ef; nothing
+// behind it can be expanded or returned) and refresh |Q| and the worst of Q.
+__device__ __forceinline__ void truncate_list(const Cand *list, ListState &st, int ef,
+                                              uint32_t pl, uint32_t pr) {
+    const int lane = threadIdx.x & 31;
+    int seen = 0;
+    st.qn = 0;
+    st.qworst = Cand{INFINITY, ESG_NONE};
+    st.first = -1;
+    for (int base = 0; base < st.len; base += 32) {
+        const int i = base + lane;
+        const uint32_t raw = i < st.len ? list[i].id : ESG_NONE;
+        const uint32_t id = raw & ESG_ID_MASK;
+        const bool inr = i < st.len && id >= pl && id <= pr;
+        const unsigned bal = __ballot_sync(0xffffffffu, inr);
+        const unsigned unexp = __ballot_sync(0xffffffffu, i < st.len && !(raw & ESG_EXPANDED));
+        const int c = __popc(bal);
+        if (seen + c >= ef) {
+            // position of the (ef - seen)-th set bit of bal
+            const int need = ef - seen;
+            unsigned b = bal;
+            for (int t = 1; t < need; ++t) b &= b - 1;
+            const int pos = base + __ffs(b) - 1;
+            st.len = pos + 1;
+            st.qn = ef;
+            st.qworst = list[pos];
+            const unsigned keep_unexp = unexp & (pos - base == 31 ? 0xffffffffu : ((1u << (pos - base + 1)) - 1));
+            if (st.first < 0 && keep_unexp) st.first = base + __ffs(keep_unexp) - 1;
+            return;
+        }
+        if (st.first < 0 && unexp) st.first = base + __ffs(unexp) - 1;
+        seen += c;
+    }
+    st.qn = seen;
+}
+
+// Admitted candidates sit in batch[0..BB) (BB a multiple of 64 and a power
+// of two; rejected slots hold +inf). Sort them and merge them into `list`,
+// returning the merged list (list or list2) after truncation. Batches of at
+// most 32 are sorted in registers.
+__device__ __forceinline__ Cand *admit_batch(Cand *batch, int BB, Cand *cbuf, Cand *list, Cand *list2,
+                                             ListState &st, int ef, int C, uint32_t pl, uint32_t pr,
+                                             int &status) {
+    const int lane = threadIdx.x & 31;
+    int b = 0;
+    for (int c = 0; c < BB; c += 32) b += __popc(__ballot_sync(0xffffffffu, batch[c + lane].id != ESG_NONE));
+    if (b == 0) return list;
+    const Cand *B;
+    if (b <= 32) {
+        const unsigned below = (1u << lane) - 1;
+        int o = 0;
+        for (int c = 0; c < BB && o < b; c += 32) {
+            const Cand x = batch[c + lane];
+            const bool k = x.id != ESG_NONE;
+            const unsigned bal = __ballot_sync(0xffffffffu, k);
+            if (k) cbuf[o + __popc(bal & below)] = x;
+            o += __popc(bal);
+        }
+        __syncwarp();
+        float d = lane < b ? cbuf[lane].d : INFINITY;
+        uint32_t id = lane < b ? cbuf[lane].id : ESG_NONE;
+        __syncwarp();
+        warp_sort32_reg(d, id);
+        cbuf[lane] = Cand{d, id};
+        __syncwarp();
+        B = cbuf;
+    } else {
+        if (BB == 64) warp_sort64(batch);
+        else warp_sort_pow2(batch, BB);
+        B = batch;
+    }
+    if (st.len + b > C) status |= ESG_Q_OVERFLOW;
+    st.len = warp_merge(list, st.len, B, b, list2, C);
+    truncate_list(list2, st, ef, pl, pr);
+    return list2;
+}
+
+struct SearchArgs {
+    const float *X;        // FP32 rows (re-rank, and traversal when st == F32)
+    const uint4 *Xv;       // traversal rows (FP32, BF16 or FP8) as 16-byte vectors
+    const float *scale8;   // FP8 per-row scales
+    int rerank;
+    const uint32_t *adj;
+    const int32_t *entries;
+    const float *queries;
+    const int64_t *qidx;   // optional: query row of an item (build: the inserted point)
+    const esg_piece *pieces;
+    const int32_t *kq;     // per-query k (validated), 0 = invalid; null = kconst
+    int kconst;
+    int qshift;            // query of item i = i >> qshift (2 pieces per query: 1)
+    int64_t n;
+    int64_t n_items;
+    int d, nvec, LPR, R, E, metric;
+    int ef, max_exp, k_max;
+    int width;             // candidates expanded per iteration (1 = Algorithm 1 order)
+    int BB;                // batch capacity: width * R rounded up to 64
+    int H, C;
+    uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
+    int G;
+    unsigned long long *queue;  // atomic work counter
+    Cand *res;             // [n_items, k_max]
+    int32_t *res_cnt;      // [n_items]
+    int32_t *res_status;   // [n_items]
+    int64_t *res_stats;    // [n_items, 4]
+};
+
+template <int ST, int VPL>
+__global__ void __launch_bounds__(64, 8)
+search_kernel(SearchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const size_t qbytes = ((size_t)a.d * 4 + 15) & ~(size_t)15;
+    const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 * 2 + (size_t)a.BB * 12 + 32 * 8 +
+                            16 + qbytes;
+    unsigned char *base = smem_raw + per_warp * wib;
+    WarpSmem w;
+    size_t off = 0;
+    w.list = (Cand *)(base + off); off += (size_t)a.C * 8;
+    w.list2 = (Cand *)(base + off); off += (size_t)a.C * 8;
+    w.batch = (Cand *)(base + off); off += (size_t)a.BB * 8;
+    Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
+    w.nbuf = (uint32_t *)(base + off); off += (size_t)a.BB * 4;
+    w.hcount = (int *)(base + off); off += 16;
+    float *qs = (float *)(base + off); off += qbytes;
+    const int gwarp = blockIdx.x * wpb + wib;
+    w.hash = (uint32_t *)(base + off);
+    Visited vis;
+    vis.hs = w.hash;
+    vis.hmask = (uint32_t)a.H - 1;
+    vis.hcount = w.hcount;
+    vis.hlimit = (a.H * 3) / 4;
+    vis.hg = a.ghash ? a.ghash + (size_t)gwarp * a.G : nullptr;
+    vis.gmask = (uint32_t)a.G - 1;
+    vis.gcount = w.hcount + 1;
+    vis.glimit = (a.G * 3) / 4;
+
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = (int64_t)atomicAdd(a.queue, 1ULL);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.n_items) break;
+        const int64_t qi = item >> a.qshift;
+        const esg_piece pc = a.pieces[item];
+        const int kq = a.kq ? a.kq[qi] : a.kconst;
+        int64_t n_exp = 0, n_eval = 0, n_oor = 0, n_rr = 0;
+        int status = 0;
+        if (pc.kind == ESG_PIECE_NONE || kq <= 0) {
+            if (lane == 0) { a.res_cnt[item] = 0; a.res_status[item] = 0; }
+            if (lane < 4) a.res_stats[item * 4 + lane] = 0;
+            continue;
+        }
+        const uint32_t pl = (uint32_t)pc.pl, pr = (uint32_t)pc.pr;
+        const bool is_graph = pc.kind == ESG_PIECE_GRAPH;
+        // low-precision scans keep ef candidates for the FP32 re-rank
+        const bool do_rerank = ST != ESG_F32 && a.rerank;
+        const int ef = (is_graph || do_rerank) ? max(a.ef, kq) : kq;
+
+        // query in shared memory (FP32)
+        {
+            const int64_t qrow = a.qidx ? a.qidx[item] : qi;
+            const float4 *q4 = reinterpret_cast<const float4 *>(a.queries + qrow * (int64_t)a.d);
+            for (int v = lane; v < a.d / 4; v += 32) reinterpret_cast<float4 *>(qs)[v] = __ldg(q4 + v);
+            __syncwarp();
+        }
+        ListState st{0, 0, Cand{INFINITY, ESG_NONE}, -1};
+        Cand *list = w.list, *list2 = w.list2;
+        bool saturated = false;
+
+        if (!is_graph) {
+            // Leaf piece: exact scan of [pl, pr] (Algorithm 4, first branch).
+            for (int64_t c0 = pl; c0 <= (int64_t)pr; c0 += kBatch) {
+                const int m = (int)(((int64_t)pr - c0 + 1) < kBatch ? ((int64_t)pr - c0 + 1) : kBatch);
+                for (int j = lane; j < m; j += 32) w.nbuf[j] = (uint32_t)(c0 + j);
+                __syncwarp();
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
+                n_eval += m;
+                for (int j = lane; j < a.BB; j += 32) {
+                    const bool keep = j < m && (st.qn < ef || cand_less(w.batch[j], st.qworst));
+                    if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
+                }
+                __syncwarp();
+                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                if (nl != list) { list2 = list; list = nl; }
+            }
+        } else {
+            // Graph piece: Algorithm 1 with POST filtering to [pl, pr].
+            for (int i = lane; i < a.H; i += 32) w.hash[i] = ESG_NONE;
+            if (lane == 0) { w.hcount[0] = 0; w.hcount[1] = 0; }
+            __syncwarp();
+            bool used_g = false;
+            const uint32_t *adj = a.adj + (size_t)pc.depth * (size_t)a.n * a.R;
+            // entry points: into P, and into Q when in range
+            {
+                uint32_t e = ESG_NONE;
+                if (lane < a.E) {
+                    const int32_t v = a.entries[(size_t)pc.heap * a.E + lane];
+                    if (v >= 0 && v < a.n) e = (uint32_t)v;
+                }
+                const bool nw = e != ESG_NONE && visit(vis, e, &saturated, &used_g);
+                const unsigned bal = __ballot_sync(0xffffffffu, nw);
+                if (nw) w.nbuf[__popc(bal & ((1u << lane) - 1))] = e;
+                const int m = __popc(bal);
+                __syncwarp();
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
+                n_eval += m;
+                for (int j = lane; j < a.BB; j += 32) {
+                    if (j >= m) w.batch[j] = Cand{INFINITY, ESG_NONE};
+                    else n_oor += (w.batch[j].id < pl || w.batch[j].id > pr);
+                }
+                __syncwarp();
+                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                if (nl != list) { list2 = list; list = nl; }
+            }
+            // all items before `hint` are expanded
+            int hint = st.first < 0 ? st.len : st.first;
+            for (;;) {
+                // the (up to) `width` best unexpanded candidates, ascending
+                int sel[4];
+                int nsel = 0;
+                for (int b0 = hint & ~31; b0 < st.len && nsel < a.width; b0 += 32) {
+                    const int i = b0 + lane;
+                    const bool f = i >= hint && i < st.len && !(list[i].id & ESG_EXPANDED);
+                    unsigned bal = __ballot_sync(0xffffffffu, f);
+                    while (bal && nsel < a.width) { sel[nsel++] = b0 + __ffs(bal) - 1; bal &= bal - 1; }
+                }
+                if (nsel == 0) break;
+                if (n_exp >= a.max_exp) { status |= ESG_Q_TRUNCATED; break; }
+                uint32_t us[4];
+                for (int t = 0; t < nsel; ++t) us[t] = list[sel[t]].id & ESG_ID_MASK;
+                __syncwarp();
+                // mark in-range ones expanded; drop out-of-range ones (they are
+                // neither in Q nor in P once expanded), highest position first
+                for (int t = nsel - 1; t >= 0; --t) {
+                    const int pos = sel[t];
+                    if (us[t] >= pl && us[t] <= pr) {
+                        if (lane == 0) list[pos].id = us[t] | ESG_EXPANDED;
+                        __syncwarp();
+                        continue;
+                    }
+                    const int cnt = st.len - 1 - pos;
+                    for (int b0 = 0; b0 < cnt; b0 += 32) {
+                        const bool act = b0 + lane < cnt;
+                        Cand nx;
+                        if (act) nx = list[pos + b0 + lane + 1];
+                        __syncwarp();
+                        if (act) list[pos + b0 + lane] = nx;
+                        __syncwarp();
+                    }
+                    st.len -= 1;
+                }
+                hint = sel[0];
+                n_exp += nsel;
+                // neighbours of the selected candidates, visited-tested, compacted
+                int m = 0;
+                for (int t = 0; t < nsel; ++t) {
+                    const uint32_t *row = adj + (size_t)us[t] * a.R;
+                    for (int c64 = 0; c64 < a.R; c64 += 64) {
+                        uint32_t v0 = c64 + lane < a.R ? __ldg(row + c64 + lane) : ESG_NONE;
+                        uint32_t v1 = c64 + lane + 32 < a.R ? __ldg(row + c64 + lane + 32) : ESG_NONE;
+                        if (v0 >= (uint64_t)a.n) v0 = ESG_NONE;   // malformed imported graph: ignore
+                        if (v1 >= (uint64_t)a.n) v1 = ESG_NONE;
+                        const bool n0 = v0 != ESG_NONE && visit(vis, v0, &saturated, &used_g);
+                        const bool n1 = v1 != ESG_NONE && visit(vis, v1, &saturated, &used_g);
+                        const unsigned b0 = __ballot_sync(0xffffffffu, n0);
+                        const unsigned b1 = __ballot_sync(0xffffffffu, n1);
+                        const int c0 = __popc(b0);
+                        if (n0) w.nbuf[m + __popc(b0 & ((1u << lane) - 1))] = v0;
+                        if (n1) w.nbuf[m + c0 + __popc(b1 & ((1u << lane) - 1))] = v1;
+                        m += c0 + __popc(b1);
+                    }
+                }
+                __syncwarp();
+                if (m == 0) continue;
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
+                n_eval += m;
+                // Algorithm 1's admission test, then de-duplication against
+                // the list (only needed once the visited set saturates)
+                const bool sat = __any_sync(0xffffffffu, saturated);
+                for (int j = lane; j < a.BB; j += 32) {
+                    bool keep = false;
+                    if (j < m) {
+                        const Cand x = w.batch[j];
+                        n_oor += (x.id < pl || x.id > pr);
+                        keep = st.qn < ef || cand_less(x, st.qworst);
+                        if (keep && sat) {
+                            const int p = lower_rank(list, st.len, x);
+                            if (p < st.len && cand_eq(list[p], x)) keep = false;
+                        }
+                    }
+                    if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
+                }
+                __syncwarp();
+                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
+                if (nl != list) {
+                    list2 = list; list = nl;
+                    hint = st.first < 0 ? st.len : st.first;
+                }
+            }
+            if (__any_sync(0xffffffffu, saturated)) status |= ESG_Q_OVERFLOW;
+            if (__any_sync(0xffffffffu, used_g)) {
+                // leave the overflow table clean for the warp's next item
+                for (int i = lane; i < a.G; i += 32) vis.hg[i] = ESG_NONE;
+                __syncwarp();
+            }
+        }
+        // FP32 re-rank of the final in-range candidates found on low-precision rows
+        if (do_rerank && st.len > 0) {
+            int cnt = 0;
+            for (int b0 = 0; b0 < st.len; b0 += 32) {
+                const int i = b0 + lane;
+                const uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
+                const bool inr = i < st.len && id >= pl && id <= pr;
+                const unsigned bal = __ballot_sync(0xffffffffu, inr);
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1));
+                if (inr && pos < ef) list2[pos] = Cand{0.f, id};
+                cnt += __popc(bal);
+                if (cnt >= ef) break;
+            }
+            cnt = min(cnt, ef);
+            __syncwarp();
+            for (int c0 = 0; c0 < cnt; c0 += kBatch) {
+                const int m = min(kBatch, cnt - c0);
+                for (int j = lane; j < m; j += 32) w.nbuf[j] = list2[c0 + j].id;
+                __syncwarp();
+                eval_rows_fp32(a.X, a.d, qs, w.nbuf, m, list2 + c0, a.metric);
+            }
+            n_rr += cnt;
+            const int P = next_pow2_int(max(cnt, 2));
+            for (int j = cnt + lane; j < P; j += 32) list2[j] = Cand{INFINITY, ESG_NONE};
+            __syncwarp();
+            warp_sort_pow2(list2, P);
+            Cand *t = list; list = list2; list2 = t;
+            st.len = cnt;
+        }
+        // emit the first min(k, |Q|) in-range items
+        {
+            int written = 0;
+            Cand *out = a.res + item * (int64_t)a.k_max;
+            for (int b0 = 0; b0 < st.len && written < kq; b0 += 32) {
+                const int i = b0 + lane;
+                const uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
+                const bool inr = i < st.len && id >= pl && id <= pr;
+                const unsigned bal = __ballot_sync(0xffffffffu, inr);
+                const int pos = written + __popc(bal & ((1u << lane) - 1));
+                if (inr && pos < kq) out[pos] = Cand{list[i].d, id};
+                written += __popc(bal);
+            }
+            written = min(written, kq);
+            n_exp = __shfl_sync(0xffffffffu, n_exp, 0);
+            for (int o = 16; o > 0; o >>= 1) n_oor += __shfl_xor_sync(0xffffffffu, n_oor, o);
+            if (lane == 0) {
+                a.res_cnt[item] = written;
+                a.res_status[item] = status;
+                a.res_stats[item * 4 + 0] = n_exp;
+                a.res_stats[item * 4 + 1] = n_eval;
+                a.res_stats[item * 4 + 2] = n_oor;
+                a.res_stats[item * 4 + 3] = n_rr;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace esg_sk
+
+namespace esg_sk {
+typedef void (*SearchFn)(SearchArgs);
+SearchFn pick_f32(int vpl);
+SearchFn pick_bf16(int vpl);
+SearchFn pick_fp8(int vpl);
+}  // namespace esg_sk

@@ -163,7 +163,7 @@ def _gpu_search(gix, Q, l, r, k, k_max, ef, dev, **kw):
     return [None if x is None else x.cpu().numpy() for x in out]
 
 
-@pytest.mark.parametrize("ef", [16, 64])
+@pytest.mark.parametrize("ef", [16, 64, 200])
 def test_search_parity_on_oracle_graph(dev, tiny_oracle_index, ef):
     w, idx = tiny_oracle_index
     gix = _import(idx, w)
@@ -275,3 +275,26 @@ def test_product_build_invariants_and_recall(dev):
         found.append(inv[ids[i, :count[i]]])
         truth.append(O.bruteforce(X, w.queries[i], int(w.l[i]), int(w.r[i]), 10, w.metric)[0])
     assert O.recall_at_k(found, truth) >= 0.95
+
+
+@pytest.mark.parametrize("width", [2, 4])
+def test_search_width_keeps_recall(dev, tiny_oracle_index, width):
+    """Expanding several candidates per iteration changes the visit order
+    only: results stay valid and recall does not fall below Algorithm 1's by
+    more than 0.5 points at the same ef."""
+    w, idx = tiny_oracle_index
+    gix = _import(idx, w)
+    ids, dist, count, status, stats = _gpu_search(gix, w.queries, w.l, w.r, None, 10, 16, dev,
+                                                  width=width)
+    inv = np.empty(idx.n, np.int64)
+    inv[idx.perm] = np.arange(idx.n)
+    found, base, truth = [], [], []
+    for i in range(len(w.queries)):
+        l, r = int(w.l[i]), int(w.r[i])
+        got = inv[ids[i, :count[i]]]
+        assert np.all((got >= l) & (got <= r)) and len(set(got.tolist())) == len(got)
+        assert count[i] == min(10, r - l + 1)
+        found.append(got)
+        base.append(O.search(idx, w.queries[i], l, r, 10, 16)[0])
+        truth.append(O.bruteforce(idx.X, w.queries[i], l, r, 10, w.metric)[0])
+    assert O.recall_at_k(found, truth) >= O.recall_at_k(base, truth) - 0.005
