@@ -125,7 +125,13 @@ typedef struct {
  *                  Algorithm 1's order (one best candidate at a time); larger
  *                  values expand the `width` best unexpanded candidates
  *                  together (more memory parallelism, slightly different
- *                  visit order).
+ *                  visit order);
+ *  warps_per_block, hash_slots, lanes_per_row
+ *                  launch shape knobs that do not change results: warps per
+ *                  CTA (1, 2 or 4), shared visited-table slots (power of two,
+ *                  1024..16384) and lanes that share one row gather (1..32,
+ *                  a power of two dividing the row's 16-byte vectors); 0 =
+ *                  automatic. esg_autotune picks them.
  */
 typedef struct {
     int32_t ef;
@@ -134,6 +140,10 @@ typedef struct {
     int32_t use_learned;
     esg_dtype traversal;
     int32_t width;
+    int32_t warps_per_block;
+    int32_t hash_slots;
+    int32_t lanes_per_row;
+    int32_t reserved;
 } esg_search_params;
 
 esg_build_params esg_build_params_default(void);
@@ -238,6 +248,42 @@ esg_status esg_search_batch(const esg_index *index, const float *queries, int64_
                             const esg_search_params *params, int64_t *out_ids, float *out_dist,
                             int32_t *out_count, int32_t *out_status, int64_t *out_stats,
                             esg_stream_t stream);
+
+/*
+ * Batched search replayed as one CUDA graph. A batch owns device buffers for
+ * up to max_nq queries (inputs: queries [max_nq, d] f32, l, r [max_nq] int64,
+ * k [max_nq] int32; outputs as in esg_search_batch, stats [max_nq, 5]) and the
+ * search's scratch memory, all allocated at creation. esg_batch_run(nq)
+ * replays the whole search (decomposition, persistent beam-search kernel over
+ * an atomic queue of (query, piece) items, merge) for the first nq entries
+ * with a single cudaGraphLaunch on `stream`; the graph for a given nq is
+ * captured on first use (on a private stream) and cached. The k buffer is
+ * used only when use_k != 0. Runs on one batch must not overlap.
+ */
+typedef struct esg_batch esg_batch;
+esg_status esg_batch_create(const esg_index *index, int64_t max_nq, int32_t k_max, int32_t use_k,
+                            const esg_search_params *params, esg_batch **out);
+esg_status esg_batch_buffers(esg_batch *batch, float **queries, int64_t **l, int64_t **r,
+                             int32_t **k, int64_t **ids, float **dist, int32_t **count,
+                             int32_t **status, int64_t **stats);
+esg_status esg_batch_run(esg_batch *batch, int64_t nq, esg_stream_t stream);
+void esg_batch_free(esg_batch *batch);
+
+/*
+ * Autotuner (library-specific; no counterpart in the paper). Given sample
+ * queries with their exact answers (gt_ids device [nq, k_max] original ids,
+ * -1 padded; gt_count device [nq]), it chooses the smallest beam width ef
+ * (from 8..1024) and search width (1 or 2) whose mean recall@k reaches
+ * target_recall, then the fastest launch shape (warps per block, visited-table
+ * slots, lanes per row) by timing with CUDA events. `base` supplies the other
+ * fields (traversal, rerank, ...). Writes the chosen parameters to `out` and,
+ * if `report` is not NULL, [recall, milliseconds per search of the sample].
+ * Synchronous on `stream`. ESG_ERR_UNSUPPORTED if no setting reaches the target.
+ */
+esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq, const int64_t *l,
+                        const int64_t *r, const int32_t *k, int32_t k_max, const int64_t *gt_ids,
+                        const int32_t *gt_count, float target_recall, const esg_search_params *base,
+                        esg_search_params *out, float *report, esg_stream_t stream);
 
 /*
  * Exact range-filtered k-NN by brute force (Definitions 1 and 2): for each

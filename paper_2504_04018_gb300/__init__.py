@@ -33,7 +33,8 @@ EXPORTED = [
     "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
     "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
-    "esg_index_export_storage", "esg_index_add_storage",
+    "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
+    "esg_batch_run", "esg_batch_free", "esg_autotune",
 ]
 
 
@@ -51,7 +52,12 @@ class _BuildParams(ctypes.Structure):
 class _SearchParams(ctypes.Structure):
     _fields_ = [("ef", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
                 ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32),
-                ("traversal", ctypes.c_int32), ("width", ctypes.c_int32)]
+                ("traversal", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 _lib = None
@@ -92,13 +98,21 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
     lib.esg_profile_enable.argtypes = [_I32]
     lib.esg_profile_read.argtypes = [_P, _P, _P, _I32]
+    lib.esg_batch_create.argtypes = [_P, _I64, _I32, _I32, ctypes.POINTER(_SearchParams), ctypes.POINTER(_P)]
+    lib.esg_batch_buffers.argtypes = [_P] + [ctypes.POINTER(_P)] * 9
+    lib.esg_batch_run.argtypes = [_P, _I64, _P]
+    lib.esg_batch_free.argtypes = [_P]
+    lib.esg_batch_free.restype = None
+    lib.esg_autotune.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _P, _P, ctypes.c_float,
+                                 ctypes.POINTER(_SearchParams), ctypes.POINTER(_SearchParams), _P, _P]
     lib.esg_status_str.restype = ctypes.c_char_p
     lib.esg_status_str.argtypes = [_I32]
     lib.esg_last_error.restype = ctypes.c_char_p
     for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
-                 "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage"]:
+                 "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage",
+                 "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -255,10 +269,19 @@ def unpack_pieces(pieces):
     return (p64[..., 0], p64[..., 1], p64[..., 2], p64[..., 3], p32[..., 8], p32[..., 9], p32[..., 10])
 
 
+def search_params(ef: int = 64, max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
+                  traversal: str = "f32", width: int = 1, warps_per_block: int = 0,
+                  hash_slots: int = 0, lanes_per_row: int = 0) -> _SearchParams:
+    """An esg_search_params record."""
+    return _SearchParams(ef, max_expansions, rerank, use_learned,
+                         STORAGE[traversal] if isinstance(traversal, str) else traversal, width,
+                         warps_per_block, hash_slots, lanes_per_row, 0)
+
+
 def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,
                      max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
-                     traversal: str = "f32", width: int = 1, out=None, want_status: bool = True,
-                     want_stats: bool = False, stream=None):
+                     traversal: str = "f32", width: int = 1, params=None, out=None,
+                     want_status: bool = True, want_stats: bool = False, stream=None):
     """Range-filtered search of CUDA float32 queries [nq, d] with CUDA int64
     ranges [nq]. Returns (ids int64 [nq,k_max], dist f32, count int32,
     status int32 or None, stats int64 [nq,5] or None)."""
@@ -274,7 +297,8 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
         stats = torch.empty((nq, 5), dtype=torch.int64, device=dev) if want_stats else None
     else:
         ids, dist, count, status, stats = out
-    p = _SearchParams(ef, max_expansions, rerank, use_learned, STORAGE[traversal], width)
+    p = params if params is not None else search_params(ef, max_expansions, rerank, use_learned,
+                                                        traversal, width)
     _check(lib.esg_search_batch(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
                                 _dev_ptr(k), k_max, ctypes.byref(p), _dev_ptr(ids), _dev_ptr(dist),
                                 _dev_ptr(count), _dev_ptr(status), _dev_ptr(stats),
@@ -340,3 +364,65 @@ def esg_profile_read(reset: bool = True):
                                            ctypes.byref(timed), 1 if reset else 0),
            "esg_profile_read")
     return ms.value, launches.value, timed.value
+
+
+class Batch:
+    """A CUDA-graph batch executor (esg_batch_*): device buffers for up to
+    max_nq queries, replayed with one graph launch per run."""
+
+    def __init__(self, index: Index, max_nq: int, k_max: int, params=None, use_k: bool = False):
+        import torch
+        lib = load_library()
+        self.index, self.max_nq, self.k_max = index, max_nq, k_max
+        p = params if params is not None else search_params()
+        h = _P()
+        _check(lib.esg_batch_create(index.handle, max_nq, k_max, 1 if use_k else 0, ctypes.byref(p),
+                                    ctypes.byref(h)), "esg_batch_create")
+        self._h = h
+        ptrs = [_P() for _ in range(9)]
+        _check(lib.esg_batch_buffers(h, *[ctypes.byref(x) for x in ptrs]), "esg_batch_buffers")
+        self.ptrs = dict(zip(["queries", "l", "r", "k", "ids", "dist", "count", "status", "stats"],
+                             [x.value for x in ptrs]))
+        self._torch = torch
+
+    def view(self, name: str, shape, dtype):
+        """A torch tensor aliasing one of the batch's device buffers (no copy)."""
+        torch = self._torch
+        n = int(np.prod(shape))
+        esize = torch.empty(0, dtype=dtype).element_size()
+
+        class _Cuda:
+            def __init__(self, ptr, nbytes):
+                self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1",
+                                                 "data": (ptr, False), "version": 3}
+        raw = torch.as_tensor(_Cuda(self.ptrs[name], n * esize), device="cuda")
+        return raw.view(dtype).view(*shape)
+
+    def run(self, nq: int, stream=None):
+        _check(load_library().esg_batch_run(self._h, nq, _stream_ptr(stream)), "esg_batch_run")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load_library().esg_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def esg_autotune(index: Index, queries, l, r, gt_ids, gt_count, k_max: int = 10, k=None,
+                 target_recall: float = 0.95, base=None, stream=None):
+    """Choose ef, search width and launch shape for a recall target on sample
+    queries with exact answers (CUDA tensors). Returns (params, recall, ms)."""
+    lib = load_library()
+    b = base if base is not None else search_params()
+    out = _SearchParams()
+    rep = np.zeros(2, dtype=np.float32)
+    _check(lib.esg_autotune(index.handle, _dev_ptr(queries), queries.shape[0], _dev_ptr(l), _dev_ptr(r),
+                            _dev_ptr(k), k_max, _dev_ptr(gt_ids), _dev_ptr(gt_count),
+                            float(target_recall), ctypes.byref(b), ctypes.byref(out), _np_ptr(rep),
+                            _stream_ptr(stream)), "esg_autotune")
+    return out, float(rep[0]), float(rep[1])

@@ -105,6 +105,10 @@ esg_search_params esg_search_params_default(void) {
     p.use_learned = 0;
     p.traversal = ESG_F32;
     p.width = 1;
+    p.warps_per_block = 0;
+    p.hash_slots = 0;
+    p.lanes_per_row = 0;
+    p.reserved = 0;
     return p;
 }
 
@@ -296,8 +300,14 @@ esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t n
     SearchLaunch s;
     s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max;
     s.p = params ? *params : esg_search_params_default();
-    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0 || s.p.width < 0 || s.p.width > 4) {
-        esg_set_error("esg_search_batch: need 1 <= ef <= 1024 and 0 <= width <= 4");
+    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0 || s.p.width < 0 || s.p.width > 4 ||
+        !(s.p.warps_per_block == 0 || s.p.warps_per_block == 1 || s.p.warps_per_block == 2 ||
+          s.p.warps_per_block == 4) ||
+        (s.p.hash_slots != 0 && (s.p.hash_slots < 1024 || s.p.hash_slots > 16384 ||
+                                 (s.p.hash_slots & (s.p.hash_slots - 1)))) ||
+        s.p.lanes_per_row < 0 || s.p.lanes_per_row > 32 ||
+        (s.p.lanes_per_row & (s.p.lanes_per_row - 1))) {
+        esg_set_error("esg_search_batch: search parameter out of range");
         return ESG_ERR_INVALID_ARG;
     }
     s.out_ids = out_ids; s.out_dist = out_dist; s.out_count = out_count;

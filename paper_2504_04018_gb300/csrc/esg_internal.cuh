@@ -79,6 +79,22 @@ esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, 
                                 int64_t nq, esg_piece *pieces, int32_t *npieces,
                                 cudaStream_t stream);
 esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream);
+
+// Launch plan of one search call (kernel, shape, shared memory, scratch).
+struct SearchPlan {
+    void *fn;
+    const void *Xt;       // traversal rows
+    int vpl, lpr, C, H, G, wpb, nvec, width, BB, ef, efk;
+    size_t smem;
+    int64_t grid, n_items;
+    size_t scratch_bytes;
+};
+// Validate and plan a search; scratch_bytes tells how much device scratch
+// esg_search_enqueue needs.
+esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan);
+// Enqueue the search on `stream` using caller-provided scratch (no allocation).
+esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, void *scratch,
+                              cudaStream_t stream);
 esg_status esg_launch_bruteforce(const float *base, int64_t n, int32_t d, int metric,
                                  const float *queries, int64_t nq, const int64_t *l,
                                  const int64_t *r, int32_t k, int64_t *out_ids, float *out_dist,

@@ -116,52 +116,60 @@ int env_int(const char *name, int dflt) {
     return v && *v ? atoi(v) : dflt;
 }
 
-// Launch shape and shared-memory plan of the beam-search kernel.
-struct SearchPlan {
-    SearchFn fn;
-    int vpl, lpr, C, H, G, wpb, nvec, width, BB;
-    size_t smem;
-    int64_t grid;
-};
-
 }  // namespace
 int esg_pick_vpl(int d, int *lpr);
+int esg_vpl_for_lpr(int nvec, int lpr);
 namespace {
 
-esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, SearchPlan &pl) {
+// Kernel, launch shape and shared memory for a search (or construction)
+// call; knobs left at 0 are chosen automatically.
+esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, int wpb_req,
+                     int hash_req, int lpr_req, SearchPlan &pl) {
     pl.width = std::max(1, std::min(width, 4));
     pl.BB = 64;
     while (pl.BB < pl.width * R) pl.BB <<= 1;
     const int esize = st == ESG_BF16 ? 2 : (st == ESG_FP8E4M3 ? 1 : 4);
     if ((d * esize) % 16 != 0 || d % 4 != 0) { esg_set_error("row size not a multiple of 16 bytes"); return ESG_ERR_UNSUPPORTED; }
     pl.nvec = d * esize / 16;
-    pl.vpl = esg_pick_vpl(pl.nvec * 4, &pl.lpr);
-    if (pl.vpl == 0) { esg_set_error("unsupported dimension"); return ESG_ERR_UNSUPPORTED; }
+    if (lpr_req > 0) {
+        pl.lpr = lpr_req;
+        pl.vpl = esg_vpl_for_lpr(pl.nvec, lpr_req);
+    } else {
+        pl.vpl = esg_pick_vpl(pl.nvec * 4, &pl.lpr);
+    }
+    if (pl.vpl == 0) { esg_set_error("unsupported dimension / lanes per row"); return ESG_ERR_UNSUPPORTED; }
     if (R > 128) { esg_set_error("R > 128"); return ESG_ERR_UNSUPPORTED; }
-    pl.fn = pick_search(st, pl.vpl);
-    if (pl.fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
+    SearchFn fn = pick_search(st, pl.vpl);
+    if (fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
+    pl.fn = (void *)fn;
     pl.C = ((std::max(8 * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
     // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
     // the global overflow table takes what does not fit
-    const int per_ef = env_int("ESG_HASH_PER_EF", 64);
-    const int hmax = env_int("ESG_HASH_MAX", 8192);
-    pl.H = 2048;
-    while (pl.H < per_ef * efk && pl.H < hmax) pl.H <<= 1;
+    if (hash_req > 0) {
+        pl.H = hash_req;
+    } else {
+        const int per_ef = env_int("ESG_HASH_PER_EF", 64);
+        const int hmax = env_int("ESG_HASH_MAX", 8192);
+        pl.H = 2048;
+        while (pl.H < per_ef * efk && pl.H < hmax) pl.H <<= 1;
+    }
     while (pl.H < 4 * R) pl.H <<= 1;
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
-    pl.wpb = 2;
+    pl.wpb = wpb_req > 0 ? wpb_req : 2;
     pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 16 + (size_t)pl.BB * 12 + 32 * 8 + 16 +
                (((size_t)d * 4 + 15) & ~(size_t)15)) * pl.wpb;
     int dev = 0, sms = 0, per_sm = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ESG_CUDA_TRY(cudaFuncSetAttribute(pl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.fn, pl.wpb * 32, pl.smem));
+    if (pl.smem > 227 * 1024) { esg_set_error("search plan needs too much shared memory"); return ESG_ERR_UNSUPPORTED; }
+    ESG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, pl.wpb * 32, pl.smem));
     if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
     pl.grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + pl.wpb - 1) / pl.wpb);
     if (pl.grid < 1) pl.grid = 1;
+    pl.n_items = n_items;
     return ESG_OK;
 }
 
@@ -182,6 +190,14 @@ int esg_pick_vpl(int d, int *lpr) {
     return 0;
 }
 
+// Vectors per lane when `lpr` lanes share a row of `nvec` 16-byte vectors
+// (0 if that split is not supported).
+int esg_vpl_for_lpr(int nvec, int lpr) {
+    if (lpr < 1 || lpr > 32 || (lpr & (lpr - 1)) || nvec % lpr) return 0;
+    const int v = nvec / lpr;
+    return (v == 1 || v == 2 || v == 3 || v == 4 || v == 6 || v == 8) ? v : 0;
+}
+
 esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
                                 int64_t nq, esg_piece *pieces, int32_t *npieces, cudaStream_t stream) {
     if (nq == 0) return ESG_OK;
@@ -190,87 +206,107 @@ esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, 
     return ESG_OK;
 }
 
-esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
+namespace {
+struct ScratchLayout {
+    size_t pieces, kq, qs, res, cnt, stats, hash, queue, total;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) {
+    const int64_t n_items = 2 * nq;
+    ScratchLayout L;
+    size_t off = 0;
+    L.pieces = off; off += al256(sizeof(esg_piece) * n_items);
+    L.kq = off; off += al256(sizeof(int32_t) * nq);
+    L.qs = off; off += al256(sizeof(int32_t) * nq);
+    L.res = off; off += al256(sizeof(Cand) * n_items * k_max);
+    L.cnt = off; off += al256(sizeof(int32_t) * n_items * 2);
+    L.stats = off; off += al256(sizeof(int64_t) * n_items * 4);
+    L.hash = off; off += al256((size_t)plan.grid * plan.wpb * plan.G * 4);
+    L.queue = off; off += 256;
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     const esg_index *ix = s.ix;
-    if (s.nq == 0) return ESG_OK;
-    int ef = std::max(s.p.ef, 1);
+    const int ef = std::max(s.p.ef, 1);
     if (ef > 1024) { esg_set_error("ef > 1024"); return ESG_ERR_INVALID_ARG; }
     const int efk = std::max(ef, s.k_max);
-    const int64_t n_items = 2 * s.nq;
-    SearchPlan plan;
     const int st_trav = s.p.traversal;
     const void *Xt = ix->X;
     if (st_trav == ESG_BF16) Xt = ix->Xb;
     else if (st_trav == ESG_FP8E4M3) Xt = ix->X8;
     else if (st_trav != ESG_F32) { esg_set_error("unknown traversal type"); return ESG_ERR_INVALID_ARG; }
     if (Xt == nullptr) { esg_set_error("index has no rows of the requested traversal type (build with that storage)"); return ESG_ERR_INVALID_ARG; }
-    esg_status pst = make_plan(ix->d, ix->R, efk, n_items, st_trav, s.p.width, plan);
+    esg_status pst = make_plan(ix->d, ix->R, efk, 2 * std::max<int64_t>(s.nq, 1), st_trav, s.p.width,
+                               s.p.warps_per_block, s.p.hash_slots, s.p.lanes_per_row, plan);
     if (pst != ESG_OK) return pst;
-    const int wpb = plan.wpb;
-    const int64_t grid = plan.grid;
+    plan.Xt = Xt;
+    plan.ef = ef;
+    plan.efk = efk;
+    plan.scratch_bytes = scratch_layout(std::max<int64_t>(s.nq, 1), s.k_max, plan).total;
+    return ESG_OK;
+}
 
-    // scratch: pieces, k, status, per-item results, global visited sets
-    size_t bytes_pieces = sizeof(esg_piece) * n_items;
-    size_t bytes_kq = sizeof(int32_t) * s.nq;
-    size_t bytes_qs = sizeof(int32_t) * s.nq;
-    size_t bytes_res = sizeof(Cand) * n_items * s.k_max;
-    size_t bytes_cnt = sizeof(int32_t) * n_items * 2;
-    size_t bytes_stats = sizeof(int64_t) * n_items * 4;
-    size_t bytes_hash = (size_t)grid * wpb * plan.G * 4;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t total = al(bytes_pieces) + al(bytes_kq) + al(bytes_qs) + al(bytes_res) + al(bytes_cnt) +
-                   al(bytes_stats) + al(bytes_hash) + 256;
-    unsigned char *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, total, stream));
-    unsigned char *p = scratch;
-    esg_piece *pieces = (esg_piece *)p; p += al(bytes_pieces);
-    int32_t *kq = (int32_t *)p; p += al(bytes_kq);
-    int32_t *qs = (int32_t *)p; p += al(bytes_qs);
-    Cand *res = (Cand *)p; p += al(bytes_res);
-    int32_t *res_cnt = (int32_t *)p;
+esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, void *scratch_v,
+                              cudaStream_t stream) {
+    const esg_index *ix = s.ix;
+    if (s.nq == 0) return ESG_OK;
+    const int64_t n_items = 2 * s.nq;
+    const ScratchLayout L = scratch_layout(s.nq, s.k_max, plan);
+    unsigned char *scratch = (unsigned char *)scratch_v;
+    esg_piece *pieces = (esg_piece *)(scratch + L.pieces);
+    int32_t *kq = (int32_t *)(scratch + L.kq);
+    int32_t *qs = (int32_t *)(scratch + L.qs);
+    Cand *res = (Cand *)(scratch + L.res);
+    int32_t *res_cnt = (int32_t *)(scratch + L.cnt);
     int32_t *res_status = res_cnt + n_items;
-    p += al(bytes_cnt);
-    int64_t *res_stats = (int64_t *)p; p += al(bytes_stats);
-    uint32_t *ghash = (uint32_t *)p; p += al(bytes_hash);
-    unsigned long long *queue = (unsigned long long *)p;
+    int64_t *res_stats = (int64_t *)(scratch + L.stats);
+    uint32_t *ghash = (uint32_t *)(scratch + L.hash);
+    unsigned long long *queue = (unsigned long long *)(scratch + L.queue);
+    const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
 
-    esg_status st = ESG_OK;
-    cudaError_t ce = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream);
-    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    if (st == ESG_OK) {
-        prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(ix->n, ix->leaf_size, s.l, s.r, s.k,
-                                                               s.k_max, s.nq, pieces, kq, qs);
-        ce = cudaGetLastError();
-        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    }
-    if (st == ESG_OK) {
-        SearchArgs a;
-        a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
-        a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
-        a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
-        a.d = ix->d; a.nvec = plan.nvec; a.R = ix->R; a.E = ix->E;
-        a.Xv = reinterpret_cast<const uint4 *>(Xt); a.scale8 = ix->scale8; a.rerank = s.p.rerank;
-        a.width = plan.width; a.BB = plan.BB;
-        a.metric = ix->metric; a.ef = ef; a.LPR = plan.lpr;
-        a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * ef + 256;
-        a.k_max = s.k_max; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
-        a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
-        const int pidx = esg_prof_begin(stream);
-        plan.fn<<<(unsigned)grid, wpb * 32, plan.smem, stream>>>(a);
-        ce = cudaGetLastError();
-        esg_prof_end(pidx, stream);
-        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    }
-    if (st == ESG_OK) {
-        esg_prof_count(3);  // prep, search, merge
-        merge_kernel<<<ceil_div_i(s.nq, 128), 128, 0, stream>>>(
-            s.nq, s.k_max, kq, res, res_cnt, res_status, res_stats, qs, ix->perm, pieces,
-            s.out_ids, s.out_dist, s.out_count, s.out_status, s.out_stats);
-        ce = cudaGetLastError();
-        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    }
-    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    ESG_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
+    ESG_CUDA_TRY(cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream));
+    prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(ix->n, ix->leaf_size, s.l, s.r, s.k,
+                                                           s.k_max, s.nq, pieces, kq, qs);
+    ESG_CUDA_TRY(cudaGetLastError());
+    SearchArgs a;
+    a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
+    a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
+    a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
+    a.d = ix->d; a.nvec = plan.nvec; a.R = ix->R; a.E = ix->E;
+    a.Xv = reinterpret_cast<const uint4 *>(plan.Xt); a.scale8 = ix->scale8; a.rerank = s.p.rerank;
+    a.width = plan.width; a.BB = plan.BB; a.LPR = plan.lpr;
+    a.metric = ix->metric; a.ef = plan.ef;
+    a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * plan.ef + 256;
+    a.k_max = s.k_max; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
+    a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
+    const int pidx = esg_prof_begin(stream);
+    ((SearchFn)plan.fn)<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
+    const cudaError_t ce = cudaGetLastError();
+    esg_prof_end(pidx, stream);
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
+    esg_prof_count(3);  // prep, search, merge
+    merge_kernel<<<ceil_div_i(s.nq, 128), 128, 0, stream>>>(
+        s.nq, s.k_max, kq, res, res_cnt, res_status, res_stats, qs, ix->perm, pieces,
+        s.out_ids, s.out_dist, s.out_count, s.out_status, s.out_stats);
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
+esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
+    if (s.nq == 0) return ESG_OK;
+    SearchPlan plan;
+    esg_status st = esg_search_prepare(s, plan);
+    if (st != ESG_OK) return st;
+    void *scratch = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync(&scratch, plan.scratch_bytes, stream));
+    st = esg_search_enqueue(s, plan, scratch, stream);
+    const cudaError_t fe = cudaFreeAsync(scratch, stream);
     if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }
     return st;
 }
@@ -285,7 +321,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
     SearchPlan plan;
-    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, 1, plan);
+    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, 1, 0, 0, 0, plan);
     if (pst != ESG_OK) return pst;
     const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
     unsigned char *scratch = nullptr;
@@ -305,7 +341,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
         a.metric = metric; a.ef = ef; a.max_exp = max_exp > 0 ? max_exp : 16 * ef + 256;
         a.k_max = k; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
-        plan.fn<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
+        ((SearchFn)plan.fn)<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }

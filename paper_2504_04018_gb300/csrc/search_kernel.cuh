@@ -336,7 +336,7 @@ struct SearchArgs {
 };
 
 template <int ST, int VPL>
-__global__ void __launch_bounds__(64, 8)
+__global__ void __launch_bounds__(128, 4)
 search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;

@@ -1,0 +1,78 @@
+"""Batched CUDA-graph executor, launch-shape knobs and the autotuner."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic
+
+torch = pytest.importorskip("torch")
+E = pytest.importorskip("paper_2504_04018_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    w = synthetic.small_mixture(8000, 32, 300, n_comp=16, seed=13, M=12, leaf_size=64)
+    gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
+    dev = torch.device("cuda:0")
+    t = {"q": torch.as_tensor(w.queries, device=dev), "l": torch.as_tensor(w.l, device=dev),
+         "r": torch.as_tensor(w.r, device=dev)}
+    return w, gix, t
+
+
+def _search(gix, t, params, k_max=10):
+    out = E.esg_search_batch(gix, t["q"], t["l"], t["r"], None, k_max, params=params)
+    torch.cuda.synchronize()
+    return out[0].cpu().numpy(), out[1].cpu().numpy(), out[2].cpu().numpy()
+
+
+def test_launch_shape_knobs_do_not_change_results(setup):
+    w, gix, t = setup
+    ref = _search(gix, t, E.search_params(ef=32))
+    for wpb in (1, 2, 4):
+        for hs in (1024, 4096, 16384):
+            for lpr in (0, 1, 2, 4, 8):
+                got = _search(gix, t, E.search_params(ef=32, warps_per_block=wpb, hash_slots=hs,
+                                                      lanes_per_row=lpr))
+                assert np.array_equal(got[0], ref[0]) and np.array_equal(got[2], ref[2])
+                assert np.allclose(got[1], ref[1], rtol=1e-6, atol=1e-6)
+
+
+def test_batch_graph_matches_direct_search(setup):
+    w, gix, t = setup
+    params = E.search_params(ef=24)
+    ref_ids, ref_d, ref_c = _search(gix, t, params)
+    b = E.Batch(gix, max_nq=400, k_max=10, params=params)
+    nq = len(w.queries)
+    for run_nq in (nq, 100, nq):                 # two graphs, one replayed
+        b.view("queries", (len(w.queries), w.d), torch.float32)[:run_nq].copy_(t["q"][:run_nq])
+        b.view("l", (len(w.queries),), torch.int64)[:run_nq].copy_(t["l"][:run_nq])
+        b.view("r", (len(w.queries),), torch.int64)[:run_nq].copy_(t["r"][:run_nq])
+        b.run(run_nq)
+        torch.cuda.synchronize()
+        ids = b.view("ids", (run_nq, 10), torch.int64).cpu().numpy()
+        cnt = b.view("count", (run_nq,), torch.int32).cpu().numpy()
+        assert np.array_equal(ids, ref_ids[:run_nq])
+        assert np.array_equal(cnt, ref_c[:run_nq])
+    b.close()
+
+
+def test_autotune_meets_target(setup):
+    w, gix, t = setup
+    _, _, perm = E.esg_index_export(gix)
+    X = w.base[perm].astype(np.float64)
+    gt = np.full((len(w.queries), 10), -1, np.int64)
+    gc = np.zeros(len(w.queries), np.int32)
+    for i in range(len(w.queries)):
+        ids, _ = O.bruteforce(X, w.queries[i], int(w.l[i]), int(w.r[i]), 10, w.metric)
+        gt[i, :len(ids)] = perm[ids]
+        gc[i] = len(ids)
+    dev = torch.device("cuda:0")
+    params, rec, ms = E.esg_autotune(gix, t["q"], t["l"], t["r"], torch.as_tensor(gt, device=dev),
+                                     torch.as_tensor(gc, device=dev), k_max=10, target_recall=0.97)
+    assert rec >= 0.97 and ms > 0
+    assert 1 <= params.ef <= 1024 and params.width in (1, 2)
+    ids, _, cnt = _search(gix, t, params)
+    hits = sum(len(set(ids[i, :cnt[i]].tolist()) & set(gt[i, :gc[i]].tolist())) for i in range(len(gc)))
+    assert hits / gc.sum() >= 0.97
