@@ -33,8 +33,12 @@ def test_launch_shape_knobs_do_not_change_results(setup):
     for wpb in (1, 2, 4):
         for hs in (1024, 4096, 16384):
             for lpr in (0, 1, 2, 4, 8):
-                got = _search(gix, t, E.search_params(ef=32, warps_per_block=wpb, hash_slots=hs,
-                                                      lanes_per_row=lpr))
+                try:
+                    got = _search(gix, t, E.search_params(ef=32, warps_per_block=wpb, hash_slots=hs,
+                                                          lanes_per_row=lpr))
+                except E.EsgError as e:       # shape that does not fit (shared memory, row split)
+                    assert "unsupported" in str(e)
+                    continue
                 assert np.array_equal(got[0], ref[0]) and np.array_equal(got[2], ref[2])
                 assert np.allclose(got[1], ref[1], rtol=1e-6, atol=1e-6)
 
