@@ -250,6 +250,30 @@ esg_status esg_search_batch(const esg_index *index, const float *queries, int64_
                             esg_stream_t stream);
 
 /*
+ * esg_search_batch without any device allocation (no counterpart in the
+ * paper; a deployment aid). For callers that cannot call cudaMalloc or
+ * cudaMallocAsync while searching: processes whose GPU memory is owned by
+ * another allocator (a framework's caching pool or a fixed budget), and code
+ * that must not allocate on a latency-critical path. Same arguments, results
+ * and asynchrony as esg_search_batch; the scratch memory comes from one fixed
+ * 64 MiB array in device global memory inside this library, which every GPU
+ * that loads the library holds until the process exits. Limits: a batch
+ * whose scratch cannot fit in 64 MiB is rejected with ESG_ERR_INVALID_ARG
+ * (scratch grows with nq * k_max; about 350 bytes per query at k_max = 10
+ * plus the visited-set overflow tables, which shrink by running fewer
+ * concurrent warps before a batch is refused). The first call on each device
+ * looks the array's device address up once (make it before any stream
+ * capture). All calls on a device share the array: calls whose GPU work
+ * overlaps in time (different streams, or concurrent host threads) race and
+ * corrupt each other's results; serialise them.
+ */
+esg_status esg_search_batch_noalloc(const esg_index *index, const float *queries, int64_t nq,
+                                    const int64_t *l, const int64_t *r, const int32_t *k,
+                                    int32_t k_max, const esg_search_params *params,
+                                    int64_t *out_ids, float *out_dist, int32_t *out_count,
+                                    int32_t *out_status, int64_t *out_stats, esg_stream_t stream);
+
+/*
  * Batched search replayed as one CUDA graph. A batch owns device buffers for
  * up to max_nq queries (inputs: queries [max_nq, d] f32, l, r [max_nq] int64,
  * k [max_nq] int32; outputs as in esg_search_batch, stats [max_nq, 5]) and the

@@ -34,7 +34,7 @@ EXPORTED = [
     "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
-    "esg_batch_run", "esg_batch_free", "esg_autotune",
+    "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
 ]
 
 
@@ -98,6 +98,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
     lib.esg_profile_enable.argtypes = [_I32]
     lib.esg_profile_read.argtypes = [_P, _P, _P, _I32]
+    lib.esg_search_batch_noalloc.argtypes = [_P, _P, _I64, _P, _P, _P, _I32,
+                                             ctypes.POINTER(_SearchParams), _P, _P, _P, _P, _P, _P]
     lib.esg_batch_create.argtypes = [_P, _I64, _I32, _I32, ctypes.POINTER(_SearchParams), ctypes.POINTER(_P)]
     lib.esg_batch_buffers.argtypes = [_P] + [ctypes.POINTER(_P)] * 9
     lib.esg_batch_run.argtypes = [_P, _I64, _P]
@@ -112,7 +114,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
                  "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage",
-                 "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune"]:
+                 "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune",
+                 "esg_search_batch_noalloc"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -426,3 +429,19 @@ def esg_autotune(index: Index, queries, l, r, gt_ids, gt_count, k_max: int = 10,
                             float(target_recall), ctypes.byref(b), ctypes.byref(out), _np_ptr(rep),
                             _stream_ptr(stream)), "esg_autotune")
     return out, float(rep[0]), float(rep[1])
+
+
+def esg_search_batch_noalloc(index: Index, queries, l, r, out, k=None, k_max: int = 10,
+                             params=None, stream=None):
+    """esg_search_batch with no device allocation: scratch comes from the
+    library's fixed device array. `out` = (ids, dist, count, status or None,
+    stats or None) caller-allocated CUDA tensors."""
+    lib = load_library()
+    ids, dist, count, status, stats = out
+    p = params if params is not None else search_params()
+    _check(lib.esg_search_batch_noalloc(index.handle, _dev_ptr(queries), queries.shape[0],
+                                        _dev_ptr(l), _dev_ptr(r), _dev_ptr(k), k_max, ctypes.byref(p),
+                                        _dev_ptr(ids), _dev_ptr(dist), _dev_ptr(count),
+                                        _dev_ptr(status), _dev_ptr(stats), _stream_ptr(stream)),
+           "esg_search_batch_noalloc")
+    return out

@@ -92,6 +92,10 @@ struct SearchPlan {
 // Validate and plan a search; scratch_bytes tells how much device scratch
 // esg_search_enqueue needs.
 esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan);
+// As esg_search_prepare, but shrink the persistent grid (fewer concurrent
+// warps; results do not depend on it) until the scratch fits in max_scratch
+// bytes. ESG_ERR_INVALID_ARG if it cannot fit even with one block.
+esg_status esg_search_prepare_capped(const SearchLaunch &s, size_t max_scratch, SearchPlan &plan);
 // Enqueue the search on `stream` using caller-provided scratch (no allocation).
 esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, void *scratch,
                               cudaStream_t stream);

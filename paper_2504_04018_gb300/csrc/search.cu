@@ -251,6 +251,21 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     return ESG_OK;
 }
 
+esg_status esg_search_prepare_capped(const SearchLaunch &s, size_t max_scratch, SearchPlan &plan) {
+    esg_status st = esg_search_prepare(s, plan);
+    if (st != ESG_OK) return st;
+    const int64_t nq = std::max<int64_t>(s.nq, 1);
+    while (plan.scratch_bytes > max_scratch && plan.grid > 1) {
+        plan.grid = std::max<int64_t>(1, plan.grid / 2);
+        plan.scratch_bytes = scratch_layout(nq, s.k_max, plan).total;
+    }
+    if (plan.scratch_bytes > max_scratch) {
+        esg_set_error("batch too large for the fixed scratch array (reduce nq or k_max)");
+        return ESG_ERR_INVALID_ARG;
+    }
+    return ESG_OK;
+}
+
 esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, void *scratch_v,
                               cudaStream_t stream) {
     const esg_index *ix = s.ix;
