@@ -310,6 +310,70 @@ esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq
                         esg_search_params *out, float *report, esg_stream_t stream);
 
 /*
+ * Learned search budget (no counterpart in the paper). A small MLP
+ * (8 query features -> 64 -> 64 -> 2, ReLU) predicts for each query log2 of
+ * the beam width ef and of an expansion budget; the search uses them when
+ * esg_search_params.use_learned is 1 and a predictor is trained (otherwise
+ * the fixed ef). Features: log2 range width, number of pieces, log2 of each
+ * piece's node size over its size, whether the first piece is a graph piece,
+ * log2 k, min / mean distance to the first piece's entry points, log2 of the
+ * first piece's node size.
+ *
+ * esg_train_predictor: traces the plain search (fixed ef over a grid within
+ * [ef_lo, ef_hi]) on training queries with exact answers (gt_ids device
+ * [nq, k_max] original ids, -1 padded; gt_count device [nq]); labels each
+ * query with the smallest ef whose recall reaches per_query_recall and the
+ * expansions it used; trains the MLP with a pinball loss at `quantile` using
+ * the library's GPU forward/backward/Adam kernels (epochs, batch, lr, seed);
+ * then calibrates a margin on the last val_fraction of the queries so their
+ * mean recall reaches target_recall. report (may be NULL) receives
+ * [final training loss, held-out recall, ef margin (log2), held-out distance
+ * evaluations per query]. Synchronous. ESG_ERR_UNSUPPORTED if no margin
+ * reaches the target.
+ */
+typedef struct {
+    float target_recall;     /* mean recall@k to reach on held-out queries (0.95) */
+    float per_query_recall;  /* label threshold per training query (1.0) */
+    float quantile;          /* pinball quantile (0.9) */
+    float lr;                /* Adam learning rate (1e-3) */
+    float val_fraction;      /* held-out share for calibration (0.2) */
+    int32_t epochs;          /* (60) */
+    int32_t batch;           /* (1024) */
+    int32_t ef_lo, ef_hi;    /* predicted ef range (8, 128) */
+    esg_dtype traversal;     /* rows the traced and predicted searches use */
+    uint64_t seed;           /* initial weights and minibatch order */
+} esg_train_params;
+
+esg_train_params esg_train_params_default(void);
+esg_status esg_train_predictor(esg_index *index, const float *queries, int64_t nq, const int64_t *l,
+                               const int64_t *r, const int32_t *k, int32_t k_max,
+                               const int64_t *gt_ids, const int32_t *gt_count,
+                               const esg_train_params *params, float *report, esg_stream_t stream);
+
+/* Trained predictor as a host blob [params, mu[8], sigma[8], margin_ef,
+ * margin_expansions] (esg_mlp_num_params() + 18 floats) with its ef range;
+ * set installs one (e.g. a saved one), get reads it back. */
+esg_status esg_predictor_set(esg_index *index, const float *blob, int32_t ef_lo, int32_t ef_hi);
+esg_status esg_predictor_get(const esg_index *index, float *blob, int32_t *ef_lo, int32_t *ef_hi);
+
+/* The MLP's own GPU kernels, exposed for checking: parameter count; forward
+ * y [B, 2] = f(X [B, 8]) with standardisation mu, sigma [8]; pinball loss and
+ * its gradient [num_params] (deterministic order); one Adam step (beta1 0.9,
+ * beta2 0.999, eps 1e-8) at step >= 1; and the query features [nq, 8]. Device
+ * pointers, asynchronous (loss, a host pointer, makes loss_grad synchronous). */
+int32_t esg_mlp_num_params(void);
+esg_status esg_mlp_forward(const float *params, const float *X, const float *mu, const float *sigma,
+                           int64_t B, float *Y, esg_stream_t stream);
+esg_status esg_mlp_loss_grad(const float *params, const float *X, const float *T, const float *mu,
+                             const float *sigma, int64_t B, float quantile, float *grad, float *loss,
+                             esg_stream_t stream);
+esg_status esg_mlp_adam_step(float *params, const float *grad, float *m, float *v, int32_t step,
+                             float lr, esg_stream_t stream);
+esg_status esg_query_features(const esg_index *index, const float *queries, int64_t nq,
+                              const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
+                              float *features, esg_stream_t stream);
+
+/*
  * Exact range-filtered k-NN by brute force (Definitions 1 and 2): for each
  * query the min(k, r - l + 1) rows of `base` with row index in [l, r] closest
  * to q, ordered by (distance, row). Distances are evaluated in float32 in

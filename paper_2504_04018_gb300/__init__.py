@@ -35,6 +35,9 @@ EXPORTED = [
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
+    "esg_train_params_default", "esg_train_predictor", "esg_predictor_set", "esg_predictor_get",
+    "esg_mlp_num_params", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
+    "esg_query_features",
 ]
 
 
@@ -47,6 +50,13 @@ class _BuildParams(ctypes.Structure):
                 ("ef_construction", ctypes.c_int32), ("batch_div", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("metric", ctypes.c_int32),
                 ("storage", ctypes.c_int32)]
+
+
+class _TrainParams(ctypes.Structure):
+    _fields_ = [("target_recall", ctypes.c_float), ("per_query_recall", ctypes.c_float),
+                ("quantile", ctypes.c_float), ("lr", ctypes.c_float), ("val_fraction", ctypes.c_float),
+                ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("ef_lo", ctypes.c_int32),
+                ("ef_hi", ctypes.c_int32), ("traversal", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class _SearchParams(ctypes.Structure):
@@ -98,6 +108,16 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
     lib.esg_profile_enable.argtypes = [_I32]
     lib.esg_profile_read.argtypes = [_P, _P, _P, _I32]
+    lib.esg_train_params_default.restype = _TrainParams
+    lib.esg_train_predictor.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _P, _P,
+                                        ctypes.POINTER(_TrainParams), _P, _P]
+    lib.esg_predictor_set.argtypes = [_P, _P, _I32, _I32]
+    lib.esg_predictor_get.argtypes = [_P, _P, _P, _P]
+    lib.esg_mlp_num_params.restype = _I32
+    lib.esg_mlp_forward.argtypes = [_P, _P, _P, _P, _I64, _P, _P]
+    lib.esg_mlp_loss_grad.argtypes = [_P, _P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]
+    lib.esg_mlp_adam_step.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_float, _P]
+    lib.esg_query_features.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _P, _P]
     lib.esg_search_batch_noalloc.argtypes = [_P, _P, _I64, _P, _P, _P, _I32,
                                              ctypes.POINTER(_SearchParams), _P, _P, _P, _P, _P, _P]
     lib.esg_batch_create.argtypes = [_P, _I64, _I32, _I32, ctypes.POINTER(_SearchParams), ctypes.POINTER(_P)]
@@ -115,7 +135,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
                  "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage",
                  "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune",
-                 "esg_search_batch_noalloc"]:
+                 "esg_search_batch_noalloc", "esg_train_predictor", "esg_predictor_set",
+                 "esg_predictor_get", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
+                 "esg_query_features"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -445,3 +467,71 @@ def esg_search_batch_noalloc(index: Index, queries, l, r, out, k=None, k_max: in
                                         _dev_ptr(status), _dev_ptr(stats), _stream_ptr(stream)),
            "esg_search_batch_noalloc")
     return out
+
+
+def esg_train_predictor(index: Index, queries, l, r, gt_ids, gt_count, k_max: int = 10, k=None,
+                        stream=None, **overrides):
+    """Train and calibrate the learned search budget on CUDA tensors of
+    queries with exact answers. Returns [train loss, held-out recall, ef
+    margin, held-out distance evaluations per query]."""
+    lib = load_library()
+    tp = lib.esg_train_params_default()
+    for key, v in overrides.items():
+        setattr(tp, key, STORAGE[v] if key == "traversal" and isinstance(v, str) else v)
+    rep = np.zeros(4, dtype=np.float32)
+    _check(lib.esg_train_predictor(index.handle, _dev_ptr(queries), queries.shape[0], _dev_ptr(l),
+                                   _dev_ptr(r), _dev_ptr(k), k_max, _dev_ptr(gt_ids), _dev_ptr(gt_count),
+                                   ctypes.byref(tp), _np_ptr(rep), _stream_ptr(stream)),
+           "esg_train_predictor")
+    return rep
+
+
+def esg_predictor_get(index: Index):
+    lib = load_library()
+    blob = np.empty(lib.esg_mlp_num_params() + 18, dtype=np.float32)
+    lo, hi = _I32(), _I32()
+    _check(lib.esg_predictor_get(index.handle, _np_ptr(blob), ctypes.byref(lo), ctypes.byref(hi)),
+           "esg_predictor_get")
+    return blob, lo.value, hi.value
+
+
+def esg_predictor_set(index: Index, blob: np.ndarray, ef_lo: int, ef_hi: int):
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    _check(load_library().esg_predictor_set(index.handle, _np_ptr(blob), ef_lo, ef_hi),
+           "esg_predictor_set")
+
+
+def esg_mlp_num_params() -> int:
+    return int(load_library().esg_mlp_num_params())
+
+
+def esg_mlp_forward(params, X, mu, sigma, stream=None):
+    import torch
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+    _check(load_library().esg_mlp_forward(_dev_ptr(params), _dev_ptr(X), _dev_ptr(mu), _dev_ptr(sigma),
+                                          X.shape[0], _dev_ptr(Y), _stream_ptr(stream)), "esg_mlp_forward")
+    return Y
+
+
+def esg_mlp_loss_grad(params, X, T, mu, sigma, quantile: float, stream=None):
+    import torch
+    g = torch.empty_like(params)
+    loss = ctypes.c_float()
+    _check(load_library().esg_mlp_loss_grad(_dev_ptr(params), _dev_ptr(X), _dev_ptr(T), _dev_ptr(mu),
+                                            _dev_ptr(sigma), X.shape[0], float(quantile), _dev_ptr(g),
+                                            ctypes.byref(loss), _stream_ptr(stream)), "esg_mlp_loss_grad")
+    return loss.value, g
+
+
+def esg_mlp_adam_step(params, grad, m, v, step: int, lr: float, stream=None):
+    _check(load_library().esg_mlp_adam_step(_dev_ptr(params), _dev_ptr(grad), _dev_ptr(m), _dev_ptr(v),
+                                            step, float(lr), _stream_ptr(stream)), "esg_mlp_adam_step")
+
+
+def esg_query_features(index: Index, queries, l, r, k=None, k_max: int = 10, stream=None):
+    import torch
+    f = torch.empty((queries.shape[0], 8), dtype=torch.float32, device=queries.device)
+    _check(load_library().esg_query_features(index.handle, _dev_ptr(queries), queries.shape[0],
+                                             _dev_ptr(l), _dev_ptr(r), _dev_ptr(k), k_max, _dev_ptr(f),
+                                             _stream_ptr(stream)), "esg_query_features")
+    return f

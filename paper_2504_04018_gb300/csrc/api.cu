@@ -112,6 +112,22 @@ esg_search_params esg_search_params_default(void) {
     return p;
 }
 
+esg_train_params esg_train_params_default(void) {
+    esg_train_params p;
+    p.target_recall = 0.95f;
+    p.per_query_recall = 1.0f;
+    p.quantile = 0.9f;
+    p.lr = 1e-3f;
+    p.val_fraction = 0.2f;
+    p.epochs = 60;
+    p.batch = 1024;
+    p.ef_lo = 8;
+    p.ef_hi = 128;
+    p.traversal = ESG_F32;
+    p.seed = 4005;
+    return p;
+}
+
 esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *attr,
                      const esg_build_params *params, esg_index **out) {
     if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
@@ -370,6 +386,8 @@ struct FileHeader {
     int64_t n;
     int64_t n_heap;
     uint64_t attr_count;
+    uint64_t mlp_count;       // floats of the learned predictor's blob (0: none)
+    int32_t mlp_ef_lo, mlp_ef_hi;
 };
 
 bool write_section(FILE *f, const void *data, size_t bytes) {
@@ -407,11 +425,14 @@ esg_status esg_save(const esg_index *ix, const char *path) {
     h.version = kVersion; h.d = ix->d; h.metric = ix->metric; h.storage = ix->storage;
     h.leaf_size = ix->leaf_size; h.L = ix->L; h.R = ix->R; h.E = ix->E; h.M = ix->M; h.n = ix->n;
     h.n_heap = ix->n_heap; h.attr_count = ix->attr_sorted.size();
+    h.mlp_count = ix->mlp_ready ? ix->mlp_host.size() : 0;
+    h.mlp_ef_lo = ix->mlp_ef_lo; h.mlp_ef_hi = ix->mlp_ef_hi;
     bool ok = write_section(f, &h, sizeof(h)) && write_section(f, X.data(), sizeof(float) * X.size()) &&
               write_section(f, ix->perm_host.data(), sizeof(int64_t) * ix->n) &&
               write_section(f, adj.data(), sizeof(uint32_t) * adj.size()) &&
               write_section(f, ent.data(), sizeof(int32_t) * ent.size()) &&
-              write_section(f, ix->attr_sorted.data(), sizeof(double) * ix->attr_sorted.size());
+              write_section(f, ix->attr_sorted.data(), sizeof(double) * ix->attr_sorted.size()) &&
+              write_section(f, ix->mlp_host.data(), sizeof(float) * h.mlp_count);
     ok = (fclose(f) == 0) && ok;
     if (!ok) { esg_set_error("esg_save: write failed"); return ESG_ERR_IO; }
     return ESG_OK;
@@ -428,17 +449,19 @@ esg_status esg_load(const char *path, esg_index **out) {
                         !dim_ok(h.d) || h.L < 0 || h.L > 30 || h.R < 1 || h.R > 128 || h.E < 1 ||
                         h.E > 32 || h.n_heap != (((int64_t)1 << h.L) - 1) ||
                         h.L != esg_graph_depths(h.n, h.leaf_size) ||
-                        (h.attr_count != 0 && h.attr_count != (uint64_t)h.n)))
+                        (h.attr_count != 0 && h.attr_count != (uint64_t)h.n) ||
+                        (h.mlp_count != 0 && h.mlp_count != (uint64_t)esg_mlp_param_count() + 2 * ESG_MLP_FEATURES + 2)))
         s = ESG_ERR_CORRUPT;
     std::vector<float> X;
     std::vector<int64_t> perm;
     std::vector<uint32_t> adj;
     std::vector<int32_t> ent;
     std::vector<double> attr;
+    std::vector<float> mlp;
     if (s == ESG_OK) {
         try {
             X.resize((size_t)h.n * h.d); perm.resize(h.n); adj.resize((size_t)h.L * h.n * h.R);
-            ent.resize((size_t)h.n_heap * h.E); attr.resize(h.attr_count);
+            ent.resize((size_t)h.n_heap * h.E); attr.resize(h.attr_count); mlp.resize(h.mlp_count);
         } catch (...) { s = ESG_ERR_OOM; }
     }
     if (s == ESG_OK) s = read_section(f, X.data(), sizeof(float) * X.size());
@@ -446,6 +469,7 @@ esg_status esg_load(const char *path, esg_index **out) {
     if (s == ESG_OK) s = read_section(f, adj.data(), sizeof(uint32_t) * adj.size());
     if (s == ESG_OK) s = read_section(f, ent.data(), sizeof(int32_t) * ent.size());
     if (s == ESG_OK) s = read_section(f, attr.data(), sizeof(double) * attr.size());
+    if (s == ESG_OK) s = read_section(f, mlp.data(), sizeof(float) * mlp.size());
     fclose(f);
     if (s != ESG_OK) {
         if (s == ESG_ERR_CORRUPT) esg_set_error("esg_load: file is not a valid index (header, size or CRC)");
@@ -457,6 +481,10 @@ esg_status esg_load(const char *path, esg_index **out) {
     if (s != ESG_OK) return s;
     ix->M = h.M;
     ix->attr_sorted.swap(attr);
+    if (!mlp.empty()) {
+        s = esg_predictor_set(ix, mlp.data(), h.mlp_ef_lo, h.mlp_ef_hi);
+        if (s != ESG_OK) { esg_free(ix); return s; }
+    }
     *out = ix;
     return ESG_OK;
 }

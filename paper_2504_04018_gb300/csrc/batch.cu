@@ -163,6 +163,13 @@ __global__ void recall_hits_kernel(int64_t nq, int32_t k_max, const int64_t *ids
 }
 }  // namespace
 
+esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int64_t *ids, const int32_t *cnt,
+                           const int64_t *gt, const int32_t *gcnt, int32_t *hits, cudaStream_t stream) {
+    recall_hits_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(nq, k_max, ids, cnt, gt, gcnt, hits);
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
 extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, int64_t nq,
                                    const int64_t *l, const int64_t *r, const int32_t *k,
                                    int32_t k_max, const int64_t *gt_ids, const int32_t *gt_count,

@@ -11,6 +11,7 @@
 #include "../../include/esg.h"
 
 #define ESG_NONE 0xFFFFFFFFu
+#define ESG_MLP_FEATURES 8
 #define ESG_EXPANDED 0x80000000u
 #define ESG_ID_MASK 0x7FFFFFFFu
 
@@ -50,9 +51,12 @@ struct esg_index {
     int64_t *perm = nullptr;         // [n] rank -> original id (device)
     std::vector<int64_t> perm_host;  // same on the host
     std::vector<double> attr_sorted; // sorted attribute values (host), may be empty
-    // learned beam-width predictor (device weights), null when untrained
+    // learned beam-width predictor: [params, mu, sigma, margins] on the
+    // device and the host; null / 0 when untrained
     float *mlp = nullptr;
+    std::vector<float> mlp_host;
     int32_t mlp_ready = 0;
+    int32_t mlp_ef_lo = 8, mlp_ef_hi = 128;
 };
 
 // Number of depths that hold at least one graph node.
@@ -85,6 +89,7 @@ struct SearchPlan {
     void *fn;
     const void *Xt;       // traversal rows
     int vpl, lpr, C, H, G, wpb, nvec, width, BB, ef, efk;
+    bool learned;         // per-query ef and expansion budget from the predictor
     size_t smem;
     int64_t grid, n_items;
     size_t scratch_bytes;
@@ -106,6 +111,15 @@ esg_status esg_launch_bruteforce(const float *base, int64_t n, int32_t d, int me
                                  cudaStream_t stream);
 esg_status esg_build_graphs(esg_index *ix, const esg_build_params &p, cudaStream_t stream);
 esg_status esg_make_storage(esg_index *ix, cudaStream_t stream);
+
+// learned predictor (mlp.cu): features + per-query ef and expansion budget
+int esg_mlp_param_count();
+esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+                              const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
+                              float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream);
+// per-query hits of returned ids against exact ids (batch.cu)
+esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int64_t *ids, const int32_t *cnt,
+                           const int64_t *gt, const int32_t *gcnt, int32_t *hits, cudaStream_t stream);
 
 // benchmark timing hooks (profile.cu)
 bool esg_prof_on();

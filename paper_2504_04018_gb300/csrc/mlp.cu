@@ -1,0 +1,352 @@
+// Learned search budget: a small MLP that predicts, per query, the beam
+// width ef and an expansion budget needed to reach a recall target, trained
+// on the GPU with this file's own forward, backward and Adam kernels from
+// traces of the plain fixed-ef search. The paper has no learned component.
+//
+// Network (F = 8 features):  x_hat = (x - mu) / sigma,
+//   h1 = relu(W1^T x_hat + b1) [64], h2 = relu(W2^T h1 + b2) [64],
+//   y = W3^T h2 + b3 [2] = (log2 ef, log2 expansion budget).
+// Loss: pinball (quantile q) averaged over rows and both outputs.
+// Flat parameters: W1 [F*64] row-major, b1 [64], W2 [64*64], b2 [64],
+// W3 [64*2], b3 [2].
+//
+// Features of a query (computed on the GPU from its range decomposition and
+// the distances to its first piece's entry points):
+//   0 log2 width, 1 number of pieces, 2/3 log2(node size / piece size) of
+//   piece 0 / 1, 4 piece 0 is a graph piece, 5 log2 k, 6 min / mean entry
+//   distance of piece 0 (1 for scans), 7 log2 node size of piece 0.
+#include "esg_internal.cuh"
+#include "decompose.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+constexpr int kF = ESG_MLP_FEATURES;
+constexpr int kH = 64;
+constexpr int kO = 2;
+constexpr int kP = kF * kH + kH + kH * kH + kH + kH * kO + kO;
+
+namespace {
+
+struct MlpView {
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+
+__host__ __device__ inline MlpView view(const float *p) {
+    MlpView v;
+    v.W1 = p; p += kF * kH;
+    v.b1 = p; p += kH;
+    v.W2 = p; p += kH * kH;
+    v.b2 = p; p += kH;
+    v.W3 = p; p += kH * kO;
+    v.b3 = p;
+    return v;
+}
+
+// Forward pass of one row (params in shared memory); optionally keeps the
+// pre-activations of both hidden layers.
+__device__ inline void mlp_row(const float *sp, const float *xh, float *y, float *z1_out, float *z2_out) {
+    const MlpView v = view(sp);
+    float h1[kH];
+#pragma unroll 4
+    for (int j = 0; j < kH; ++j) {
+        float s = v.b1[j];
+#pragma unroll
+        for (int i = 0; i < kF; ++i) s = fmaf(xh[i], v.W1[i * kH + j], s);
+        if (z1_out) z1_out[j] = s;
+        h1[j] = fmaxf(s, 0.f);
+    }
+    float acc0 = v.b3[0], acc1 = v.b3[1];
+    for (int j = 0; j < kH; ++j) {
+        float s = v.b2[j];
+#pragma unroll 8
+        for (int i = 0; i < kH; ++i) s = fmaf(h1[i], v.W2[i * kH + j], s);
+        if (z2_out) z2_out[j] = s;
+        const float h2 = fmaxf(s, 0.f);
+        acc0 = fmaf(h2, v.W3[j * kO + 0], acc0);
+        acc1 = fmaf(h2, v.W3[j * kO + 1], acc1);
+    }
+    y[0] = acc0;
+    y[1] = acc1;
+}
+
+// Forward over B rows; stores y [B,2], z1 [B,64], z2 [B,64] when given.
+__global__ void mlp_forward_kernel(const float *params, const float *X, const float *mu,
+                                   const float *sigma, int64_t B, float *Y, float *Z1, float *Z2) {
+    __shared__ float sp[kP];
+    for (int i = threadIdx.x; i < kP; i += blockDim.x) sp[i] = params[i];
+    __syncthreads();
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float xh[kF];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) xh[i] = (X[b * kF + i] - mu[i]) / sigma[i];
+    float y[2];
+    mlp_row(sp, xh, y, Z1 ? Z1 + b * kH : nullptr, Z2 ? Z2 + b * kH : nullptr);
+    Y[b * 2 + 0] = y[0];
+    Y[b * 2 + 1] = y[1];
+}
+
+// Per-row error signals of the pinball loss: dY [B,2], dZ2 [B,64], dZ1 [B,64]
+// (scaled by 1 / (B * 2), the mean over rows and outputs).
+__global__ void mlp_delta_kernel(const float *params, const float *Y, const float *T, const float *Z1,
+                                 const float *Z2, int64_t B, float q, float *dY, float *dZ2, float *dZ1,
+                                 float *row_loss) {
+    __shared__ float sp[kP];
+    for (int i = threadIdx.x; i < kP; i += blockDim.x) sp[i] = params[i];
+    __syncthreads();
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const MlpView v = view(sp);
+    const float inv = 1.f / (float)(B * kO);
+    float dy[kO], loss = 0.f;
+#pragma unroll
+    for (int o = 0; o < kO; ++o) {
+        const float u = T[b * kO + o] - Y[b * kO + o];
+        loss += fmaxf(q * u, (q - 1.f) * u);
+        dy[o] = (u > 0.f ? -q : 1.f - q) * inv;
+        dY[b * kO + o] = dy[o];
+    }
+    row_loss[b] = loss;
+    float dz2[kH];
+    for (int j = 0; j < kH; ++j) {
+        const float g = dy[0] * v.W3[j * kO + 0] + dy[1] * v.W3[j * kO + 1];
+        dz2[j] = Z2[b * kH + j] > 0.f ? g : 0.f;
+        dZ2[b * kH + j] = dz2[j];
+    }
+    for (int i = 0; i < kH; ++i) {
+        float g = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < kH; ++j) g = fmaf(dz2[j], v.W2[i * kH + j], g);
+        dZ1[b * kH + i] = Z1[b * kH + i] > 0.f ? g : 0.f;
+    }
+}
+
+// Weight gradients as sums over rows (one thread per parameter, fixed row
+// order: deterministic).
+__global__ void mlp_wgrad_kernel(const float *X, const float *mu, const float *sigma, const float *Z1,
+                                 const float *Z2, const float *dZ1, const float *dZ2, const float *dY,
+                                 int64_t B, float *grad) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kP) return;
+    float g = 0.f;
+    int o = t;
+    if (o < kF * kH) {                       // W1[i][j] = sum_b xh[b,i] dZ1[b,j]
+        const int i = o / kH, j = o % kH;
+        for (int64_t b = 0; b < B; ++b) g = fmaf((X[b * kF + i] - mu[i]) / sigma[i], dZ1[b * kH + j], g);
+    } else if ((o -= kF * kH) < kH) {        // b1
+        for (int64_t b = 0; b < B; ++b) g += dZ1[b * kH + o];
+    } else if ((o -= kH) < kH * kH) {        // W2[i][j] = sum_b relu(z1[b,i]) dZ2[b,j]
+        const int i = o / kH, j = o % kH;
+        for (int64_t b = 0; b < B; ++b) g = fmaf(fmaxf(Z1[b * kH + i], 0.f), dZ2[b * kH + j], g);
+    } else if ((o -= kH * kH) < kH) {        // b2
+        for (int64_t b = 0; b < B; ++b) g += dZ2[b * kH + o];
+    } else if ((o -= kH) < kH * kO) {        // W3[i][o] = sum_b relu(z2[b,i]) dY[b,o]
+        const int i = o / kO, oo = o % kO;
+        for (int64_t b = 0; b < B; ++b) g = fmaf(fmaxf(Z2[b * kH + i], 0.f), dY[b * kO + oo], g);
+    } else {                                 // b3
+        o -= kH * kO;
+        for (int64_t b = 0; b < B; ++b) g += dY[b * kO + o];
+    }
+    grad[t] = g;
+}
+
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mi = b1 * m[i] + (1.f - b1) * g[i];
+    const float vi = b2 * v[i] + (1.f - b2) * g[i] * g[i];
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Features of each query (one warp per query).
+__global__ void features_kernel(const float *X, int d, int metric, int64_t n, int32_t leaf,
+                                const int32_t *entries, int E, const float *queries, int64_t nq,
+                                const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
+                                float *feat) {
+    const int lane = threadIdx.x & 31;
+    const int64_t qi = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (qi >= nq) return;
+    esg_piece pc[2];
+    const int64_t lq = l[qi], rq = r[qi];
+    const int np = esg_decompose_one(n, leaf, lq, rq, pc);
+    float f[kF];
+    for (int i = 0; i < kF; ++i) f[i] = 0.f;
+    if (np > 0) {
+        const double w = (double)(rq - lq + 1);
+        f[0] = (float)log2(w);
+        f[1] = (float)np;
+        for (int s = 0; s < np; ++s)
+            f[2 + s] = (float)(log2((double)(pc[s].node_r - pc[s].node_l + 1)) -
+                               log2((double)(pc[s].pr - pc[s].pl + 1)));
+        f[4] = pc[0].kind == ESG_PIECE_GRAPH ? 1.f : 0.f;
+        const int kk = k ? k[qi] : k_max;
+        f[5] = kk > 0 ? log2f((float)kk) : 0.f;
+        f[7] = (float)log2((double)(pc[0].node_r - pc[0].node_l + 1));
+        f[6] = 1.f;
+        if (pc[0].kind == ESG_PIECE_GRAPH) {
+            const float *q = queries + qi * (int64_t)d;
+            float dmin = INFINITY, dsum = 0.f;
+            int cnt = 0;
+            for (int e = 0; e < E; ++e) {
+                const int32_t v = entries[(size_t)pc[0].heap * E + e];
+                if (v < 0 || v >= n) continue;
+                const float *x = X + (size_t)v * d;
+                float acc = 0.f;
+                for (int j = lane; j < d; j += 32) {
+                    if (metric == ESG_L2SQ) { const float t = q[j] - x[j]; acc = fmaf(t, t, acc); }
+                    else acc = fmaf(q[j], x[j], acc);
+                }
+                acc = warp_sum_group(acc, 32);
+                const float dist = metric == ESG_L2SQ ? acc : -acc;
+                dmin = fminf(dmin, dist);
+                dsum += dist;
+                ++cnt;
+            }
+            if (cnt > 0) {
+                const float mean = dsum / cnt;
+                f[6] = fabsf(mean) > 1e-20f ? dmin / mean : 1.f;
+            }
+        }
+    }
+    if (lane == 0)
+        for (int i = 0; i < kF; ++i) feat[qi * kF + i] = f[i];
+}
+
+// ef and expansion budget per query from the trained network; invalid
+// predictions fall back to the fixed beam width.
+__global__ void predict_kernel(const float *blob, const float *feat, int64_t nq, const int32_t *k,
+                               int32_t k_max, int ef_fixed, int ef_lo, int ef_hi, int32_t *ef_q,
+                               int32_t *maxexp_q) {
+    __shared__ float sp[kP];
+    for (int i = threadIdx.x; i < kP; i += blockDim.x) sp[i] = blob[i];
+    __syncthreads();
+    const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (qi >= nq) return;
+    const float *mu = blob + kP, *sigma = blob + kP + kF, *margin = blob + kP + 2 * kF;
+    float xh[kF];
+    for (int i = 0; i < kF; ++i) xh[i] = (feat[qi * kF + i] - mu[i]) / sigma[i];
+    float y[2];
+    mlp_row(sp, xh, y, nullptr, nullptr);
+    const int kk = k ? k[qi] : k_max;
+    int ef = ef_fixed, mx = 0;
+    if (isfinite(y[0]) && isfinite(y[1])) {
+        const float e = exp2f(fminf(fmaxf(y[0] + margin[0], 0.f), 12.f));
+        ef = (int)ceilf(e);
+        ef = max(ef_lo, min(ef, ef_hi));
+        const float x = exp2f(fminf(fmaxf(y[1] + margin[1], 0.f), 20.f));
+        mx = max(16, min((int)ceilf(x), 16 * ef + 256));
+    }
+    ef_q[qi] = max(ef, kk);
+    maxexp_q[qi] = mx;   // 0 = default cap
+}
+
+}  // namespace
+
+// Shapes shared with the host code of the search and the ABI.
+int esg_mlp_param_count() { return kP; }
+
+esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+                              const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
+                              float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream) {
+    features_kernel<<<ceil_div_i(nq, 4), 128, 0, stream>>>(ix->X, ix->d, ix->metric, ix->n, ix->leaf_size,
+                                                           ix->entries, ix->E, queries, nq, l, r, k,
+                                                           k_max, feat);
+    ESG_CUDA_TRY(cudaGetLastError());
+    predict_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(ix->mlp, feat, nq, k, k_max, ef_fixed,
+                                                            ix->mlp_ef_lo, ix->mlp_ef_hi, ef_q, maxexp_q);
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
+extern "C" {
+
+int32_t esg_mlp_num_params(void) { return kP; }
+
+esg_status esg_mlp_forward(const float *params, const float *X, const float *mu, const float *sigma,
+                           int64_t B, float *Y, esg_stream_t stream) {
+    if (!params || !X || !mu || !sigma || !Y || B < 1) { esg_set_error("esg_mlp_forward: bad argument"); return ESG_ERR_INVALID_ARG; }
+    mlp_forward_kernel<<<ceil_div_i(B, 128), 128, 0, (cudaStream_t)stream>>>(params, X, mu, sigma, B, Y,
+                                                                            nullptr, nullptr);
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
+esg_status esg_mlp_loss_grad(const float *params, const float *X, const float *T, const float *mu,
+                             const float *sigma, int64_t B, float quantile, float *grad, float *loss,
+                             esg_stream_t stream_v) {
+    if (!params || !X || !T || !mu || !sigma || !grad || B < 1 || !(quantile > 0.f && quantile < 1.f)) {
+        esg_set_error("esg_mlp_loss_grad: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    float *buf = nullptr;
+    const size_t per = 2 + kH + kH + 2 + kH + kH + 1;   // Y, Z1, Z2, dY, dZ2, dZ1, row loss
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&buf, sizeof(float) * per * B, stream));
+    float *Y = buf, *Z1 = Y + 2 * B, *Z2 = Z1 + kH * B, *dY = Z2 + kH * B, *dZ2 = dY + 2 * B,
+          *dZ1 = dZ2 + kH * B, *rl = dZ1 + kH * B;
+    mlp_forward_kernel<<<ceil_div_i(B, 128), 128, 0, stream>>>(params, X, mu, sigma, B, Y, Z1, Z2);
+    mlp_delta_kernel<<<ceil_div_i(B, 128), 128, 0, stream>>>(params, Y, T, Z1, Z2, B, quantile, dY, dZ2, dZ1, rl);
+    mlp_wgrad_kernel<<<ceil_div_i(kP, 128), 128, 0, stream>>>(X, mu, sigma, Z1, Z2, dZ1, dZ2, dY, B, grad);
+    esg_status st = ESG_OK;
+    if (cudaGetLastError() != cudaSuccess) { esg_set_error("esg_mlp_loss_grad: launch failed"); st = ESG_ERR_CUDA; }
+    if (st == ESG_OK && loss) {
+        std::vector<float> h(B);
+        if (cudaMemcpyAsync(h.data(), rl, sizeof(float) * B, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) { esg_set_error("esg_mlp_loss_grad: copy"); st = ESG_ERR_CUDA; }
+        double s = 0;
+        for (int64_t b = 0; b < B; ++b) s += h[b];
+        *loss = (float)(s / (double)(B * kO));
+    }
+    cudaFreeAsync(buf, stream);
+    return st;
+}
+
+esg_status esg_mlp_adam_step(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
+                             esg_stream_t stream) {
+    if (!params || !grad || !m || !v || step < 1 || !(lr > 0.f)) { esg_set_error("esg_mlp_adam_step: bad argument"); return ESG_ERR_INVALID_ARG; }
+    const float b1 = 0.9f, b2 = 0.999f;
+    adam_kernel<<<ceil_div_i(kP, 256), 256, 0, (cudaStream_t)stream>>>(
+        params, grad, m, v, kP, lr, b1, b2, 1e-8f, 1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step));
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
+esg_status esg_query_features(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+                              const int64_t *r, const int32_t *k, int32_t k_max, float *feat,
+                              esg_stream_t stream) {
+    if (!ix || nq < 0 || (nq > 0 && (!queries || !l || !r || !feat))) { esg_set_error("esg_query_features: bad argument"); return ESG_ERR_INVALID_ARG; }
+    if (nq == 0) return ESG_OK;
+    features_kernel<<<ceil_div_i(nq, 4), 128, 0, (cudaStream_t)stream>>>(
+        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat);
+    ESG_CUDA_TRY(cudaGetLastError());
+    return ESG_OK;
+}
+
+esg_status esg_predictor_set(esg_index *ix, const float *blob_host, int32_t ef_lo, int32_t ef_hi) {
+    if (!ix || !blob_host || ef_lo < 1 || ef_hi < ef_lo || ef_hi > 1024) { esg_set_error("esg_predictor_set: bad argument"); return ESG_ERR_INVALID_ARG; }
+    const size_t n = (size_t)kP + 2 * kF + 2;
+    if (!ix->mlp) ESG_CUDA_TRY(cudaMalloc((void **)&ix->mlp, sizeof(float) * n));
+    ESG_CUDA_TRY(cudaMemcpy(ix->mlp, blob_host, sizeof(float) * n, cudaMemcpyHostToDevice));
+    ix->mlp_host.assign(blob_host, blob_host + n);
+    ix->mlp_ef_lo = ef_lo;
+    ix->mlp_ef_hi = ef_hi;
+    ix->mlp_ready = 1;
+    return ESG_OK;
+}
+
+esg_status esg_predictor_get(const esg_index *ix, float *blob_host, int32_t *ef_lo, int32_t *ef_hi) {
+    if (!ix) { esg_set_error("esg_predictor_get: bad argument"); return ESG_ERR_INVALID_ARG; }
+    if (!ix->mlp_ready) { esg_set_error("no trained predictor"); return ESG_ERR_INVALID_ARG; }
+    if (blob_host) std::memcpy(blob_host, ix->mlp_host.data(), sizeof(float) * ix->mlp_host.size());
+    if (ef_lo) *ef_lo = ix->mlp_ef_lo;
+    if (ef_hi) *ef_hi = ix->mlp_ef_hi;
+    return ESG_OK;
+}
+
+}  // extern "C"

@@ -142,7 +142,7 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     SearchFn fn = pick_search(st, pl.vpl);
     if (fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
     pl.fn = (void *)fn;
-    pl.C = ((std::max(8 * efk, 256) + 31) / 32) * 32;
+    pl.C = ((std::max(4 * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
     // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
     // the global overflow table takes what does not fit
@@ -208,7 +208,7 @@ esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, 
 
 namespace {
 struct ScratchLayout {
-    size_t pieces, kq, qs, res, cnt, stats, hash, queue, total;
+    size_t pieces, kq, qs, res, cnt, stats, hash, feat, efq, mxq, queue, total;
 };
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -224,6 +224,9 @@ ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) 
     L.cnt = off; off += al256(sizeof(int32_t) * n_items * 2);
     L.stats = off; off += al256(sizeof(int64_t) * n_items * 4);
     L.hash = off; off += al256((size_t)plan.grid * plan.wpb * plan.G * 4);
+    L.feat = off; off += plan.learned ? al256(sizeof(float) * nq * ESG_MLP_FEATURES) : 0;
+    L.efq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
+    L.mxq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
     L.queue = off; off += 256;
     L.total = off;
     return L;
@@ -234,7 +237,9 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     const esg_index *ix = s.ix;
     const int ef = std::max(s.p.ef, 1);
     if (ef > 1024) { esg_set_error("ef > 1024"); return ESG_ERR_INVALID_ARG; }
-    const int efk = std::max(ef, s.k_max);
+    const bool learned = s.p.use_learned && ix->mlp_ready;
+    // with the learned budget the list and visited table are sized for its ef range
+    const int efk = std::max(learned ? std::max(ix->mlp_ef_hi, ef) : ef, s.k_max);
     const int st_trav = s.p.traversal;
     const void *Xt = ix->X;
     if (st_trav == ESG_BF16) Xt = ix->Xb;
@@ -245,6 +250,7 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
                                s.p.warps_per_block, s.p.hash_slots, s.p.lanes_per_row, plan);
     if (pst != ESG_OK) return pst;
     plan.Xt = Xt;
+    plan.learned = learned;
     plan.ef = ef;
     plan.efk = efk;
     plan.scratch_bytes = scratch_layout(std::max<int64_t>(s.nq, 1), s.k_max, plan).total;
@@ -289,7 +295,17 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(ix->n, ix->leaf_size, s.l, s.r, s.k,
                                                            s.k_max, s.nq, pieces, kq, qs);
     ESG_CUDA_TRY(cudaGetLastError());
+    int32_t *ef_q = nullptr, *maxexp_q = nullptr;
+    if (plan.learned) {
+        ef_q = (int32_t *)(scratch + L.efq);
+        maxexp_q = (int32_t *)(scratch + L.mxq);
+        esg_status pst = esg_predict_budget(ix, s.queries, s.nq, s.l, s.r, s.k, s.k_max, plan.ef,
+                                            (float *)(scratch + L.feat), ef_q, maxexp_q, stream);
+        if (pst != ESG_OK) return pst;
+        esg_prof_count(2);
+    }
     SearchArgs a;
+    a.ef_q = ef_q; a.maxexp_q = maxexp_q;
     a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
     a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
     a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
@@ -350,6 +366,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
         SearchArgs a;
         a.X = X; a.adj = adj; a.entries = entries; a.queries = X; a.qidx = qidx;
         a.pieces = pieces; a.kq = nullptr; a.kconst = k; a.qshift = 0;
+        a.ef_q = nullptr; a.maxexp_q = nullptr;
         a.n = n; a.n_items = n_items; a.d = d; a.nvec = plan.nvec; a.LPR = plan.lpr; a.R = R; a.E = E;
         a.Xv = reinterpret_cast<const uint4 *>(X); a.scale8 = nullptr; a.rerank = 0;
         a.width = plan.width; a.BB = plan.BB;

@@ -319,6 +319,8 @@ struct SearchArgs {
     const int32_t *kq;     // per-query k (validated), 0 = invalid; null = kconst
     int kconst;
     int qshift;            // query of item i = i >> qshift (2 pieces per query: 1)
+    const int32_t *ef_q;       // per-query beam width (learned budget) or null
+    const int32_t *maxexp_q;   // per-query expansion cap (0 = default) or null
     int64_t n;
     int64_t n_items;
     int d, nvec, LPR, R, E, metric;
@@ -386,7 +388,10 @@ search_kernel(SearchArgs a) {
         const bool is_graph = pc.kind == ESG_PIECE_GRAPH;
         // low-precision scans keep ef candidates for the FP32 re-rank
         const bool do_rerank = ST != ESG_F32 && a.rerank;
-        const int ef = (is_graph || do_rerank) ? max(a.ef, kq) : kq;
+        const int efq = a.ef_q ? a.ef_q[qi] : a.ef;
+        const int ef = (is_graph || do_rerank) ? max(efq, kq) : kq;
+        const int mxq = a.maxexp_q ? a.maxexp_q[qi] : 0;
+        const int max_exp = mxq > 0 ? mxq : a.max_exp;
 
         // query in shared memory (FP32)
         {
@@ -457,7 +462,7 @@ search_kernel(SearchArgs a) {
                     while (bal && nsel < a.width) { sel[nsel++] = b0 + __ffs(bal) - 1; bal &= bal - 1; }
                 }
                 if (nsel == 0) break;
-                if (n_exp >= a.max_exp) { status |= ESG_Q_TRUNCATED; break; }
+                if (n_exp >= max_exp) { status |= ESG_Q_TRUNCATED; break; }
                 uint32_t us[4];
                 for (int t = 0; t < nsel; ++t) us[t] = list[sel[t]].id & ESG_ID_MASK;
                 __syncwarp();

@@ -1,0 +1,148 @@
+"""Learned search budget: the MLP's GPU kernels against the float64 oracle,
+the query features against their definition, and the trained predictor
+against the plain fixed-ef search it learns from."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+import synthetic
+
+torch = pytest.importorskip("torch")
+E = pytest.importorskip("paper_2504_04018_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _rand_problem(seed, B=300):
+    rng = np.random.default_rng(seed)
+    F = 8
+    p = (rng.standard_normal(OM.n_params(F)) * 0.2).astype(np.float32)
+    X = (rng.standard_normal((B, F)) * 2 + 0.5).astype(np.float32)
+    T = rng.standard_normal((B, 2)).astype(np.float32)
+    mu = X.mean(0).astype(np.float32)
+    sigma = (X.std(0) + 0.3).astype(np.float32)
+    return p, X, T, mu, sigma
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def test_param_count():
+    assert E.esg_mlp_num_params() == OM.n_params(8)
+
+
+def test_mlp_forward_matches_oracle():
+    p, X, T, mu, sigma = _rand_problem(1)
+    y = E.esg_mlp_forward(_t(p), _t(X), _t(mu), _t(sigma)).cpu().numpy()
+    ref, _ = OM.forward(p, X, mu, sigma)
+    assert np.allclose(y, ref, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("q", [0.5, 0.9])
+def test_mlp_gradient_matches_oracle(q):
+    p, X, T, mu, sigma = _rand_problem(2)
+    loss, g = E.esg_mlp_loss_grad(_t(p), _t(X), _t(T), _t(mu), _t(sigma), q)
+    g = g.cpu().numpy()
+    ref_loss, ref_g = OM.loss_and_grad(p, X, T, mu, sigma, q)
+    assert abs(loss - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
+    assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g)) + 1e-8
+
+
+def test_adam_step_matches_oracle():
+    rng = np.random.default_rng(3)
+    n = OM.n_params(8)
+    p = rng.standard_normal(n).astype(np.float32)
+    g = rng.standard_normal(n).astype(np.float32)
+    m = (rng.standard_normal(n) * 0.01).astype(np.float32)
+    v = (rng.random(n) * 0.01).astype(np.float32)
+    tp, tm, tv = _t(p), _t(m), _t(v)
+    E.esg_mlp_adam_step(tp, _t(g), tm, tv, 7, 3e-3)
+    rp, rm, rv = OM.adam_step(p.astype(np.float64), g, m, v, 7, 3e-3)
+    assert np.allclose(tp.cpu().numpy(), rp, rtol=1e-5, atol=1e-6)
+    assert np.allclose(tm.cpu().numpy(), rm, rtol=1e-5, atol=1e-7)
+    assert np.allclose(tv.cpu().numpy(), rv, rtol=1e-5, atol=1e-9)
+
+
+@pytest.fixture(scope="module")
+def learned_setup():
+    w = synthetic.small_mixture(30000, 32, 5000, n_comp=64, seed=41, M=12, leaf_size=128,
+                                fracs=synthetic.log_uniform_fractions(5000, 1e-3, 1.0, 42))
+    gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
+    _, ent, perm = E.esg_index_export(gix)
+    X = w.base[perm]
+    Xd = _t(X)
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    gi, gd, gc = E.esg_bruteforce_filtered_knn(Xd, q, l, r, 10)
+    torch.cuda.synchronize()
+    gi = gi.cpu().numpy()
+    gt = np.where(gi >= 0, perm[np.maximum(gi, 0)], -1)
+    return w, gix, X, ent, perm, q, l, r, _t(gt), gc
+
+
+def test_features_match_definition(learned_setup):
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    f = E.esg_query_features(gix, q[:200], l[:200], r[:200]).cpu().numpy()
+    for i in range(200):
+        li, ri = int(w.l[i]), int(w.r[i])
+        pcs = O.decompose(gix.n, gix.leaf_size, li, ri)
+        assert np.isclose(f[i, 0], np.log2(ri - li + 1), atol=1e-4)
+        assert f[i, 1] == len(pcs)
+        for s, p in enumerate(pcs):
+            assert np.isclose(f[i, 2 + s], np.log2(p.node_r - p.node_l + 1) - np.log2(p.pr - p.pl + 1), atol=1e-4)
+        assert f[i, 4] == (1.0 if pcs[0].kind == "graph" else 0.0)
+        assert np.isclose(f[i, 5], np.log2(10))
+        assert np.isclose(f[i, 7], np.log2(pcs[0].node_r - pcs[0].node_l + 1), atol=1e-4)
+        if pcs[0].kind == "graph":
+            e = ent[pcs[0].heap]
+            e = e[e >= 0]
+            dd = O.distances(X[e].astype(np.float64), w.queries[i], w.metric)
+            assert np.isclose(f[i, 6], dd.min() / dd.mean(), rtol=1e-4)
+        else:
+            assert f[i, 6] == 1.0
+
+
+def test_trained_predictor_gains_over_fixed_ef(learned_setup):
+    """Train on the first 4000 queries (the last fifth of them calibrates the
+    margin), then compare on the 1000 unseen queries: the learned budget
+    reaches about the target while doing fewer distance evaluations than the
+    smallest fixed ef reaching the same recall."""
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    ntr = 4000
+    rep = E.esg_train_predictor(gix, q[:ntr], l[:ntr], r[:ntr], gt[:ntr], gc[:ntr], k_max=10,
+                                target_recall=0.95, epochs=80, ef_lo=8, ef_hi=128)
+    assert rep[1] >= 0.95
+    qt, lt, rt = q[ntr:], l[ntr:], r[ntr:]
+    gtt = gt[ntr:].cpu().numpy()
+    gct = gc[ntr:].cpu().numpy()
+
+    def run(**kw):
+        ids, _, cnt, _, stats = E.esg_search_batch(gix, qt, lt, rt, None, 10, want_stats=True, **kw)
+        torch.cuda.synchronize()
+        ids, cnt, stats = ids.cpu().numpy(), cnt.cpu().numpy(), stats.cpu().numpy()
+        hits = sum(len(set(ids[i, :cnt[i]].tolist()) & set(gtt[i, :gct[i]].tolist())) for i in range(len(cnt)))
+        return hits / gct.sum(), stats[:, 1].mean()
+
+    rec_l, ev_l = run(ef=128, use_learned=1)
+    assert rec_l >= 0.94
+    fixed = [(ef,) + run(ef=ef) for ef in (8, 12, 16, 24, 32, 48, 64, 96, 128)]
+    cheapest = next((ev for ef, rec, ev in fixed if rec >= rec_l), fixed[-1][2])
+    print(f"learned: recall {rec_l:.4f}, {ev_l:.0f} evals/query; fixed ef at that recall: "
+          f"{cheapest:.0f} evals/query; fixed sweep {fixed}")
+    assert ev_l < cheapest
+
+
+def test_predictor_survives_save_load(learned_setup, tmp_path):
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    blob, lo, hi = E.esg_predictor_get(gix)
+    path = str(tmp_path / "idx.esg")
+    E.esg_save(gix, path)
+    g2 = E.esg_load(path)
+    blob2, lo2, hi2 = E.esg_predictor_get(g2)
+    assert np.array_equal(blob, blob2) and (lo, hi) == (lo2, hi2)
+    a = E.esg_search_batch(gix, q[:300], l[:300], r[:300], None, 10, ef=128, use_learned=1)[0]
+    b = E.esg_search_batch(g2, q[:300], l[:300], r[:300], None, 10, ef=128, use_learned=1)[0]
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)

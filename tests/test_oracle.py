@@ -349,3 +349,42 @@ def test_lowprec_search_reranks_exactly(small_index):
         c, cd = O.search(idx, w.queries[i], int(w.l[i]), int(w.r[i]), 10, 16,
                          trav_X=O.traversal_rows(idx.X.astype(np.float32), "bf16"))
         assert np.allclose(cd, O.distances(idx.X[c], w.queries[i], w.metric))
+
+
+# --------------------------------------------- learned predictor (MLP)
+
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    F, B = 8, 37
+    p = rng.standard_normal(mlp.n_params(F)) * 0.3
+    X = rng.standard_normal((B, F)) * 3 + 1
+    T = rng.standard_normal((B, 2))
+    mu, sigma = X.mean(0), X.std(0) + 0.5
+    for q in (0.5, 0.9):
+        loss, g = mlp.loss_and_grad(p, X, T, mu, sigma, q)
+        assert np.isclose(loss, mlp.pinball(mlp.forward(p, X, mu, sigma)[0], T, q))
+        h = 1e-6
+        idx = rng.choice(len(p), 120, replace=False)
+        num = np.array([(mlp.pinball(mlp.forward(p + h * e, X, mu, sigma)[0], T, q) -
+                         mlp.pinball(mlp.forward(p - h * e, X, mu, sigma)[0], T, q)) / (2 * h)
+                        for e in np.eye(len(p))[idx]])
+        assert np.allclose(g[idx], num, rtol=1e-4, atol=1e-8)
+
+
+def test_mlp_pinball_quantile_property():
+    """Minimising the pinball loss of a constant predicts the q-quantile."""
+    from oracle import mlp
+    t = np.linspace(0, 1, 1001)[:, None].repeat(2, 1)
+    grid = np.linspace(0, 1, 201)
+    best = grid[np.argmin([mlp.pinball(np.full_like(t, c), t, 0.9) for c in grid])]
+    assert abs(best - 0.9) <= 0.005
+
+
+def test_adam_first_step_moves_by_lr():
+    from oracle import mlp
+    p = np.zeros(5)
+    g = np.array([1.0, -2.0, 0.5, 0.0, 3.0])
+    p1, m, v = mlp.adam_step(p, g, np.zeros(5), np.zeros(5), 1, 0.01)
+    # bias-corrected first step is lr * sign(g) (where g != 0)
+    assert np.allclose(p1, -0.01 * np.sign(g), atol=1e-9)
