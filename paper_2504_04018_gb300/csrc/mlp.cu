@@ -153,12 +153,14 @@ __global__ void mlp_wgrad_kernel(const float *X, const float *mu, const float *s
     grad[t] = g;
 }
 
+// One Adam step; (1 - beta) is passed separately, rounded from its exact
+// decimal value (1 - 0.999f in float32 would be off by 1.3e-5 relative).
 __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n, float lr, float b1,
-                            float b2, float eps, float c1, float c2) {
+                            float omb1, float b2, float omb2, float eps, float c1, float c2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float mi = b1 * m[i] + (1.f - b1) * g[i];
-    const float vi = b2 * v[i] + (1.f - b2) * g[i] * g[i];
+    const float mi = b1 * m[i] + omb1 * g[i];
+    const float vi = b2 * v[i] + omb2 * g[i] * g[i];
     m[i] = mi;
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -310,9 +312,10 @@ esg_status esg_mlp_loss_grad(const float *params, const float *X, const float *T
 esg_status esg_mlp_adam_step(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
                              esg_stream_t stream) {
     if (!params || !grad || !m || !v || step < 1 || !(lr > 0.f)) { esg_set_error("esg_mlp_adam_step: bad argument"); return ESG_ERR_INVALID_ARG; }
-    const float b1 = 0.9f, b2 = 0.999f;
+    const double b1 = 0.9, b2 = 0.999;
     adam_kernel<<<ceil_div_i(kP, 256), 256, 0, (cudaStream_t)stream>>>(
-        params, grad, m, v, kP, lr, b1, b2, 1e-8f, 1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step));
+        params, grad, m, v, kP, lr, (float)b1, (float)(1.0 - b1), (float)b2, (float)(1.0 - b2), 1e-8f,
+        (float)(1.0 - std::pow(b1, step)), (float)(1.0 - std::pow(b2, step)));
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }

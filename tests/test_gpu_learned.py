@@ -60,15 +60,19 @@ def test_adam_step_matches_oracle():
     v = (rng.random(n) * 0.01).astype(np.float32)
     tp, tm, tv = _t(p), _t(m), _t(v)
     E.esg_mlp_adam_step(tp, _t(g), tm, tv, 7, 3e-3)
-    rp, rm, rv = OM.adam_step(p.astype(np.float64), g, m, v, 7, 3e-3)
+    rp, rm, rv = OM.adam_step(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64),
+                              v.astype(np.float64), 7, 3e-3)
+    # float32 state on the GPU: a few units in the last place of each moment
+    assert np.allclose(tm.cpu().numpy(), rm, rtol=1e-5, atol=1e-8)
+    assert np.allclose(tv.cpu().numpy(), rv, rtol=1e-5, atol=1e-8)
     assert np.allclose(tp.cpu().numpy(), rp, rtol=1e-5, atol=1e-6)
-    assert np.allclose(tm.cpu().numpy(), rm, rtol=1e-5, atol=1e-7)
-    assert np.allclose(tv.cpu().numpy(), rv, rtol=1e-5, atol=1e-9)
 
 
 @pytest.fixture(scope="module")
 def learned_setup():
-    w = synthetic.small_mixture(30000, 32, 5000, n_comp=64, seed=41, M=12, leaf_size=128,
+    # 1,024 clusters of ~100 points and a sparse graph (M = 8): fixed beam
+    # widths from 10 to 24 span recall 0.91-0.97, so the budget matters
+    w = synthetic.small_mixture(100_000, 64, 5000, n_comp=1024, seed=41, M=8, leaf_size=128,
                                 fracs=synthetic.log_uniform_fractions(5000, 1e-3, 1.0, 42))
     gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
     _, ent, perm = E.esg_index_export(gix)
@@ -127,7 +131,7 @@ def test_trained_predictor_gains_over_fixed_ef(learned_setup):
 
     rec_l, ev_l = run(ef=128, use_learned=1)
     assert rec_l >= 0.94
-    fixed = [(ef,) + run(ef=ef) for ef in (8, 12, 16, 24, 32, 48, 64, 96, 128)]
+    fixed = [(ef,) + run(ef=ef) for ef in range(10, 65, 2)]
     cheapest = next((ev for ef, rec, ev in fixed if rec >= rec_l), fixed[-1][2])
     print(f"learned: recall {rec_l:.4f}, {ev_l:.0f} evals/query; fixed ef at that recall: "
           f"{cheapest:.0f} evals/query; fixed sweep {fixed}")
