@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget variant")
     return ap.parse_args()
 
 
@@ -210,8 +211,9 @@ def cpu_baseline(ix, w, ef, seconds):
 
 # (name, traversal rows, search width); "plain" is Algorithm 1's order on FP32 rows
 VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16", "fp8")
-                                    for wd in (1, 2, 4) if not (t == "f32" and wd == 1)]
+                                    for wd in (1, 2) if not (t == "f32" and wd == 1)]
 ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
+N_TRAIN = 20_000
 
 
 def run_ours(args, rank, world, local):
@@ -236,15 +238,17 @@ def run_ours(args, rank, world, local):
     L = torch.as_tensor(w.l, device=dev)
     Rr = torch.as_tensor(w.r, device=dev)
     nq = Q.shape[0]
-    # exact ground truth on the GPU (brute force over the rank-ordered rows)
     Xr = torch.as_tensor(w.base[perm], device=dev)
-    gi, gd, gc = E.esg_bruteforce_filtered_knn(Xr, Q, L, Rr, 10)
-    torch.cuda.synchronize()
-    gi = gi.cpu().numpy()
-    gc = gc.cpu().numpy()
-    gt = np.where(gi >= 0, perm[np.maximum(gi, 0)], -1)
-    del Xr
 
+    def ground_truth(q, l, r):
+        """Exact answers (original ids) from the GPU brute force over the
+        rank-ordered rows."""
+        gi, _, gc = E.esg_bruteforce_filtered_knn(Xr, q, l, r, 10)
+        torch.cuda.synchronize()
+        gi, gc = gi.cpu().numpy(), gc.cpu().numpy()
+        return np.where(gi >= 0, perm[np.maximum(gi, 0)], -1), gc
+
+    gt, gc = ground_truth(Q, L, Rr)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out = (torch.empty((nq, 10), dtype=torch.int64, device=dev),
            torch.empty((nq, 10), dtype=torch.float32, device=dev),
@@ -254,27 +258,32 @@ def run_ours(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     results = {}
-    chosen_variants = [v for v in VARIANTS if not args.variants or v[0] in args.variants.split(",")]
-    if not any(v[0] == "plain" for v in chosen_variants):
-        chosen_variants = [VARIANTS[0]] + chosen_variants
-    for name, trav, width in chosen_variants:
-        sweep = []
-        chosen = args.ef
-        for ef in ([args.ef] if args.ef else EF_SWEEP):
-            ids, dist, cnt, st, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=ef,
-                                                           traversal=trav, width=width)
-            torch.cuda.synchronize()
-            rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
-            sweep.append({"ef": ef, "recall": round(rec, 5)})
-            if not args.ef and rec >= TARGET_RECALL:
-                chosen = ef
-                break
-        if not chosen:
-            chosen = EF_SWEEP[-1]
-        # per-step algorithmic bytes from the search's own counters
-        _, _, _, _, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=chosen, traversal=trav,
-                                               width=width, want_stats=True)
+
+    def timed(step_fn, name):
+        for _ in range(args.warmup):
+            step_fn()
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.nvtx.range_push(f"timed_{name}")
+        evs = [step_fn() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+        return total_ms
+
+    def measure(name, params, trav):
+        """Recall, per-step time, kernel time and algorithmic bytes of one
+        parameter setting with direct esg_search_batch calls."""
+        ids, dist, cnt, st, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, params=params,
+                                                       want_stats=True)
+        torch.cuda.synchronize()
+        rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
         stats = stats.cpu().numpy()
         alg_bytes = float(stats[:, 1].sum() * ix.d * ESIZE[trav] + stats[:, 0].sum() * ix.R * 4
                           + stats[:, 3].sum() * ix.d * 4)
@@ -284,43 +293,99 @@ def run_ours(args, rank, world, local):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=chosen, traversal=trav, width=width,
-                               out=out)
+            E.esg_search_batch(ix, Q, L, Rr, None, 10, params=params, out=out)
             ev1.record(stream)
             return ev0, ev1
 
-        for _ in range(args.warmup):
-            one_step()
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
         E.esg_profile_enable(True)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push(f"timed_{name}")
-        evs = [one_step() for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        kernel_ms, launches, timed = E.esg_profile_read(reset=True)
+        total_ms = timed(one_step, name)
+        kernel_ms, launches, nt = E.esg_profile_read(reset=True)
         E.esg_profile_enable(False)
-        total_ms = sum(a.elapsed_time(b) for a, b in evs)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-            torch.distributed.barrier()
-        results[name] = {"trav": trav, "width": width, "ef": chosen, "recall": sweep[-1]["recall"], "sweep": sweep,
-                         "qps": world * nq * args.steps / (total_ms / 1e3),
-                         "ms_per_step": total_ms / args.steps, "kernel_ms": kernel_ms / max(1, timed),
-                         "alg_bytes": alg_bytes, "launches": launches,
-                         "evals_per_query": float(stats[:, 1].mean()),
-                         "expansions_per_query": float(stats[:, 0].mean())}
+        launches_per_step = launches // max(1, args.steps + args.warmup)
+        return {"trav": trav, "params": params.as_dict(), "recall": round(rec, 5),
+                "qps": world * nq * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                "kernel_ms": kernel_ms / max(1, nt), "alg_bytes": alg_bytes,
+                "launches": launches_per_step * args.steps,
+                "evals_per_query": float(stats[:, 1].mean()),
+                "expansions_per_query": float(stats[:, 0].mean())}
+
+    sweeps = {}
+    chosen_variants = [v for v in VARIANTS if not args.variants or v[0] in args.variants.split(",")]
+    if not any(v[0] == "plain" for v in chosen_variants):
+        chosen_variants = [VARIANTS[0]] + chosen_variants
+    for name, trav, width in chosen_variants:
+        sweep, chosen = [], args.ef
+        for ef in ([args.ef] if args.ef else EF_SWEEP):
+            ids, _, cnt, _, _ = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=ef, traversal=trav,
+                                                   width=width)
+            torch.cuda.synchronize()
+            rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
+            sweep.append({"ef": ef, "recall": round(rec, 5)})
+            if not args.ef and rec >= TARGET_RECALL:
+                chosen = ef
+                break
+        sweeps[name] = sweep
+        results[name] = measure(name, E.search_params(ef=chosen or EF_SWEEP[-1], traversal=trav,
+                                                      width=width), trav)
+
+    # learned budget + low-precision rows + autotuned launch shape + CUDA graph
+    learned_info = {}
+    if not args.no_learned:
+        mixed = {k: v for k, v in results.items() if k != "plain" and v["recall"] >= TARGET_RECALL
+                 and v["params"]["width"] == 1}
+        trav = results[max(mixed, key=lambda k: mixed[k]["qps"])]["trav"] if mixed else "f32"
+        tq, tl, tr = synthetic.training_queries(w, N_TRAIN, 1024, seed=4002)
+        TQ, TL, TR = (torch.as_tensor(a, device=dev) for a in (tq, tl, tr))
+        tgt, tgc = ground_truth(TQ, TL, TR)
+        t1 = time.perf_counter()
+        rep = E.esg_train_predictor(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
+                                    torch.as_tensor(tgc, device=dev), k_max=10,
+                                    target_recall=TARGET_RECALL + 0.005, ef_lo=8, ef_hi=128,
+                                    traversal=trav, epochs=40)
+        train_s = time.perf_counter() - t1
+        base = E.search_params(ef=128, traversal=trav, use_learned=1)
+        tuned, trec, tms = E.esg_autotune(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
+                                          torch.as_tensor(tgc, device=dev), k_max=10,
+                                          target_recall=TARGET_RECALL, base=base)
+        name = f"learned-{trav}"
+        results[name] = measure(name, tuned, trav)
+        # the same setting replayed as one CUDA graph per batch
+        b = E.Batch(ix, max_nq=nq, k_max=10, params=tuned)
+        b.view("queries", (nq, ix.d), torch.float32).copy_(Q)
+        b.view("l", (nq,), torch.int64).copy_(L)
+        b.view("r", (nq,), torch.int64).copy_(Rr)
+
+        def graph_step():
+            flush.fill_(1.0)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.run(nq, stream=stream)
+            ev1.record(stream)
+            return ev0, ev1
+
+        E.esg_profile_enable(True)
+        total_ms = timed(graph_step, name + "-graph")
+        _, launches, _ = E.esg_profile_read(reset=True)
+        E.esg_profile_enable(False)
+        ids = b.view("ids", (nq, 10), torch.int64).cpu().numpy()
+        cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
+        g = dict(results[name])
+        g.update({"recall": round(recall_at_10(ids, cnt, gt, gc), 5),
+                  "qps": world * nq * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                  "launches": launches // max(1, args.steps + args.warmup) * args.steps, "graph": True})
+        results[name + "-graph"] = g
+        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "train_s": round(train_s, 2),
+                        "train_loss": float(rep[0]), "heldout_recall": float(rep[1]),
+                        "ef_margin_log2": float(rep[2]), "heldout_evals_per_query": float(rep[3]),
+                        "autotune": {"params": tuned.as_dict(), "recall": trec, "ms": tms}}
     clk = clocks.stop()
     ok = {k: v for k, v in results.items() if v["recall"] >= TARGET_RECALL}
-    mixed = {k: v for k, v in ok.items() if k != "plain"}
-    head_name = max(mixed, key=lambda k: mixed[k]["qps"]) if mixed else "plain"
+    opt = {k: v for k, v in ok.items() if k != "plain"}
+    head_name = max(opt, key=lambda k: opt[k]["qps"]) if opt else "plain"
     head = results[head_name]
 
-    # end to end through the public call with host buffers (headline variant)
+    # end to end through the public call with host buffers (headline setting)
     Qh = torch.as_tensor(w.queries).pin_memory()
     Lh = torch.as_tensor(w.l).pin_memory()
     Rh = torch.as_tensor(w.r).pin_memory()
@@ -328,6 +393,7 @@ def run_ours(args, rank, world, local):
     dist_h = torch.empty((nq, 10), dtype=torch.float32).pin_memory()
     cnt_h = torch.empty(nq, dtype=torch.int32).pin_memory()
     Qd, Ld, Rd = torch.empty_like(Q), torch.empty_like(L), torch.empty_like(Rr)
+    head_params = E.search_params(**head["params"])
 
     def e2e_step():
         flush.fill_(1.0)
@@ -337,24 +403,14 @@ def run_ours(args, rank, world, local):
         Qd.copy_(Qh, non_blocking=True)
         Ld.copy_(Lh, non_blocking=True)
         Rd.copy_(Rh, non_blocking=True)
-        E.esg_search_batch(ix, Qd, Ld, Rd, None, 10, ef=head["ef"], traversal=head["trav"],
-                           width=head["width"], out=out)
+        E.esg_search_batch(ix, Qd, Ld, Rd, None, 10, params=head_params, out=out)
         ids_h.copy_(out[0], non_blocking=True)
         dist_h.copy_(out[1], non_blocking=True)
         cnt_h.copy_(out[2], non_blocking=True)
         ev1.record(stream)
         return ev0, ev1
 
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_evs = [e2e_step() for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_evs)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = timed(e2e_step, "e2e")
     h2d = Qh.numel() * 4 + Lh.numel() * 8 + Rh.numel() * 8
     d2h = ids_h.numel() * 8 + dist_h.numel() * 4 + cnt_h.numel() * 4
 
@@ -372,27 +428,24 @@ def run_ours(args, rank, world, local):
                 "algorithmic_bytes_per_launch": head["alg_bytes"],
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     variants = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
-                    if kk not in ("sweep", "alg_bytes", "launches")} for k, v in results.items()}
+                    if kk not in ("alg_bytes",)} for k, v in results.items()}
     line = {"metric": METRIC_NAME, "value": head["qps"], "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": head["trav"] if head["trav"] != "f32" else "f32",
-            "data": "synthetic",
-            "config": workload_config(args, {"parallelism": f"replicas{world}", "ef": head["ef"],
-                                             "variant": head_name}),
+            "dtype": head["trav"], "data": "synthetic",
+            "config": workload_config(args, {"parallelism": f"replicas{world}",
+                                             "variant": head_name, "params": head["params"]}),
             "recall_at_10": head["recall"],
-            "plain_fp32": {"qps": results["plain"]["qps"], "ef": results["plain"]["ef"],
+            "plain_fp32": {"qps": results["plain"]["qps"], "ef": results["plain"]["params"]["ef"],
                            "recall_at_10": results["plain"]["recall"]},
             "speedup_vs_plain": head["qps"] / results["plain"]["qps"],
-            "variants": variants,
-            "ef_sweeps": {k: v["sweep"] for k, v in results.items()},
-            "build_s": round(build_s, 2),
-            "roofline": roofline, "clocks": clk,
+            "variants": variants, "ef_sweeps": sweeps, "learned": learned_info,
+            "build_s": round(build_s, 2), "roofline": roofline, "clocks": clk,
             "e2e": {"value": world * nq * args.steps / (e2e_ms / 1e3), "unit": "queries/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": head["launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(ix, w, results["plain"]["ef"], args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(ix, w, results["plain"]["params"]["ef"], args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -153,6 +153,20 @@ def scale(n: int = 1_000_000, nq: int = 10_000, d: int = 128, n_comp: int = 1024
     return _mixture_workload("scale", n, d, n_comp, nq, fr, 2, "l2", 32, 64)
 
 
+def training_queries(wl: Workload, nq: int, n_comp: int, seed: int, sigma: float = 0.1):
+    """Extra queries from the same mixture as `wl` (its centers are redrawn
+    from the workload's seed) with range widths drawn like wl's (resampled
+    from its width distribution), for training a search-budget predictor.
+    Returns (queries float32 [nq, d], l, r int64 [nq])."""
+    cfg = {"tiny": 1, "scale": 2, "precision": 3, "batching": 4}[wl.name]
+    centers = mixture_centers(n_comp, wl.d, 1000 + cfg)
+    q = mixture_points(centers, nq, sigma, seed, normalise=(wl.metric == "ip"))
+    widths = (wl.r - wl.l + 1).astype(np.float64) / wl.n
+    fr = _rng(seed + 1).choice(widths, size=nq)
+    l, r = ranges_from_fractions(wl.n, fr, seed + 2)
+    return q, l, r
+
+
 def precision(n: int = 1_000_000, nq: int = 10_000, d: int = 96, n_comp: int = 1024) -> Workload:
     """N=10^6, d=96 unit-normalised mixture, inner product; log-uniform
     widths 0.1%-100%; k=10; M=32."""
