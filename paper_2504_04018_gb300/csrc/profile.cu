@@ -24,6 +24,9 @@ void esg_prof_count(int64_t launches) {
 
 int esg_prof_begin(cudaStream_t stream) {
     if (!g_on) return -1;
+    // no timing events inside a graph capture (they would belong to the graph)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_used == g_pairs.size()) {
         cudaEvent_t a, b;
