@@ -1,0 +1,120 @@
+"""Full-size checks on the 1M-point workloads, in the launch configuration the
+benchmark times: outputs sampled against the float64 oracle one by one, and
+properties that hold at any size checked on every query."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic
+
+torch = pytest.importorskip("torch")
+E = pytest.importorskip("paper_2504_04018_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+SAMPLE = 48
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def _properties(w, ids, dist, cnt, perm):
+    inv = np.empty(len(perm), np.int64)
+    inv[perm] = np.arange(len(perm))
+    for i in range(len(cnt)):
+        l, r = int(w.l[i]), int(w.r[i])
+        assert cnt[i] == min(10, r - l + 1)
+        ranks = inv[ids[i, :cnt[i]]]
+        assert np.all((ranks >= l) & (ranks <= r))
+        assert len(np.unique(ranks)) == cnt[i]
+        assert np.all(np.diff(dist[i, :cnt[i]]) >= 0)
+
+
+def _recall(ids, cnt, gt, gc):
+    return sum(len(set(ids[i, :cnt[i]].tolist()) & set(gt[i, :gc[i]].tolist()))
+               for i in range(len(cnt))) / gc.sum()
+
+
+@pytest.fixture(scope="module")
+def scale_index():
+    w = synthetic.scale()
+    ix = E.esg_build(w.base, w.attr, M=32, leaf_size=256, n_entries=16, ef_construction=200,
+                     metric="l2", storage="bf16")
+    E.esg_index_add_storage(ix, "fp8")
+    _, _, perm = E.esg_index_export(ix)
+    return w, ix, perm
+
+
+def test_scale_decomposition_bit_exact(scale_index):
+    w, ix, perm = scale_index
+    pieces, npieces = E.esg_decompose_batch(ix.n, ix.leaf_size, _t(w.l), _t(w.r))
+    torch.cuda.synchronize()
+    nl, nr, pl, pr, heap, depth, kind = [c.cpu().numpy() for c in E.unpack_pieces(pieces)]
+    npieces = npieces.cpu().numpy()
+    for i in range(len(w.l)):
+        want = O.decompose(ix.n, ix.leaf_size, int(w.l[i]), int(w.r[i]))
+        assert npieces[i] == len(want)
+        for s, p in enumerate(want):
+            assert (nl[i, s], nr[i, s], pl[i, s], pr[i, s], heap[i, s]) == \
+                (p.node_l, p.node_r, p.pl, p.pr, p.heap)
+
+
+def test_scale_ground_truth_and_search(scale_index):
+    w, ix, perm = scale_index
+    X = w.base[perm]
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    gi, gd, gc = E.esg_bruteforce_filtered_knn(_t(X), q, l, r, 10)
+    torch.cuda.synchronize()
+    gi, gd, gc = gi.cpu().numpy(), gd.cpu().numpy(), gc.cpu().numpy()
+    # the GPU ground truth against the float64 oracle on a sample
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(w.l), SAMPLE, replace=False):
+        ref, rd = O.bruteforce(X.astype(np.float64), w.queries[i], int(w.l[i]), int(w.r[i]), 11, "l2")
+        c = gc[i]
+        tol = 4e-5 * abs(rd).max()
+        assert set(ref[:c][rd[:c] < rd[c - 1] - tol].tolist()) <= set(gi[i, :c].tolist())
+        assert np.allclose(gd[i, :c], O.distances(X[gi[i, :c]].astype(np.float64), w.queries[i], "l2"),
+                           rtol=1e-5)
+    gt = np.where(gi >= 0, perm[np.maximum(gi, 0)], -1)
+    # the plain search at the benchmark's operating point
+    ids, dist, cnt, st, _ = E.esg_search_batch(ix, q, l, r, None, 10, ef=24)
+    torch.cuda.synchronize()
+    ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
+    _properties(w, ids, dist, cnt, perm)
+    rec = _recall(ids, cnt, gt, gc)
+    print(f"scale plain ef=24 recall@10 {rec:.4f}")
+    assert rec >= 0.95
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_precision_workload(dtype):
+    """1M unit-norm 96-d vectors, inner product: recall@10 and distance error
+    against the float64 oracle per storage type (traversal in that type, FP32
+    re-rank of the final candidates)."""
+    w = synthetic.precision()
+    ix = E.esg_build(w.base, w.attr, M=32, leaf_size=256, n_entries=16, metric="ip",
+                     storage=dtype if dtype != "f32" else "f32")
+    _, _, perm = E.esg_index_export(ix)
+    X = w.base[perm]
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    gi, _, gc = E.esg_bruteforce_filtered_knn(_t(X), q, l, r, 10, metric="ip")
+    torch.cuda.synchronize()
+    gi, gc = gi.cpu().numpy(), gc.cpu().numpy()
+    gt = np.where(gi >= 0, perm[np.maximum(gi, 0)], -1)
+    ids, dist, cnt, st, _ = E.esg_search_batch(ix, q, l, r, None, 10, ef=48, traversal=dtype)
+    torch.cuda.synchronize()
+    ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
+    _properties(w, ids, dist, cnt, perm)
+    rec = _recall(ids, cnt, gt, gc)
+    inv = np.empty(len(perm), np.int64)
+    inv[perm] = np.arange(len(perm))
+    errs = []
+    rng = np.random.default_rng(1)
+    for i in rng.choice(len(w.l), SAMPLE, replace=False):
+        ranks = inv[ids[i, :cnt[i]]]
+        ref = O.distances(X[ranks].astype(np.float64), w.queries[i], "ip")
+        errs.append(np.max(np.abs(dist[i, :cnt[i]] - ref)))
+    print(f"precision {dtype}: recall@10 {rec:.4f}, max |distance error| {max(errs):.2e}")
+    assert max(errs) <= 1e-5        # re-ranked (or FP32) distances are exact to FP32 rounding
+    assert rec >= 0.95
