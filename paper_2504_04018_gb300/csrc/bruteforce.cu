@@ -11,6 +11,8 @@
 #include "esg_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
+#include <vector>
 
 namespace {
 
@@ -251,11 +253,90 @@ esg_status esg_launch_bruteforce_mode(int mode, const float *base, int64_t n, in
     return ESG_OK;
 }
 
+namespace {
+__global__ void gather_queries_kernel(const float *Q, const int64_t *l, const int64_t *r, int d,
+                                      const int64_t *idx, int64_t m, float *Qg, int64_t *lg, int64_t *rg) {
+    const int64_t i = blockIdx.x;
+    if (i >= m) return;
+    const int64_t q = idx[i];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) Qg[i * d + j] = Q[q * d + j];
+    if (threadIdx.x == 0) { lg[i] = l[q]; rg[i] = r[q]; }
+}
+
+__global__ void scatter_results_kernel(const int64_t *idx, int64_t m, int k, const int64_t *ids_g,
+                                       const float *dist_g, const int32_t *cnt_g, int64_t *ids,
+                                       float *dist, int32_t *cnt) {
+    const int64_t i = blockIdx.x;
+    if (i >= m) return;
+    const int64_t q = idx[i];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        ids[q * k + j] = ids_g[i * k + j];
+        dist[q * k + j] = dist_g[i * k + j];
+    }
+    if (threadIdx.x == 0) cnt[q] = cnt_g[i];
+}
+}  // namespace
+
+// Exact SIMT brute force for the listed queries only (results scattered into
+// the full output arrays).
+esg_status esg_bruteforce_redo(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                               int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
+                               const std::vector<int64_t> &idx, int64_t *out_ids, float *out_dist,
+                               int32_t *out_count, cudaStream_t stream) {
+    (void)nq;
+    const int64_t m = (int64_t)idx.size();
+    if (m == 0) return ESG_OK;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bytes = al(sizeof(int64_t) * m) + al(sizeof(float) * m * d) + 2 * al(sizeof(int64_t) * m) +
+                         al(sizeof(int64_t) * m * k) + al(sizeof(float) * m * k) + al(sizeof(int32_t) * m);
+    unsigned char *s = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&s, bytes, stream));
+    unsigned char *p = s;
+    int64_t *didx = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    float *Qg = (float *)p; p += al(sizeof(float) * m * d);
+    int64_t *lg = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    int64_t *rg = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    int64_t *ig = (int64_t *)p; p += al(sizeof(int64_t) * m * k);
+    float *dg = (float *)p; p += al(sizeof(float) * m * k);
+    int32_t *cg = (int32_t *)p;
+    esg_status st = ESG_OK;
+    cudaError_t ce = cudaMemcpyAsync(didx, idx.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess) {
+        gather_queries_kernel<<<(unsigned)m, 128, 0, stream>>>(queries, l, r, d, didx, m, Qg, lg, rg);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    if (st == ESG_OK)
+        st = esg_launch_bruteforce_mode(metric == ESG_IP ? 1 : 0, base, n, d, Qg, m, lg, rg, k, ig, dg, cg,
+                                        nullptr, 0, nullptr, nullptr, stream);
+    if (st == ESG_OK) {
+        scatter_results_kernel<<<(unsigned)m, 128, 0, stream>>>(didx, m, k, ig, dg, cg, out_ids, out_dist, out_count);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    }
+    // the host vector must outlive the copy above
+    cudaError_t se = cudaStreamSynchronize(stream);
+    if (st == ESG_OK && se != cudaSuccess) { esg_set_error(cudaGetErrorString(se)); st = ESG_ERR_CUDA; }
+    cudaFreeAsync(s, stream);
+    return st;
+}
+
+esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                             int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
+                             float *out_dist, int32_t *out_count, cudaStream_t stream);
+
 esg_status esg_launch_bruteforce(const float *base, int64_t n, int32_t d, int metric,
                                  const float *queries, int64_t nq, const int64_t *l,
                                  const int64_t *r, int32_t k, int64_t *out_ids, float *out_dist,
                                  int32_t *out_count, const int64_t *id_map, int32_t exclude_self,
                                  cudaStream_t stream) {
+    // tensor-core path (split-precision BF16 MMAs, certified) when it applies
+    const char *simt = getenv("ESG_BF_SIMT");
+    if (!id_map && !exclude_self && !(simt && *simt == '1')) {
+        esg_status st = esg_bruteforce_tc(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist,
+                                          out_count, stream);
+        if (st != ESG_ERR_UNSUPPORTED) return st;
+    }
     return esg_launch_bruteforce_mode(metric == ESG_IP ? 1 : 0, base, n, d, queries, nq, l, r, k,
                                       out_ids, out_dist, out_count, id_map, exclude_self, nullptr,
                                       nullptr, stream);

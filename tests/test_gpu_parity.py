@@ -298,3 +298,30 @@ def test_search_width_keeps_recall(dev, tiny_oracle_index, width):
         base.append(O.search(idx, w.queries[i], l, r, 10, 16)[0])
         truth.append(O.bruteforce(idx.X, w.queries[i], l, r, 10, w.metric)[0])
     assert O.recall_at_k(found, truth) >= O.recall_at_k(base, truth) - 0.005
+
+
+@pytest.mark.parametrize("metric", ["l2", "ip"])
+@pytest.mark.parametrize("d,k", [(64, 1), (64, 10), (128, 32), (192, 10)])
+def test_bruteforce_tensor_core_vs_oracle(dev, metric, d, k, monkeypatch):
+    """Shapes that take the tcgen05 path (d a multiple of 64, k <= 32): split
+    BF16 MMAs, certified FP32 re-rank, SIMT redo of uncertified queries."""
+    w = synthetic.small_mixture(5000, d, 300, n_comp=16, seed=17 + d + k, metric=metric,
+                                normalise=(metric == "ip"))
+    X, Q = w.base, w.queries
+    l, r = w.l.copy(), w.r.copy()
+    l[:5] = [0, 9, 0, 4990, 100]
+    r[:5] = [4999, 9, 3, 4999, 99]       # full, single point, tiny, tail, invalid
+    monkeypatch.delenv("ESG_BF_SIMT", raising=False)
+    ids, dist, count = E.esg_bruteforce_filtered_knn(_t(X, dev), _t(Q, dev), _t(l, dev, torch.int64),
+                                                     _t(r, dev, torch.int64), k, metric)
+    torch.cuda.synchronize()
+    ids, dist, count = ids.cpu().numpy(), dist.cpu().numpy(), count.cpu().numpy()
+    _check_bruteforce(X, Q, l, r, k, metric, ids, dist, count)
+    # the SIMT kernel agrees
+    monkeypatch.setenv("ESG_BF_SIMT", "1")
+    ids2, dist2, count2 = E.esg_bruteforce_filtered_knn(_t(X, dev), _t(Q, dev), _t(l, dev, torch.int64),
+                                                        _t(r, dev, torch.int64), k, metric)
+    torch.cuda.synchronize()
+    assert np.array_equal(count, count2.cpu().numpy())
+    fin = np.isfinite(dist)
+    assert np.allclose(dist[fin], dist2.cpu().numpy()[fin], rtol=1e-5, atol=1e-6)
