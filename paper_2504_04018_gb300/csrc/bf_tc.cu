@@ -21,6 +21,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 esg_status esg_bruteforce_redo(const float *base, int64_t n, int32_t d, int metric, const float *queries,
@@ -329,7 +331,7 @@ __global__ void rerank_certify_kernel(const float *X, const float *Q, int d, int
     __syncwarp();
     warp_sort_pow2(b, P);
     const int c = min(k, m);
-    bool certified = true;
+    bool certified = c > 0;
     if (m == K1) {   // the list is full: points may have been left out
         // |approximate - exact| for any point of the range (unit roundoff of
         // BF16 2^-8, of FP32 2^-24): the split residuals and the dropped
@@ -423,6 +425,10 @@ esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric
         if (st == ESG_OK) {
             std::vector<int64_t> idx;
             for (int64_t i = 0; i < nq; ++i) if (h_redo[i]) idx.push_back(i);
+            const char *dbg = getenv("ESG_BF_STATS");
+            if (dbg && *dbg == '1')
+                fprintf(stderr, "tensor-core brute force: %lld of %lld queries recomputed\n",
+                        (long long)idx.size(), (long long)nq);
             if (!idx.empty())
                 st = esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist,
                                          out_count, stream);
