@@ -209,6 +209,39 @@ def cpu_baseline(ix, w, ef, seconds):
                       f"Algorithm 4 + Algorithm 1 in C float64 on the same graph, ef={ef}"}
 
 
+def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
+    """Exact filtered k-NN of the benchmark queries: tcgen05 split-precision
+    path against the SIMT FP32 kernel (CUDA events, median of 3)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    out = {}
+    for name, env in (("tcgen05", "0"), ("simt", "1")):
+        os.environ["ESG_BF_SIMT"] = env
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name + "_ms"] = round(sorted(ts)[1], 3)
+    os.environ.pop("ESG_BF_SIMT", None)
+    pairs = float(np.sum(w.r - w.l + 1))
+    useful = 2.0 * w.d * pairs                      # one dot product per in-range pair
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    t = out["tcgen05_ms"] / 1e3
+    out.update({"queries": int(len(w.l)), "pairs": pairs,
+                "qps_tcgen05": len(w.l) / t, "qps_simt": len(w.l) / (out["simt_ms"] / 1e3),
+                "useful_tflops": useful / t / 1e12,
+                "issued_tflops_bf16": 3 * useful / t / 1e12,
+                "frac_of_bf16_peak": 3 * useful / t / 1e12 / peak})
+    return out
+
+
 # (name, traversal rows, search width); "plain" is Algorithm 1's order on FP32 rows
 VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16", "fp8")
                                     for wd in (1, 2) if not (t == "f32" and wd == 1)]
@@ -249,6 +282,7 @@ def run_ours(args, rank, world, local):
         return np.where(gi >= 0, perm[np.maximum(gi, 0)], -1), gc
 
     gt, gc = ground_truth(Q, L, Rr)
+    bf_info = bruteforce_timing(E, torch, Xr, Q, L, Rr, w, args)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out = (torch.empty((nq, 10), dtype=torch.int64, device=dev),
            torch.empty((nq, 10), dtype=torch.float32, device=dev),
@@ -441,6 +475,7 @@ def run_ours(args, rank, world, local):
             "speedup_vs_plain": head["qps"] / results["plain"]["qps"],
             "variants": variants, "ef_sweeps": sweeps, "learned": learned_info,
             "build_s": round(build_s, 2), "roofline": roofline, "clocks": clk,
+            "bruteforce": bf_info,
             "e2e": {"value": world * nq * args.steps / (e2e_ms / 1e3), "unit": "queries/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": head["launches"]}
