@@ -252,6 +252,7 @@ N_TRAIN = 20_000
 def run_ours(args, rank, world, local):
     import torch
     import paper_2504_04018_gb300 as E
+    from paper_2504_04018_gb300 import replicas as R
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -297,18 +298,13 @@ def run_ours(args, rank, world, local):
         for _ in range(args.warmup):
             step_fn()
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        R.barrier()
         torch.cuda.nvtx.range_push(f"timed_{name}")
         evs = [step_fn() for _ in range(args.steps)]
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        total_ms = sum(a.elapsed_time(b) for a, b in evs)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-            torch.distributed.barrier()
+        total_ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
+        R.barrier()
         return total_ms
 
     def measure(name, params, trav):
@@ -337,7 +333,7 @@ def run_ours(args, rank, world, local):
         E.esg_profile_enable(False)
         launches_per_step = launches // max(1, args.steps + args.warmup)
         return {"trav": trav, "params": params.as_dict(), "recall": round(rec, 5),
-                "qps": world * nq * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
                 "kernel_ms": kernel_ms / max(1, nt), "alg_bytes": alg_bytes,
                 "launches": launches_per_step * args.steps,
                 "evals_per_query": float(stats[:, 1].mean()),
@@ -406,7 +402,7 @@ def run_ours(args, rank, world, local):
         cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
         g = dict(results[name])
         g.update({"recall": round(recall_at_10(ids, cnt, gt, gc), 5),
-                  "qps": world * nq * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                  "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
                   "launches": launches // max(1, args.steps + args.warmup) * args.steps, "graph": True})
         results[name + "-graph"] = g
         learned_info = {"traversal": trav, "train_queries": N_TRAIN, "train_s": round(train_s, 2),
@@ -476,7 +472,7 @@ def run_ours(args, rank, world, local):
             "variants": variants, "ef_sweeps": sweeps, "learned": learned_info,
             "build_s": round(build_s, 2), "roofline": roofline, "clocks": clk,
             "bruteforce": bf_info,
-            "e2e": {"value": world * nq * args.steps / (e2e_ms / 1e3), "unit": "queries/s",
+            "e2e": {"value": R.job_rate(nq, world, args.steps, e2e_ms), "unit": "queries/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": head["launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
