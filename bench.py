@@ -210,8 +210,9 @@ def cpu_baseline(ix, w, ef, seconds):
 
 
 def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
-    """Exact filtered k-NN of the benchmark queries: tcgen05 split-precision
-    path against the SIMT FP32 kernel (CUDA events, median of 3)."""
+    """Exact filtered k-NN of the benchmark queries: the tcgen05 path (whole
+    call, and its MMA kernel alone with the MMA FLOPs it issued) against the
+    SIMT FP32 kernel (CUDA events, median of 3)."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -230,6 +231,13 @@ def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
             ts.append(e0.elapsed_time(e1))
         out[name + "_ms"] = round(sorted(ts)[1], 3)
     os.environ.pop("ESG_BF_SIMT", None)
+    # the MMA kernel alone
+    E.esg_profile_enable(True)
+    E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10)
+    torch.cuda.synchronize()
+    kms, _, _ = E.esg_profile_read(reset=True)
+    mma_flops = E.esg_profile_tensor_work(reset=True)
+    E.esg_profile_enable(False)
     pairs = float(np.sum(w.r - w.l + 1))
     useful = 2.0 * w.d * pairs                      # one dot product per in-range pair
     peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -237,8 +245,12 @@ def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
     out.update({"queries": int(len(w.l)), "pairs": pairs,
                 "qps_tcgen05": len(w.l) / t, "qps_simt": len(w.l) / (out["simt_ms"] / 1e3),
                 "useful_tflops": useful / t / 1e12,
-                "issued_tflops_bf16": 3 * useful / t / 1e12,
-                "frac_of_bf16_peak": 3 * useful / t / 1e12 / peak})
+                "mma_kernel_ms": round(kms, 4),
+                "mma_tflops_issued": mma_flops,
+                "mma_kernel_tflops": (mma_flops / (kms / 1e3) / 1e12) if kms > 0 else None,
+                "mma_frac_of_bf16_peak": (mma_flops / (kms / 1e3) / 1e12 / peak) if kms > 0 else None,
+                "bf16_peak_tflops": peak,
+                "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"})
     return out
 
 

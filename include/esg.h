@@ -409,7 +409,8 @@ esg_status esg_load(const char *path, esg_index **out);
 /*
  * Benchmark timing (library-specific; no counterpart in the paper). While
  * enabled, every esg_search_batch records a CUDA event pair around its beam
- * search kernel on the call's stream and counts the kernels it launches.
+ * search kernel on the call's stream and counts the kernels it launches;
+ * esg_bruteforce_filtered_knn does the same around its tensor-core kernel.
  * esg_profile_read waits for the recorded events and returns the summed
  * kernel milliseconds, the number of kernels launched and the number of
  * timed kernel launches since the last reset (reset != 0 clears them).
@@ -418,6 +419,11 @@ esg_status esg_load(const char *path, esg_index **out);
 esg_status esg_profile_enable(int32_t on);
 esg_status esg_profile_read(double *kernel_ms, int64_t *kernel_launches, int64_t *timed_launches,
                             int32_t reset);
+/* Tensor-core work issued while profiling was enabled: the FLOPs of the
+ * BF16 MMAs the pipelined brute-force kernel issued (three per 128 x 128 x 64
+ * block, masked pairs included), for a tensor-pipe roofline. Host pointer,
+ * may be NULL; reset != 0 clears the count. */
+esg_status esg_profile_tensor_work(double *mma_flops, int32_t reset);
 
 const char *esg_status_str(esg_status s);
 const char *esg_last_error(void);

@@ -32,7 +32,7 @@ EXPORTED = [
     "esg_build_params_default", "esg_search_params_default", "esg_build", "esg_index_import",
     "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
     "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
-    "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read",
+    "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read", "esg_profile_tensor_work",
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
     "esg_train_params_default", "esg_train_predictor", "esg_predictor_set", "esg_predictor_get",
@@ -108,6 +108,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
     lib.esg_profile_enable.argtypes = [_I32]
     lib.esg_profile_read.argtypes = [_P, _P, _P, _I32]
+    lib.esg_profile_tensor_work.argtypes = [_P, _I32]
     lib.esg_train_params_default.restype = _TrainParams
     lib.esg_train_predictor.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _P, _P,
                                         ctypes.POINTER(_TrainParams), _P, _P]
@@ -133,7 +134,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
-                 "esg_profile_read", "esg_index_export_storage", "esg_index_add_storage",
+                 "esg_profile_read", "esg_profile_tensor_work", "esg_index_export_storage", "esg_index_add_storage",
                  "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune",
                  "esg_search_batch_noalloc", "esg_train_predictor", "esg_predictor_set",
                  "esg_predictor_get", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
@@ -389,6 +390,15 @@ def esg_profile_read(reset: bool = True):
                                            ctypes.byref(timed), 1 if reset else 0),
            "esg_profile_read")
     return ms.value, launches.value, timed.value
+
+
+def esg_profile_tensor_work(reset: bool = True) -> float:
+    """FLOPs of the tensor-core MMAs issued by the brute force while
+    profiling was enabled."""
+    f = ctypes.c_double()
+    _check(load_library().esg_profile_tensor_work(ctypes.byref(f), 1 if reset else 0),
+           "esg_profile_tensor_work")
+    return f.value
 
 
 class Batch:

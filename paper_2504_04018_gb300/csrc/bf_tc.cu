@@ -355,11 +355,524 @@ __global__ void rerank_certify_kernel(const float *X, const float *Q, int d, int
     if (lane == 0) { out_count[q] = c; redo[q] = certified ? 0 : 1; }
 }
 
+
+// ------------------------------------------------------------------------
+// Pipelined version. The operands are pre-tiled in global memory in exactly
+// the shared-memory layout the MMA descriptors name (one 32 KB block per
+// 128 rows x 64 dimensions: BF16 hi part, then lo part, 128-byte swizzle,
+// zero padding past the last row and dimension), so every stage is one bulk
+// copy on the TMA engine. Queries are sorted by (log2 of range width, l)
+// and grouped into tiles of 128; a query tile only visits the point tiles
+// that its queries' ranges cover, cut into work items of at most CH tiles
+// so that all SMs are busy. Each CTA is warp-specialised:
+//   warp 0      bulk copies: the item's query tile (resident), then a ring of
+//               S point-tile stages;
+//   warp 1      one thread issues the MMAs into one of two TMEM accumulators
+//               (128 columns each) and commits them to mbarriers;
+//   warps 2..9  epilogue: each reads half a row (64 columns) of the finished
+//               accumulator into registers and releases it; the tile is then
+//               passed through shared memory half by half so that one warp
+//               handles one query row at a time: range mask, distance, a
+//               ballot against the row's current K1-th distance, and, for the
+//               rare candidates that pass, an insertion into the row's sorted
+//               list held across the warp's lanes. A CTA runs a contiguous
+//               share of the items, so a row's list carries over between its
+//               items of the same query tile; the lists go to global memory
+//               and a merge kernel combines them per query.
+// Every wait is bounded (2 s of global time); a wait that runs out sets the
+// error flag and all roles leave their loops.
+
+constexpr int STAGE = 2 * CHUNK;          // hi + lo of a 128 x 64 block
+constexpr int kEpiWarps = 8;
+constexpr int kThreads2 = 64 + 32 * kEpiWarps;
+constexpr int kMaxK1v2 = 64;
+constexpr int kTS = 65;                   // row stride of the transposed half tile
+constexpr int kMaxStages = 6;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+struct WorkItem {
+    int32_t qtile, off, cnt, pad;
+};
+
+struct Tc2Args {
+    const unsigned char *xs, *qs;   // tiled operand blocks
+    const float *xnorm, *qnorm;     // squared norms (queries in caller order)
+    const int64_t *l, *r;
+    const int32_t *qorder;          // sorted position -> caller's query index
+    const WorkItem *items;
+    const int32_t *tiles;           // point-tile ids of all items
+    int n_items;
+    int64_t nv;                     // number of valid (sorted) queries
+    int nk, metric, K1, S;
+    int64_t n;                      // points
+    float *part_d;                  // [n_items][128][K1]
+    int32_t *part_i;                // [n_items][128][K1]
+    int32_t *part_n;                // [n_items][128]
+    int32_t *err;
+};
+
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase of the given parity. Gives up when another role
+// has aborted (unless `ignore_abort`) or after kWaitNs; on a timeout it
+// raises the abort flag and the error flag.
+__device__ bool wait_phase(uint32_t mbar, uint32_t parity, volatile int *abort_f, int32_t *err,
+                           bool ignore_abort = false) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((it & 127) == 0) {
+            if (!ignore_abort && *abort_f) return false;
+            const unsigned long long t = gtime();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) {
+                *abort_f = 1;
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+// Bulk global -> shared copy on the TMA engine, completion counted in bytes
+// on the mbarrier (addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void epi_bar() {   // the 256 epilogue threads
+    asm volatile("bar.sync 1, %0;" :: "n"(32 * kEpiWarps) : "memory");
+}
+
+// Lexicographic (distance, row) order of the candidate lists.
+__device__ __forceinline__ bool dl_less(float da, int32_t ia, float db, int32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int K1 = a.K1;
+    unsigned char *sA = base;
+    unsigned char *sB = sA + (size_t)a.nk * STAGE;
+    float *T = (float *)(sB + (size_t)a.S * STAGE);          // [128][kTS] half tile, transposed
+    float *L_d = T + TM * kTS;                               // [128][K1] per-row lists
+    int32_t *L_i = (int32_t *)(L_d + TM * K1);
+    int32_t *r_lo = L_i + TM * K1, *r_hi = r_lo + TM, *r_cnt = r_hi + TM, *r_ti = r_cnt + TM;
+    float *r_qn = (float *)(r_ti + TM), *r_td = r_qn + TM;
+    uint64_t *bars = (uint64_t *)(r_td + TM);
+    uint64_t *full = bars, *empty = bars + a.S;
+    uint64_t *a_full = bars + 2 * a.S, *a_empty = a_full + 1;
+    uint64_t *acc_full = a_full + 2, *acc_empty = a_full + 4, *drain = a_full + 6;
+    uint32_t *tmem_slot = (uint32_t *)(a_full + 7);
+    volatile int *abort_f = (volatile int *)(tmem_slot + 1);
+    volatile int *abort_snap = (volatile int *)(tmem_slot + 2);   // epilogue's shared view
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this CTA's contiguous share of the work items
+    const int it_begin = (int)((int64_t)blockIdx.x * a.n_items / gridDim.x);
+    const int it_end = (int)((int64_t)(blockIdx.x + 1) * a.n_items / gridDim.x);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.S; ++s) {
+            mbar_init(smem_u32(full + s), 1);
+            mbar_init(smem_u32(empty + s), 1);
+        }
+        mbar_init(smem_u32(a_full), 1);
+        mbar_init(smem_u32(a_empty), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(acc_full + b), 1);
+            mbar_init(smem_u32(acc_empty + b), kEpiWarps);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_f = 0;
+        *abort_snap = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(2 * TN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer
+            uint32_t s = 0, ps = 0, pa = 0;
+            uint32_t issued[kMaxStages] = {0};
+            uint32_t ipar[kMaxStages] = {0};
+            bool a_pending = false;
+            uint32_t a_par = 0;
+            bool ok = true;
+            for (int it = it_begin; ok && it < it_end; ++it) {
+                const WorkItem I = a.items[it];
+                if (!wait_phase(smem_u32(a_empty), pa ^ 1u, abort_f, a.err)) { ok = false; break; }
+                mbar_expect_tx(smem_u32(a_full), (uint32_t)(a.nk * STAGE));
+                for (int kc = 0; kc < a.nk; ++kc)
+                    bulk_g2s(smem_u32(sA + (size_t)kc * STAGE),
+                             a.qs + ((int64_t)I.qtile * a.nk + kc) * STAGE, STAGE, smem_u32(a_full));
+                a_pending = true; a_par = pa;
+                pa ^= 1u;
+                for (int j = 0; ok && j < I.cnt; ++j) {
+                    const int64_t t = a.tiles[I.off + j];
+                    for (int kc = 0; kc < a.nk; ++kc) {
+                        if (!wait_phase(smem_u32(empty + s), ps ^ 1u, abort_f, a.err)) { ok = false; break; }
+                        mbar_expect_tx(smem_u32(full + s), STAGE);
+                        bulk_g2s(smem_u32(sB + (size_t)s * STAGE), a.xs + (t * a.nk + kc) * STAGE, STAGE,
+                                 smem_u32(full + s));
+                        issued[s] = 1; ipar[s] = ps;
+                        if (++s == (uint32_t)a.S) { s = 0; ps ^= 1u; }
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA can exit
+                for (int q = 0; q < a.S; ++q)
+                    if (issued[q]) wait_phase(smem_u32(full + q), ipar[q], abort_f, a.err, true);
+                if (a_pending) wait_phase(smem_u32(a_full), a_par, abort_f, a.err, true);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            uint32_t s = 0, ps = 0, pa = 0, acc_it = 0;
+            uint32_t pacc[2] = {0u, 0u};
+            bool ok = true;
+            for (int it = it_begin; ok && it < it_end; ++it) {
+                const int cnt = a.items[it].cnt;
+                if (!wait_phase(smem_u32(a_full), pa, abort_f, a.err)) { ok = false; break; }
+                pa ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int j = 0; ok && j < cnt; ++j) {
+                    const uint32_t b = acc_it & 1u;
+                    if (!wait_phase(smem_u32(acc_empty + b), pacc[b] ^ 1u, abort_f, a.err)) { ok = false; break; }
+                    pacc[b] ^= 1u;
+                    ++acc_it;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dt = tmem + b * TN;
+                    for (int kc = 0; kc < a.nk; ++kc) {
+                        if (!wait_phase(smem_u32(full + s), ps, abort_f, a.err)) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t ah = smem_u32(sA + (size_t)kc * STAGE), al = ah + CHUNK;
+                        const uint32_t bh = smem_u32(sB + (size_t)s * STAGE), bl = bh + CHUNK;
+#pragma unroll
+                        for (int st = 0; st < TK / 16; ++st) {
+                            const uint32_t off = st * 32;
+                            mma_bf16(dt, sdesc(ah + off), sdesc(bh + off), (kc == 0 && st == 0) ? 0u : 1u);
+                            mma_bf16(dt, sdesc(ah + off), sdesc(bl + off), 1u);
+                            mma_bf16(dt, sdesc(al + off), sdesc(bh + off), 1u);
+                        }
+                        mma_commit(smem_u32(empty + s));
+                        if (++s == (uint32_t)a.S) { s = 0; ps ^= 1u; }
+                    }
+                    if (ok) mma_commit(smem_u32(acc_full + b));
+                }
+                if (ok) mma_commit(smem_u32(a_empty));
+            }
+            // all MMAs issued by this thread complete before the CTA exits
+            mma_commit(smem_u32(drain));
+            wait_phase(smem_u32(drain), 0u, abort_f, a.err, true);
+        }
+    } else {
+        // ---------------- epilogue (256 threads)
+        const int ew = warp - 2;            // 0..7
+        const int et = ew * 32 + lane;      // 0..255
+        const int quarter = warp & 3;       // TMEM lanes this warp may read
+        const int half = ew >> 2;           // column half it reads
+        const int my_row = quarter * 32 + lane;
+        const bool l2 = a.metric == ESG_L2SQ;
+        uint32_t acc_it = 0;
+        uint32_t pe[2] = {0u, 0u};
+        bool ok = true;
+        int cur_qt = -1;
+        for (int it = it_begin; ok && it < it_end; ++it) {
+            const WorkItem I = a.items[it];
+            if (I.qtile != cur_qt) {
+                // new query tile: per-row state (the lists of the previous tile
+                // were written out at the end of its last item)
+                if (et < TM) {
+                    const int64_t sp = (int64_t)I.qtile * TM + et;
+                    int32_t lo = 1, hi = 0;
+                    float qn = 0.f;
+                    if (sp < a.nv) {
+                        const int32_t o = a.qorder[sp];
+                        lo = (int32_t)a.l[o]; hi = (int32_t)a.r[o];
+                        if (l2) qn = a.qnorm[o];
+                    }
+                    r_lo[et] = lo; r_hi[et] = hi; r_qn[et] = qn;
+                    r_cnt[et] = 0; r_td[et] = INFINITY; r_ti[et] = 0x7FFFFFFF;
+                }
+                cur_qt = I.qtile;
+                epi_bar();
+            }
+            for (int j = 0; j < I.cnt; ++j) {
+                const int32_t pt = a.tiles[I.off + j] * TN;   // first point of the tile
+                // norms of this lane's columns (both halves), loaded early
+                float xn[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int32_t p = pt + c * 32 + lane;
+                    xn[c] = (l2 && p < a.n) ? __ldg(a.xnorm + p) : 0.f;
+                }
+                const uint32_t b = acc_it & 1u;
+                if (!wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err)) { ok = false; }
+                // (a failed wait still takes part in the barriers below, so that
+                // the other epilogue warps are not left waiting)
+                pe[b] ^= 1u;
+                ++acc_it;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v[64];
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + b * TN + half * 64;
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + 32, v + 32);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (half == h) {
+#pragma unroll
+                        for (int c = 0; c < 64; ++c) T[my_row * kTS + c] = v[c];
+                    }
+                    epi_bar();
+                    const int32_t pb = pt + h * 64;
+                    const float xn0 = xn[2 * h], xn1 = xn[2 * h + 1];
+                    for (int rr = 0; rr < TM / kEpiWarps; ++rr) {
+                        const int r = ew + kEpiWarps * rr;
+                        const int32_t lo = r_lo[r], hi = r_hi[r];
+                        if (hi < pb || lo > pb + 63) continue;          // warp-uniform
+                        const int32_t p0 = pb + lane, p1 = p0 + 32;
+                        const float x0 = T[r * kTS + lane], x1 = T[r * kTS + lane + 32];
+                        const float qn = r_qn[r];
+                        const bool in0 = p0 >= lo && p0 <= hi, in1 = p1 >= lo && p1 <= hi;
+                        const float d0 = l2 ? qn + xn0 - 2.f * x0 : -x0;
+                        const float d1 = l2 ? qn + xn1 - 2.f * x1 : -x1;
+                        float td = r_td[r];
+                        int32_t ti = r_ti[r];
+                        uint32_t m0 = __ballot_sync(0xffffffffu, in0 && dl_less(d0, p0, td, ti));
+                        uint32_t m1 = __ballot_sync(0xffffffffu, in1 && dl_less(d1, p1, td, ti));
+                        if ((m0 | m1) == 0u) continue;                  // warp-uniform
+                        // the row's list in registers: entries lane and lane + 32
+                        int cnt = r_cnt[r];
+                        float ld0 = lane < cnt ? L_d[r * K1 + lane] : INFINITY;
+                        int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
+                        float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
+                        int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
+                        while ((m0 | m1) != 0u) {
+                            const bool second = m0 == 0u;
+                            const int src = __ffs(second ? m1 : m0) - 1;
+                            if (second) m1 &= m1 - 1; else m0 &= m0 - 1;
+                            const float cd = __shfl_sync(0xffffffffu, second ? d1 : d0, src);
+                            const int32_t ci = (second ? p1 : p0) - lane + src;
+                            if (cnt == K1 && !dl_less(cd, ci, td, ti)) continue;
+                            const int pos = __popc(__ballot_sync(0xffffffffu, lane < cnt && dl_less(ld0, li0, cd, ci))) +
+                                            __popc(__ballot_sync(0xffffffffu, lane + 32 < cnt && dl_less(ld1, li1, cd, ci)));
+                            const float u0d = __shfl_up_sync(0xffffffffu, ld0, 1);
+                            const int32_t u0i = __shfl_up_sync(0xffffffffu, li0, 1);
+                            float u1d = __shfl_up_sync(0xffffffffu, ld1, 1);
+                            int32_t u1i = __shfl_up_sync(0xffffffffu, li1, 1);
+                            const float t31d = __shfl_sync(0xffffffffu, ld0, 31);
+                            const int32_t t31i = __shfl_sync(0xffffffffu, li0, 31);
+                            if (lane == 0) { u1d = t31d; u1i = t31i; }
+                            if (lane > pos) { ld0 = u0d; li0 = u0i; }
+                            else if (lane == pos) { ld0 = cd; li0 = ci; }
+                            if (lane + 32 > pos) { ld1 = u1d; li1 = u1i; }
+                            else if (lane + 32 == pos) { ld1 = cd; li1 = ci; }
+                            if (cnt < K1) ++cnt;
+                            if (cnt == K1) {
+                                const int e = K1 - 1;
+                                td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
+                                ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
+                            }
+                        }
+                        if (lane < cnt) { L_d[r * K1 + lane] = ld0; L_i[r * K1 + lane] = li0; }
+                        if (lane + 32 < cnt) { L_d[r * K1 + lane + 32] = ld1; L_i[r * K1 + lane + 32] = li1; }
+                        if (lane == 0) { r_cnt[r] = cnt; r_td[r] = td; r_ti[r] = ti; }
+                        __syncwarp();
+                    }
+                    // one thread samples the abort flag before the last barrier
+                    // of the tile, all read the sample after it: every epilogue
+                    // warp takes the same decision at the same point
+                    if (h == 1 && et == 0) *abort_snap = *abort_f;
+                    epi_bar();
+                }
+                if (*abort_snap) ok = false;
+            }
+            if (!ok) break;
+            // write the lists out when this is the CTA's last item of the
+            // query tile (a row's list then covers all of the tile's items
+            // this CTA ran); other items record empty lists
+            const bool flush = it + 1 == it_end || a.items[it + 1].qtile != I.qtile;
+            for (int r = et; r < TM; r += 32 * kEpiWarps) {
+                const int c = flush ? r_cnt[r] : 0;
+                a.part_n[(int64_t)it * TM + r] = c;
+            }
+            if (flush) {
+                for (int idx = et; idx < TM * K1; idx += 32 * kEpiWarps) {
+                    const int r = idx / K1, e = idx % K1;
+                    if (e < r_cnt[r]) {
+                        a.part_d[(int64_t)it * TM * K1 + idx] = L_d[idx];
+                        a.part_i[(int64_t)it * TM * K1 + idx] = L_i[idx];
+                    }
+                }
+                epi_bar();
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * TN) : "memory");
+    }
+}
+
+// One thread per (row, 8 dimensions) of the padded matrix: FP32 -> BF16 hi
+// and lo parts, written into the tiled, swizzled block layout. Row `i` of the
+// output is input row order[i] (or i), rows past `rows` are zero.
+__global__ void tile_split_kernel(const float *X, int64_t rows, int d, int nk, const int32_t *order,
+                                  int64_t rows_pad, unsigned char *out) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= rows_pad * nk * 8) return;
+    const int64_t row = idx / (nk * 8);
+    const int g = (int)(idx % (nk * 8));
+    const int kc = g >> 3, c = g & 7;
+    const int64_t src = row < rows ? (order ? (int64_t)order[row] : row) : -1;
+    __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __nv_bfloat16 lo[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = kc * TK + c * 8 + e;
+        const float v = (src >= 0 && k < d) ? X[src * d + k] : 0.f;
+        h[e] = __float2bfloat16_rn(v);
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+    }
+    const int64_t tile = row >> 7;
+    const int t = (int)(row & 127);
+    unsigned char *blk = out + (tile * nk + kc) * (int64_t)STAGE;
+    const uint32_t off = t * 128 + ((c ^ (t & 7)) << 4);
+    *(uint4 *)(blk + off) = *(const uint4 *)h;
+    *(uint4 *)(blk + CHUNK + off) = *(const uint4 *)lo;
+}
+
+__global__ void norms_kernel(const float *X, int64_t rows, int d, float *norm, float *rownorm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const float *x = X + i * d;
+    float s = 0.f;
+    for (int j = 0; j < d; ++j) s = fmaf(x[j], x[j], s);
+    norm[i] = s;
+    rownorm[i] = sqrtf(s);
+}
+
+// Merge the per-item top-K1 lists of each valid query (one warp per sorted
+// position) into one top-K1 list in the caller's query order. Lists are
+// ascending in (distance, row) and hold distinct rows, so the position of
+// an element in the merged list is its own index plus the number of
+// elements of the other list that precede it.
+__global__ void merge_parts_kernel(const float *part_d, const int32_t *part_i, const int32_t *part_n,
+                                   const int32_t *item_begin, const int32_t *qorder, int64_t nv, int K1,
+                                   float *cand_d, int32_t *cand_i, int32_t *cand_n) {
+    __shared__ Cand buf[4][3][kMaxK1v2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t sp = blockIdx.x * (int64_t)4 + w;
+    if (sp >= nv) return;
+    const int64_t qt = sp / TM;
+    const int row = (int)(sp % TM);
+    Cand *A = buf[w][0], *B = buf[w][1], *C = buf[w][2];
+    int na = 0;
+    for (int it = item_begin[qt]; it < item_begin[qt + 1]; ++it) {
+        const int64_t sub = (int64_t)it * TM + row;
+        const int nb = part_n[sub];
+        if (nb <= 0) continue;
+        for (int e = lane; e < nb; e += 32)
+            B[e] = Cand{part_d[sub * K1 + e], (uint32_t)part_i[sub * K1 + e]};
+        __syncwarp();
+        for (int i = lane; i < na; i += 32) {
+            int lo = 0, hi = nb;   // number of B elements before A[i]
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if (cand_less(B[m].d, B[m].id, A[i].d, A[i].id)) lo = m + 1; else hi = m;
+            }
+            if (i + lo < K1) C[i + lo] = A[i];
+        }
+        for (int j = lane; j < nb; j += 32) {
+            int lo = 0, hi = na;   // number of A elements before B[j]
+            while (lo < hi) {
+                const int m = (lo + hi) >> 1;
+                if (cand_less(A[m].d, A[m].id, B[j].d, B[j].id)) lo = m + 1; else hi = m;
+            }
+            if (j + lo < K1) C[j + lo] = B[j];
+        }
+        __syncwarp();
+        Cand *t = A; A = C; C = t;
+        na = min(K1, na + nb);
+    }
+    const int32_t o = qorder[sp];
+    for (int e = lane; e < na; e += 32) {
+        cand_d[(int64_t)o * K1 + e] = A[e].d;
+        cand_i[(int64_t)o * K1 + e] = (int32_t)A[e].id;
+    }
+    if (lane == 0) cand_n[o] = na;
+}
+
 }  // namespace
 
-// Tensor-core path of esg_bruteforce_filtered_knn; returns ESG_ERR_UNSUPPORTED
-// when the shape is outside it (the caller then uses the SIMT kernel).
-esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+// Exact FP32 re-rank of the candidate lists, certificate, and the exact SIMT
+// pass for the queries left uncertified (or for all, after an aborted wait).
+static esg_status certify_and_redo(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                                   int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int K1,
+                                   const float *cand_d, const int32_t *cand_i, const int32_t *cand_n,
+                                   const float *qrow, const float *xmax, int32_t *redo, const int32_t *err,
+                                   int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    rerank_certify_kernel<<<ceil_div_i(nq, 4), 128, 0, stream>>>(
+        base, queries, d, metric, nq, k, K1, cand_d, cand_i, cand_n, qrow, xmax, out_ids, out_dist, out_count, redo);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
+    std::vector<int32_t> h_redo(nq);
+    int32_t h_err = 0;
+    ce = cudaMemcpyAsync(h_redo.data(), redo, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
+    if (h_err) { esg_set_error("tensor-core brute force: an mbarrier wait timed out"); return ESG_ERR_TIMEOUT; }
+    std::vector<int64_t> idx;
+    for (int64_t i = 0; i < nq; ++i) if (h_redo[i]) idx.push_back(i);
+    const char *dbg = getenv("ESG_BF_STATS");
+    if (dbg && *dbg == '1')
+        fprintf(stderr, "tensor-core brute force: %lld of %lld queries recomputed\n", (long long)idx.size(), (long long)nq);
+    if (idx.empty()) return ESG_OK;
+    return esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist, out_count, stream);
+}
+
+// Single-pass tensor-core path: one CTA per 128 queries walks the union of
+// their ranges with a synchronous load -> MMA -> epilogue loop (kept for the
+// shapes the pipelined kernel does not take: d > 192 or k > 16).
+static esg_status bruteforce_tc_v1(const float *base, int64_t n, int32_t d, int metric, const float *queries,
                              int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
                              float *out_dist, int32_t *out_count, cudaStream_t stream) {
     if (d % TK != 0 || k < 1 || 2 * k + 8 > kMaxK1 || n >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
@@ -406,34 +919,174 @@ esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric
         ce = cudaGetLastError();
         esg_prof_end(pidx, stream);
     }
-    if (ce == cudaSuccess) {
-        rerank_certify_kernel<<<ceil_div_i(nq, 4), 128, 0, stream>>>(
-            base, queries, d, metric, nq, k, K1, cand_d, cand_i, cand_n, qrow, xmax,
-            out_ids, out_dist, out_count, redo);
-        ce = cudaGetLastError();
-    }
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    // queries without a certificate (or any aborted wait): exact SIMT pass
-    if (st == ESG_OK) {
-        std::vector<int32_t> h_redo(nq);
-        int32_t h_err = 0;
-        ce = cudaMemcpyAsync(h_redo.data(), redo, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, stream);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
-        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-        if (st == ESG_OK && h_err) { esg_set_error("tensor-core brute force: an mbarrier wait timed out"); st = ESG_ERR_TIMEOUT; }
-        if (st == ESG_OK) {
-            std::vector<int64_t> idx;
-            for (int64_t i = 0; i < nq; ++i) if (h_redo[i]) idx.push_back(i);
-            const char *dbg = getenv("ESG_BF_STATS");
-            if (dbg && *dbg == '1')
-                fprintf(stderr, "tensor-core brute force: %lld of %lld queries recomputed\n",
-                        (long long)idx.size(), (long long)nq);
-            if (!idx.empty())
-                st = esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist,
-                                         out_count, stream);
-        }
-    }
+    if (st == ESG_OK)
+        st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, xmax,
+                              redo, err, out_ids, out_dist, out_count, stream);
     cudaFreeAsync(scratch, stream);
     return st;
+}
+
+// Pipelined tensor-core path; ESG_ERR_UNSUPPORTED when the shape does not fit
+// (k > 16, or shared memory for fewer than two stages).
+static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                                   int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
+                                   float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    const int K1 = 2 * k + 8;
+    if (k < 1 || K1 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
+    const int nk = (d + TK - 1) / TK;
+    int dev = 0, max_smem = 0, sms = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + (size_t)TM * K1 * 8 + 6 * TM * 4 +
+                         8 * (2 * kMaxStages + 8) + 16;
+    if ((size_t)max_smem < fixed + 2 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
+    const int S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - fixed) / STAGE);
+    const size_t smem = fixed + (size_t)S * STAGE;
+    if (nq == 0) return ESG_OK;
+
+    // ---- host plan: sort queries by (log2 width, l), tile them, list the
+    // point tiles each query tile covers and cut the lists into work items
+    std::vector<int64_t> hl(nq), hr(nq);
+    ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaStreamSynchronize(stream));
+    std::vector<int32_t> order;
+    order.reserve(nq);
+    for (int64_t i = 0; i < nq; ++i)
+        if (hl[i] >= 0 && hl[i] <= hr[i] && hr[i] < n) order.push_back((int32_t)i);
+    auto wbits = [&](int32_t i) { return 63 - __builtin_clzll((unsigned long long)(hr[i] - hl[i] + 1)); };
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const int wa = wbits(a), wb = wbits(b);
+        if (wa != wb) return wa < wb;
+        if (hl[a] != hl[b]) return hl[a] < hl[b];
+        return a < b;
+    });
+    const int64_t nv = (int64_t)order.size();
+    const int64_t nqt = (nv + TM - 1) / TM;
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> spans(nqt);
+    int64_t total_tiles = 0;
+    for (int64_t qt = 0; qt < nqt; ++qt) {
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (int64_t s = qt * TM; s < std::min(nv, (qt + 1) * TM); ++s)
+            iv.push_back({hl[order[s]] / TN, hr[order[s]] / TN});
+        std::sort(iv.begin(), iv.end());
+        for (auto &x : iv) {
+            if (!spans[qt].empty() && x.first <= spans[qt].back().second + 1)
+                spans[qt].back().second = std::max(spans[qt].back().second, x.second);
+            else
+                spans[qt].push_back(x);
+        }
+        for (auto &x : spans[qt]) total_tiles += x.second - x.first + 1;
+    }
+    const int64_t CH = std::max<int64_t>(8, std::min<int64_t>(1024, (total_tiles + 4 * sms - 1) / (4 * (int64_t)sms)));
+    std::vector<int32_t> tiles;
+    tiles.reserve(total_tiles);
+    std::vector<WorkItem> items;
+    std::vector<int32_t> item_begin(nqt + 1, 0);
+    for (int64_t qt = 0; qt < nqt; ++qt) {
+        item_begin[qt] = (int32_t)items.size();
+        const int64_t first = (int64_t)tiles.size();
+        for (auto &x : spans[qt])
+            for (int64_t t = x.first; t <= x.second; ++t) tiles.push_back((int32_t)t);
+        for (int64_t o = first; o < (int64_t)tiles.size(); o += CH)
+            items.push_back(WorkItem{(int32_t)qt, (int32_t)o, (int32_t)std::min<int64_t>(CH, (int64_t)tiles.size() - o), 0});
+    }
+    item_begin[nqt] = (int32_t)items.size();
+    const int64_t n_items = (int64_t)items.size();
+    if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
+
+    // ---- device scratch
+    const int64_t xt = (n + TN - 1) / TN;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t bytes = al((size_t)xt * nk * STAGE) + al((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE) +
+                   4 * al(sizeof(float) * std::max<int64_t>(n, nq)) + al(sizeof(float) * 4) +
+                   al(sizeof(int32_t) * std::max<int64_t>(nv, 1)) + al(sizeof(WorkItem) * std::max<int64_t>(n_items, 1)) +
+                   al(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1)) + al(sizeof(int32_t) * (nqt + 1)) +
+                   2 * al((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM) +
+                   al(sizeof(int32_t) * std::max<int64_t>(n_items, 1) * TM) +
+                   al((sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1) + 3 * al(sizeof(int32_t) * nq) + 256;
+    unsigned char *scratch = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
+    unsigned char *p = scratch;
+    auto take = [&](size_t b) { unsigned char *q = p; p += al(b); return q; };
+    unsigned char *xs = take((size_t)xt * nk * STAGE);
+    unsigned char *qs = take((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE);
+    float *xnorm = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
+    float *xrow = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
+    float *qnorm = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
+    float *qrow = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
+    float *xmax = (float *)take(sizeof(float) * 4);
+    int32_t *d_order = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(nv, 1));
+    WorkItem *d_items = (WorkItem *)take(sizeof(WorkItem) * std::max<int64_t>(n_items, 1));
+    int32_t *d_tiles = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1));
+    int32_t *d_ib = (int32_t *)take(sizeof(int32_t) * (nqt + 1));
+    float *part_d = (float *)take((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM);
+    int32_t *part_i = (int32_t *)take((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM);
+    int32_t *part_n = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(n_items, 1) * TM);
+    float *cand_d = (float *)take(sizeof(float) * (size_t)nq * K1);
+    int32_t *cand_i = (int32_t *)take(sizeof(int32_t) * (size_t)nq * K1);
+    int32_t *cand_n = (int32_t *)take(sizeof(int32_t) * nq);
+    int32_t *redo = (int32_t *)take(sizeof(int32_t) * nq);
+    int32_t *err = (int32_t *)take(sizeof(int32_t) * 4);
+
+    esg_status st = ESG_OK;
+    cudaError_t ce = cudaMemsetAsync(xmax, 0, sizeof(float) * 4, stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(cand_n, 0xFF, sizeof(int32_t) * nq, stream);   // -1: invalid
+    if (ce == cudaSuccess && nv > 0)
+        ce = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess && n_items > 0)
+        ce = cudaMemcpyAsync(d_items, items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess && total_tiles > 0)
+        ce = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int32_t) * total_tiles, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_ib, item_begin.data(), sizeof(int32_t) * (nqt + 1), cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess) {
+        norms_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(base, n, d, xnorm, xrow);
+        norms_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(queries, nq, d, qnorm, qrow);
+        max_kernel<<<152, 256, 0, stream>>>(xrow, n, xmax);
+        tile_split_kernel<<<ceil_div_i(xt * TN * nk * 8, 256), 256, 0, stream>>>(base, n, d, nk, nullptr, xt * TN, xs);
+        if (nqt > 0)
+            tile_split_kernel<<<ceil_div_i(nqt * TM * nk * 8, 256), 256, 0, stream>>>(queries, nv, d, nk, d_order,
+                                                                                     nqt * TM, qs);
+        ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaFuncSetAttribute(tc_knn2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce == cudaSuccess && n_items > 0) {
+        // MMA work issued: three 128 x 128 x 64 BF16 products per point tile and K chunk
+        esg_prof_tensor_flops((double)total_tiles * nk * 3.0 * 2.0 * TM * TN * TK);
+        Tc2Args a{xs, qs, xnorm, qnorm, l, r, d_order, d_items, d_tiles, (int)n_items, nv, nk, metric, K1, S,
+                  n, part_d, part_i, part_n, err};
+        const int pidx = esg_prof_begin(stream);
+        tc_knn2_kernel<<<(unsigned)std::min<int64_t>(n_items, sms), kThreads2, smem, stream>>>(a);
+        ce = cudaGetLastError();
+        esg_prof_end(pidx, stream);
+        if (ce == cudaSuccess) {
+            merge_parts_kernel<<<ceil_div_i(nv, 4), 128, 0, stream>>>(part_d, part_i, part_n, d_ib, d_order, nv, K1,
+                                                                      cand_d, cand_i, cand_n);
+            ce = cudaGetLastError();
+        }
+    }
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    const char *dbg = getenv("ESG_BF_STATS");
+    if (dbg && *dbg == '1')
+        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items of <= %lld, %d stages\n",
+                (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S);
+    if (st == ESG_OK)
+        st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, xmax,
+                              redo, err, out_ids, out_dist, out_count, stream);
+    cudaFreeAsync(scratch, stream);
+    return st;
+}
+
+// Tensor-core path of esg_bruteforce_filtered_knn; returns ESG_ERR_UNSUPPORTED
+// when the shape is outside both versions (the caller then uses the SIMT kernel).
+esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                             int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
+                             float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    esg_status st = bruteforce_tc_v2(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
+    if (st != ESG_ERR_UNSUPPORTED) return st;
+    return bruteforce_tc_v1(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
 }

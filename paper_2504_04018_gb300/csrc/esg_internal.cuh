@@ -124,6 +124,7 @@ esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int64_t *ids, const 
 // benchmark timing hooks (profile.cu)
 bool esg_prof_on();
 void esg_prof_count(int64_t launches);
+void esg_prof_tensor_flops(double flops);
 int esg_prof_begin(cudaStream_t stream);
 void esg_prof_end(int idx, cudaStream_t stream);
 

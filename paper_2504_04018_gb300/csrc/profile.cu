@@ -12,9 +12,16 @@ bool g_on = false;
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_pairs;
 size_t g_used = 0;
 int64_t g_launches = 0;
+double g_tensor_flops = 0.0;
 }  // namespace
 
 bool esg_prof_on() { return g_on; }
+
+void esg_prof_tensor_flops(double flops) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tensor_flops += flops;
+}
 
 void esg_prof_count(int64_t launches) {
     if (!g_on) return;
@@ -52,6 +59,7 @@ esg_status esg_profile_enable(int32_t on) {
     g_on = on != 0;
     g_used = 0;
     g_launches = 0;
+    g_tensor_flops = 0.0;
     return ESG_OK;
 }
 
@@ -71,6 +79,13 @@ esg_status esg_profile_read(double *kernel_ms, int64_t *kernel_launches, int64_t
     if (kernel_launches) *kernel_launches = g_launches;
     if (timed_launches) *timed_launches = (int64_t)g_used;
     if (reset) { g_used = 0; g_launches = 0; }
+    return ESG_OK;
+}
+
+esg_status esg_profile_tensor_work(double *mma_flops, int32_t reset) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (mma_flops) *mma_flops = g_tensor_flops;
+    if (reset) g_tensor_flops = 0.0;
     return ESG_OK;
 }
 

@@ -301,10 +301,12 @@ def test_search_width_keeps_recall(dev, tiny_oracle_index, width):
 
 
 @pytest.mark.parametrize("metric", ["l2", "ip"])
-@pytest.mark.parametrize("d,k", [(64, 1), (64, 10), (128, 32), (192, 10)])
+@pytest.mark.parametrize("d,k", [(64, 1), (64, 10), (64, 16), (96, 10), (128, 32), (192, 10), (320, 10)])
 def test_bruteforce_tensor_core_vs_oracle(dev, metric, d, k, monkeypatch):
-    """Shapes that take the tcgen05 path (d a multiple of 64, k <= 32): split
-    BF16 MMAs, certified FP32 re-rank, SIMT redo of uncertified queries."""
+    """Shapes that take the tcgen05 paths: the pipelined kernel (k <= 16,
+    d <= 192, d padded to a multiple of 64) and the single-pass kernel
+    (k up to 32, d a multiple of 64): split BF16 MMAs, certified FP32
+    re-rank, SIMT redo of uncertified queries."""
     w = synthetic.small_mixture(5000, d, 300, n_comp=16, seed=17 + d + k, metric=metric,
                                 normalise=(metric == "ip"))
     X, Q = w.base, w.queries
