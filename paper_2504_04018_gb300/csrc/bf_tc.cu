@@ -479,11 +479,13 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     unsigned char *sA = base;
     unsigned char *sB = sA + (size_t)a.nk * STAGE;
     float *T = (float *)(sB + (size_t)a.S * STAGE);          // [128][kTS] half tile, transposed
-    float *L_d = T + TM * kTS;                               // [128][K1] per-row lists
+    float *s_xn = T + TM * kTS;                              // [2][128] tile norms
+    float *L_d = s_xn + 2 * TN;                              // [128][K1] per-row lists
     int32_t *L_i = (int32_t *)(L_d + TM * K1);
     int32_t *r_lo = L_i + TM * K1, *r_hi = r_lo + TM, *r_cnt = r_hi + TM, *r_ti = r_cnt + TM;
     float *r_qn = (float *)(r_ti + TM), *r_td = r_qn + TM;
-    uint64_t *bars = (uint64_t *)(r_td + TM);
+    uint32_t *s_flag = (uint32_t *)(r_td + TM);              // [2 halves][4 quarters] row masks
+    uint64_t *bars = (uint64_t *)(s_flag + 8);
     uint64_t *full = bars, *empty = bars + a.S;
     uint64_t *a_full = bars + 2 * a.S, *a_empty = a_full + 1;
     uint64_t *acc_full = a_full + 2, *acc_empty = a_full + 4, *drain = a_full + 6;
@@ -606,7 +608,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
         const int half = ew >> 2;           // column half it reads
         const int my_row = quarter * 32 + lane;
         const bool l2 = a.metric == ESG_L2SQ;
-        uint32_t acc_it = 0;
+        uint32_t acc_it = 0, tcount = 0;
         uint32_t pe[2] = {0u, 0u};
         bool ok = true;
         int cur_qt = -1;
@@ -632,12 +634,13 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             }
             for (int j = 0; j < I.cnt; ++j) {
                 const int32_t pt = a.tiles[I.off + j] * TN;   // first point of the tile
-                // norms of this lane's columns (both halves), loaded early
-                float xn[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int32_t p = pt + c * 32 + lane;
-                    xn[c] = (l2 && p < a.n) ? __ldg(a.xnorm + p) : 0.f;
+                // the tile's squared norms into shared memory (double buffered:
+                // the previous tile's readers are past a barrier)
+                float *xs_cur = s_xn + (tcount & 1u) * TN;
+                ++tcount;
+                if (et < TN) {
+                    const int32_t p = pt + et;
+                    xs_cur[et] = (l2 && p < a.n) ? __ldg(a.xnorm + p) : 0.f;
                 }
                 const uint32_t b = acc_it & 1u;
                 if (!wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err)) { ok = false; }
@@ -653,67 +656,100 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+                epi_bar();
+                // filter, one thread per row and half: distances of the 64
+                // columns, range mask, and the columns at or below the row's
+                // current K1-th distance (a superset of the insertions)
+                const int32_t pbm = pt + half * 64;
+                const int32_t lo = r_lo[my_row], hi = r_hi[my_row];
+                const float qn = r_qn[my_row], tdm = r_td[my_row];
+                const int jl = lo - pbm > 0 ? lo - pbm : 0;
+                const int jh = hi - pbm < 63 ? hi - pbm : 63;
+                const uint64_t rng = jl <= jh ? ((~0ull >> (63 - (jh - jl))) << jl) : 0ull;
+                uint64_t cand = 0ull;
+                const float4 *xv = (const float4 *)(xs_cur + half * 64);
+#pragma unroll
+                for (int c4 = 0; c4 < 16; ++c4) {
+                    const float4 x4 = xv[c4];
+                    const float xx[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = c4 * 4 + e;
+                        const float dd = l2 ? qn + xx[e] - 2.f * v[c] : -v[c];
+                        v[c] = dd;
+                        cand |= (uint64_t)(dd <= tdm) << c;
+                    }
+                }
+                cand &= rng;
+                const bool fl = cand != 0ull;
+                const uint32_t wm = __ballot_sync(0xffffffffu, fl);
+                if (lane == 0) s_flag[half * 4 + quarter] = wm;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (half == h) {
+                    // flagged rows of this half pass their distances through
+                    // shared memory (out-of-range columns as +inf)
+                    if (half == h && fl) {
 #pragma unroll
-                        for (int c = 0; c < 64; ++c) T[my_row * kTS + c] = v[c];
+                        for (int c = 0; c < 64; ++c)
+                            T[my_row * kTS + c] = ((rng >> c) & 1ull) ? v[c] : INFINITY;
                     }
                     epi_bar();
+                    // warp-cooperative insertion: the k-th flagged row goes to
+                    // epilogue warp k mod 8
                     const int32_t pb = pt + h * 64;
-                    const float xn0 = xn[2 * h], xn1 = xn[2 * h + 1];
-                    for (int rr = 0; rr < TM / kEpiWarps; ++rr) {
-                        const int r = ew + kEpiWarps * rr;
-                        const int32_t lo = r_lo[r], hi = r_hi[r];
-                        if (hi < pb || lo > pb + 63) continue;          // warp-uniform
-                        const int32_t p0 = pb + lane, p1 = p0 + 32;
-                        const float x0 = T[r * kTS + lane], x1 = T[r * kTS + lane + 32];
-                        const float qn = r_qn[r];
-                        const bool in0 = p0 >= lo && p0 <= hi, in1 = p1 >= lo && p1 <= hi;
-                        const float d0 = l2 ? qn + xn0 - 2.f * x0 : -x0;
-                        const float d1 = l2 ? qn + xn1 - 2.f * x1 : -x1;
-                        float td = r_td[r];
-                        int32_t ti = r_ti[r];
-                        uint32_t m0 = __ballot_sync(0xffffffffu, in0 && dl_less(d0, p0, td, ti));
-                        uint32_t m1 = __ballot_sync(0xffffffffu, in1 && dl_less(d1, p1, td, ti));
-                        if ((m0 | m1) == 0u) continue;                  // warp-uniform
-                        // the row's list in registers: entries lane and lane + 32
-                        int cnt = r_cnt[r];
-                        float ld0 = lane < cnt ? L_d[r * K1 + lane] : INFINITY;
-                        int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
-                        float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
-                        int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
-                        while ((m0 | m1) != 0u) {
-                            const bool second = m0 == 0u;
-                            const int src = __ffs(second ? m1 : m0) - 1;
-                            if (second) m1 &= m1 - 1; else m0 &= m0 - 1;
-                            const float cd = __shfl_sync(0xffffffffu, second ? d1 : d0, src);
-                            const int32_t ci = (second ? p1 : p0) - lane + src;
-                            if (cnt == K1 && !dl_less(cd, ci, td, ti)) continue;
-                            const int pos = __popc(__ballot_sync(0xffffffffu, lane < cnt && dl_less(ld0, li0, cd, ci))) +
-                                            __popc(__ballot_sync(0xffffffffu, lane + 32 < cnt && dl_less(ld1, li1, cd, ci)));
-                            const float u0d = __shfl_up_sync(0xffffffffu, ld0, 1);
-                            const int32_t u0i = __shfl_up_sync(0xffffffffu, li0, 1);
-                            float u1d = __shfl_up_sync(0xffffffffu, ld1, 1);
-                            int32_t u1i = __shfl_up_sync(0xffffffffu, li1, 1);
-                            const float t31d = __shfl_sync(0xffffffffu, ld0, 31);
-                            const int32_t t31i = __shfl_sync(0xffffffffu, li0, 31);
-                            if (lane == 0) { u1d = t31d; u1i = t31i; }
-                            if (lane > pos) { ld0 = u0d; li0 = u0i; }
-                            else if (lane == pos) { ld0 = cd; li0 = ci; }
-                            if (lane + 32 > pos) { ld1 = u1d; li1 = u1i; }
-                            else if (lane + 32 == pos) { ld1 = cd; li1 = ci; }
-                            if (cnt < K1) ++cnt;
-                            if (cnt == K1) {
-                                const int e = K1 - 1;
-                                td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
-                                ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
+                    int k = 0;
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w = s_flag[h * 4 + q];
+                        while (w != 0u) {
+                            const int bit = __ffs(w) - 1;
+                            w &= w - 1;
+                            if ((k++ & (kEpiWarps - 1)) != ew) continue;
+                            const int r = q * 32 + bit;
+                            const int32_t p0 = pb + lane, p1 = p0 + 32;
+                            const float d0 = T[r * kTS + lane], d1 = T[r * kTS + lane + 32];
+                            float td = r_td[r];
+                            int32_t ti = r_ti[r];
+                            uint32_t m0 = __ballot_sync(0xffffffffu, d0 < INFINITY && dl_less(d0, p0, td, ti));
+                            uint32_t m1 = __ballot_sync(0xffffffffu, d1 < INFINITY && dl_less(d1, p1, td, ti));
+                            if ((m0 | m1) == 0u) continue;                  // warp-uniform
+                            // the row's list in registers: entries lane and lane + 32
+                            int cnt = r_cnt[r];
+                            float ld0 = lane < cnt ? L_d[r * K1 + lane] : INFINITY;
+                            int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
+                            float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
+                            int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
+                            while ((m0 | m1) != 0u) {
+                                const bool second = m0 == 0u;
+                                const int src = __ffs(second ? m1 : m0) - 1;
+                                if (second) m1 &= m1 - 1; else m0 &= m0 - 1;
+                                const float cd = __shfl_sync(0xffffffffu, second ? d1 : d0, src);
+                                const int32_t ci = pb + (second ? 32 : 0) + src;
+                                if (cnt == K1 && !dl_less(cd, ci, td, ti)) continue;
+                                const int pos = __popc(__ballot_sync(0xffffffffu, lane < cnt && dl_less(ld0, li0, cd, ci))) +
+                                                __popc(__ballot_sync(0xffffffffu, lane + 32 < cnt && dl_less(ld1, li1, cd, ci)));
+                                const float u0d = __shfl_up_sync(0xffffffffu, ld0, 1);
+                                const int32_t u0i = __shfl_up_sync(0xffffffffu, li0, 1);
+                                float u1d = __shfl_up_sync(0xffffffffu, ld1, 1);
+                                int32_t u1i = __shfl_up_sync(0xffffffffu, li1, 1);
+                                const float t31d = __shfl_sync(0xffffffffu, ld0, 31);
+                                const int32_t t31i = __shfl_sync(0xffffffffu, li0, 31);
+                                if (lane == 0) { u1d = t31d; u1i = t31i; }
+                                if (lane > pos) { ld0 = u0d; li0 = u0i; }
+                                else if (lane == pos) { ld0 = cd; li0 = ci; }
+                                if (lane + 32 > pos) { ld1 = u1d; li1 = u1i; }
+                                else if (lane + 32 == pos) { ld1 = cd; li1 = ci; }
+                                if (cnt < K1) ++cnt;
+                                if (cnt == K1) {
+                                    const int e = K1 - 1;
+                                    td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
+                                    ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
+                                }
                             }
+                            if (lane < cnt) { L_d[r * K1 + lane] = ld0; L_i[r * K1 + lane] = li0; }
+                            if (lane + 32 < cnt) { L_d[r * K1 + lane + 32] = ld1; L_i[r * K1 + lane + 32] = li1; }
+                            if (lane == 0) { r_cnt[r] = cnt; r_td[r] = td; r_ti[r] = ti; }
+                            __syncwarp();
                         }
-                        if (lane < cnt) { L_d[r * K1 + lane] = ld0; L_i[r * K1 + lane] = li0; }
-                        if (lane + 32 < cnt) { L_d[r * K1 + lane + 32] = ld1; L_i[r * K1 + lane + 32] = li1; }
-                        if (lane == 0) { r_cnt[r] = cnt; r_td[r] = td; r_ti[r] = ti; }
-                        __syncwarp();
                     }
                     // one thread samples the abort flag before the last barrier
                     // of the tile, all read the sample after it: every epilogue
@@ -842,13 +878,15 @@ __global__ void merge_parts_kernel(const float *part_d, const int32_t *part_i, c
 
 }  // namespace
 
-// Exact FP32 re-rank of the candidate lists, certificate, and the exact SIMT
-// pass for the queries left uncertified (or for all, after an aborted wait).
+// Exact FP32 re-rank of the candidate lists and certificate. The queries left
+// uncertified go to `leftover` when it is given, else through the exact SIMT
+// pass here.
 static esg_status certify_and_redo(const float *base, int64_t n, int32_t d, int metric, const float *queries,
                                    int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int K1,
                                    const float *cand_d, const int32_t *cand_i, const int32_t *cand_n,
                                    const float *qrow, const float *xmax, int32_t *redo, const int32_t *err,
-                                   int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
+                                   int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream,
+                                   std::vector<int64_t> *leftover = nullptr) {
     rerank_certify_kernel<<<ceil_div_i(nq, 4), 128, 0, stream>>>(
         base, queries, d, metric, nq, k, K1, cand_d, cand_i, cand_n, qrow, xmax, out_ids, out_dist, out_count, redo);
     cudaError_t ce = cudaGetLastError();
@@ -864,7 +902,9 @@ static esg_status certify_and_redo(const float *base, int64_t n, int32_t d, int 
     for (int64_t i = 0; i < nq; ++i) if (h_redo[i]) idx.push_back(i);
     const char *dbg = getenv("ESG_BF_STATS");
     if (dbg && *dbg == '1')
-        fprintf(stderr, "tensor-core brute force: %lld of %lld queries recomputed\n", (long long)idx.size(), (long long)nq);
+        fprintf(stderr, "tensor-core brute force: %lld of %lld queries left uncertified (list of %d)\n",
+                (long long)idx.size(), (long long)nq, K1);
+    if (leftover) { leftover->swap(idx); return ESG_OK; }
     if (idx.empty()) return ESG_OK;
     return esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist, out_count, stream);
 }
@@ -927,24 +967,114 @@ static esg_status bruteforce_tc_v1(const float *base, int64_t n, int32_t d, int 
     return st;
 }
 
-// Pipelined tensor-core path; ESG_ERR_UNSUPPORTED when the shape does not fit
-// (k > 16, or shared memory for fewer than two stages).
-static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int metric, const float *queries,
-                                   int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
-                                   float *out_dist, int32_t *out_count, cudaStream_t stream) {
-    const int K1 = 2 * k + 8;
-    if (k < 1 || K1 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
+// Shared-memory plan of the pipelined kernel for a dimension and list length:
+// ESG_ERR_UNSUPPORTED when fewer than two point stages fit.
+static esg_status bf2_smem(int32_t d, int K1, int max_smem, int *S, size_t *smem) {
+    if (K1 > kMaxK1v2 || d < 1) return ESG_ERR_UNSUPPORTED;
     const int nk = (d + TK - 1) / TK;
-    int dev = 0, max_smem = 0, sms = 0;
+    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + 2 * TN * 4 + (size_t)TM * K1 * 8 +
+                         6 * TM * 4 + 8 * 4 + 8 * (2 * kMaxStages + 8) + 16;
+    if ((size_t)max_smem < fixed + 2 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
+    *S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - fixed) / STAGE);
+    *smem = fixed + (size_t)*S * STAGE;
+    return ESG_OK;
+}
+
+// The point side, prepared once per call: tiled BF16 splits, squared norms,
+// row norms and their maximum.
+struct PreparedX {
+    const unsigned char *xs;
+    const float *xnorm, *xrow, *xmax;
+};
+
+__global__ void gather_subset_kernel(const float *Q, const int64_t *l, const int64_t *r, int d,
+                                     const int64_t *idx, int64_t m, float *Qg, int64_t *lg, int64_t *rg) {
+    const int64_t i = blockIdx.x;
+    if (i >= m) return;
+    const int64_t q = idx[i];
+    for (int j = threadIdx.x; j < d; j += blockDim.x) Qg[i * d + j] = Q[q * d + j];
+    if (threadIdx.x == 0) { lg[i] = l[q]; rg[i] = r[q]; }
+}
+
+__global__ void scatter_subset_kernel(const int64_t *idx, int64_t m, int k, const int64_t *ids_g,
+                                      const float *dist_g, const int32_t *cnt_g, int64_t *ids, float *dist,
+                                      int32_t *cnt) {
+    const int64_t i = blockIdx.x;
+    if (i >= m) return;
+    const int64_t q = idx[i];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        ids[q * k + j] = ids_g[i * k + j];
+        dist[q * k + j] = dist_g[i * k + j];
+    }
+    if (threadIdx.x == 0) cnt[q] = cnt_g[i];
+}
+
+static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
+                              const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
+                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream);
+
+// Queries whose list of K1 candidates could not be certified run again with
+// the longest list that fits the kernel (their own plan, a few query tiles), and
+// through the exact SIMT kernel if they are still uncertified.
+static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
+                               const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
+                               int K1, const std::vector<int64_t> &idx, int64_t *out_ids, float *out_dist,
+                               int32_t *out_count, cudaStream_t stream) {
+    int dev = 0, max_smem = 0, S = 0;
+    size_t smem = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int K2 = kMaxK1v2;   // the longest list that fits
+    while (K2 > K1 && bf2_smem(d, K2, max_smem, &S, &smem) != ESG_OK) --K2;
+    if (K2 <= K1)
+        return esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist, out_count, stream);
+    const int64_t m = (int64_t)idx.size();
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bytes = al(sizeof(int64_t) * m) + al(sizeof(float) * m * d) + 2 * al(sizeof(int64_t) * m) +
+                         al(sizeof(int64_t) * m * k) + al(sizeof(float) * m * k) + al(sizeof(int32_t) * m);
+    unsigned char *sc = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&sc, bytes, stream));
+    unsigned char *p = sc;
+    int64_t *didx = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    float *Qg = (float *)p; p += al(sizeof(float) * m * d);
+    int64_t *lg = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    int64_t *rg = (int64_t *)p; p += al(sizeof(int64_t) * m);
+    int64_t *ig = (int64_t *)p; p += al(sizeof(int64_t) * m * k);
+    float *dg = (float *)p; p += al(sizeof(float) * m * k);
+    int32_t *cg = (int32_t *)p;
+    esg_status st = ESG_OK;
+    cudaError_t ce = cudaMemcpyAsync(didx, idx.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess) {
+        gather_subset_kernel<<<(unsigned)m, 128, 0, stream>>>(queries, l, r, d, didx, m, Qg, lg, rg);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    if (st == ESG_OK) st = bf2_queries(X, base, n, d, metric, Qg, m, lg, rg, k, K2, ig, dg, cg, stream);
+    if (st == ESG_OK) {
+        scatter_subset_kernel<<<(unsigned)m, 128, 0, stream>>>(didx, m, k, ig, dg, cg, out_ids, out_dist, out_count);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    }
+    // the host index vector must outlive the copy above
+    const cudaError_t se = cudaStreamSynchronize(stream);
+    if (st == ESG_OK && se != cudaSuccess) { esg_set_error(cudaGetErrorString(se)); st = ESG_ERR_CUDA; }
+    cudaFreeAsync(sc, stream);
+    return st;
+}
+
+// One pass of the pipelined kernel over a batch of queries against the
+// prepared points, then merge, re-rank, certificate and escalation.
+static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
+                              const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
+                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    if (nq == 0) return ESG_OK;
+    const int nk = (d + TK - 1) / TK;
+    int dev = 0, max_smem = 0, sms = 0, S = 0;
+    size_t smem = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + (size_t)TM * K1 * 8 + 6 * TM * 4 +
-                         8 * (2 * kMaxStages + 8) + 16;
-    if ((size_t)max_smem < fixed + 2 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
-    const int S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - fixed) / STAGE);
-    const size_t smem = fixed + (size_t)S * STAGE;
-    if (nq == 0) return ESG_OK;
+    if (bf2_smem(d, K1, max_smem, &S, &smem) != ESG_OK) return ESG_ERR_UNSUPPORTED;
 
     // ---- host plan: sort queries by (log2 width, l), tile them, list the
     // point tiles each query tile covers and cut the lists into work items
@@ -980,6 +1110,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
         }
         for (auto &x : spans[qt]) total_tiles += x.second - x.first + 1;
     }
+    if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
     const int64_t CH = std::max<int64_t>(8, std::min<int64_t>(1024, (total_tiles + 4 * sms - 1) / (4 * (int64_t)sms)));
     std::vector<int32_t> tiles;
     tiles.reserve(total_tiles);
@@ -995,36 +1126,30 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     }
     item_begin[nqt] = (int32_t)items.size();
     const int64_t n_items = (int64_t)items.size();
-    if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
 
-    // ---- device scratch
-    const int64_t xt = (n + TN - 1) / TN;
+    // ---- query-side scratch
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t bytes = al((size_t)xt * nk * STAGE) + al((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE) +
-                   4 * al(sizeof(float) * std::max<int64_t>(n, nq)) + al(sizeof(float) * 4) +
-                   al(sizeof(int32_t) * std::max<int64_t>(nv, 1)) + al(sizeof(WorkItem) * std::max<int64_t>(n_items, 1)) +
+    const int64_t ni1 = std::max<int64_t>(n_items, 1);
+    size_t bytes = al((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE) + 2 * al(sizeof(float) * nq) +
+                   al(sizeof(int32_t) * std::max<int64_t>(nv, 1)) + al(sizeof(WorkItem) * ni1) +
                    al(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1)) + al(sizeof(int32_t) * (nqt + 1)) +
-                   2 * al((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM) +
-                   al(sizeof(int32_t) * std::max<int64_t>(n_items, 1) * TM) +
-                   al((sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1) + 3 * al(sizeof(int32_t) * nq) + 256;
+                   2 * al((size_t)4 * ni1 * K1 * TM) + al(sizeof(int32_t) * ni1 * TM) +
+                   al((sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1) + 3 * al(sizeof(int32_t) * nq) +
+                   al(sizeof(int32_t) * 4);
     unsigned char *scratch = nullptr;
     ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
     unsigned char *p = scratch;
     auto take = [&](size_t b) { unsigned char *q = p; p += al(b); return q; };
-    unsigned char *xs = take((size_t)xt * nk * STAGE);
     unsigned char *qs = take((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE);
-    float *xnorm = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
-    float *xrow = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
-    float *qnorm = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
-    float *qrow = (float *)take(sizeof(float) * std::max<int64_t>(n, nq));
-    float *xmax = (float *)take(sizeof(float) * 4);
+    float *qnorm = (float *)take(sizeof(float) * nq);
+    float *qrow = (float *)take(sizeof(float) * nq);
     int32_t *d_order = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(nv, 1));
-    WorkItem *d_items = (WorkItem *)take(sizeof(WorkItem) * std::max<int64_t>(n_items, 1));
+    WorkItem *d_items = (WorkItem *)take(sizeof(WorkItem) * ni1);
     int32_t *d_tiles = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1));
     int32_t *d_ib = (int32_t *)take(sizeof(int32_t) * (nqt + 1));
-    float *part_d = (float *)take((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM);
-    int32_t *part_i = (int32_t *)take((size_t)4 * std::max<int64_t>(n_items, 1) * K1 * TM);
-    int32_t *part_n = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(n_items, 1) * TM);
+    float *part_d = (float *)take((size_t)4 * ni1 * K1 * TM);
+    int32_t *part_i = (int32_t *)take((size_t)4 * ni1 * K1 * TM);
+    int32_t *part_n = (int32_t *)take(sizeof(int32_t) * ni1 * TM);
     float *cand_d = (float *)take(sizeof(float) * (size_t)nq * K1);
     int32_t *cand_i = (int32_t *)take(sizeof(int32_t) * (size_t)nq * K1);
     int32_t *cand_n = (int32_t *)take(sizeof(int32_t) * nq);
@@ -1032,8 +1157,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     int32_t *err = (int32_t *)take(sizeof(int32_t) * 4);
 
     esg_status st = ESG_OK;
-    cudaError_t ce = cudaMemsetAsync(xmax, 0, sizeof(float) * 4, stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, stream);
+    cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(int32_t) * 4, stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(cand_n, 0xFF, sizeof(int32_t) * nq, stream);   // -1: invalid
     if (ce == cudaSuccess && nv > 0)
         ce = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nv, cudaMemcpyHostToDevice, stream);
@@ -1044,10 +1168,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(d_ib, item_begin.data(), sizeof(int32_t) * (nqt + 1), cudaMemcpyHostToDevice, stream);
     if (ce == cudaSuccess) {
-        norms_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(base, n, d, xnorm, xrow);
         norms_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(queries, nq, d, qnorm, qrow);
-        max_kernel<<<152, 256, 0, stream>>>(xrow, n, xmax);
-        tile_split_kernel<<<ceil_div_i(xt * TN * nk * 8, 256), 256, 0, stream>>>(base, n, d, nk, nullptr, xt * TN, xs);
         if (nqt > 0)
             tile_split_kernel<<<ceil_div_i(nqt * TM * nk * 8, 256), 256, 0, stream>>>(queries, nv, d, nk, d_order,
                                                                                      nqt * TM, qs);
@@ -1057,7 +1178,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     if (ce == cudaSuccess && n_items > 0) {
         // MMA work issued: three 128 x 128 x 64 BF16 products per point tile and K chunk
         esg_prof_tensor_flops((double)total_tiles * nk * 3.0 * 2.0 * TM * TN * TK);
-        Tc2Args a{xs, qs, xnorm, qnorm, l, r, d_order, d_items, d_tiles, (int)n_items, nv, nk, metric, K1, S,
+        Tc2Args a{X.xs, qs, X.xnorm, qnorm, l, r, d_order, d_items, d_tiles, (int)n_items, nv, nk, metric, K1, S,
                   n, part_d, part_i, part_n, err};
         const int pidx = esg_prof_begin(stream);
         tc_knn2_kernel<<<(unsigned)std::min<int64_t>(n_items, sms), kThreads2, smem, stream>>>(a);
@@ -1074,9 +1195,57 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     if (dbg && *dbg == '1')
         fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items of <= %lld, %d stages\n",
                 (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S);
+    std::vector<int64_t> left;
     if (st == ESG_OK)
-        st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, xmax,
-                              redo, err, out_ids, out_dist, out_count, stream);
+        st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, X.xmax,
+                              redo, err, out_ids, out_dist, out_count, stream, &left);
+    cudaFreeAsync(scratch, stream);
+    if (st == ESG_OK && !left.empty())
+        st = bf2_escalate(X, base, n, d, metric, queries, nq, l, r, k, K1, left, out_ids, out_dist, out_count, stream);
+    return st;
+}
+
+// Pipelined tensor-core path; ESG_ERR_UNSUPPORTED when the shape does not fit
+// (k > 56, or shared memory for fewer than two stages). Each list keeps
+// K1 = k + 8 approximate candidates: the certificate needs the exact k-th
+// distance below the approximate K1-th minus the error bound, which holds for
+// nearly every query, and a short list makes the epilogue's filter sharp; the
+// few queries left uncertified run again with 64 candidates.
+static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int metric, const float *queries,
+                                   int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
+                                   float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    const int K1 = k + 8;
+    if (k < 1 || K1 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
+    int dev = 0, max_smem = 0, S = 0;
+    size_t smem = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (bf2_smem(d, K1, max_smem, &S, &smem) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+    if (nq == 0) return ESG_OK;
+    const int nk = (d + TK - 1) / TK;
+    const int64_t xt = (n + TN - 1) / TN;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bytes = al((size_t)xt * nk * STAGE) + 2 * al(sizeof(float) * n) + al(sizeof(float) * 4);
+    unsigned char *scratch = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
+    unsigned char *p = scratch;
+    unsigned char *xs = p; p += al((size_t)xt * nk * STAGE);
+    float *xnorm = (float *)p; p += al(sizeof(float) * n);
+    float *xrow = (float *)p; p += al(sizeof(float) * n);
+    float *xmax = (float *)p;
+    esg_status st = ESG_OK;
+    cudaError_t ce = cudaMemsetAsync(xmax, 0, sizeof(float) * 4, stream);
+    if (ce == cudaSuccess) {
+        norms_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(base, n, d, xnorm, xrow);
+        max_kernel<<<152, 256, 0, stream>>>(xrow, n, xmax);
+        tile_split_kernel<<<ceil_div_i(xt * TN * nk * 8, 256), 256, 0, stream>>>(base, n, d, nk, nullptr, xt * TN, xs);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    if (st == ESG_OK) {
+        const PreparedX X{xs, xnorm, xrow, xmax};
+        st = bf2_queries(X, base, n, d, metric, queries, nq, l, r, k, K1, out_ids, out_dist, out_count, stream);
+    }
     cudaFreeAsync(scratch, stream);
     return st;
 }

@@ -141,6 +141,26 @@ def test_bruteforce_ties_by_row(dev):
         assert ids[i, :3].tolist() == sorted(ids[i, :3].tolist())
 
 
+def test_bruteforce_uncertified_queries_escalate(dev, monkeypatch):
+    """Equal distances leave no gap for the tensor-core certificate: such
+    queries run again with a longer candidate list and then through the
+    exact SIMT kernel; the answer is still the oracle's (ties by row)."""
+    monkeypatch.delenv("ESG_BF_SIMT", raising=False)
+    rng = np.random.default_rng(11)
+    X = np.repeat(rng.standard_normal((1, 64)).astype(np.float32), 3000, axis=0)
+    X[::7] += 0.5                           # some rows farther away
+    Q = rng.standard_normal((40, 64)).astype(np.float32)
+    l = rng.integers(0, 2000, 40).astype(np.int64)
+    r = (l + rng.integers(0, 999, 40)).astype(np.int64)
+    ids, dist, count = E.esg_bruteforce_filtered_knn(_t(X, dev), _t(Q, dev), _t(l, dev), _t(r, dev), 10)
+    torch.cuda.synchronize()
+    ids, count = ids.cpu().numpy(), count.cpu().numpy()
+    for i in range(40):
+        gt, _ = O.bruteforce(X.astype(np.float64), Q[i].astype(np.float64), int(l[i]), int(r[i]), 10, "l2")
+        assert count[i] == len(gt)
+        assert ids[i, :count[i]].tolist() == gt.tolist()
+
+
 # ----------------------------------------------------- search on oracle graph
 
 @pytest.fixture(scope="module")
