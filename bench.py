@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget variant")
+    ap.add_argument("--mode", default="search", choices=["search", "bruteforce"],
+                    help="bruteforce: time only the exact filtered k-NN of the workload's queries")
     return ap.parse_args()
 
 
@@ -259,6 +261,27 @@ VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16
                                     for wd in (1, 2) if not (t == "f32" and wd == 1)]
 ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
 N_TRAIN = 20_000
+
+
+def run_bruteforce_only(args, local):
+    """Exact filtered k-NN of the workload's queries over the rank-ordered
+    points, tcgen05 path against the SIMT kernel (no index is built)."""
+    import torch
+    import paper_2504_04018_gb300 as E
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E.load_library()
+    w = workload(args)
+    perm = np.argsort(w.attr, kind="stable")      # rank order: attribute, ties by id
+    Xr = torch.as_tensor(w.base[perm], device=dev)
+    Q = torch.as_tensor(w.queries, device=dev)
+    L = torch.as_tensor(w.l, device=dev)
+    Rr = torch.as_tensor(w.r, device=dev)
+    info = bruteforce_timing(E, torch, Xr, Q, L, Rr, w, args)
+    print(json.dumps({"mode": "bruteforce", "metric": "exact RF-kNN queries/sec (k=10)",
+                      "value": info["qps_tcgen05"], "unit": "queries/s", "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "bf16x3+f32", "data": "synthetic",
+                      "config": workload_config(args), "bruteforce": info}), flush=True)
 
 
 def run_ours(args, rank, world, local):
@@ -500,6 +523,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "bruteforce":
+        if rank == 0:
+            run_bruteforce_only(args, local)
         return
     run_ours(args, rank, world, local)
 
