@@ -261,6 +261,9 @@ VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16
                                     for wd in (1, 2) if not (t == "f32" and wd == 1)]
 ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
 N_TRAIN = 20_000
+# largest beam width the learned budget may pick: the candidate list and the
+# visited table are sized for it, so a tight cap keeps more warps resident
+LEARNED_EF_HI = 64
 
 
 def run_bruteforce_only(args, local):
@@ -405,10 +408,10 @@ def run_ours(args, rank, world, local):
         t1 = time.perf_counter()
         rep = E.esg_train_predictor(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
                                     torch.as_tensor(tgc, device=dev), k_max=10,
-                                    target_recall=TARGET_RECALL + 0.005, ef_lo=8, ef_hi=128,
+                                    target_recall=TARGET_RECALL + 0.005, ef_lo=8, ef_hi=LEARNED_EF_HI,
                                     traversal=trav, epochs=40)
         train_s = time.perf_counter() - t1
-        base = E.search_params(ef=128, traversal=trav, use_learned=1)
+        base = E.search_params(ef=LEARNED_EF_HI, traversal=trav, use_learned=1)
         tuned, trec, tms = E.esg_autotune(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
                                           torch.as_tensor(tgc, device=dev), k_max=10,
                                           target_recall=TARGET_RECALL, base=base)
@@ -440,7 +443,7 @@ def run_ours(args, rank, world, local):
                   "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
                   "launches": launches // max(1, args.steps + args.warmup) * args.steps, "graph": True})
         results[name + "-graph"] = g
-        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "train_s": round(train_s, 2),
+        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "ef_hi": LEARNED_EF_HI, "train_s": round(train_s, 2),
                         "train_loss": float(rep[0]), "heldout_recall": float(rep[1]),
                         "ef_margin_log2": float(rep[2]), "heldout_evals_per_query": float(rep[3]),
                         "autotune": {"params": tuned.as_dict(), "recall": trec, "ms": tms}}

@@ -401,8 +401,12 @@ esg_status esg_bruteforce_filtered_knn(const float *base, int64_t n, int32_t d, 
 esg_status esg_attr_to_rank_range(const esg_index *index, const double *lo, const double *hi,
                                   int64_t nq, int64_t *l, int64_t *r);
 
-/* Save / load an index (graphs, vectors, permutation, parameters) with a
- * versioned header and per-section CRC32. */
+/* Save / load an index (graphs, vectors, permutation, parameters, the
+ * learned predictor) with a versioned header and per-section CRC32. The
+ * FP32 rows are stored; the BF16 / FP8 copies the index held are rebuilt on
+ * load (quantisation is deterministic). Host path; ESG_ERR_IO when the file
+ * cannot be opened or written, ESG_ERR_CORRUPT when the header, a size or a
+ * CRC does not match (including files of another format version). */
 esg_status esg_save(const esg_index *index, const char *path);
 esg_status esg_load(const char *path, esg_index **out);
 

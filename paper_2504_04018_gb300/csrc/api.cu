@@ -377,7 +377,7 @@ esg_status esg_attr_to_rank_range(const esg_index *ix, const double *lo, const d
 
 namespace {
 const char kMagic[8] = {'E', 'S', 'G', 'G', 'B', '3', '0', '0'};
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;
 
 struct FileHeader {
     char magic[8];
@@ -388,6 +388,8 @@ struct FileHeader {
     uint64_t attr_count;
     uint64_t mlp_count;       // floats of the learned predictor's blob (0: none)
     int32_t mlp_ef_lo, mlp_ef_hi;
+    int32_t storage_mask;     // bit t: rows of esg_dtype t are held (low-precision copies are rebuilt on load)
+    int32_t reserved;
 };
 
 bool write_section(FILE *f, const void *data, size_t bytes) {
@@ -427,6 +429,7 @@ esg_status esg_save(const esg_index *ix, const char *path) {
     h.n_heap = ix->n_heap; h.attr_count = ix->attr_sorted.size();
     h.mlp_count = ix->mlp_ready ? ix->mlp_host.size() : 0;
     h.mlp_ef_lo = ix->mlp_ef_lo; h.mlp_ef_hi = ix->mlp_ef_hi;
+    h.storage_mask = (1 << ESG_F32) | (ix->Xb ? 1 << ESG_BF16 : 0) | (ix->X8 ? 1 << ESG_FP8E4M3 : 0);
     bool ok = write_section(f, &h, sizeof(h)) && write_section(f, X.data(), sizeof(float) * X.size()) &&
               write_section(f, ix->perm_host.data(), sizeof(int64_t) * ix->n) &&
               write_section(f, adj.data(), sizeof(uint32_t) * adj.size()) &&
@@ -481,6 +484,11 @@ esg_status esg_load(const char *path, esg_index **out) {
     if (s != ESG_OK) return s;
     ix->M = h.M;
     ix->attr_sorted.swap(attr);
+    for (int t : {ESG_BF16, ESG_FP8E4M3}) {
+        if (!(h.storage_mask & (1 << t))) continue;
+        s = esg_index_add_storage(ix, (esg_dtype)t);
+        if (s != ESG_OK) { esg_free(ix); return s; }
+    }
     if (!mlp.empty()) {
         s = esg_predictor_set(ix, mlp.data(), h.mlp_ef_lo, h.mlp_ef_hi);
         if (s != ESG_OK) { esg_free(ix); return s; }

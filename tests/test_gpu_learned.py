@@ -150,3 +150,23 @@ def test_predictor_survives_save_load(learned_setup, tmp_path):
     b = E.esg_search_batch(g2, q[:300], l[:300], r[:300], None, 10, ef=128, use_learned=1)[0]
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_low_precision_rows_survive_save_load(learned_setup, tmp_path):
+    """BF16 and FP8 copies added to an index are rebuilt on load, bit for bit."""
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    for t in ("bf16", "fp8"):
+        E.esg_index_add_storage(gix, t)
+    path = str(tmp_path / "idx_lp.esg")
+    E.esg_save(gix, path)
+    g2 = E.esg_load(path)
+    for t in ("bf16", "fp8"):
+        rows_a, scale_a = E.esg_index_export_storage(gix, t)
+        rows_b, scale_b = E.esg_index_export_storage(g2, t)
+        assert np.array_equal(rows_a, rows_b)
+        if scale_a is not None:
+            assert np.array_equal(scale_a, scale_b)
+        a = E.esg_search_batch(gix, q[:300], l[:300], r[:300], None, 10, ef=32, traversal=t)[0]
+        b = E.esg_search_batch(g2, q[:300], l[:300], r[:300], None, 10, ef=32, traversal=t)[0]
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
