@@ -297,8 +297,10 @@ void esg_batch_free(esg_batch *batch);
  * Autotuner (library-specific; no counterpart in the paper). Given sample
  * queries with their exact answers (gt_ids device [nq, k_max] original ids,
  * -1 padded; gt_count device [nq]), it chooses the smallest beam width ef
- * (from 8..1024) and search width (1 or 2) whose mean recall@k reaches
- * target_recall, then the fastest launch shape (warps per block, visited-table
+ * (from 8..1024) and search width (1 or 2) whose recall reaches
+ * target_recall (hits among each query's first min(k_i, gt_count_i) exact ids,
+ * summed, over the sum of min(k_i, gt_count_i); k_i = k[i], or k_max when k
+ * is NULL), then the fastest launch shape (warps per block, visited-table
  * slots, lanes per row) by timing with CUDA events. `base` supplies the other
  * fields (traversal, rerank, ...). Writes the chosen parameters to `out` and,
  * if `report` is not NULL, [recall, milliseconds per search of the sample].
@@ -324,7 +326,8 @@ esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq
  * esg_train_predictor: traces the plain search (fixed ef over a grid within
  * [ef_lo, ef_hi]) on training queries with exact answers (gt_ids device
  * [nq, k_max] original ids, -1 padded; gt_count device [nq]); labels each
- * query with the smallest ef whose recall reaches per_query_recall and the
+ * query with the smallest ef whose recall (denominator min(k_i, gt_count_i),
+ * as in esg_autotune) reaches per_query_recall and the
  * expansions it used; trains the MLP with a pinball loss at `quantile` using
  * the library's GPU forward/backward/Adam kernels (epochs, batch, lr, seed);
  * then calibrates a margin on the last val_fraction of the queries so their

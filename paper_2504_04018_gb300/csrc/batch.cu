@@ -148,24 +148,28 @@ void esg_batch_free(esg_batch *b) {
 // ------------------------------------------------------------------ autotune
 
 namespace {
-// hits[i] = |returned ids of query i  ∩  gt ids of query i|
-__global__ void recall_hits_kernel(int64_t nq, int32_t k_max, const int64_t *ids, const int32_t *cnt,
-                                   const int64_t *gt, const int32_t *gcnt, int32_t *hits) {
+// hits[i] = |returned ids of query i  ∩  its first min(k_i, gcnt_i) gt ids|
+// (k null: k_i = k_max); the recall denominator of query i is min(k_i, gcnt_i)
+__global__ void recall_hits_kernel(int64_t nq, int32_t k_max, const int32_t *k, const int64_t *ids,
+                                   const int32_t *cnt, const int64_t *gt, const int32_t *gcnt, int32_t *hits) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq) return;
+    int kk = k ? k[i] : k_max;
+    kk = kk < 0 ? 0 : (kk > k_max ? k_max : kk);
+    const int g = min(gcnt[i], kk);
     int h = 0;
-    for (int a = 0; a < cnt[i]; ++a) {
+    for (int a = 0; a < min(cnt[i], kk); ++a) {
         const int64_t x = ids[i * k_max + a];
-        for (int b = 0; b < gcnt[i]; ++b)
+        for (int b = 0; b < g; ++b)
             if (gt[i * k_max + b] == x) { ++h; break; }
     }
     hits[i] = h;
 }
 }  // namespace
 
-esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int64_t *ids, const int32_t *cnt,
+esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int32_t *k, const int64_t *ids, const int32_t *cnt,
                            const int64_t *gt, const int32_t *gcnt, int32_t *hits, cudaStream_t stream) {
-    recall_hits_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(nq, k_max, ids, cnt, gt, gcnt, hits);
+    recall_hits_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(nq, k_max, k, ids, cnt, gt, gcnt, hits);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }
@@ -211,7 +215,7 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
     auto recall_of = [&](const esg_search_params &pp, double &rec) -> esg_status {
         esg_status s2 = search(pp);
         if (s2 != ESG_OK) return s2;
-        recall_hits_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(nq, k_max, ids, cnt, gt_ids, gt_count, hits);
+        recall_hits_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(nq, k_max, k, ids, cnt, gt_ids, gt_count, hits);
         if (cudaMemcpyAsync(h_hits.data(), hits, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) { esg_set_error("autotune: recall copy"); return ESG_ERR_CUDA; }
         double h = 0;
@@ -246,10 +250,12 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
         st = ESG_ERR_OOM;
     }
     if (st == ESG_OK) {
-        if (cudaMemcpy(h_gc.data(), gt_count, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        std::vector<int32_t> h_k(nq, k_max);
+        if (cudaMemcpy(h_gc.data(), gt_count, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (k && cudaMemcpy(h_k.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost) != cudaSuccess)) {
             esg_set_error("autotune: gt copy"); st = ESG_ERR_CUDA;
         }
-        for (int64_t i = 0; i < nq; ++i) gt_total += h_gc[i];
+        for (int64_t i = 0; i < nq; ++i) gt_total += std::min(h_gc[i], std::max(0, std::min(h_k[i], k_max)));
     }
     // 1. smallest ef reaching the target, per search width (with the learned
     //    budget, ef is only the fallback: keep it and check the recall)

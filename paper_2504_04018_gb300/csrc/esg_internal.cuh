@@ -118,7 +118,7 @@ esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t
                               const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
                               float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream);
 // per-query hits of returned ids against exact ids (batch.cu)
-esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int64_t *ids, const int32_t *cnt,
+esg_status esg_recall_hits(int64_t nq, int32_t k_max, const int32_t *k, const int64_t *ids, const int32_t *cnt,
                            const int64_t *gt, const int32_t *gcnt, int32_t *hits, cudaStream_t stream);
 
 // benchmark timing hooks (profile.cu)

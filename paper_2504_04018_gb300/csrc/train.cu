@@ -85,6 +85,12 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     std::vector<int32_t> gc(nq), h_hits(nq);
     std::vector<int64_t> h_stats(nq * 5);
     ESG_CUDA_TRY(cudaMemcpy(gc.data(), gt_count, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
+    {
+        // recall denominators: min(k_i, ground-truth count)
+        std::vector<int32_t> hk(nq, k_max);
+        if (k) ESG_CUDA_TRY(cudaMemcpy(hk.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nq; ++i) gc[i] = std::min(gc[i], std::max(0, std::min(hk[i], k_max)));
+    }
     esg_search_params sp = esg_search_params_default();
     sp.traversal = (esg_dtype)tp.traversal;
     sp.width = 1;
@@ -103,7 +109,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max; s.p = sp;
         s.out_ids = ids; s.out_dist = dist; s.out_count = cnt; s.out_status = nullptr; s.out_stats = stats;
         esg_status st = esg_launch_search(s, stream);
-        if (st == ESG_OK) st = esg_recall_hits(nq, k_max, ids, cnt, gt_ids, gt_count, hits, stream);
+        if (st == ESG_OK) st = esg_recall_hits(nq, k_max, k, ids, cnt, gt_ids, gt_count, hits, stream);
         if (st != ESG_OK) return st;
         ESG_CUDA_TRY(cudaMemcpyAsync(h_hits.data(), hits, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, stream));
         ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * nq * 5, cudaMemcpyDeviceToHost, stream));
@@ -211,7 +217,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         s.k = k ? k + n_tr : nullptr; s.k_max = k_max; s.p = q;
         s.out_ids = ids; s.out_dist = dist; s.out_count = cnt; s.out_status = nullptr; s.out_stats = stats;
         st = esg_launch_search(s, stream);
-        if (st == ESG_OK) st = esg_recall_hits(n_val, k_max, ids, cnt, gt_ids + n_tr * k_max, gt_count + n_tr, hits, stream);
+        if (st == ESG_OK) st = esg_recall_hits(n_val, k_max, k ? k + n_tr : nullptr, ids, cnt, gt_ids + n_tr * k_max, gt_count + n_tr, hits, stream);
         if (st != ESG_OK) return st;
         ESG_CUDA_TRY(cudaMemcpyAsync(h_hits.data(), hits, sizeof(int32_t) * n_val, cudaMemcpyDeviceToHost, stream));
         ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * n_val * 5, cudaMemcpyDeviceToHost, stream));
