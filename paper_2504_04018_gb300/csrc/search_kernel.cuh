@@ -528,33 +528,6 @@ search_kernel(SearchArgs a) {
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                // The next expansion is the best unexpanded candidate after this
-                // admission: the best admitted row or the best unexpanded list
-                // entry. Start pulling both adjacency rows into L2 now, so that
-                // their latency overlaps the merge below.
-                {
-                    Cand bc{INFINITY, ESG_NONE};
-                    for (int j = lane; j < a.BB; j += 32) {
-                        const Cand x = w.batch[j];
-                        if (cand_less(x, bc)) bc = x;
-                    }
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float od = __shfl_xor_sync(0xffffffffu, bc.d, o);
-                        const uint32_t oi = __shfl_xor_sync(0xffffffffu, bc.id, o);
-                        if (cand_less(od, oi, bc.d, bc.id)) { bc.d = od; bc.id = oi; }
-                    }
-                    const int i = (hint & ~31) + lane;
-                    const bool f = i >= hint && i < st.len && !(list[i].id & ESG_EXPANDED);
-                    const unsigned bal = __ballot_sync(0xffffffffu, f);
-                    const uint32_t cid = f ? list[i].id : ESG_NONE;
-                    const uint32_t nl_id = bal ? __shfl_sync(0xffffffffu, cid, __ffs(bal) - 1) : ESG_NONE;
-                    const uint32_t pf = lane < 2 ? (bc.id & ESG_ID_MASK) : (nl_id & ESG_ID_MASK);
-                    if (lane < 4 && pf < (uint64_t)a.n && (lane & 1) * 32 < a.R &&
-                        (lane < 2 ? bc.id != ESG_NONE : nl_id != ESG_NONE)) {
-                        const uint32_t *prow = adj + (size_t)pf * a.R + (lane & 1) * 32;
-                        asm volatile("prefetch.global.L2 [%0];" :: "l"(prow));
-                    }
-                }
                 Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
                 if (nl != list) {
                     list2 = list; list = nl;
