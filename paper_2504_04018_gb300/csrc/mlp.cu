@@ -166,17 +166,30 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// Features of each query (one warp per query).
+// Features of each query (one warp per query; the entry points of the first
+// piece are evaluated in parallel, 32 / E' lanes per entry with E' the next
+// power of two >= E). With PREDICT the same warp then runs the network on
+// its features (parameters in shared memory, two hidden units per lane) and
+// writes the query's ef and expansion budget; invalid predictions fall back
+// to the fixed beam width.
+template <bool PREDICT>
 __global__ void features_kernel(const float *X, int d, int metric, int64_t n, int32_t leaf,
                                 const int32_t *entries, int E, const float *queries, int64_t nq,
                                 const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
-                                float *feat) {
+                                float *feat, const float *blob, int ef_fixed, int ef_lo, int ef_hi,
+                                int32_t *ef_q, int32_t *maxexp_q) {
+    __shared__ float sp[PREDICT ? kP : 1];
+    if (PREDICT) {
+        for (int i = threadIdx.x; i < kP; i += blockDim.x) sp[i] = blob[i];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int64_t qi = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (qi >= nq) return;
     esg_piece pc[2];
     const int64_t lq = l[qi], rq = r[qi];
     const int np = esg_decompose_one(n, leaf, lq, rq, pc);
+    const int kk = k ? k[qi] : k_max;
     float f[kF];
     for (int i = 0; i < kF; ++i) f[i] = 0.f;
     if (np > 0) {
@@ -187,28 +200,42 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
             f[2 + s] = (float)(log2((double)(pc[s].node_r - pc[s].node_l + 1)) -
                                log2((double)(pc[s].pr - pc[s].pl + 1)));
         f[4] = pc[0].kind == ESG_PIECE_GRAPH ? 1.f : 0.f;
-        const int kk = k ? k[qi] : k_max;
         f[5] = kk > 0 ? log2f((float)kk) : 0.f;
         f[7] = (float)log2((double)(pc[0].node_r - pc[0].node_l + 1));
         f[6] = 1.f;
         if (pc[0].kind == ESG_PIECE_GRAPH) {
-            const float *q = queries + qi * (int64_t)d;
-            float dmin = INFINITY, dsum = 0.f;
-            int cnt = 0;
-            for (int e = 0; e < E; ++e) {
-                const int32_t v = entries[(size_t)pc[0].heap * E + e];
-                if (v < 0 || v >= n) continue;
-                const float *x = X + (size_t)v * d;
-                float acc = 0.f;
-                for (int j = lane; j < d; j += 32) {
-                    if (metric == ESG_L2SQ) { const float t = q[j] - x[j]; acc = fmaf(t, t, acc); }
-                    else acc = fmaf(q[j], x[j], acc);
+            int ep = 1;
+            while (ep < E) ep <<= 1;
+            const int lpe = 32 / ep;                 // lanes per entry
+            const int g = lane / lpe, sub = lane % lpe;
+            int32_t v = -1;
+            if (g < E) v = entries[(size_t)pc[0].heap * E + g];
+            const bool ok = v >= 0 && v < n;
+            const float4 *q4 = reinterpret_cast<const float4 *>(queries + qi * (int64_t)d);
+            const float4 *x4 = reinterpret_cast<const float4 *>(X + (size_t)(ok ? v : 0) * d);
+            float acc = 0.f;
+            if (ok) {
+                for (int j = sub; j < d / 4; j += lpe) {
+                    const float4 a = __ldg(q4 + j), b = __ldg(x4 + j);
+                    if (metric == ESG_L2SQ) {
+                        const float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+                        acc = fmaf(t0, t0, acc); acc = fmaf(t1, t1, acc);
+                        acc = fmaf(t2, t2, acc); acc = fmaf(t3, t3, acc);
+                    } else {
+                        acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
+                        acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
+                    }
                 }
-                acc = warp_sum_group(acc, 32);
-                const float dist = metric == ESG_L2SQ ? acc : -acc;
-                dmin = fminf(dmin, dist);
-                dsum += dist;
-                ++cnt;
+            }
+            for (int o = lpe >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const bool head = ok && sub == 0;
+            const float dist = metric == ESG_L2SQ ? acc : -acc;
+            float dmin = head ? dist : INFINITY, dsum = head ? dist : 0.f;
+            int cnt = head ? 1 : 0;
+            for (int o = 16; o > 0; o >>= 1) {
+                dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+                dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             }
             if (cnt > 0) {
                 const float mean = dsum / cnt;
@@ -218,34 +245,56 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
     }
     if (lane == 0)
         for (int i = 0; i < kF; ++i) feat[qi * kF + i] = f[i];
-}
-
-// ef and expansion budget per query from the trained network; invalid
-// predictions fall back to the fixed beam width.
-__global__ void predict_kernel(const float *blob, const float *feat, int64_t nq, const int32_t *k,
-                               int32_t k_max, int ef_fixed, int ef_lo, int ef_hi, int32_t *ef_q,
-                               int32_t *maxexp_q) {
-    __shared__ float sp[kP];
-    for (int i = threadIdx.x; i < kP; i += blockDim.x) sp[i] = blob[i];
-    __syncthreads();
-    const int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (qi >= nq) return;
+    if (!PREDICT) return;
+    const MlpView v = view(sp);
     const float *mu = blob + kP, *sigma = blob + kP + kF, *margin = blob + kP + 2 * kF;
     float xh[kF];
-    for (int i = 0; i < kF; ++i) xh[i] = (feat[qi * kF + i] - mu[i]) / sigma[i];
-    float y[2];
-    mlp_row(sp, xh, y, nullptr, nullptr);
-    const int kk = k ? k[qi] : k_max;
-    int ef = ef_fixed, mx = 0;
-    if (isfinite(y[0]) && isfinite(y[1])) {
-        const float e = exp2f(fminf(fmaxf(y[0] + margin[0], 0.f), 12.f));
-        ef = (int)ceilf(e);
-        ef = max(ef_lo, min(ef, ef_hi));
-        const float x = exp2f(fminf(fmaxf(y[1] + margin[1], 0.f), 20.f));
-        mx = max(16, min((int)ceilf(x), 16 * ef + 256));
+#pragma unroll
+    for (int i = 0; i < kF; ++i) xh[i] = (f[i] - __ldg(mu + i)) / __ldg(sigma + i);
+    // hidden layer 1: units lane and lane + 32
+    float h1a = v.b1[lane], h1b = v.b1[lane + 32];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) {
+        h1a = fmaf(xh[i], v.W1[i * kH + lane], h1a);
+        h1b = fmaf(xh[i], v.W1[i * kH + lane + 32], h1b);
     }
-    ef_q[qi] = max(ef, kk);
-    maxexp_q[qi] = mx;   // 0 = default cap
+    h1a = fmaxf(h1a, 0.f);
+    h1b = fmaxf(h1b, 0.f);
+    // hidden layer 2: units lane and lane + 32, inputs broadcast by shuffle
+    float s2a = v.b2[lane], s2b = v.b2[lane + 32];
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        const float hi = __shfl_sync(0xffffffffu, h1a, i);
+        s2a = fmaf(hi, v.W2[i * kH + lane], s2a);
+        s2b = fmaf(hi, v.W2[i * kH + lane + 32], s2b);
+    }
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        const float hi = __shfl_sync(0xffffffffu, h1b, i);
+        s2a = fmaf(hi, v.W2[(i + 32) * kH + lane], s2a);
+        s2b = fmaf(hi, v.W2[(i + 32) * kH + lane + 32], s2b);
+    }
+    const float h2a = fmaxf(s2a, 0.f), h2b = fmaxf(s2b, 0.f);
+    float y0 = h2a * v.W3[lane * kO + 0] + h2b * v.W3[(lane + 32) * kO + 0];
+    float y1 = h2a * v.W3[lane * kO + 1] + h2b * v.W3[(lane + 32) * kO + 1];
+    for (int o = 16; o > 0; o >>= 1) {
+        y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    }
+    y0 += v.b3[0];
+    y1 += v.b3[1];
+    if (lane == 0) {
+        int ef = ef_fixed, mx = 0;
+        if (isfinite(y0) && isfinite(y1)) {
+            const float e = exp2f(fminf(fmaxf(y0 + margin[0], 0.f), 12.f));
+            ef = (int)ceilf(e);
+            ef = max(ef_lo, min(ef, ef_hi));
+            const float x = exp2f(fminf(fmaxf(y1 + margin[1], 0.f), 20.f));
+            mx = max(16, min((int)ceilf(x), 16 * ef + 256));
+        }
+        ef_q[qi] = max(ef, kk);
+        maxexp_q[qi] = mx;   // 0 = default cap
+    }
 }
 
 }  // namespace
@@ -256,12 +305,9 @@ int esg_mlp_param_count() { return kP; }
 esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
                               const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
                               float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream) {
-    features_kernel<<<ceil_div_i(nq, 4), 128, 0, stream>>>(ix->X, ix->d, ix->metric, ix->n, ix->leaf_size,
-                                                           ix->entries, ix->E, queries, nq, l, r, k,
-                                                           k_max, feat);
-    ESG_CUDA_TRY(cudaGetLastError());
-    predict_kernel<<<ceil_div_i(nq, 128), 128, 0, stream>>>(ix->mlp, feat, nq, k, k_max, ef_fixed,
-                                                            ix->mlp_ef_lo, ix->mlp_ef_hi, ef_q, maxexp_q);
+    features_kernel<true><<<ceil_div_i(nq, 4), 128, 0, stream>>>(
+        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat,
+        ix->mlp, ef_fixed, ix->mlp_ef_lo, ix->mlp_ef_hi, ef_q, maxexp_q);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }
@@ -325,8 +371,9 @@ esg_status esg_query_features(const esg_index *ix, const float *queries, int64_t
                               esg_stream_t stream) {
     if (!ix || nq < 0 || (nq > 0 && (!queries || !l || !r || !feat))) { esg_set_error("esg_query_features: bad argument"); return ESG_ERR_INVALID_ARG; }
     if (nq == 0) return ESG_OK;
-    features_kernel<<<ceil_div_i(nq, 4), 128, 0, (cudaStream_t)stream>>>(
-        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat);
+    features_kernel<false><<<ceil_div_i(nq, 4), 128, 0, (cudaStream_t)stream>>>(
+        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat,
+        nullptr, 0, 0, 0, nullptr, nullptr);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }

@@ -302,7 +302,7 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
         esg_status pst = esg_predict_budget(ix, s.queries, s.nq, s.l, s.r, s.k, s.k_max, plan.ef,
                                             (float *)(scratch + L.feat), ef_q, maxexp_q, stream);
         if (pst != ESG_OK) return pst;
-        esg_prof_count(2);
+        esg_prof_count(1);   // features + network, one kernel
     }
     SearchArgs a;
     a.ef_q = ef_q; a.maxexp_q = maxexp_q;
