@@ -193,15 +193,15 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
     float f[kF];
     for (int i = 0; i < kF; ++i) f[i] = 0.f;
     if (np > 0) {
-        const double w = (double)(rq - lq + 1);
-        f[0] = (float)log2(w);
+        // single precision throughout: FP64 is slow on this part and the
+        // sizes (< 2^31) are exact enough as floats for network inputs
+        f[0] = log2f((float)(rq - lq + 1));
         f[1] = (float)np;
         for (int s = 0; s < np; ++s)
-            f[2 + s] = (float)(log2((double)(pc[s].node_r - pc[s].node_l + 1)) -
-                               log2((double)(pc[s].pr - pc[s].pl + 1)));
+            f[2 + s] = log2f((float)(pc[s].node_r - pc[s].node_l + 1)) - log2f((float)(pc[s].pr - pc[s].pl + 1));
         f[4] = pc[0].kind == ESG_PIECE_GRAPH ? 1.f : 0.f;
         f[5] = kk > 0 ? log2f((float)kk) : 0.f;
-        f[7] = (float)log2((double)(pc[0].node_r - pc[0].node_l + 1));
+        f[7] = log2f((float)(pc[0].node_r - pc[0].node_l + 1));
         f[6] = 1.f;
         if (pc[0].kind == ESG_PIECE_GRAPH) {
             int ep = 1;
