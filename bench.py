@@ -266,6 +266,25 @@ N_TRAIN = 20_000
 LEARNED_EF_HI = 64
 
 
+def measured_traffic(variant, params):
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, when it was taken for this variant, these parameters and the
+    current kernel sources (None otherwise)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")))[variant]
+    except Exception:
+        return None
+    m = hashlib.sha256()
+    for p in rec["kernel_sources"]:
+        m.update(open(os.path.join(ROOT, p), "rb").read())
+    if m.hexdigest()[:16] != rec["kernel_sources_sha256_16"]:
+        return None
+    if any(params.get(k) != v for k, v in rec["params"].items()):
+        return None
+    return rec["traffic_bytes_per_launch"]
+
+
 def run_bruteforce_only(args, local):
     """Exact filtered k-NN of the workload's queries over the rank-ordered
     points, tcgen05 path against the SIMT kernel (no index is built)."""
@@ -490,7 +509,7 @@ def run_ours(args, rank, world, local):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = head["alg_bytes"] / (head["kernel_ms"] / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": measured_traffic(head_name, head["params"]),
                 "kernel": f"search_kernel ({head_name})",
                 "kernel_ms_per_launch": round(head["kernel_ms"], 4),
                 "algorithmic_bytes_per_launch": head["alg_bytes"],
