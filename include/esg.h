@@ -237,9 +237,11 @@ esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, c
  *  out_count   device [nq] int32: results written, min(k, r - l + 1) when the
  *              graphs reach enough in-range points;
  *  out_status  device [nq] int32 (ESG_Q_* bits) or NULL;
- *  out_stats   device [nq, 5] int64 (expansions, distance evaluations on
+ *  out_stats   device [nq, 6] int64 (expansions, distance evaluations on
  *              traversal rows, out-of-range evaluations, FP32 re-rank rows,
- *              pieces) or NULL.
+ *              pieces, device latency in ns from the first of the query's
+ *              pieces being taken by a warp to the last one finished,
+ *              read from %globaltimer) or NULL.
  * Asynchronous on `stream`; temporary device memory is taken from and
  * returned to the stream-ordered allocator of that stream.
  */
@@ -276,7 +278,7 @@ esg_status esg_search_batch_noalloc(const esg_index *index, const float *queries
 /*
  * Batched search replayed as one CUDA graph. A batch owns device buffers for
  * up to max_nq queries (inputs: queries [max_nq, d] f32, l, r [max_nq] int64,
- * k [max_nq] int32; outputs as in esg_search_batch, stats [max_nq, 5]) and the
+ * k [max_nq] int32; outputs as in esg_search_batch, stats [max_nq, 6]) and the
  * search's scratch memory, all allocated at creation. esg_batch_run(nq)
  * replays the whole search (decomposition, persistent beam-search kernel over
  * an atomic queue of (query, piece) items, merge) for the first nq entries

@@ -310,7 +310,7 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
                      want_status: bool = True, want_stats: bool = False, stream=None):
     """Range-filtered search of CUDA float32 queries [nq, d] with CUDA int64
     ranges [nq]. Returns (ids int64 [nq,k_max], dist f32, count int32,
-    status int32 or None, stats int64 [nq,5] or None)."""
+    status int32 or None, stats int64 [nq,6] or None)."""
     import torch
     lib = load_library()
     nq = queries.shape[0]
@@ -320,7 +320,7 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
         dist = torch.empty((nq, k_max), dtype=torch.float32, device=dev)
         count = torch.empty(nq, dtype=torch.int32, device=dev)
         status = torch.empty(nq, dtype=torch.int32, device=dev) if want_status else None
-        stats = torch.empty((nq, 5), dtype=torch.int64, device=dev) if want_stats else None
+        stats = torch.empty((nq, 6), dtype=torch.int64, device=dev) if want_stats else None
     else:
         ids, dist, count, status, stats = out
     p = params if params is not None else search_params(ef, max_expansions, rerank, use_learned,

@@ -73,7 +73,7 @@ esg_status esg_batch_create(const esg_index *ix, int64_t max_nq, int32_t k_max, 
     A((void **)&b->dist, sizeof(float) * max_nq * k_max);
     A((void **)&b->count, sizeof(int32_t) * max_nq);
     A((void **)&b->status, sizeof(int32_t) * max_nq);
-    A((void **)&b->stats, sizeof(int64_t) * max_nq * 5);
+    A((void **)&b->stats, sizeof(int64_t) * max_nq * ESG_QUERY_STATS);
     if (st == ESG_OK) {
         // scratch sized for the largest batch (per-item buffers grow with nq)
         SearchPlan plan;

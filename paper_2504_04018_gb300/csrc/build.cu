@@ -227,7 +227,7 @@ esg_status esg_build_graphs(esg_index *ix, const esg_build_params &p, cudaStream
     B_TRY(cudaMalloc(&pieces, sizeof(esg_piece) * cap_items));
     B_TRY(cudaMalloc(&res, sizeof(Cand) * cap_items * efc));
     B_TRY(cudaMalloc(&res_cnt, sizeof(int32_t) * cap_items * 2));
-    B_TRY(cudaMalloc(&stats, sizeof(int64_t) * cap_items * 4));
+    B_TRY(cudaMalloc(&stats, sizeof(int64_t) * cap_items * ESG_ITEM_STATS));
     B_TRY(cudaMalloc(&indeg, sizeof(int32_t) * (n + 1)));
     B_TRY(cudaMalloc(&cursor, sizeof(int32_t) * n));
     B_TRY(cudaMalloc(&off, sizeof(int64_t) * (n + 1)));

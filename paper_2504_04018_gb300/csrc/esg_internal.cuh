@@ -12,6 +12,11 @@
 
 #define ESG_NONE 0xFFFFFFFFu
 #define ESG_MLP_FEATURES 8
+// per-item search statistics: expansions, evaluations, out-of-range
+// evaluations, re-ranked rows, start and end time (ns, %globaltimer)
+#define ESG_ITEM_STATS 6
+// per-query statistics returned by esg_search_batch (see esg.h)
+#define ESG_QUERY_STATS 6
 #define ESG_EXPANDED 0x80000000u
 #define ESG_ID_MASK 0x7FFFFFFFu
 

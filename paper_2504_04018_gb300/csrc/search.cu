@@ -85,10 +85,19 @@ __global__ void merge_kernel(int64_t nq, int32_t k_max, const int32_t *kq, const
         out_status[i] = s;
     }
     if (out_stats) {
-        int64_t np = (pieces[2 * i].kind != ESG_PIECE_NONE) + (pieces[2 * i + 1].kind != ESG_PIECE_NONE);
-        for (int c = 0; c < 4; ++c)
-            out_stats[i * 5 + c] = k > 0 ? res_stats[2 * i * 4 + c] + res_stats[(2 * i + 1) * 4 + c] : 0;
-        out_stats[i * 5 + 4] = np;
+        const bool va = pieces[2 * i].kind != ESG_PIECE_NONE, vb = pieces[2 * i + 1].kind != ESG_PIECE_NONE;
+        const int64_t *sa = res_stats + 2 * i * ESG_ITEM_STATS, *sb = sa + ESG_ITEM_STATS;
+        int64_t *os = out_stats + i * ESG_QUERY_STATS;
+        for (int c = 0; c < 4; ++c) os[c] = k > 0 ? sa[c] + sb[c] : 0;
+        os[4] = (int64_t)va + (int64_t)vb;
+        // device latency: first item taken by a warp to last item finished
+        int64_t lat = 0;
+        if (k > 0 && (va || vb)) {
+            const int64_t t0 = va && vb ? min(sa[4], sb[4]) : (va ? sa[4] : sb[4]);
+            const int64_t t1 = va && vb ? max(sa[5], sb[5]) : (va ? sa[5] : sb[5]);
+            lat = t1 - t0;
+        }
+        os[5] = lat;
     }
 }
 
@@ -222,7 +231,7 @@ ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) 
     L.qs = off; off += al256(sizeof(int32_t) * nq);
     L.res = off; off += al256(sizeof(Cand) * n_items * k_max);
     L.cnt = off; off += al256(sizeof(int32_t) * n_items * 2);
-    L.stats = off; off += al256(sizeof(int64_t) * n_items * 4);
+    L.stats = off; off += al256(sizeof(int64_t) * n_items * ESG_ITEM_STATS);
     L.hash = off; off += al256((size_t)plan.grid * plan.wpb * plan.G * 4);
     L.feat = off; off += plan.learned ? al256(sizeof(float) * nq * ESG_MLP_FEATURES) : 0;
     L.efq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;

@@ -334,7 +334,7 @@ struct SearchArgs {
     Cand *res;             // [n_items, k_max]
     int32_t *res_cnt;      // [n_items]
     int32_t *res_status;   // [n_items]
-    int64_t *res_stats;    // [n_items, 4]
+    int64_t *res_stats;    // [n_items, ESG_ITEM_STATS]
 };
 
 template <int ST, int VPL>
@@ -374,6 +374,8 @@ search_kernel(SearchArgs a) {
         if (lane == 0) item = (int64_t)atomicAdd(a.queue, 1ULL);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
+        unsigned long long t_start;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int64_t qi = item >> a.qshift;
         const esg_piece pc = a.pieces[item];
         const int kq = a.kq ? a.kq[qi] : a.kconst;
@@ -381,7 +383,8 @@ search_kernel(SearchArgs a) {
         int status = 0;
         if (pc.kind == ESG_PIECE_NONE || kq <= 0) {
             if (lane == 0) { a.res_cnt[item] = 0; a.res_status[item] = 0; }
-            if (lane < 4) a.res_stats[item * 4 + lane] = 0;
+            if (lane < 4) a.res_stats[item * ESG_ITEM_STATS + lane] = 0;
+            if (lane == 0) { a.res_stats[item * ESG_ITEM_STATS + 4] = (int64_t)t_start; a.res_stats[item * ESG_ITEM_STATS + 5] = (int64_t)t_start; }
             continue;
         }
         const uint32_t pl = (uint32_t)pc.pl, pr = (uint32_t)pc.pr;
@@ -589,10 +592,15 @@ search_kernel(SearchArgs a) {
             if (lane == 0) {
                 a.res_cnt[item] = written;
                 a.res_status[item] = status;
-                a.res_stats[item * 4 + 0] = n_exp;
-                a.res_stats[item * 4 + 1] = n_eval;
-                a.res_stats[item * 4 + 2] = n_oor;
-                a.res_stats[item * 4 + 3] = n_rr;
+                unsigned long long t_end;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+                int64_t *rs = a.res_stats + item * ESG_ITEM_STATS;
+                rs[0] = n_exp;
+                rs[1] = n_eval;
+                rs[2] = n_oor;
+                rs[3] = n_rr;
+                rs[4] = (int64_t)t_start;
+                rs[5] = (int64_t)t_end;
             }
         }
         __syncwarp();

@@ -71,7 +71,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     DevBuf ids_b, dist_b, cnt_b, stats_b, hits_b, feat_b;
     auto alloc = [&](DevBuf &b, size_t bytes) -> bool { return cudaMalloc(&b.p, bytes) == cudaSuccess; };
     if (!alloc(ids_b, sizeof(int64_t) * nq * k_max) || !alloc(dist_b, sizeof(float) * nq * k_max) ||
-        !alloc(cnt_b, sizeof(int32_t) * nq) || !alloc(stats_b, sizeof(int64_t) * nq * 5) ||
+        !alloc(cnt_b, sizeof(int32_t) * nq) || !alloc(stats_b, sizeof(int64_t) * nq * ESG_QUERY_STATS) ||
         !alloc(hits_b, sizeof(int32_t) * nq) || !alloc(feat_b, sizeof(float) * nq * F)) {
         esg_set_error("esg_train_predictor: allocation");
         return ESG_ERR_OOM;
@@ -83,7 +83,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     float *feat = (float *)feat_b.p;
 
     std::vector<int32_t> gc(nq), h_hits(nq);
-    std::vector<int64_t> h_stats(nq * 5);
+    std::vector<int64_t> h_stats(nq * ESG_QUERY_STATS);
     ESG_CUDA_TRY(cudaMemcpy(gc.data(), gt_count, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
     {
         // recall denominators: min(k_i, ground-truth count)
@@ -112,15 +112,15 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         if (st == ESG_OK) st = esg_recall_hits(nq, k_max, k, ids, cnt, gt_ids, gt_count, hits, stream);
         if (st != ESG_OK) return st;
         ESG_CUDA_TRY(cudaMemcpyAsync(h_hits.data(), hits, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, stream));
-        ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * nq * 5, cudaMemcpyDeviceToHost, stream));
+        ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * nq * ESG_QUERY_STATS, cudaMemcpyDeviceToHost, stream));
         ESG_CUDA_TRY(cudaStreamSynchronize(stream));
         for (int64_t i = 0; i < nq; ++i) {
             const double rec = gc[i] > 0 ? (double)h_hits[i] / gc[i] : 1.0;
-            if (ef == grid.back() && !done[i]) label_exp[i] = std::log2((float)std::max<int64_t>(1, h_stats[i * 5]));
+            if (ef == grid.back() && !done[i]) label_exp[i] = std::log2((float)std::max<int64_t>(1, h_stats[i * ESG_QUERY_STATS]));
             if (!done[i] && rec >= tp.per_query_recall) {
                 done[i] = 1;
                 label_ef[i] = std::log2((float)ef);
-                label_exp[i] = std::log2((float)std::max<int64_t>(1, h_stats[i * 5]));
+                label_exp[i] = std::log2((float)std::max<int64_t>(1, h_stats[i * ESG_QUERY_STATS]));
             }
         }
     }
@@ -220,10 +220,10 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         if (st == ESG_OK) st = esg_recall_hits(n_val, k_max, k ? k + n_tr : nullptr, ids, cnt, gt_ids + n_tr * k_max, gt_count + n_tr, hits, stream);
         if (st != ESG_OK) return st;
         ESG_CUDA_TRY(cudaMemcpyAsync(h_hits.data(), hits, sizeof(int32_t) * n_val, cudaMemcpyDeviceToHost, stream));
-        ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * n_val * 5, cudaMemcpyDeviceToHost, stream));
+        ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * n_val * ESG_QUERY_STATS, cudaMemcpyDeviceToHost, stream));
         ESG_CUDA_TRY(cudaStreamSynchronize(stream));
         double h = 0, ev = 0;
-        for (int64_t i = 0; i < n_val; ++i) { h += h_hits[i]; ev += h_stats[i * 5 + 1]; }
+        for (int64_t i = 0; i < n_val; ++i) { h += h_hits[i]; ev += h_stats[i * ESG_QUERY_STATS + 1]; }
         rec = gv > 0 ? h / gv : 1.0;
         mean_ef = ev / n_val;   // distance evaluations per query
         return ESG_OK;

@@ -65,6 +65,13 @@ def _oracle_sample(X, queries, l, r, k, metric, gi, gd, idx):
         assert np.allclose(gd[i, :c], exact, rtol=1e-5, atol=1e-6)
 
 
+def npieces_all(ix, w):
+    """Pieces per query from the GPU decomposition (valid ranges all)."""
+    _, npieces = E.esg_decompose_batch(ix.n, ix.leaf_size, _t(w.l), _t(w.r))
+    torch.cuda.synchronize()
+    return npieces.cpu().numpy().astype(np.int64)
+
+
 @pytest.fixture(scope="module")
 def batching_index():
     w = synthetic.batching()
@@ -115,6 +122,12 @@ def test_batching_workload(batching_index):
     ids = b.view("ids", (nq, 100), torch.int64).cpu().numpy()
     dist = b.view("dist", (nq, 100), torch.float32).cpu().numpy()
     cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
+    stats = b.view("stats", (nq, 6), torch.int64).cpu().numpy()
+    lat = stats[:, 5]
+    assert np.all(lat[cnt > 0] > 0) and np.all(lat < 10**10)   # ns, within the launch
+    assert np.array_equal(stats[:, 4], npieces_all(ix, w))
+    print(f"batching workload: per-query device latency p50 {np.percentile(lat, 50) / 1e3:.1f} us, "
+          f"p99 {np.percentile(lat, 99) / 1e3:.1f} us")
     # the graph replay equals a direct call
     d_ids, _, d_cnt, _, _ = E.esg_search_batch(ix, _t(w.queries[:5000]), _t(w.l[:5000]), _t(w.r[:5000]),
                                                _t(w.k[:5000]), 100, params=params)

@@ -23,7 +23,7 @@ def _outputs(nq, k_max, dev):
             torch.full((nq, k_max), -7.0, dtype=torch.float32, device=dev),
             torch.full((nq,), -7, dtype=torch.int32, device=dev),
             torch.full((nq,), -7, dtype=torch.int32, device=dev),
-            torch.full((nq, 5), -7, dtype=torch.int64, device=dev))
+            torch.full((nq, 6), -7, dtype=torch.int64, device=dev))
 
 
 def test_noalloc_matches_search_batch_twice():
