@@ -49,7 +49,9 @@ def test_noalloc_matches_search_batch_twice():
         fin = np.isfinite(ref[1])
         assert np.allclose(dist[fin], ref[1][fin], rtol=1e-6, atol=1e-6)
         assert np.array_equal(st, ref[3]), call
-        assert np.array_equal(stats, ref[4]), call
+        # counters are deterministic; the last column is a measured latency
+        assert np.array_equal(stats[:, :5], ref[4][:, :5]), call
+        assert np.all(stats[cnt > 0, 5] > 0), call
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
