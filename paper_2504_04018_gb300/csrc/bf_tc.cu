@@ -467,6 +467,10 @@ __device__ __forceinline__ void epi_bar() {   // the 256 epilogue threads
     asm volatile("bar.sync 1, %0;" :: "n"(32 * kEpiWarps) : "memory");
 }
 
+__device__ __forceinline__ void pair_bar(int quarter) {   // the two warps of a lane quarter
+    asm volatile("bar.sync %0, 64;" :: "r"(2 + quarter) : "memory");
+}
+
 // Lexicographic (distance, row) order of the candidate lists.
 __device__ __forceinline__ bool dl_less(float da, int32_t ia, float db, int32_t ib) {
     return da < db || (da == db && ia < ib);
@@ -479,8 +483,8 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     unsigned char *sA = base;
     unsigned char *sB = sA + (size_t)a.nk * STAGE;
     float *T = (float *)(sB + (size_t)a.S * STAGE);          // [128][kTS] half tile, transposed
-    float *s_xn = T + TM * kTS;                              // [2][128] tile norms
-    float *L_d = s_xn + 2 * TN;                              // [128][K1] per-row lists
+    float *s_xn = T + TM * kTS;                              // [4 pairs][2][128] tile norms
+    float *L_d = s_xn + 8 * TN;                              // [128][K1] per-row lists
     int32_t *L_i = (int32_t *)(L_d + TM * K1);
     int32_t *r_lo = L_i + TM * K1, *r_hi = r_lo + TM, *r_cnt = r_hi + TM, *r_ti = r_cnt + TM;
     float *r_qn = (float *)(r_ti + TM), *r_td = r_qn + TM;
@@ -491,7 +495,6 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     uint64_t *acc_full = a_full + 2, *acc_empty = a_full + 4, *drain = a_full + 6;
     uint32_t *tmem_slot = (uint32_t *)(a_full + 7);
     volatile int *abort_f = (volatile int *)(tmem_slot + 1);
-    volatile int *abort_snap = (volatile int *)(tmem_slot + 2);   // epilogue's shared view
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this CTA's contiguous share of the work items
     const int it_begin = (int)((int64_t)blockIdx.x * a.n_items / gridDim.x);
@@ -510,7 +513,6 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
         }
         mbar_init(smem_u32(drain), 1);
         *abort_f = 0;
-        *abort_snap = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -601,18 +603,33 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             wait_phase(smem_u32(drain), 0u, abort_f, a.err, true);
         }
     } else {
-        // ---------------- epilogue (256 threads)
+        // ---------------- epilogue (256 threads, 4 pairs of warps)
+        // The two warps of a pair read the same 32 TMEM lanes (rows), one
+        // column half each, and are the only ones to touch those rows' state:
+        // within a tile they synchronise with a 64-thread barrier of their
+        // own. Block-wide barriers remain only where rows change hands (a new
+        // query tile, the write-out). After an aborted wait the loops still
+        // run to the end (every wait then returns at once), so that all
+        // threads meet the same barriers; the host reports the error.
         const int ew = warp - 2;            // 0..7
         const int et = ew * 32 + lane;      // 0..255
         const int quarter = warp & 3;       // TMEM lanes this warp may read
         const int half = ew >> 2;           // column half it reads
+        const int pt_i = half * 32 + lane;  // thread index within the pair
         const int my_row = quarter * 32 + lane;
         const bool l2 = a.metric == ESG_L2SQ;
         uint32_t acc_it = 0, tcount = 0;
         uint32_t pe[2] = {0u, 0u};
-        bool ok = true;
         int cur_qt = -1;
-        for (int it = it_begin; ok && it < it_end; ++it) {
+        // squared norms of a tile into the pair's buffer
+        auto load_norms = [&](int32_t tile, float *dst) {
+            if (!l2) return;
+            const int32_t p0 = tile * TN + pt_i, p1 = p0 + 64;
+            dst[pt_i] = p0 < a.n ? __ldg(a.xnorm + p0) : 0.f;
+            dst[pt_i + 64] = p1 < a.n ? __ldg(a.xnorm + p1) : 0.f;
+        };
+        if (it_begin < it_end) load_norms(a.tiles[a.items[it_begin].off], s_xn + (quarter * 2) * TN);
+        for (int it = it_begin; it < it_end; ++it) {
             const WorkItem I = a.items[it];
             if (I.qtile != cur_qt) {
                 // new query tile: per-row state (the lists of the previous tile
@@ -634,18 +651,18 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             }
             for (int j = 0; j < I.cnt; ++j) {
                 const int32_t pt = a.tiles[I.off + j] * TN;   // first point of the tile
-                // the tile's squared norms into shared memory (double buffered:
-                // the previous tile's readers are past a barrier)
-                float *xs_cur = s_xn + (tcount & 1u) * TN;
-                ++tcount;
-                if (et < TN) {
-                    const int32_t p = pt + et;
-                    xs_cur[et] = (l2 && p < a.n) ? __ldg(a.xnorm + p) : 0.f;
+                float *xs_cur = s_xn + (quarter * 2 + (tcount & 1u)) * TN;
+                // the next tile's norms into the pair's other buffer (its last
+                // readers finished before the previous tile's pair barriers)
+                {
+                    int32_t nt = -1;
+                    if (j + 1 < I.cnt) nt = a.tiles[I.off + j + 1];
+                    else if (it + 1 < it_end) nt = a.tiles[a.items[it + 1].off];
+                    if (nt >= 0) load_norms(nt, s_xn + (quarter * 2 + ((tcount + 1u) & 1u)) * TN);
                 }
+                ++tcount;
                 const uint32_t b = acc_it & 1u;
-                if (!wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err)) { ok = false; }
-                // (a failed wait still takes part in the barriers below, so that
-                // the other epilogue warps are not left waiting)
+                wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err);
                 pe[b] ^= 1u;
                 ++acc_it;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -656,7 +673,6 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
-                epi_bar();
                 // filter, one thread per row and half: distances of the 64
                 // columns, range mask, and the columns at or below the row's
                 // current K1-th distance (a superset of the insertions)
@@ -693,77 +709,70 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                         for (int c = 0; c < 64; ++c)
                             T[my_row * kTS + c] = ((rng >> c) & 1ull) ? v[c] : INFINITY;
                     }
-                    epi_bar();
-                    // warp-cooperative insertion: the k-th flagged row goes to
-                    // epilogue warp k mod 8
+                    pair_bar(quarter);
+                    // warp-cooperative insertion: the k-th flagged row of the
+                    // pair's 32 goes to the pair's warp k mod 2
                     const int32_t pb = pt + h * 64;
+                    uint32_t w = s_flag[h * 4 + quarter];
                     int k = 0;
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t w = s_flag[h * 4 + q];
-                        while (w != 0u) {
-                            const int bit = __ffs(w) - 1;
-                            w &= w - 1;
-                            if ((k++ & (kEpiWarps - 1)) != ew) continue;
-                            const int r = q * 32 + bit;
-                            const int32_t p0 = pb + lane, p1 = p0 + 32;
-                            const float d0 = T[r * kTS + lane], d1 = T[r * kTS + lane + 32];
-                            float td = r_td[r];
-                            int32_t ti = r_ti[r];
-                            uint32_t m0 = __ballot_sync(0xffffffffu, d0 < INFINITY && dl_less(d0, p0, td, ti));
-                            uint32_t m1 = __ballot_sync(0xffffffffu, d1 < INFINITY && dl_less(d1, p1, td, ti));
-                            if ((m0 | m1) == 0u) continue;                  // warp-uniform
-                            // the row's list in registers: entries lane and lane + 32
-                            int cnt = r_cnt[r];
-                            float ld0 = lane < cnt ? L_d[r * K1 + lane] : INFINITY;
-                            int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
-                            float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
-                            int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
-                            while ((m0 | m1) != 0u) {
-                                const bool second = m0 == 0u;
-                                const int src = __ffs(second ? m1 : m0) - 1;
-                                if (second) m1 &= m1 - 1; else m0 &= m0 - 1;
-                                const float cd = __shfl_sync(0xffffffffu, second ? d1 : d0, src);
-                                const int32_t ci = pb + (second ? 32 : 0) + src;
-                                if (cnt == K1 && !dl_less(cd, ci, td, ti)) continue;
-                                const int pos = __popc(__ballot_sync(0xffffffffu, lane < cnt && dl_less(ld0, li0, cd, ci))) +
-                                                __popc(__ballot_sync(0xffffffffu, lane + 32 < cnt && dl_less(ld1, li1, cd, ci)));
-                                const float u0d = __shfl_up_sync(0xffffffffu, ld0, 1);
-                                const int32_t u0i = __shfl_up_sync(0xffffffffu, li0, 1);
-                                float u1d = __shfl_up_sync(0xffffffffu, ld1, 1);
-                                int32_t u1i = __shfl_up_sync(0xffffffffu, li1, 1);
-                                const float t31d = __shfl_sync(0xffffffffu, ld0, 31);
-                                const int32_t t31i = __shfl_sync(0xffffffffu, li0, 31);
-                                if (lane == 0) { u1d = t31d; u1i = t31i; }
-                                if (lane > pos) { ld0 = u0d; li0 = u0i; }
-                                else if (lane == pos) { ld0 = cd; li0 = ci; }
-                                if (lane + 32 > pos) { ld1 = u1d; li1 = u1i; }
-                                else if (lane + 32 == pos) { ld1 = cd; li1 = ci; }
-                                if (cnt < K1) ++cnt;
-                                if (cnt == K1) {
-                                    const int e = K1 - 1;
-                                    td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
-                                    ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
-                                }
+                    while (w != 0u) {
+                        const int bit = __ffs(w) - 1;
+                        w &= w - 1;
+                        if ((k++ & 1) != half) continue;
+                        const int r = quarter * 32 + bit;
+                        const int32_t p0 = pb + lane, p1 = p0 + 32;
+                        const float d0 = T[r * kTS + lane], d1 = T[r * kTS + lane + 32];
+                        float td = r_td[r];
+                        int32_t ti = r_ti[r];
+                        uint32_t m0 = __ballot_sync(0xffffffffu, d0 < INFINITY && dl_less(d0, p0, td, ti));
+                        uint32_t m1 = __ballot_sync(0xffffffffu, d1 < INFINITY && dl_less(d1, p1, td, ti));
+                        if ((m0 | m1) == 0u) continue;                  // warp-uniform
+                        // the row's list in registers: entries lane and lane + 32
+                        int cnt = r_cnt[r];
+                        float ld0 = lane < cnt ? L_d[r * K1 + lane] : INFINITY;
+                        int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
+                        float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
+                        int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
+                        while ((m0 | m1) != 0u) {
+                            const bool second = m0 == 0u;
+                            const int src = __ffs(second ? m1 : m0) - 1;
+                            if (second) m1 &= m1 - 1; else m0 &= m0 - 1;
+                            const float cd = __shfl_sync(0xffffffffu, second ? d1 : d0, src);
+                            const int32_t ci = pb + (second ? 32 : 0) + src;
+                            if (cnt == K1 && !dl_less(cd, ci, td, ti)) continue;
+                            const int pos = __popc(__ballot_sync(0xffffffffu, lane < cnt && dl_less(ld0, li0, cd, ci))) +
+                                            __popc(__ballot_sync(0xffffffffu, lane + 32 < cnt && dl_less(ld1, li1, cd, ci)));
+                            const float u0d = __shfl_up_sync(0xffffffffu, ld0, 1);
+                            const int32_t u0i = __shfl_up_sync(0xffffffffu, li0, 1);
+                            float u1d = __shfl_up_sync(0xffffffffu, ld1, 1);
+                            int32_t u1i = __shfl_up_sync(0xffffffffu, li1, 1);
+                            const float t31d = __shfl_sync(0xffffffffu, ld0, 31);
+                            const int32_t t31i = __shfl_sync(0xffffffffu, li0, 31);
+                            if (lane == 0) { u1d = t31d; u1i = t31i; }
+                            if (lane > pos) { ld0 = u0d; li0 = u0i; }
+                            else if (lane == pos) { ld0 = cd; li0 = ci; }
+                            if (lane + 32 > pos) { ld1 = u1d; li1 = u1i; }
+                            else if (lane + 32 == pos) { ld1 = cd; li1 = ci; }
+                            if (cnt < K1) ++cnt;
+                            if (cnt == K1) {
+                                const int e = K1 - 1;
+                                td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
+                                ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
                             }
-                            if (lane < cnt) { L_d[r * K1 + lane] = ld0; L_i[r * K1 + lane] = li0; }
-                            if (lane + 32 < cnt) { L_d[r * K1 + lane + 32] = ld1; L_i[r * K1 + lane + 32] = li1; }
-                            if (lane == 0) { r_cnt[r] = cnt; r_td[r] = td; r_ti[r] = ti; }
-                            __syncwarp();
                         }
+                        if (lane < cnt) { L_d[r * K1 + lane] = ld0; L_i[r * K1 + lane] = li0; }
+                        if (lane + 32 < cnt) { L_d[r * K1 + lane + 32] = ld1; L_i[r * K1 + lane + 32] = li1; }
+                        if (lane == 0) { r_cnt[r] = cnt; r_td[r] = td; r_ti[r] = ti; }
+                        __syncwarp();
                     }
-                    // one thread samples the abort flag before the last barrier
-                    // of the tile, all read the sample after it: every epilogue
-                    // warp takes the same decision at the same point
-                    if (h == 1 && et == 0) *abort_snap = *abort_f;
-                    epi_bar();
+                    pair_bar(quarter);
                 }
-                if (*abort_snap) ok = false;
             }
-            if (!ok) break;
             // write the lists out when this is the CTA's last item of the
             // query tile (a row's list then covers all of the tile's items
             // this CTA ran); other items record empty lists
             const bool flush = it + 1 == it_end || a.items[it + 1].qtile != I.qtile;
+            if (flush) epi_bar();   // every pair's insertions are done
             for (int r = et; r < TM; r += 32 * kEpiWarps) {
                 const int c = flush ? r_cnt[r] : 0;
                 a.part_n[(int64_t)it * TM + r] = c;
@@ -972,7 +981,7 @@ static esg_status bruteforce_tc_v1(const float *base, int64_t n, int32_t d, int 
 static esg_status bf2_smem(int32_t d, int K1, int max_smem, int *S, size_t *smem) {
     if (K1 > kMaxK1v2 || d < 1) return ESG_ERR_UNSUPPORTED;
     const int nk = (d + TK - 1) / TK;
-    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + 2 * TN * 4 + (size_t)TM * K1 * 8 +
+    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + 8 * TN * 4 + (size_t)TM * K1 * 8 +
                          6 * TM * 4 + 8 * 4 + 8 * (2 * kMaxStages + 8) + 16;
     if ((size_t)max_smem < fixed + 2 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
     *S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - fixed) / STAGE);
