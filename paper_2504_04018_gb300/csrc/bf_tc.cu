@@ -401,6 +401,7 @@ struct Tc2Args {
     const int32_t *qorder;          // sorted position -> caller's query index
     const WorkItem *items;
     const int32_t *tiles;           // point-tile ids of all items
+    const int32_t *cta_first;       // [grid + 1]: CTA c runs items [cta_first[c], cta_first[c + 1])
     int n_items;
     int64_t nv;                     // number of valid (sorted) queries
     int nk, metric, K1, S;
@@ -497,8 +498,8 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     volatile int *abort_f = (volatile int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this CTA's contiguous share of the work items
-    const int it_begin = (int)((int64_t)blockIdx.x * a.n_items / gridDim.x);
-    const int it_end = (int)((int64_t)(blockIdx.x + 1) * a.n_items / gridDim.x);
+    const int it_begin = a.cta_first[blockIdx.x];
+    const int it_end = a.cta_first[blockIdx.x + 1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.S; ++s) {
@@ -1120,20 +1121,40 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         for (auto &x : spans[qt]) total_tiles += x.second - x.first + 1;
     }
     if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
-    const int64_t CH = std::max<int64_t>(8, std::min<int64_t>(1024, (total_tiles + 4 * sms - 1) / (4 * (int64_t)sms)));
+    // the covered tiles of all query tiles in one sequence (query tile by query
+    // tile); CTA c runs the equal share [c T / G, (c + 1) T / G) of it, cut into
+    // work items at query-tile boundaries, so the CTAs get the same number of
+    // point tiles (items in query-tile order, each CTA's items contiguous)
     std::vector<int32_t> tiles;
     tiles.reserve(total_tiles);
-    std::vector<WorkItem> items;
-    std::vector<int32_t> item_begin(nqt + 1, 0);
+    std::vector<int64_t> qt_first(nqt + 1, 0);
     for (int64_t qt = 0; qt < nqt; ++qt) {
-        item_begin[qt] = (int32_t)items.size();
-        const int64_t first = (int64_t)tiles.size();
+        qt_first[qt] = (int64_t)tiles.size();
         for (auto &x : spans[qt])
             for (int64_t t = x.first; t <= x.second; ++t) tiles.push_back((int32_t)t);
-        for (int64_t o = first; o < (int64_t)tiles.size(); o += CH)
-            items.push_back(WorkItem{(int32_t)qt, (int32_t)o, (int32_t)std::min<int64_t>(CH, (int64_t)tiles.size() - o), 0});
     }
-    item_begin[nqt] = (int32_t)items.size();
+    qt_first[nqt] = (int64_t)tiles.size();
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(sms, total_tiles));
+    std::vector<WorkItem> items;
+    std::vector<int32_t> item_begin(nqt + 1, 0), cta_first(G + 1, 0);
+    for (int64_t c = 0; c < G; ++c) {
+        cta_first[c] = (int32_t)items.size();
+        const int64_t t0 = c * total_tiles / G, t1 = (c + 1) * total_tiles / G;
+        int64_t t = t0;
+        int64_t qt = std::upper_bound(qt_first.begin(), qt_first.end(), t0) - qt_first.begin() - 1;
+        while (t < t1) {
+            while (qt_first[qt + 1] <= t) ++qt;
+            const int64_t e = std::min(t1, qt_first[qt + 1]);
+            items.push_back(WorkItem{(int32_t)qt, (int32_t)t, (int32_t)(e - t), 0});
+            t = e;
+        }
+    }
+    cta_first[G] = (int32_t)items.size();
+    for (int64_t qt = 0, i = 0; qt <= nqt; ++qt) {   // first item of each query tile
+        while (i < (int64_t)items.size() && items[i].qtile < qt) ++i;
+        item_begin[qt] = (int32_t)i;
+    }
+    const int64_t CH = G > 0 ? (total_tiles + G - 1) / G : 0;
     const int64_t n_items = (int64_t)items.size();
 
     // ---- query-side scratch
@@ -1142,7 +1163,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     size_t bytes = al((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE) + 2 * al(sizeof(float) * nq) +
                    al(sizeof(int32_t) * std::max<int64_t>(nv, 1)) + al(sizeof(WorkItem) * ni1) +
                    al(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1)) + al(sizeof(int32_t) * (nqt + 1)) +
-                   2 * al((size_t)4 * ni1 * K1 * TM) + al(sizeof(int32_t) * ni1 * TM) +
+                   al(sizeof(int32_t) * (G + 1)) + 2 * al((size_t)4 * ni1 * K1 * TM) + al(sizeof(int32_t) * ni1 * TM) +
                    al((sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1) + 3 * al(sizeof(int32_t) * nq) +
                    al(sizeof(int32_t) * 4);
     unsigned char *scratch = nullptr;
@@ -1156,6 +1177,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     WorkItem *d_items = (WorkItem *)take(sizeof(WorkItem) * ni1);
     int32_t *d_tiles = (int32_t *)take(sizeof(int32_t) * std::max<int64_t>(total_tiles, 1));
     int32_t *d_ib = (int32_t *)take(sizeof(int32_t) * (nqt + 1));
+    int32_t *d_cta = (int32_t *)take(sizeof(int32_t) * (G + 1));
     float *part_d = (float *)take((size_t)4 * ni1 * K1 * TM);
     int32_t *part_i = (int32_t *)take((size_t)4 * ni1 * K1 * TM);
     int32_t *part_n = (int32_t *)take(sizeof(int32_t) * ni1 * TM);
@@ -1176,6 +1198,8 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         ce = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int32_t) * total_tiles, cudaMemcpyHostToDevice, stream);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(d_ib, item_begin.data(), sizeof(int32_t) * (nqt + 1), cudaMemcpyHostToDevice, stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d_cta, cta_first.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, stream);
     if (ce == cudaSuccess) {
         norms_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(queries, nq, d, qnorm, qrow);
         if (nqt > 0)
@@ -1187,10 +1211,10 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (ce == cudaSuccess && n_items > 0) {
         // MMA work issued: three 128 x 128 x 64 BF16 products per point tile and K chunk
         esg_prof_tensor_flops((double)total_tiles * nk * 3.0 * 2.0 * TM * TN * TK);
-        Tc2Args a{X.xs, qs, X.xnorm, qnorm, l, r, d_order, d_items, d_tiles, (int)n_items, nv, nk, metric, K1, S,
+        Tc2Args a{X.xs, qs, X.xnorm, qnorm, l, r, d_order, d_items, d_tiles, d_cta, (int)n_items, nv, nk, metric, K1, S,
                   n, part_d, part_i, part_n, err};
         const int pidx = esg_prof_begin(stream);
-        tc_knn2_kernel<<<(unsigned)std::min<int64_t>(n_items, sms), kThreads2, smem, stream>>>(a);
+        tc_knn2_kernel<<<(unsigned)G, kThreads2, smem, stream>>>(a);
         ce = cudaGetLastError();
         esg_prof_end(pidx, stream);
         if (ce == cudaSuccess) {
@@ -1202,7 +1226,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     const char *dbg = getenv("ESG_BF_STATS");
     if (dbg && *dbg == '1')
-        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items of <= %lld, %d stages\n",
+        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items, %lld tiles per CTA, %d stages\n",
                 (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S);
     std::vector<int64_t> left;
     if (st == ESG_OK)
