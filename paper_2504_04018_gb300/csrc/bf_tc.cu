@@ -3,20 +3,19 @@
 // Dot products q.x come from three BF16 MMAs per K step accumulated in FP32
 // in tensor memory (split precision: q = q_hi + q_lo, x = x_hi + x_lo with
 // BF16 parts, q.x ~ q_hi.x_hi + q_hi.x_lo + q_lo.x_hi; the dropped q_lo.x_lo
-// and the split residuals are below 2^-17 relative). A CTA owns 128 queries
-// (one TMEM lane each) and walks the union of their rank ranges in tiles of
-// 128 points (128 TMEM columns). Operands are staged with cp.async into
-// shared memory in the 128-byte-swizzled K-major layout the MMA descriptors
-// name; one thread issues the MMAs and commits them to an mbarrier; all 128
-// threads then read their row from TMEM, mask it by the query's range and
-// keep the K1 = k' + 1 best approximate distances per query.
+// and the split residuals are below 2^-17 relative). Queries are sorted and
+// tiled by 128 (one TMEM lane each); a query tile visits the 128-point tiles
+// its ranges cover (128 TMEM columns per tile). The pipelined kernel below
+// is warp-specialised: bulk copies of pre-swizzled operand blocks, one MMA
+// thread, and eight epilogue warps that keep the K1 best approximate
+// distances per query.
 //
 // A second kernel recomputes exact FP32 distances (direct form) of those
 // candidates, sorts them, and certifies the result: with delta_q a bound on
 // |approximate - exact| for every point of the range, the top k is proven
 // when the exact k-th distance is below (K1-th approximate distance -
-// delta_q). Queries without a certificate are recomputed by the exact SIMT
-// brute force.
+// delta_q). Queries without a certificate run again with a longer list, then
+// through the exact SIMT brute force.
 #include "esg_internal.cuh"
 
 #include <algorithm>
@@ -36,8 +35,6 @@ constexpr int TM = 128;            // queries per CTA (TMEM lanes)
 constexpr int TN = 128;            // points per tile (TMEM columns)
 constexpr int TK = 64;             // K chunk: 64 BF16 = one 128-byte swizzled row
 constexpr int CHUNK = TM * TK * 2; // bytes of one 128 x 64 BF16 operand chunk (16 KB)
-constexpr int kMaxK1 = 72;
-constexpr long kSpinLimit = 1L << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -73,24 +70,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  :: "r"(mbar) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (long it = 0; it < kSpinLimit; ++it) {
-        uint32_t done = 0;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
-    const int sz = valid ? 16 : 0;   // zero-fill rows past the end
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(sz) : "memory");
-}
-
 // 32 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
@@ -107,185 +86,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Copy a 128-row x 64-element BF16 chunk (rows row0.., elements k0..k0+63 of
-// a row-major [rows, d] matrix) into 128-byte-swizzled shared memory:
-// 16-byte piece c of row t lands at t * 128 + ((c ^ (t & 7)) * 16).
-__device__ __forceinline__ void load_chunk(uint32_t sdst, const __nv_bfloat16 *src, int64_t rows,
-                                           int64_t row0, int d, int k0) {
-    for (int idx = threadIdx.x; idx < TM * 8; idx += blockDim.x) {
-        const int t = idx >> 3, c = idx & 7;
-        const int64_t row = row0 + t;
-        const bool ok = row >= 0 && row < rows;
-        const __nv_bfloat16 *g = src + (ok ? row : 0) * (int64_t)d + k0 + c * 8;
-        cp_async16(sdst + t * 128 + ((c ^ (t & 7)) << 4), g, ok);
-    }
-}
-
-struct TcArgs {
-    const __nv_bfloat16 *qhi, *qlo, *xhi, *xlo;   // [nq, d], [n, d]
-    const float *qnorm, *xnorm;                    // squared norms (L2)
-    const int64_t *l, *r;
-    int64_t n, nq;
-    int d, metric, K1;
-    float *cand_d;      // [nq, K1] approximate distances (ascending)
-    int32_t *cand_i;    // [nq, K1] rows
-    int32_t *cand_n;    // [nq]
-    int32_t *err;       // set when a bounded wait ran out
-};
-
-__global__ void __launch_bounds__(128, 1) tc_knn_kernel(TcArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // 1024-byte aligned operand area: A hi/lo chunk, B hi/lo chunk
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA_hi = base, *sA_lo = base + CHUNK, *sB_hi = base + 2 * CHUNK, *sB_lo = base + 3 * CHUNK;
-    float *ld = (float *)(base + 4 * CHUNK);                       // [TM][K1 + 1] distances
-    int32_t *li = (int32_t *)(ld + TM * (a.K1 + 1));               // [TM][K1 + 1] rows
-    uint64_t *mbar = (uint64_t *)(li + TM * (a.K1 + 1) + 1);       // 8-byte aligned below
-    mbar = (uint64_t *)(((uintptr_t)mbar + 7) & ~(uintptr_t)7);
-    uint32_t *tmem_slot = (uint32_t *)(mbar + 1);
-    __shared__ long long s_lo, s_hi;
-    __shared__ int s_abort;
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t q0 = (int64_t)blockIdx.x * TM;
-    const int64_t qi = q0 + tid;
-    int64_t my_lo = 1, my_hi = 0;
-    if (qi < a.nq) {
-        const int64_t l = a.l[qi], r = a.r[qi];
-        if (l >= 0 && l <= r && r < a.n) { my_lo = l; my_hi = r; }
-    }
-    const float qn = (qi < a.nq && a.metric == ESG_L2SQ) ? a.qnorm[qi] : 0.f;
-    const int K1 = a.K1;
-    float *myd = ld + tid;        // column-interleaved: entry e at myd[e * TM]
-    int32_t *myi = li + tid;
-    int cnt = 0;
-    float thr = INFINITY;
-    int32_t thr_id = 0x7FFFFFFF;
-
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_lo = 0x7FFFFFFFFFFFFFFFLL; s_hi = -1; s_abort = 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tmem_slot)), "r"(TN) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    if (my_lo <= my_hi) {
-        atomicMin(&s_lo, (long long)my_lo);
-        atomicMax(&s_hi, (long long)my_hi);
-    }
-    __syncthreads();
-    const int64_t ulo = s_lo, uhi = s_hi;
-    uint32_t phase = 0;
-    const int nk = a.d / TK;
-
-    for (int64_t t0 = (uhi >= 0 ? ulo : 1); t0 <= uhi; t0 += TN) {
-        // skip tiles no query of this CTA overlaps (uniform: barrier + OR)
-        const bool overlaps = my_lo <= my_hi && my_lo <= t0 + TN - 1 && my_hi >= t0;
-        if (!__syncthreads_or(overlaps)) continue;
-        for (int kc = 0; kc < nk; ++kc) {
-            load_chunk(smem_u32(sA_hi), a.qhi, a.nq, q0, a.d, kc * TK);
-            load_chunk(smem_u32(sA_lo), a.qlo, a.nq, q0, a.d, kc * TK);
-            load_chunk(smem_u32(sB_hi), a.xhi, a.n, t0, a.d, kc * TK);
-            load_chunk(smem_u32(sB_lo), a.xlo, a.n, t0, a.d, kc * TK);
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ah = smem_u32(sA_hi), al = smem_u32(sA_lo);
-                const uint32_t bh = smem_u32(sB_hi), bl = smem_u32(sB_lo);
-#pragma unroll
-                for (int s = 0; s < TK / 16; ++s) {
-                    const uint32_t off = s * 32;   // 16 BF16 along K inside the swizzled row
-                    const uint32_t first = (kc == 0 && s == 0) ? 0u : 1u;
-                    mma_bf16(tmem, sdesc(ah + off), sdesc(bh + off), first);
-                    mma_bf16(tmem, sdesc(ah + off), sdesc(bl + off), 1u);
-                    mma_bf16(tmem, sdesc(al + off), sdesc(bh + off), 1u);
-                }
-                mma_commit(smem_u32(mbar));
-            }
-            // the MMAs read the operand chunk: wait before overwriting it
-            if (!mbar_wait(smem_u32(mbar), phase)) {
-                if (tid == 0) { s_abort = 1; atomicExch(a.err, 1); }
-            }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (s_abort) break;
-        }
-        if (s_abort) break;
-        // epilogue: this thread's row of the 128 x 128 tile (every lane of a
-        // warp executes the tcgen05.ld; rows outside the tile ignore theirs)
-        const bool active = my_lo <= my_hi && my_lo <= t0 + TN - 1 && my_hi >= t0;
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (!active) continue;
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) {
-                const int64_t p = t0 + c0 + j;
-                if (p < my_lo || p > my_hi) continue;
-                const float dist = a.metric == ESG_L2SQ ? qn + __ldg(a.xnorm + p) - 2.f * v[j] : -v[j];
-                const int32_t pid = (int32_t)p;
-                if (cnt == K1 && !(dist < thr || (dist == thr && pid < thr_id))) continue;
-                // insertion into the row's ascending list
-                int e = cnt < K1 ? cnt : K1 - 1;
-                while (e > 0) {
-                    const float pd = myd[(e - 1) * TM];
-                    const int32_t pi = myi[(e - 1) * TM];
-                    if (pd < dist || (pd == dist && pi < pid)) break;
-                    myd[e * TM] = pd;
-                    myi[e * TM] = pi;
-                    --e;
-                }
-                myd[e * TM] = dist;
-                myi[e * TM] = pid;
-                if (cnt < K1) ++cnt;
-                if (cnt == K1) { thr = myd[(K1 - 1) * TM]; thr_id = myi[(K1 - 1) * TM]; }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-    }
-    if (qi < a.nq) {
-        for (int e = 0; e < cnt; ++e) {
-            a.cand_d[qi * K1 + e] = myd[e * TM];
-            a.cand_i[qi * K1 + e] = myi[e * TM];
-        }
-        a.cand_n[qi] = (my_lo <= my_hi) ? cnt : -1;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TN) : "memory");
-    }
-}
-
-// FP32 -> (hi, lo) BF16 split and squared norms, one thread per row.
-__global__ void split_rows_kernel(const float *X, int64_t rows, int d, __nv_bfloat16 *hi,
-                                  __nv_bfloat16 *lo, float *norm, float *rownorm) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    const float *x = X + i * d;
-    float s = 0.f;
-    for (int j = 0; j < d; ++j) {
-        const float v = x[j];
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i * d + j] = h;
-        lo[i * d + j] = __float2bfloat16_rn(v - __bfloat162float(h));
-        s = fmaf(v, v, s);
-    }
-    if (norm) norm[i] = s;
-    if (rownorm) rownorm[i] = sqrtf(s);
 }
 
 __global__ void max_kernel(const float *v, int64_t n, float *out) {
@@ -405,6 +205,7 @@ struct Tc2Args {
     int n_items;
     int64_t nv;                     // number of valid (sorted) queries
     int nk, metric, K1, S;
+    int stream_a;                   // 1: each stage carries the query tile's K chunk too
     int64_t n;                      // points
     float *part_d;                  // [n_items][128][K1]
     int32_t *part_i;                // [n_items][128][K1]
@@ -481,9 +282,13 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int K1 = a.K1;
+    // resident query tile: sA holds its nk K chunks for the whole item, a stage
+    // one point chunk; streamed (large d): a stage holds the query chunk and
+    // the point chunk of one K step
+    const int stage_bytes = a.stream_a ? 2 * STAGE : STAGE;
     unsigned char *sA = base;
-    unsigned char *sB = sA + (size_t)a.nk * STAGE;
-    float *T = (float *)(sB + (size_t)a.S * STAGE);          // [128][kTS] half tile, transposed
+    unsigned char *sB = sA + (a.stream_a ? (size_t)0 : (size_t)a.nk * STAGE);
+    float *T = (float *)(sB + (size_t)a.S * stage_bytes);    // [128][kTS] half tile, transposed
     float *s_xn = T + TM * kTS;                              // [4 pairs][2][128] tile norms
     float *L_d = s_xn + 8 * TN;                              // [128][K1] per-row lists
     int32_t *L_i = (int32_t *)(L_d + TM * K1);
@@ -536,20 +341,27 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             bool ok = true;
             for (int it = it_begin; ok && it < it_end; ++it) {
                 const WorkItem I = a.items[it];
-                if (!wait_phase(smem_u32(a_empty), pa ^ 1u, abort_f, a.err)) { ok = false; break; }
-                mbar_expect_tx(smem_u32(a_full), (uint32_t)(a.nk * STAGE));
-                for (int kc = 0; kc < a.nk; ++kc)
-                    bulk_g2s(smem_u32(sA + (size_t)kc * STAGE),
-                             a.qs + ((int64_t)I.qtile * a.nk + kc) * STAGE, STAGE, smem_u32(a_full));
-                a_pending = true; a_par = pa;
-                pa ^= 1u;
+                if (!a.stream_a) {
+                    if (!wait_phase(smem_u32(a_empty), pa ^ 1u, abort_f, a.err)) { ok = false; break; }
+                    mbar_expect_tx(smem_u32(a_full), (uint32_t)(a.nk * STAGE));
+                    for (int kc = 0; kc < a.nk; ++kc)
+                        bulk_g2s(smem_u32(sA + (size_t)kc * STAGE),
+                                 a.qs + ((int64_t)I.qtile * a.nk + kc) * STAGE, STAGE, smem_u32(a_full));
+                    a_pending = true; a_par = pa;
+                    pa ^= 1u;
+                }
                 for (int j = 0; ok && j < I.cnt; ++j) {
                     const int64_t t = a.tiles[I.off + j];
                     for (int kc = 0; kc < a.nk; ++kc) {
                         if (!wait_phase(smem_u32(empty + s), ps ^ 1u, abort_f, a.err)) { ok = false; break; }
-                        mbar_expect_tx(smem_u32(full + s), STAGE);
-                        bulk_g2s(smem_u32(sB + (size_t)s * STAGE), a.xs + (t * a.nk + kc) * STAGE, STAGE,
-                                 smem_u32(full + s));
+                        unsigned char *sg = sB + (size_t)s * stage_bytes;
+                        mbar_expect_tx(smem_u32(full + s), (uint32_t)stage_bytes);
+                        if (a.stream_a) {
+                            bulk_g2s(smem_u32(sg), a.qs + ((int64_t)I.qtile * a.nk + kc) * STAGE, STAGE,
+                                     smem_u32(full + s));
+                            sg += STAGE;
+                        }
+                        bulk_g2s(smem_u32(sg), a.xs + (t * a.nk + kc) * STAGE, STAGE, smem_u32(full + s));
                         issued[s] = 1; ipar[s] = ps;
                         if (++s == (uint32_t)a.S) { s = 0; ps ^= 1u; }
                     }
@@ -570,8 +382,10 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             bool ok = true;
             for (int it = it_begin; ok && it < it_end; ++it) {
                 const int cnt = a.items[it].cnt;
-                if (!wait_phase(smem_u32(a_full), pa, abort_f, a.err)) { ok = false; break; }
-                pa ^= 1u;
+                if (!a.stream_a) {
+                    if (!wait_phase(smem_u32(a_full), pa, abort_f, a.err)) { ok = false; break; }
+                    pa ^= 1u;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int j = 0; ok && j < cnt; ++j) {
                     const uint32_t b = acc_it & 1u;
@@ -583,8 +397,9 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                     for (int kc = 0; kc < a.nk; ++kc) {
                         if (!wait_phase(smem_u32(full + s), ps, abort_f, a.err)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t ah = smem_u32(sA + (size_t)kc * STAGE), al = ah + CHUNK;
-                        const uint32_t bh = smem_u32(sB + (size_t)s * STAGE), bl = bh + CHUNK;
+                        const uint32_t sg = smem_u32(sB + (size_t)s * stage_bytes);
+                        const uint32_t ah = a.stream_a ? sg : smem_u32(sA + (size_t)kc * STAGE), al = ah + CHUNK;
+                        const uint32_t bh = a.stream_a ? sg + STAGE : sg, bl = bh + CHUNK;
 #pragma unroll
                         for (int st = 0; st < TK / 16; ++st) {
                             const uint32_t off = st * 32;
@@ -597,7 +412,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                     }
                     if (ok) mma_commit(smem_u32(acc_full + b));
                 }
-                if (ok) mma_commit(smem_u32(a_empty));
+                if (ok && !a.stream_a) mma_commit(smem_u32(a_empty));
             }
             // all MMAs issued by this thread complete before the CTA exits
             mma_commit(smem_u32(drain));
@@ -919,74 +734,26 @@ static esg_status certify_and_redo(const float *base, int64_t n, int32_t d, int 
     return esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist, out_count, stream);
 }
 
-// Single-pass tensor-core path: one CTA per 128 queries walks the union of
-// their ranges with a synchronous load -> MMA -> epilogue loop (kept for the
-// shapes the pipelined kernel does not take: d > 192 or k > 16).
-static esg_status bruteforce_tc_v1(const float *base, int64_t n, int32_t d, int metric, const float *queries,
-                             int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
-                             float *out_dist, int32_t *out_count, cudaStream_t stream) {
-    if (d % TK != 0 || k < 1 || 2 * k + 8 > kMaxK1 || n >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
-    if (nq == 0) return ESG_OK;
-    const int K1 = 2 * k + 8;
-    // device scratch: BF16 splits, norms, candidates, flags
-    const size_t nb = sizeof(__nv_bfloat16);
-    size_t bytes = nb * (size_t)d * (2 * n + 2 * nq) + sizeof(float) * (2 * n + 2 * nq + 4) +
-                   (sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1 + sizeof(int32_t) * (2 * nq + 4);
-    bytes += 8 * 256;
-    unsigned char *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    unsigned char *p = scratch;
-    __nv_bfloat16 *xhi = (__nv_bfloat16 *)p; p += al(nb * n * d);
-    __nv_bfloat16 *xlo = (__nv_bfloat16 *)p; p += al(nb * n * d);
-    __nv_bfloat16 *qhi = (__nv_bfloat16 *)p; p += al(nb * nq * d);
-    __nv_bfloat16 *qlo = (__nv_bfloat16 *)p; p += al(nb * nq * d);
-    float *xnorm = (float *)p; p += al(sizeof(float) * n);
-    float *xrow = (float *)p; p += al(sizeof(float) * n);
-    float *qnorm = (float *)p; p += al(sizeof(float) * nq);
-    float *qrow = (float *)p; p += al(sizeof(float) * nq);
-    float *xmax = (float *)p; p += al(sizeof(float) * 4);
-    float *cand_d = (float *)p; p += al(sizeof(float) * nq * K1);
-    int32_t *cand_i = (int32_t *)p; p += al(sizeof(int32_t) * nq * K1);
-    int32_t *cand_n = (int32_t *)p; p += al(sizeof(int32_t) * nq);
-    int32_t *redo = (int32_t *)p; p += al(sizeof(int32_t) * nq);
-    int32_t *err = (int32_t *)p;
-    esg_status st = ESG_OK;
-    cudaError_t ce = cudaMemsetAsync(xmax, 0, sizeof(float) * 4, stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(err, 0, sizeof(int32_t), stream);
-    if (ce == cudaSuccess) {
-        split_rows_kernel<<<ceil_div_i(n, 256), 256, 0, stream>>>(base, n, d, xhi, xlo, xnorm, xrow);
-        split_rows_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(queries, nq, d, qhi, qlo, qnorm, qrow);
-        max_kernel<<<152, 256, 0, stream>>>(xrow, n, xmax);
-        ce = cudaGetLastError();
-    }
-    const size_t smem = 1024 + 4 * CHUNK + (size_t)TM * (K1 + 1) * 8 + 64;
-    if (ce == cudaSuccess) ce = cudaFuncSetAttribute(tc_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (ce == cudaSuccess) {
-        TcArgs a{qhi, qlo, xhi, xlo, qnorm, xnorm, l, r, n, nq, d, metric, K1, cand_d, cand_i, cand_n, err};
-        const int pidx = esg_prof_begin(stream);
-        tc_knn_kernel<<<(unsigned)((nq + TM - 1) / TM), 128, smem, stream>>>(a);
-        ce = cudaGetLastError();
-        esg_prof_end(pidx, stream);
-    }
-    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
-    if (st == ESG_OK)
-        st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, xmax,
-                              redo, err, out_ids, out_dist, out_count, stream);
-    cudaFreeAsync(scratch, stream);
-    return st;
-}
-
 // Shared-memory plan of the pipelined kernel for a dimension and list length:
-// ESG_ERR_UNSUPPORTED when fewer than two point stages fit.
-static esg_status bf2_smem(int32_t d, int K1, int max_smem, int *S, size_t *smem) {
+// the query tile resident when that leaves room for two point stages, else
+// streamed with the point chunks (stages of 64 KB); ESG_ERR_UNSUPPORTED when
+// not even two streamed stages fit.
+static esg_status bf2_smem(int32_t d, int K1, int max_smem, int *S, size_t *smem, int *stream_a) {
     if (K1 > kMaxK1v2 || d < 1) return ESG_ERR_UNSUPPORTED;
     const int nk = (d + TK - 1) / TK;
-    const size_t fixed = 1024 + (size_t)nk * STAGE + (size_t)TM * kTS * 4 + 8 * TN * 4 + (size_t)TM * K1 * 8 +
-                         6 * TM * 4 + 8 * 4 + 8 * (2 * kMaxStages + 8) + 16;
-    if ((size_t)max_smem < fixed + 2 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
-    *S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - fixed) / STAGE);
-    *smem = fixed + (size_t)*S * STAGE;
+    const size_t common = 1024 + (size_t)TM * kTS * 4 + 8 * TN * 4 + (size_t)TM * K1 * 8 + 6 * TM * 4 + 8 * 4 +
+                          8 * (2 * kMaxStages + 8) + 16;
+    const size_t resident = common + (size_t)nk * STAGE;
+    if ((size_t)max_smem >= resident + 2 * (size_t)STAGE) {
+        *stream_a = 0;
+        *S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - resident) / STAGE);
+        *smem = resident + (size_t)*S * STAGE;
+        return ESG_OK;
+    }
+    if ((size_t)max_smem < common + 4 * (size_t)STAGE) return ESG_ERR_UNSUPPORTED;
+    *stream_a = 1;
+    *S = (int)std::min<size_t>(kMaxStages, ((size_t)max_smem - common) / (2 * STAGE));
+    *smem = common + (size_t)*S * 2 * STAGE;
     return ESG_OK;
 }
 
@@ -1035,7 +802,8 @@ static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n,
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     int K2 = kMaxK1v2;   // the longest list that fits
-    while (K2 > K1 && bf2_smem(d, K2, max_smem, &S, &smem) != ESG_OK) --K2;
+    int sa_mode = 0;
+    while (K2 > K1 && bf2_smem(d, K2, max_smem, &S, &smem, &sa_mode) != ESG_OK) --K2;
     if (K2 <= K1)
         return esg_bruteforce_redo(base, n, d, metric, queries, nq, l, r, k, idx, out_ids, out_dist, out_count, stream);
     const int64_t m = (int64_t)idx.size();
@@ -1079,12 +847,12 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
                               int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
     if (nq == 0) return ESG_OK;
     const int nk = (d + TK - 1) / TK;
-    int dev = 0, max_smem = 0, sms = 0, S = 0;
+    int dev = 0, max_smem = 0, sms = 0, S = 0, stream_a = 0;
     size_t smem = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (bf2_smem(d, K1, max_smem, &S, &smem) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
 
     // ---- host plan: sort queries by (log2 width, l), tile them, list the
     // point tiles each query tile covers and cut the lists into work items
@@ -1212,7 +980,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         // MMA work issued: three 128 x 128 x 64 BF16 products per point tile and K chunk
         esg_prof_tensor_flops((double)total_tiles * nk * 3.0 * 2.0 * TM * TN * TK);
         Tc2Args a{X.xs, qs, X.xnorm, qnorm, l, r, d_order, d_items, d_tiles, d_cta, (int)n_items, nv, nk, metric, K1, S,
-                  n, part_d, part_i, part_n, err};
+                  stream_a, n, part_d, part_i, part_n, err};
         const int pidx = esg_prof_begin(stream);
         tc_knn2_kernel<<<(unsigned)G, kThreads2, smem, stream>>>(a);
         ce = cudaGetLastError();
@@ -1226,8 +994,9 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     const char *dbg = getenv("ESG_BF_STATS");
     if (dbg && *dbg == '1')
-        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items, %lld tiles per CTA, %d stages\n",
-                (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S);
+        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items, %lld tiles per CTA, %d stages%s\n",
+                (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S,
+                stream_a ? " (query tile streamed)" : "");
     std::vector<int64_t> left;
     if (st == ESG_OK)
         st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, X.xmax,
@@ -1249,11 +1018,11 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
                                    float *out_dist, int32_t *out_count, cudaStream_t stream) {
     const int K1 = k + 8;
     if (k < 1 || K1 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
-    int dev = 0, max_smem = 0, S = 0;
+    int dev = 0, max_smem = 0, S = 0, stream_a = 0;
     size_t smem = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (bf2_smem(d, K1, max_smem, &S, &smem) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
     if (nq == 0) return ESG_OK;
     const int nk = (d + TK - 1) / TK;
     const int64_t xt = (n + TN - 1) / TN;
@@ -1288,7 +1057,5 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
 esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric, const float *queries,
                              int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
                              float *out_dist, int32_t *out_count, cudaStream_t stream) {
-    esg_status st = bruteforce_tc_v2(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
-    if (st != ESG_ERR_UNSUPPORTED) return st;
-    return bruteforce_tc_v1(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
+    return bruteforce_tc_v2(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
 }
