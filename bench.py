@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget variant")
+    ap.add_argument("--bf-workload", default="scale", choices=["scale", "learned"],
+                    help="workload of --mode bruteforce: the 128-d scale mixture or the 768-d "
+                         "anisotropic inner-product workload (its held-out queries)")
     ap.add_argument("--mode", default="search", choices=["search", "bruteforce", "batching"],
                     help="bruteforce: time only the exact filtered k-NN of the workload's queries; "
                          "batching: the 10M-point, 100k-query workload in one CUDA-graph launch")
@@ -228,7 +231,7 @@ def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10)
+            E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10, w.metric)
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
@@ -236,7 +239,7 @@ def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
     os.environ.pop("ESG_BF_SIMT", None)
     # the MMA kernel alone
     E.esg_profile_enable(True)
-    E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10)
+    E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10, w.metric)
     torch.cuda.synchronize()
     kms, _, _ = E.esg_profile_read(reset=True)
     mma_flops = E.esg_profile_tensor_work(reset=True)
@@ -294,7 +297,10 @@ def run_bruteforce_only(args, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     E.load_library()
-    w = workload(args)
+    if args.bf_workload == "learned":
+        w = synthetic.learned(n=args.n, nq=args.nq, n_train=0)
+    else:
+        w = workload(args)
     perm = np.argsort(w.attr, kind="stable")      # rank order: attribute, ties by id
     Xr = torch.as_tensor(w.base[perm], device=dev)
     Q = torch.as_tensor(w.queries, device=dev)
@@ -304,7 +310,10 @@ def run_bruteforce_only(args, local):
     print(json.dumps({"mode": "bruteforce", "metric": "exact RF-kNN queries/sec (k=10)",
                       "value": info["qps_tcgen05"], "unit": "queries/s", "n_gpus": 1,
                       "higher_is_better": True, "dtype": "bf16x3+f32", "data": "synthetic",
-                      "config": workload_config(args), "bruteforce": info}), flush=True)
+                      "config": (workload_config(args) if args.bf_workload == "scale" else
+                                 {"workload": f"N={w.n}, d={w.d} anisotropic unit vectors, inner product, "
+                                              f"{len(w.l)} queries, widths log-uniform 0.1%-100%, k=10"}),
+                      "bruteforce": info}), flush=True)
 
 
 def run_batching(args, local):
