@@ -306,8 +306,9 @@ void esg_batch_free(esg_batch *batch);
  * slots, lanes per row) by timing with CUDA events. `base` supplies the other
  * fields (traversal, rerank, ...). Writes the chosen parameters to `out` and,
  * if `report` is not NULL, [recall, milliseconds per search of the sample].
- * With base->use_learned = 1 and a trained predictor, ef and width are kept
- * (the predictor sets ef per query) and only the launch shape is tuned.
+ * With base->use_learned = 1 and a trained predictor, ef is kept (the
+ * predictor sets ef per query); widths 1 and 2 are checked against the target
+ * and the launch shape is tuned for each that reaches it.
  * Synchronous on `stream`. ESG_ERR_UNSUPPORTED if no setting reaches the target.
  */
 esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq, const int64_t *l,

@@ -260,9 +260,13 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
     // 1. smallest ef reaching the target, per search width (with the learned
     //    budget, ef is only the fallback: keep it and check the recall)
     if (st == ESG_OK && p.use_learned && ix->mlp_ready) {
-        double rec = 0;
-        st = recall_of(p, rec);
-        if (st == ESG_OK && rec >= target_recall) found.push_back({p, rec, 0.f});
+        for (int width = 1; width <= 2 && st == ESG_OK; ++width) {
+            esg_search_params pp = p;
+            pp.width = width;
+            double rec = 0;
+            st = recall_of(pp, rec);
+            if (st == ESG_OK && rec >= target_recall) found.push_back({pp, rec, 0.f});
+        }
     }
     for (int width = 1; width <= 2 && st == ESG_OK && !(p.use_learned && ix->mlp_ready); ++width) {
         for (int ef : efs) {

@@ -425,7 +425,10 @@ search_kernel(SearchArgs a) {
             }
         } else {
             // Graph piece: Algorithm 1 with POST filtering to [pl, pr].
-            for (int i = lane; i < a.H; i += 32) w.hash[i] = ESG_NONE;
+            {   // the table starts 16-byte aligned and H is a power of two >= 256
+                uint4 *h4 = reinterpret_cast<uint4 *>(w.hash);
+                for (int i = lane; i < a.H / 4; i += 32) h4[i] = make_uint4(ESG_NONE, ESG_NONE, ESG_NONE, ESG_NONE);
+            }
             if (lane == 0) { w.hcount[0] = 0; w.hcount[1] = 0; }
             __syncwarp();
             bool used_g = false;
