@@ -272,8 +272,9 @@ LEARNED_EF_HI = 64
 
 def measured_traffic(variant, params):
     """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, when it was taken for this variant, these parameters and the
-    current kernel sources (None otherwise)."""
+    summary, when it was taken for this variant, these search parameters
+    (ef, budget, row type, width; not the launch shape) and the current
+    kernel sources (None otherwise)."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")))[variant]
