@@ -170,3 +170,27 @@ def test_low_precision_rows_survive_save_load(learned_setup, tmp_path):
         b = E.esg_search_batch(g2, q[:300], l[:300], r[:300], None, 10, ef=32, traversal=t)[0]
         torch.cuda.synchronize()
         assert torch.equal(a, b)
+
+
+def test_constant_predictor_equals_fixed_ef(learned_setup):
+    """A network whose output is the constant (log2 32, large) sets every
+    query's beam width to 32 and its expansion cap to the default one: the
+    learned-budget search must then return exactly what the fixed ef = 32
+    search returns (same results, same counters)."""
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    saved = E.esg_predictor_get(gix)
+    try:
+        blob = np.zeros(E.esg_mlp_num_params() + 18, np.float32)
+        nparam = E.esg_mlp_num_params()
+        blob[nparam - 2] = 5.0          # b3[0]: log2 ef
+        blob[nparam - 1] = 20.0         # b3[1]: log2 expansion budget (clamped to 16 ef + 256)
+        blob[nparam + 8:nparam + 16] = 1.0   # feature standard deviations
+        E.esg_predictor_set(gix, blob, 8, 32)
+        a = E.esg_search_batch(gix, q, l, r, None, 10, ef=32, use_learned=1, want_stats=True)
+        b = E.esg_search_batch(gix, q, l, r, None, 10, ef=32, want_stats=True)
+        torch.cuda.synchronize()
+        for x, y in zip(a[:4], b[:4]):
+            assert torch.equal(x, y)
+        assert torch.equal(a[4][:, :5], b[4][:, :5])
+    finally:
+        E.esg_predictor_set(gix, *saved)
