@@ -318,13 +318,14 @@ esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq
 
 /*
  * Learned search budget (no counterpart in the paper). A small MLP
- * (8 query features -> 64 -> 64 -> 2, ReLU) predicts for each query log2 of
+ * (9 query features -> 64 -> 64 -> 2, ReLU) predicts for each query log2 of
  * the beam width ef and of an expansion budget; the search uses them when
  * esg_search_params.use_learned is 1 and a predictor is trained (otherwise
  * the fixed ef). Features: log2 range width, number of pieces, log2 of each
  * piece's node size over its size, whether the first piece is a graph piece,
  * log2 k, min / mean distance to the first piece's entry points, log2 of the
- * first piece's node size.
+ * first piece's node size, and the first hop's top-k gap: (min(k, E)-th
+ * smallest - smallest entry distance) / |mean entry distance|.
  *
  * esg_train_predictor: traces the plain search (fixed ef over a grid within
  * [ef_lo, ef_hi]) on training queries with exact answers (gt_ids device
@@ -358,18 +359,21 @@ esg_status esg_train_predictor(esg_index *index, const float *queries, int64_t n
                                const int64_t *gt_ids, const int32_t *gt_count,
                                const esg_train_params *params, float *report, esg_stream_t stream);
 
-/* Trained predictor as a host blob [params, mu[8], sigma[8], margin_ef,
- * margin_expansions] (esg_mlp_num_params() + 18 floats) with its ef range;
+/* Trained predictor as a host blob [params, mu[F], sigma[F], margin_ef,
+ * margin_expansions] (F = esg_mlp_num_features(); esg_mlp_num_params() + 2 F + 2
+ * floats) with its ef range;
  * set installs one (e.g. a saved one), get reads it back. */
 esg_status esg_predictor_set(esg_index *index, const float *blob, int32_t ef_lo, int32_t ef_hi);
 esg_status esg_predictor_get(const esg_index *index, float *blob, int32_t *ef_lo, int32_t *ef_hi);
 
-/* The MLP's own GPU kernels, exposed for checking: parameter count; forward
- * y [B, 2] = f(X [B, 8]) with standardisation mu, sigma [8]; pinball loss and
- * its gradient [num_params] (deterministic order); one Adam step (beta1 0.9,
- * beta2 0.999, eps 1e-8) at step >= 1; and the query features [nq, 8]. Device
- * pointers, asynchronous (loss, a host pointer, makes loss_grad synchronous). */
+/* The MLP's own GPU kernels, exposed for checking: parameter count and
+ * feature count F; forward y [B, 2] = f(X [B, F]) with standardisation mu,
+ * sigma [F]; pinball loss and its gradient [num_params] (deterministic order);
+ * one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step >= 1; and the query
+ * features [nq, F]. Device pointers, asynchronous (loss, a host pointer, makes
+ * loss_grad synchronous). */
 int32_t esg_mlp_num_params(void);
+int32_t esg_mlp_num_features(void);
 esg_status esg_mlp_forward(const float *params, const float *X, const float *mu, const float *sigma,
                            int64_t B, float *Y, esg_stream_t stream);
 esg_status esg_mlp_loss_grad(const float *params, const float *X, const float *T, const float *mu,

@@ -36,7 +36,7 @@ EXPORTED = [
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
     "esg_train_params_default", "esg_train_predictor", "esg_predictor_set", "esg_predictor_get",
-    "esg_mlp_num_params", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
+    "esg_mlp_num_params", "esg_mlp_num_features", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
     "esg_query_features",
 ]
 
@@ -115,6 +115,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_predictor_set.argtypes = [_P, _P, _I32, _I32]
     lib.esg_predictor_get.argtypes = [_P, _P, _P, _P]
     lib.esg_mlp_num_params.restype = _I32
+    lib.esg_mlp_num_features.restype = _I32
     lib.esg_mlp_forward.argtypes = [_P, _P, _P, _P, _I64, _P, _P]
     lib.esg_mlp_loss_grad.argtypes = [_P, _P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]
     lib.esg_mlp_adam_step.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_float, _P]
@@ -498,7 +499,7 @@ def esg_train_predictor(index: Index, queries, l, r, gt_ids, gt_count, k_max: in
 
 def esg_predictor_get(index: Index):
     lib = load_library()
-    blob = np.empty(lib.esg_mlp_num_params() + 18, dtype=np.float32)
+    blob = np.empty(lib.esg_mlp_num_params() + 2 * lib.esg_mlp_num_features() + 2, dtype=np.float32)
     lo, hi = _I32(), _I32()
     _check(lib.esg_predictor_get(index.handle, _np_ptr(blob), ctypes.byref(lo), ctypes.byref(hi)),
            "esg_predictor_get")
@@ -513,6 +514,10 @@ def esg_predictor_set(index: Index, blob: np.ndarray, ef_lo: int, ef_hi: int):
 
 def esg_mlp_num_params() -> int:
     return int(load_library().esg_mlp_num_params())
+
+
+def esg_mlp_num_features() -> int:
+    return int(load_library().esg_mlp_num_features())
 
 
 def esg_mlp_forward(params, X, mu, sigma, stream=None):
@@ -540,7 +545,8 @@ def esg_mlp_adam_step(params, grad, m, v, step: int, lr: float, stream=None):
 
 def esg_query_features(index: Index, queries, l, r, k=None, k_max: int = 10, stream=None):
     import torch
-    f = torch.empty((queries.shape[0], 8), dtype=torch.float32, device=queries.device)
+    f = torch.empty((queries.shape[0], esg_mlp_num_features()), dtype=torch.float32,
+                    device=queries.device)
     _check(load_library().esg_query_features(index.handle, _dev_ptr(queries), queries.shape[0],
                                              _dev_ptr(l), _dev_ptr(r), _dev_ptr(k), k_max, _dev_ptr(f),
                                              _stream_ptr(stream)), "esg_query_features")

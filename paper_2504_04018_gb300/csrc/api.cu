@@ -377,7 +377,7 @@ esg_status esg_attr_to_rank_range(const esg_index *ix, const double *lo, const d
 
 namespace {
 const char kMagic[8] = {'E', 'S', 'G', 'G', 'B', '3', '0', '0'};
-const uint32_t kVersion = 2;
+const uint32_t kVersion = 3;
 
 struct FileHeader {
     char magic[8];

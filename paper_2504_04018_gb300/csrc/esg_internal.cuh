@@ -11,7 +11,7 @@
 #include "../../include/esg.h"
 
 #define ESG_NONE 0xFFFFFFFFu
-#define ESG_MLP_FEATURES 8
+#define ESG_MLP_FEATURES 9
 // per-item search statistics: expansions, evaluations, out-of-range
 // evaluations, re-ranked rows, start and end time (ns, %globaltimer)
 #define ESG_ITEM_STATS 6

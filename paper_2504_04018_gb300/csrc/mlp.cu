@@ -3,7 +3,7 @@
 // on the GPU with this file's own forward, backward and Adam kernels from
 // traces of the plain fixed-ef search. The paper has no learned component.
 //
-// Network (F = 8 features):  x_hat = (x - mu) / sigma,
+// Network (F = 9 features):  x_hat = (x - mu) / sigma,
 //   h1 = relu(W1^T x_hat + b1) [64], h2 = relu(W2^T h1 + b2) [64],
 //   y = W3^T h2 + b3 [2] = (log2 ef, log2 expansion budget).
 // Loss: pinball (quantile q) averaged over rows and both outputs.
@@ -14,7 +14,9 @@
 // the distances to its first piece's entry points):
 //   0 log2 width, 1 number of pieces, 2/3 log2(node size / piece size) of
 //   piece 0 / 1, 4 piece 0 is a graph piece, 5 log2 k, 6 min / mean entry
-//   distance of piece 0 (1 for scans), 7 log2 node size of piece 0.
+//   distance of piece 0 (1 for scans), 7 log2 node size of piece 0, 8 the
+//   top-k gap of the first hop: (min(k, E)-th smallest - smallest entry
+//   distance) / |mean entry distance| (0 for scans).
 #include "esg_internal.cuh"
 #include "decompose.cuh"
 
@@ -237,9 +239,21 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
                 dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
                 cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             }
+            // the min(k, cnt)-th smallest entry distance: the head lane whose
+            // rank (entries before it in (distance, lane) order) is that minus one
+            int rank = 0;
+            for (int j = 0; j < 32; ++j) {
+                const float dj = __shfl_sync(0xffffffffu, dist, j);
+                const bool hj = __shfl_sync(0xffffffffu, head ? 1 : 0, j) != 0;
+                rank += (hj && (dj < dist || (dj == dist && j < lane))) ? 1 : 0;
+            }
+            const int kth = min(max(kk, 1), max(cnt, 1)) - 1;
+            const unsigned at = __ballot_sync(0xffffffffu, head && rank == kth);
+            const float dk = at ? __shfl_sync(0xffffffffu, dist, __ffs(at) - 1) : dmin;
             if (cnt > 0) {
                 const float mean = dsum / cnt;
                 f[6] = fabsf(mean) > 1e-20f ? dmin / mean : 1.f;
+                f[8] = fabsf(mean) > 1e-20f ? (dk - dmin) / fabsf(mean) : 0.f;
             }
         }
     }
@@ -315,6 +329,8 @@ esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t
 extern "C" {
 
 int32_t esg_mlp_num_params(void) { return kP; }
+
+int32_t esg_mlp_num_features(void) { return kF; }
 
 esg_status esg_mlp_forward(const float *params, const float *X, const float *mu, const float *sigma,
                            int64_t B, float *Y, esg_stream_t stream) {

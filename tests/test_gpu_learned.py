@@ -17,7 +17,7 @@ DEV = "cuda:0"
 
 def _rand_problem(seed, B=300):
     rng = np.random.default_rng(seed)
-    F = 8
+    F = E.esg_mlp_num_features()
     p = (rng.standard_normal(OM.n_params(F)) * 0.2).astype(np.float32)
     X = (rng.standard_normal((B, F)) * 2 + 0.5).astype(np.float32)
     T = rng.standard_normal((B, 2)).astype(np.float32)
@@ -31,7 +31,8 @@ def _t(a):
 
 
 def test_param_count():
-    assert E.esg_mlp_num_params() == OM.n_params(8)
+    assert E.esg_mlp_num_features() == 9
+    assert E.esg_mlp_num_params() == OM.n_params(9)
 
 
 def test_mlp_forward_matches_oracle():
@@ -53,7 +54,7 @@ def test_mlp_gradient_matches_oracle(q):
 
 def test_adam_step_matches_oracle():
     rng = np.random.default_rng(3)
-    n = OM.n_params(8)
+    n = OM.n_params(E.esg_mlp_num_features())
     p = rng.standard_normal(n).astype(np.float32)
     g = rng.standard_normal(n).astype(np.float32)
     m = (rng.standard_normal(n) * 0.01).astype(np.float32)
@@ -104,8 +105,11 @@ def test_features_match_definition(learned_setup):
             e = e[e >= 0]
             dd = O.distances(X[e].astype(np.float64), w.queries[i], w.metric)
             assert np.isclose(f[i, 6], dd.min() / dd.mean(), rtol=1e-4)
+            # first-hop top-k gap: k-th smallest minus smallest, over |mean|
+            kth = np.sort(dd)[min(10, len(dd)) - 1]
+            assert np.isclose(f[i, 8], (kth - dd.min()) / abs(dd.mean()), rtol=1e-3, atol=1e-5)
         else:
-            assert f[i, 6] == 1.0
+            assert f[i, 6] == 1.0 and f[i, 8] == 0.0
 
 
 def test_trained_predictor_gains_over_fixed_ef(learned_setup):
@@ -180,11 +184,11 @@ def test_constant_predictor_equals_fixed_ef(learned_setup):
     w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
     saved = E.esg_predictor_get(gix)
     try:
-        blob = np.zeros(E.esg_mlp_num_params() + 18, np.float32)
-        nparam = E.esg_mlp_num_params()
+        nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
+        blob = np.zeros(nparam + 2 * F + 2, np.float32)
         blob[nparam - 2] = 5.0          # b3[0]: log2 ef
         blob[nparam - 1] = 20.0         # b3[1]: log2 expansion budget (clamped to 16 ef + 256)
-        blob[nparam + 8:nparam + 16] = 1.0   # feature standard deviations
+        blob[nparam + F:nparam + 2 * F] = 1.0   # feature standard deviations
         E.esg_predictor_set(gix, blob, 8, 32)
         a = E.esg_search_batch(gix, q, l, r, None, 10, ef=32, use_learned=1, want_stats=True)
         b = E.esg_search_batch(gix, q, l, r, None, 10, ef=32, want_stats=True)
