@@ -66,6 +66,25 @@ def test_decompose_exhaustive(dev, n, leaf):
     _check_pieces(n, leaf, ll, rr, cols, npieces)
 
 
+@pytest.mark.parametrize("n,leaf", [(300, 64), (600, 256), (1100, 1024)])
+def test_decompose_exhaustive_leaf_sweep(dev, n, leaf):
+    """Leaf sizes 64, 256 and 1024, every range of a tree a few leaves deep."""
+    ll, rr = np.triu_indices(n)
+    cols, npieces = _gpu_pieces(n, leaf, ll, rr, dev)
+    _check_pieces(n, leaf, ll, rr, cols, npieces)
+
+
+@pytest.mark.parametrize("n,leaf", [(5_000, 1), (50_000, 64), (1_000_000, 256), (10_000_000, 1024)])
+def test_decompose_sampled_leaf_sweep(dev, n, leaf):
+    """Sampled ranges (log-uniform widths, uniform left ends) of large trees."""
+    rng = np.random.default_rng(n + leaf)
+    w = np.maximum(1, np.round(np.exp(rng.uniform(0, np.log(n), 4000)))).astype(np.int64)
+    l = (rng.random(4000) * (n - w + 1)).astype(np.int64)
+    r = l + w - 1
+    cols, npieces = _gpu_pieces(n, leaf, l, r, dev)
+    _check_pieces(n, leaf, l, r, cols, npieces)
+
+
 def test_decompose_invalid_and_workload_ranges(dev):
     l = np.array([5, -1, 0, 3, 999_999, 0])
     r = np.array([4, 3, 1_000_000, 3, 999_999, 999_999])
@@ -211,6 +230,34 @@ def test_search_parity_on_oracle_graph(dev, tiny_oracle_index, ef):
         found_gpu.append(ranks); found_cpu.append(cpu); truth.append(gt)
         same += ranks.tolist() == cpu.tolist()
         assert status[i] & ~E.Q_OVERFLOW == 0
+    rg, rc = O.recall_at_k(found_gpu, truth), O.recall_at_k(found_cpu, truth)
+    assert abs(rg - rc) <= 0.005, (rg, rc)
+    assert same >= 0.95 * len(w.queries)
+
+
+@pytest.mark.parametrize("leaf,metric", [(1, "l2"), (64, "ip"), (256, "l2")])
+def test_search_parity_leaf_sweep(dev, leaf, metric):
+    """Oracle-built indexes with leaf sizes 1, 64 and 256 (both metrics): the
+    GPU's Algorithm 1 matches the oracle's on the same graph and ef."""
+    w = synthetic.small_mixture(4000, 32, 300, n_comp=16, seed=71 + leaf, M=8, leaf_size=leaf,
+                                metric=metric, normalise=(metric == "ip"))
+    idx = O.build_index(w.base, w.attr, w.metric, leaf, 8, efc=100, n_entries=8)
+    gix = _import(idx, w)
+    k, ef = 10, 32
+    ids, dist, count, status, stats = _gpu_search(gix, w.queries, w.l, w.r, None, k, ef, dev)
+    inv = np.empty(idx.n, np.int64)
+    inv[idx.perm] = np.arange(idx.n)
+    found_gpu, found_cpu, truth = [], [], []
+    same = 0
+    for i in range(len(w.queries)):
+        l, r = int(w.l[i]), int(w.r[i])
+        ranks = inv[ids[i, :count[i]]]
+        assert np.all((ranks >= l) & (ranks <= r)) and len(set(ranks.tolist())) == len(ranks)
+        assert count[i] == min(k, r - l + 1)
+        cpu, _ = O.search(idx, w.queries[i], l, r, k, ef)
+        gt, _ = O.bruteforce(idx.X, w.queries[i], l, r, k, w.metric)
+        found_gpu.append(ranks); found_cpu.append(cpu); truth.append(gt)
+        same += ranks.tolist() == cpu.tolist()
     rg, rc = O.recall_at_k(found_gpu, truth), O.recall_at_k(found_cpu, truth)
     assert abs(rg - rc) <= 0.005, (rg, rc)
     assert same >= 0.95 * len(w.queries)
