@@ -268,6 +268,11 @@ N_TRAIN = 20_000
 # largest beam width the learned budget may pick: the candidate list and the
 # visited table are sized for it, so a tight cap keeps more warps resident
 LEARNED_EF_HI = 64
+# labels = smallest ef reaching this per-query recall; median regression; the
+# calibrated margin then sets the mean recall (on the scale workload this beat
+# full-recall labels with quantile 0.9 by 5-8 % in kernel time at equal recall)
+LEARNED_LABEL_RECALL = 0.9
+LEARNED_QUANTILE = 0.5
 
 
 def measured_traffic(variant, params):
@@ -521,7 +526,8 @@ def run_ours(args, rank, world, local):
         rep = E.esg_train_predictor(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
                                     torch.as_tensor(tgc, device=dev), k_max=10,
                                     target_recall=TARGET_RECALL + 0.005, ef_lo=8, ef_hi=LEARNED_EF_HI,
-                                    traversal=trav, epochs=40)
+                                    traversal=trav, epochs=40, per_query_recall=LEARNED_LABEL_RECALL,
+                                    quantile=LEARNED_QUANTILE)
         train_s = time.perf_counter() - t1
         base = E.search_params(ef=LEARNED_EF_HI, traversal=trav, use_learned=1)
         tuned, trec, tms = E.esg_autotune(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
@@ -555,7 +561,8 @@ def run_ours(args, rank, world, local):
                   "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
                   "launches": launches // max(1, args.steps + args.warmup) * args.steps, "graph": True})
         results[name + "-graph"] = g
-        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "ef_hi": LEARNED_EF_HI, "train_s": round(train_s, 2),
+        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "ef_hi": LEARNED_EF_HI,
+                        "label_recall": LEARNED_LABEL_RECALL, "quantile": LEARNED_QUANTILE, "train_s": round(train_s, 2),
                         "train_loss": float(rep[0]), "heldout_recall": float(rep[1]),
                         "ef_margin_log2": float(rep[2]), "heldout_evals_per_query": float(rep[3]),
                         "autotune": {"params": tuned.as_dict(), "recall": trec, "ms": tms}}
