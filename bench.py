@@ -530,8 +530,9 @@ def run_ours(args, rank, world, local):
                                     quantile=LEARNED_QUANTILE)
         train_s = time.perf_counter() - t1
         base = E.search_params(ef=LEARNED_EF_HI, traversal=trav, use_learned=1)
-        tuned, trec, tms = E.esg_autotune(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
-                                          torch.as_tensor(tgc, device=dev), k_max=10,
+        # launch shape timed on training batches of the benchmark's batch size
+        tuned, trec, tms = E.esg_autotune(ix, TQ[:nq], TL[:nq], TR[:nq], torch.as_tensor(tgt[:nq], device=dev),
+                                          torch.as_tensor(tgc[:nq], device=dev), k_max=10,
                                           target_recall=TARGET_RECALL, base=base)
         name = f"learned-{trav}"
         results[name] = measure(name, tuned, trav)

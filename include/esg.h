@@ -303,7 +303,8 @@ void esg_batch_free(esg_batch *batch);
  * target_recall (hits among each query's first min(k_i, gt_count_i) exact ids,
  * summed, over the sum of min(k_i, gt_count_i); k_i = k[i], or k_max when k
  * is NULL), then the fastest launch shape (warps per block, visited-table
- * slots, lanes per row) by timing with CUDA events. `base` supplies the other
+ * slots, lanes per row) by timing with CUDA events (every shape best of
+ * three, then the six fastest best of eleven). `base` supplies the other
  * fields (traversal, rerank, ...). Writes the chosen parameters to `out` and,
  * if `report` is not NULL, [recall, milliseconds per search of the sample].
  * With base->use_learned = 1 and a trained predictor, ef is kept (the

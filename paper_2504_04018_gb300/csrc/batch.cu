@@ -223,9 +223,9 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
         rec = gt_total > 0 ? h / gt_total : 1.0;
         return ESG_OK;
     };
-    auto time_of = [&](const esg_search_params &pp, float &ms) -> esg_status {
+    auto time_of = [&](const esg_search_params &pp, float &ms, int reps) -> esg_status {
         float best = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
+        for (int rep = 0; rep < reps; ++rep) {
             cudaEventRecord(e0, stream);
             esg_status s2 = search(pp);
             if (s2 != ESG_OK) return s2;
@@ -280,10 +280,12 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
             if (rec >= target_recall) { found.push_back({pp, rec, 0.f}); break; }
         }
     }
-    // 2. fastest launch shape for each candidate
-    esg_search_params best{};
-    double best_rec = 0;
-    float best_ms = 1e30f;
+    // 2. fastest launch shape for each candidate: every shape timed once
+    //    (best of 3 after a warm-up run), then the few fastest re-timed with
+    //    more repetitions, since neighbouring shapes often differ by less
+    //    than the run-to-run spread of a single timing
+    struct Timed { esg_search_params p; double recall; float ms; };
+    std::vector<Timed> timed;
     for (auto &c : found) {
         if (st != ESG_OK) break;
         const int lprs[] = {0, 4, 8, 16, 32};
@@ -293,15 +295,24 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
                     esg_search_params pp = c.p;
                     pp.warps_per_block = wpb; pp.hash_slots = hs; pp.lanes_per_row = lpr;
                     float ms = 0.f;
-                    esg_status s2 = time_of(pp, ms);
+                    esg_status s2 = time_of(pp, ms, 4);
                     if (s2 == ESG_ERR_UNSUPPORTED) continue;   // shape not valid for this row
                     if (s2 != ESG_OK) { st = s2; break; }
-                    if (ms < best_ms) { best_ms = ms; best = pp; best_rec = c.recall; }
+                    timed.push_back({pp, c.recall, ms});
                 }
                 if (st != ESG_OK) break;
             }
             if (st != ESG_OK) break;
         }
+    }
+    std::sort(timed.begin(), timed.end(), [](const Timed &x, const Timed &y) { return x.ms < y.ms; });
+    esg_search_params best{};
+    double best_rec = 0;
+    float best_ms = 1e30f;
+    for (size_t i = 0; st == ESG_OK && i < std::min<size_t>(timed.size(), 6); ++i) {
+        float ms = 0.f;
+        st = time_of(timed[i].p, ms, 12);
+        if (st == ESG_OK && ms < best_ms) { best_ms = ms; best = timed[i].p; best_rec = timed[i].recall; }
     }
     if (st == ESG_OK && found.empty()) { esg_set_error("autotune: no setting reaches the target recall"); st = ESG_ERR_UNSUPPORTED; }
     if (st == ESG_OK) {
