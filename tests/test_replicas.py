@@ -88,3 +88,30 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_roofline_traffic_only_for_unchanged_kernel(tmp_path, monkeypatch):
+    """The bench reports the recorded DRAM traffic only for the captured
+    variant and search parameters, and only while the kernel sources hash to
+    the recorded value."""
+    import importlib
+    bench = importlib.import_module("bench")
+    rec = json.load(open(os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")))
+    name, r = next(iter(rec.items()))
+    params = dict(r["params"], max_expansions=0, rerank=1, warps_per_block=1, hash_slots=0,
+                  lanes_per_row=4)
+    assert bench.measured_traffic("some-other-variant", params) is None
+    assert bench.measured_traffic(name, dict(params, ef=params["ef"] + 1)) is None
+    # a copy of the tree whose kernel source differs by one byte
+    root = tmp_path / "tree"
+    for rel in r["kernel_sources"] + ["profiles/search_kernel_traffic.txt"]:
+        dst = root / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    same = bench.measured_traffic(name, params)
+    src = root / r["kernel_sources"][0]
+    src.write_bytes(src.read_bytes() + b"\n")
+    assert bench.measured_traffic(name, params) is None
+    if same is not None:
+        assert same == r["traffic_bytes_per_launch"]
