@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget variant")
+    ap.add_argument("--learned-trav", default="", choices=["", "f32", "bf16", "fp8"],
+                    help="row type of the learned variant (default: the fastest fixed-ef variant's)")
     ap.add_argument("--bf-workload", default="scale", choices=["scale", "learned"],
                     help="workload of --mode bruteforce: the 128-d scale mixture or the 768-d "
                          "anisotropic inner-product workload (its held-out queries)")
@@ -519,6 +521,8 @@ def run_ours(args, rank, world, local):
         mixed = {k: v for k, v in results.items() if k != "plain" and v["recall"] >= TARGET_RECALL
                  and v["params"]["width"] == 1}
         trav = results[max(mixed, key=lambda k: mixed[k]["qps"])]["trav"] if mixed else "f32"
+        if args.learned_trav:
+            trav = args.learned_trav
         tq, tl, tr = synthetic.training_queries(w, N_TRAIN, 1024, seed=4002)
         TQ, TL, TR = (torch.as_tensor(a, device=dev) for a in (tq, tl, tr))
         tgt, tgc = ground_truth(TQ, TL, TR)
