@@ -163,8 +163,9 @@ __global__ void rerank_certify_kernel(const float *X, const float *Q, int d, int
 // zero padding past the last row and dimension), so every stage is one bulk
 // copy on the TMA engine. Queries are sorted by (log2 of range width, l)
 // and grouped into tiles of 128; a query tile only visits the point tiles
-// that its queries' ranges cover, cut into work items of at most CH tiles
-// so that all SMs are busy. Each CTA is warp-specialised:
+// that its queries' ranges cover; the CTAs (one per SM) run contiguous
+// shares of that sequence of equal estimated cost, cut into work items at
+// query-tile boundaries. Each CTA is warp-specialised:
 //   warp 0      bulk copies: the item's query tile (resident), then a ring of
 //               S point-tile stages;
 //   warp 1      one thread issues the MMAs into one of two TMEM accumulators
@@ -277,6 +278,55 @@ __device__ __forceinline__ void pair_bar(int quarter) {   // the two warps of a 
 __device__ __forceinline__ bool dl_less(float da, int32_t ia, float db, int32_t ib) {
     return da < db || (da == db && ia < ib);
 }
+
+// One compare-exchange stage of a bitonic network over 64 (distance, index)
+// pairs, element e = lane + 32 h in (d[h], i[h]); pairs compare by dl_less.
+// Element e meets e ^ j; in a block of size kk that sorts ascending (up) the
+// lower position keeps the smaller pair. `desc` flips every direction.
+__device__ __forceinline__ void bitonic_stage(float (&d)[2], int32_t (&i)[2], int lane, int kk, int j, bool desc) {
+    if (j == 32) {   // partners in the same lane (only in the 64-wide block)
+        const bool sw = desc ? dl_less(d[0], i[0], d[1], i[1]) : dl_less(d[1], i[1], d[0], i[0]);
+        if (sw) {
+            const float td = d[0]; d[0] = d[1]; d[1] = td;
+            const int32_t ti = i[0]; i[0] = i[1]; i[1] = ti;
+        }
+        return;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float od = __shfl_xor_sync(0xffffffffu, d[h], j);
+        const int32_t oi = __shfl_xor_sync(0xffffffffu, i[h], j);
+        const bool up = (((lane + 32 * h) & kk) == 0) != desc;
+        const bool low = (lane & j) == 0;
+        const bool take = low == up ? dl_less(od, oi, d[h], i[h]) : dl_less(d[h], i[h], od, oi);
+        if (take) { d[h] = od; i[h] = oi; }
+    }
+}
+
+// Bitonic sort of the 64 pairs (ascending, or descending with `desc`).
+__device__ __forceinline__ void bitonic_sort64(float (&d)[2], int32_t (&i)[2], int lane, bool desc) {
+#pragma unroll
+    for (int kk = 2; kk <= 64; kk <<= 1)
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) bitonic_stage(d, i, lane, kk, j, desc);
+}
+
+// A sorted list (ascending) and 64 sorted candidates (descending), both padded
+// with (+inf, INT32_MAX): the element-wise smaller pairs are the 64 smallest of
+// the union as a bitonic sequence, which one merge pass sorts ascending.
+__device__ __forceinline__ void bitonic_merge_into(float (&ld)[2], int32_t (&li)[2], const float (&cd)[2],
+                                                   const int32_t (&ci)[2], int lane) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (dl_less(cd[h], ci[h], ld[h], li[h])) { ld[h] = cd[h]; li[h] = ci[h]; }
+#pragma unroll
+    for (int j = 32; j > 0; j >>= 1) bitonic_stage(ld, li, lane, 64, j, false);
+}
+
+// Candidates of one row and half tile from which the epilogue sorts and
+// merges them in one network instead of inserting them one at a time (a list
+// that is still filling: the first tile of a work item).
+constexpr int kBulkMin = 32;
 
 __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -549,6 +599,26 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                         int32_t li0 = lane < cnt ? L_i[r * K1 + lane] : 0x7FFFFFFF;
                         float ld1 = lane + 32 < cnt ? L_d[r * K1 + lane + 32] : INFINITY;
                         int32_t li1 = lane + 32 < cnt ? L_i[r * K1 + lane + 32] : 0x7FFFFFFF;
+                        const int nc = __popc(m0) + __popc(m1);
+                        if (nc >= kBulkMin) {
+                            // the K1 smallest of list and candidates in one
+                            // network: the same list as inserting one by one
+                            const bool in0 = (m0 >> lane) & 1u, in1 = (m1 >> lane) & 1u;
+                            float cd[2] = {in0 ? d0 : INFINITY, in1 ? d1 : INFINITY};
+                            int32_t ci[2] = {in0 ? p0 : 0x7FFFFFFF, in1 ? p1 : 0x7FFFFFFF};
+                            bitonic_sort64(cd, ci, lane, true);
+                            float ld[2] = {ld0, ld1};
+                            int32_t li[2] = {li0, li1};
+                            bitonic_merge_into(ld, li, cd, ci, lane);
+                            ld0 = ld[0]; li0 = li[0]; ld1 = ld[1]; li1 = li[1];
+                            cnt = min(K1, cnt + nc);
+                            if (cnt == K1) {
+                                const int e = K1 - 1;
+                                td = __shfl_sync(0xffffffffu, e < 32 ? ld0 : ld1, e & 31);
+                                ti = __shfl_sync(0xffffffffu, e < 32 ? li0 : li1, e & 31);
+                            }
+                            m0 = m1 = 0u;
+                        }
                         while ((m0 | m1) != 0u) {
                             const bool second = m0 == 0u;
                             const int src = __ffs(second ? m1 : m0) - 1;
@@ -842,6 +912,134 @@ static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n,
 
 // One pass of the pipelined kernel over a batch of queries against the
 // prepared points, then merge, re-rank, certificate and escalation.
+// Cuts the sequence of covered point tiles (query tile by query tile) into G
+// contiguous shares of about equal estimated epilogue cost. A tile costs a
+// fixed amount (TMEM load, filter, barriers) plus the insertions into the row
+// lists. A list starts empty at each work item: with the points in random
+// order with respect to the query, its first covered tile costs a fixed
+// amount (every column in range is a candidate) and the next m - 1 about
+// K1 ln m insertions in all, so a tile of a narrow-range query tile (lists
+// restarted every few tiles) costs several times one of a wide-range query
+// tile, and each cut inside a query tile restarts the lists of the queries
+// that span it. The
+// shares are chosen greedily (each CTA takes the remaining cost over the
+// remaining CTAs); a second pass adds the restart cost of the first pass's
+// later cuts to the remaining cost, and the pass with the smaller largest
+// share is kept. `lt`/`rt` are the first and last covered tile of each sorted
+// query; `cut` receives G + 1 positions.
+constexpr double kTileCost = 16.0;    // fixed cost of one tile, in insertions
+constexpr double kFirstTile = 160.0;  // a list's first covered tile, in insertions
+
+static void bf2_shares(const std::vector<int32_t> &tiles, const std::vector<int64_t> &qt_first,
+                       const std::vector<int32_t> &lt, const std::vector<int32_t> &rt, int64_t n, int K1,
+                       int64_t G, std::vector<int64_t> &cut) {
+    const int64_t T = (int64_t)tiles.size(), nqt = (int64_t)qt_first.size() - 1;
+    const int64_t nv = (int64_t)lt.size();
+    cut.assign(G + 1, T);
+    cut[0] = 0;
+    if (G <= 1 || nqt <= 0) return;
+    int32_t mmax = 1;   // longest covered span of a query, in tiles
+    for (int64_t s = 0; s < nv; ++s) mmax = std::max(mmax, rt[s] - lt[s] + 1);
+    std::vector<float> lnm((size_t)mmax + 1, 0.f);
+    for (size_t m = 1; m < lnm.size(); ++m) lnm[m] = std::log((float)m);
+    // estimated cost of tiles [t0, t1) of query tile qt, run as one item
+    auto cost = [&](int64_t qt, int64_t t0, int64_t t1) -> double {
+        if (t1 <= t0) return 0.0;
+        const int32_t a = tiles[t0], b = tiles[t1 - 1];
+        const int32_t *lq = lt.data() + qt * TM, *rq = rt.data() + qt * TM;
+        const int ns = (int)(std::min(nv, (qt + 1) * TM) - qt * TM);
+        int nover = 0;
+        float lsum = 0.f;
+        for (int s = 0; s < ns; ++s) {
+            const int32_t m = std::min(b, rq[s]) - std::max(a, lq[s]) + 1;
+            const bool ov = m >= 1;
+            nover += ov;
+            lsum += lnm[ov ? m : 0];
+        }
+        return kTileCost * (double)(t1 - t0) + kFirstTile * nover + (double)K1 * lsum;
+    };
+    std::vector<double> pre(nqt + 1, 0.0);   // prefix sums of whole query tiles
+    for (int64_t qt = 0; qt < nqt; ++qt) pre[qt + 1] = pre[qt] + cost(qt, qt_first[qt], qt_first[qt + 1]);
+    // about the largest e in [lo, hi] with f(e) = cost(qt, t0, e) <= budget,
+    // given f(lo) = flo <= budget < f(hi) = fhi: interpolation steps
+    // alternating with bisection, stopping within 1 % of the budget; f(e) in *fe
+    auto last_within = [&](int64_t qt, int64_t t0, int64_t lo, int64_t hi, double flo, double fhi, double budget,
+                           double *fe) {
+        for (int step = 0; hi - lo > 1 && fhi - flo > 1e-2 * budget; ++step) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (step % 2 == 0) mid = lo + (int64_t)((budget - flo) / (fhi - flo) * (double)(hi - lo));
+            mid = std::min(std::max(mid, lo + 1), hi - 1);
+            const double fm = cost(qt, t0, mid);
+            if (fm <= budget) { lo = mid; flo = fm; } else { hi = mid; fhi = fm; }
+        }
+        *fe = flo;
+        return lo;
+    };
+    // one greedy pass: CTA c takes about (remaining cost + later[c]) / (G - c);
+    // returns the largest share's cost, the heads (cost from each cut to the
+    // end of its query tile) in `head`
+    std::vector<double> head(G, 0.0);
+    auto greedy = [&](const std::vector<double> &later, std::vector<int64_t> &cu) {
+        cu.assign(G + 1, T);
+        cu[0] = 0;
+        int64_t t = 0, qt = 0;
+        double worst = 0.0;
+        for (int64_t c = 0; c < G; ++c) {
+            while (qt_first[qt + 1] <= t) ++qt;
+            const int64_t qend = qt_first[qt + 1];
+            const double h = t == qt_first[qt] ? pre[qt + 1] - pre[qt] : cost(qt, t, qend);
+            head[c] = h;
+            const double rest = h + pre[nqt] - pre[qt + 1];
+            if (c + 1 == G) { worst = std::max(worst, rest); break; }
+            const double target = (rest + later[c]) / (double)(G - c);
+            int64_t e;
+            double share;
+            if (h > target) {
+                e = last_within(qt, t, t, qend, 0.0, h, target, &share);
+            } else {
+                // the query tile the cut falls in, then the position inside it
+                const double rem = target - h;
+                const int64_t qe = std::upper_bound(pre.begin() + qt + 1, pre.end(), pre[qt + 1] + rem) - pre.begin() - 1;
+                if (qe >= nqt) {
+                    e = T;
+                    share = rest;
+                } else {
+                    double part = 0.0;
+                    e = last_within(qe, qt_first[qe], qt_first[qe], qt_first[qe + 1], 0.0, pre[qe + 1] - pre[qe],
+                                    rem - (pre[qe] - pre[qt + 1]), &part);
+                    share = h + (pre[qe] - pre[qt + 1]) + part;
+                }
+            }
+            if (e < t + 1 || e > T - (G - c - 1)) {
+                e = std::min(std::max(e, t + 1), T - (G - c - 1));
+                const int64_t qe = std::upper_bound(qt_first.begin(), qt_first.end(), e - 1) - qt_first.begin() - 1;
+                share = qe == qt ? cost(qt, t, e) : h + (pre[qe] - pre[qt + 1]) + cost(qe, qt_first[qe], e);
+            }
+            worst = std::max(worst, share);
+            cu[c + 1] = e;
+            t = e;
+        }
+        return worst;
+    };
+    std::vector<double> later(G, 0.0);
+    const double w0 = greedy(later, cut);
+    // restart cost of each cut of the first pass (the next share's head plus
+    // the query tile's cost up to the cut, minus the whole query tile),
+    // summed over the later cuts
+    for (int64_t c = G - 2; c >= 0; --c) {
+        const int64_t t = cut[c + 1];
+        double o = 0.0;
+        if (t < T) {
+            const int64_t qt = std::upper_bound(qt_first.begin(), qt_first.end(), t) - qt_first.begin() - 1;
+            if (t > qt_first[qt]) o = head[c + 1] + cost(qt, qt_first[qt], t) - (pre[qt + 1] - pre[qt]);
+        }
+        later[c] = later[c + 1] + o;
+    }
+    std::vector<int64_t> cut1;
+    const double w1 = greedy(later, cut1);
+    if (w1 < w0) cut.swap(cut1);
+}
+
 static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
                               const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
                               int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
@@ -890,9 +1088,9 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     }
     if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
     // the covered tiles of all query tiles in one sequence (query tile by query
-    // tile); CTA c runs the equal share [c T / G, (c + 1) T / G) of it, cut into
-    // work items at query-tile boundaries, so the CTAs get the same number of
-    // point tiles (items in query-tile order, each CTA's items contiguous)
+    // tile); CTA c runs the share [cut[c], cut[c + 1]) of it, shares of equal
+    // estimated cost, cut into work items at query-tile boundaries (items in
+    // query-tile order, each CTA's items contiguous)
     std::vector<int32_t> tiles;
     tiles.reserve(total_tiles);
     std::vector<int64_t> qt_first(nqt + 1, 0);
@@ -903,11 +1101,17 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     }
     qt_first[nqt] = (int64_t)tiles.size();
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(sms, total_tiles));
+    std::vector<int64_t> cut;
+    {
+        std::vector<int32_t> lt(nv), rt(nv);
+        for (int64_t s = 0; s < nv; ++s) { lt[s] = (int32_t)(hl[order[s]] / TN); rt[s] = (int32_t)(hr[order[s]] / TN); }
+        bf2_shares(tiles, qt_first, lt, rt, n, K1, G, cut);
+    }
     std::vector<WorkItem> items;
     std::vector<int32_t> item_begin(nqt + 1, 0), cta_first(G + 1, 0);
     for (int64_t c = 0; c < G; ++c) {
         cta_first[c] = (int32_t)items.size();
-        const int64_t t0 = c * total_tiles / G, t1 = (c + 1) * total_tiles / G;
+        const int64_t t0 = cut[c], t1 = cut[c + 1];
         int64_t t = t0;
         int64_t qt = std::upper_bound(qt_first.begin(), qt_first.end(), t0) - qt_first.begin() - 1;
         while (t < t1) {
@@ -922,7 +1126,8 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         while (i < (int64_t)items.size() && items[i].qtile < qt) ++i;
         item_begin[qt] = (int32_t)i;
     }
-    const int64_t CH = G > 0 ? (total_tiles + G - 1) / G : 0;
+    int64_t CH = 0;   // largest share
+    for (int64_t c = 0; c < G; ++c) CH = std::max(CH, cut[c + 1] - cut[c]);
     const int64_t n_items = (int64_t)items.size();
 
     // ---- query-side scratch
@@ -994,7 +1199,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
     const char *dbg = getenv("ESG_BF_STATS");
     if (dbg && *dbg == '1')
-        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items, %lld tiles per CTA, %d stages%s\n",
+        fprintf(stderr, "tensor-core brute force (pipelined): %lld query tiles, %lld point tiles, %lld items, largest share %lld tiles, %d stages%s\n",
                 (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S,
                 stream_a ? " (query tile streamed)" : "");
     std::vector<int64_t> left;
