@@ -70,22 +70,30 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  :: "r"(mbar) : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
+// 64 consecutive accumulator columns of the warp's 32 TMEM lanes (one
+// register each), waiting for the load inside the same asm statement so that
+// no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,"
+        "%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,"
+        "%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __global__ void max_kernel(const float *v, int64_t n, float *out) {
@@ -494,7 +502,16 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             dst[pt_i] = p0 < a.n ? __ldg(a.xnorm + p0) : 0.f;
             dst[pt_i + 64] = p1 < a.n ? __ldg(a.xnorm + p1) : 0.f;
         };
-        if (it_begin < it_end) load_norms(a.tiles[a.items[it_begin].off], s_xn + (quarter * 2) * TN);
+        // the CTA's items are consecutive pieces of the covered-tile sequence,
+        // so its tiles are one run a.tiles[g_beg, g_end): the index of the
+        // tile after next and the next tile's norms are fetched into
+        // registers a tile ahead of their use
+        const int32_t g_beg = it_begin < it_end ? a.items[it_begin].off : 0;
+        const int32_t g_end = it_begin < it_end ? a.items[it_end - 1].off + a.items[it_end - 1].cnt : 0;
+        int32_t g_cur = g_beg;
+        int32_t tile_cur = g_beg < g_end ? a.tiles[g_beg] : 0;
+        int32_t tile_nx = g_beg + 1 < g_end ? a.tiles[g_beg + 1] : -1;
+        if (g_beg < g_end) load_norms(tile_cur, s_xn + (quarter * 2) * TN);
         for (int it = it_begin; it < it_end; ++it) {
             const WorkItem I = a.items[it];
             if (I.qtile != cur_qt) {
@@ -515,54 +532,61 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                 cur_qt = I.qtile;
                 epi_bar();
             }
-            for (int j = 0; j < I.cnt; ++j) {
-                const int32_t pt = a.tiles[I.off + j] * TN;   // first point of the tile
+            for (int j = 0; j < I.cnt; ++j, ++g_cur) {
+                const int32_t pt = tile_cur * TN;   // first point of the tile
                 float *xs_cur = s_xn + (quarter * 2 + (tcount & 1u)) * TN;
-                // the next tile's norms into the pair's other buffer (its last
-                // readers finished before the previous tile's pair barriers)
-                {
-                    int32_t nt = -1;
-                    if (j + 1 < I.cnt) nt = a.tiles[I.off + j + 1];
-                    else if (it + 1 < it_end) nt = a.tiles[a.items[it + 1].off];
-                    if (nt >= 0) load_norms(nt, s_xn + (quarter * 2 + ((tcount + 1u) & 1u)) * TN);
+                // the next tile's norms (stored after the filter into the
+                // pair's other buffer, whose last readers finished before the
+                // previous tile's pair barriers) and the index after it
+                float *xs_nx = s_xn + (quarter * 2 + ((tcount + 1u) & 1u)) * TN;
+                float xn_a = 0.f, xn_b = 0.f;
+                if (l2 && tile_nx >= 0) {
+                    const int32_t p0 = tile_nx * TN + pt_i, p1 = p0 + 64;
+                    xn_a = p0 < a.n ? __ldg(a.xnorm + p0) : 0.f;
+                    xn_b = p1 < a.n ? __ldg(a.xnorm + p1) : 0.f;
                 }
+                const int32_t tile_nx2 = g_cur + 2 < g_end ? __ldg(a.tiles + g_cur + 2) : -1;
                 ++tcount;
                 const uint32_t b = acc_it & 1u;
                 wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err);
                 pe[b] ^= 1u;
                 ++acc_it;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // the row's range within this half tile; a warp none of whose
+                // 32 rows covers it skips the accumulator load and the filter
+                const int32_t pbm = pt + half * 64;
+                const int32_t lo = r_lo[my_row], hi = r_hi[my_row];
+                const int jl = lo - pbm > 0 ? lo - pbm : 0;
+                const int jh = hi - pbm < 63 ? hi - pbm : 63;
+                const uint64_t rng = jl <= jh ? ((~0ull >> (63 - (jh - jl))) << jl) : 0ull;
+                const bool warp_in = __any_sync(0xffffffffu, rng != 0ull);
                 float v[64];
-                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + b * TN + half * 64;
-                tmem_ld32(ta, v);
-                tmem_ld32(ta + 32, v + 32);
+                if (warp_in) tmem_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + b * TN + half * 64, v);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
                 // filter, one thread per row and half: distances of the 64
                 // columns, range mask, and the columns at or below the row's
                 // current K1-th distance (a superset of the insertions)
-                const int32_t pbm = pt + half * 64;
-                const int32_t lo = r_lo[my_row], hi = r_hi[my_row];
-                const float qn = r_qn[my_row], tdm = r_td[my_row];
-                const int jl = lo - pbm > 0 ? lo - pbm : 0;
-                const int jh = hi - pbm < 63 ? hi - pbm : 63;
-                const uint64_t rng = jl <= jh ? ((~0ull >> (63 - (jh - jl))) << jl) : 0ull;
                 uint64_t cand = 0ull;
-                const float4 *xv = (const float4 *)(xs_cur + half * 64);
+                if (warp_in) {
+                    const float qn = r_qn[my_row], tdm = r_td[my_row];
+                    const float4 *xv = (const float4 *)(xs_cur + half * 64);
 #pragma unroll
-                for (int c4 = 0; c4 < 16; ++c4) {
-                    const float4 x4 = xv[c4];
-                    const float xx[4] = {x4.x, x4.y, x4.z, x4.w};
+                    for (int c4 = 0; c4 < 16; ++c4) {
+                        const float4 x4 = xv[c4];
+                        const float xx[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = c4 * 4 + e;
-                        const float dd = l2 ? qn + xx[e] - 2.f * v[c] : -v[c];
-                        v[c] = dd;
-                        cand |= (uint64_t)(dd <= tdm) << c;
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = c4 * 4 + e;
+                            const float dd = l2 ? qn + xx[e] - 2.f * v[c] : -v[c];
+                            v[c] = dd;
+                            cand |= (uint64_t)(dd <= tdm) << c;
+                        }
                     }
+                    cand &= rng;
                 }
-                cand &= rng;
+                if (l2 && tile_nx >= 0) { xs_nx[pt_i] = xn_a; xs_nx[pt_i + 64] = xn_b; }
                 const bool fl = cand != 0ull;
                 const uint32_t wm = __ballot_sync(0xffffffffu, fl);
                 if (lane == 0) s_flag[half * 4 + quarter] = wm;
@@ -653,6 +677,8 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                     }
                     pair_bar(quarter);
                 }
+                tile_cur = tile_nx;
+                tile_nx = tile_nx2;
             }
             // write the lists out when this is the CTA's last item of the
             // query tile (a row's list then covers all of the tile's items
@@ -913,35 +939,32 @@ static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n,
 // One pass of the pipelined kernel over a batch of queries against the
 // prepared points, then merge, re-rank, certificate and escalation.
 // Cuts the sequence of covered point tiles (query tile by query tile) into G
-// contiguous shares of about equal estimated epilogue cost. A tile costs a
-// fixed amount (TMEM load, filter, barriers) plus the insertions into the row
-// lists. A list starts empty at each work item: with the points in random
-// order with respect to the query, its first covered tile costs a fixed
-// amount (every column in range is a candidate) and the next m - 1 about
-// K1 ln m insertions in all, so a tile of a narrow-range query tile (lists
-// restarted every few tiles) costs several times one of a wide-range query
-// tile, and each cut inside a query tile restarts the lists of the queries
-// that span it. The
-// shares are chosen greedily (each CTA takes the remaining cost over the
-// remaining CTAs); a second pass adds the restart cost of the first pass's
-// later cuts to the remaining cost, and the pass with the smaller largest
-// share is kept. `lt`/`rt` are the first and last covered tile of each sorted
-// query; `cut` receives G + 1 positions.
-constexpr double kTileCost = 16.0;    // fixed cost of one tile, in insertions
-constexpr double kFirstTile = 160.0;  // a list's first covered tile, in insertions
+// contiguous shares of about equal estimated cost. A share's cost is its
+// number of tiles plus `restart` for every (query, work item) pair in which
+// the query covers at least one of the item's tiles: a row list starts empty
+// at each item, and while it fills the epilogue inserts many candidates per
+// tile. Per-CTA clock counters at d = 128 (two 64-wide K chunks) put a list
+// start at about six tiles of MMA and filter time (the later insertions did
+// not improve the fit). The epilogue work does not grow with d while a tile's
+// MMA work does, and the longer MMA time per tile also hides more of the
+// burst: the weight 6.25 (2 / nk)^2 tiles fits the best measured weights at
+// d = 128 (6.25) and d = 768 (0 to 0.5, where equal shares are as good).
+// Each cut inside a query tile costs the restarts of the lists of the queries
+// that span it. The shares are chosen greedily (each
+// CTA takes the remaining cost over the remaining CTAs); a second pass adds
+// the restart cost of the first pass's later cuts to the remaining cost, and
+// the pass with the smaller largest share is kept. `lt`/`rt` are the first
+// and last covered tile of each sorted query; `cut` receives G + 1 positions.
+constexpr double kRestart2 = 6.25;   // one list start, in tiles, at two K chunks
 
 static void bf2_shares(const std::vector<int32_t> &tiles, const std::vector<int64_t> &qt_first,
-                       const std::vector<int32_t> &lt, const std::vector<int32_t> &rt, int64_t n, int K1,
-                       int64_t G, std::vector<int64_t> &cut) {
+                       const std::vector<int32_t> &lt, const std::vector<int32_t> &rt, int64_t G,
+                       double restart, std::vector<int64_t> &cut) {
     const int64_t T = (int64_t)tiles.size(), nqt = (int64_t)qt_first.size() - 1;
     const int64_t nv = (int64_t)lt.size();
     cut.assign(G + 1, T);
     cut[0] = 0;
     if (G <= 1 || nqt <= 0) return;
-    int32_t mmax = 1;   // longest covered span of a query, in tiles
-    for (int64_t s = 0; s < nv; ++s) mmax = std::max(mmax, rt[s] - lt[s] + 1);
-    std::vector<float> lnm((size_t)mmax + 1, 0.f);
-    for (size_t m = 1; m < lnm.size(); ++m) lnm[m] = std::log((float)m);
     // estimated cost of tiles [t0, t1) of query tile qt, run as one item
     auto cost = [&](int64_t qt, int64_t t0, int64_t t1) -> double {
         if (t1 <= t0) return 0.0;
@@ -949,14 +972,8 @@ static void bf2_shares(const std::vector<int32_t> &tiles, const std::vector<int6
         const int32_t *lq = lt.data() + qt * TM, *rq = rt.data() + qt * TM;
         const int ns = (int)(std::min(nv, (qt + 1) * TM) - qt * TM);
         int nover = 0;
-        float lsum = 0.f;
-        for (int s = 0; s < ns; ++s) {
-            const int32_t m = std::min(b, rq[s]) - std::max(a, lq[s]) + 1;
-            const bool ov = m >= 1;
-            nover += ov;
-            lsum += lnm[ov ? m : 0];
-        }
-        return kTileCost * (double)(t1 - t0) + kFirstTile * nover + (double)K1 * lsum;
+        for (int s = 0; s < ns; ++s) nover += rq[s] >= a && lq[s] <= b;
+        return (double)(t1 - t0) + restart * nover;
     };
     std::vector<double> pre(nqt + 1, 0.0);   // prefix sums of whole query tiles
     for (int64_t qt = 0; qt < nqt; ++qt) pre[qt + 1] = pre[qt] + cost(qt, qt_first[qt], qt_first[qt + 1]);
@@ -1071,6 +1088,15 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     });
     const int64_t nv = (int64_t)order.size();
     const int64_t nqt = (nv + TM - 1) / TM;
+    // the rows of each full query tile interleaved over the four TMEM lane
+    // quarters (sorted position s -> row (s mod 4) * 32 + s / 4): queries
+    // with nearby ranges take their insertions in the same point tiles, and
+    // an accumulator is free only when all four epilogue warp pairs are done
+    for (int64_t qt = 0; qt < nv / TM; ++qt) {
+        int32_t rows[TM];
+        for (int i = 0; i < TM; ++i) rows[(i & 3) * 32 + (i >> 2)] = order[qt * TM + i];
+        std::copy(rows, rows + TM, order.begin() + qt * TM);
+    }
     std::vector<std::vector<std::pair<int64_t, int64_t>>> spans(nqt);
     int64_t total_tiles = 0;
     for (int64_t qt = 0; qt < nqt; ++qt) {
@@ -1105,7 +1131,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     {
         std::vector<int32_t> lt(nv), rt(nv);
         for (int64_t s = 0; s < nv; ++s) { lt[s] = (int32_t)(hl[order[s]] / TN); rt[s] = (int32_t)(hr[order[s]] / TN); }
-        bf2_shares(tiles, qt_first, lt, rt, n, K1, G, cut);
+        bf2_shares(tiles, qt_first, lt, rt, G, kRestart2 * (2.0 / nk) * (2.0 / nk), cut);
     }
     std::vector<WorkItem> items;
     std::vector<int32_t> item_begin(nqt + 1, 0), cta_first(G + 1, 0);
