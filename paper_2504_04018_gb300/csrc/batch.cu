@@ -132,7 +132,9 @@ esg_status esg_batch_run(esg_batch *b, int64_t nq, esg_stream_t stream) {
         if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); return ESG_ERR_CUDA; }
         it = b->graphs.emplace(nq, exec).first;
     }
-    if (!fresh) esg_prof_count(3);   // a capture already counted its kernels
+    // a capture already counted its kernels: prep, order, search, merge, and
+    // the budget network with the learned budget
+    if (!fresh) esg_prof_count(4 + (b->p.use_learned && b->ix->mlp_ready ? 1 : 0));
     ESG_CUDA_TRY(cudaGraphLaunch(it->second, (cudaStream_t)stream));
     return ESG_OK;
 }

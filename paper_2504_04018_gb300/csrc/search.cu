@@ -53,6 +53,41 @@ __global__ void prep_kernel(int64_t n, int32_t leaf, const int64_t *l, const int
     qstatus[i] = (ok && cnt > 0) ? 0 : ESG_Q_INVALID;
 }
 
+// Processing order of the search items, longest first (one block, counting
+// sort over log-spaced cost buckets; the order within a bucket is arbitrary
+// and does not change any result). Estimated cost of an item: a graph piece
+// ~ ef (1 + log2 of its node size), a scan piece ~ its width / 64 rows, an
+// empty piece 0.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int order_bucket(const esg_piece &pc, int ef) {
+    float c = 0.f;
+    if (pc.kind == ESG_PIECE_GRAPH)
+        c = (float)ef * (1.f + log2f((float)(pc.node_r - pc.node_l + 1)));
+    else if (pc.kind == ESG_PIECE_SCAN)
+        c = (float)(pc.pr - pc.pl + 1) * (1.f / 64.f);
+    const int b = (int)(4.f * log2f(1.f + c));   // 4 buckets per doubling
+    return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+}
+
+__global__ void __launch_bounds__(kOrderThreads) order_items_kernel(const esg_piece *pieces, const int32_t *ef_q,
+                                                                    int ef, int64_t n_items, int32_t *order) {
+    __shared__ int32_t cnt[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n_items; i += kOrderThreads)
+        atomicAdd(&cnt[order_bucket(pieces[i], ef_q ? ef_q[i >> 1] : ef)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) { const int32_t c = cnt[b]; cnt[b] = run; run += c; }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n_items; i += kOrderThreads)
+        order[atomicAdd(&cnt[order_bucket(pieces[i], ef_q ? ef_q[i >> 1] : ef)], 1)] = (int32_t)i;
+}
+
 // Merge the (at most two) sorted piece lists of each query into its top k
 // (Algorithm 4, last step), map ranks to original ids, pad the rest.
 __global__ void merge_kernel(int64_t nq, int32_t k_max, const int32_t *kq, const Cand *res,
@@ -217,7 +252,7 @@ esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, 
 
 namespace {
 struct ScratchLayout {
-    size_t pieces, kq, qs, res, cnt, stats, hash, feat, efq, mxq, queue, total;
+    size_t pieces, kq, qs, res, cnt, stats, hash, feat, efq, mxq, order, queue, total;
 };
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -236,6 +271,7 @@ ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) 
     L.feat = off; off += plan.learned ? al256(sizeof(float) * nq * ESG_MLP_FEATURES) : 0;
     L.efq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
     L.mxq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
+    L.order = off; off += al256(sizeof(int32_t) * n_items);
     L.queue = off; off += 256;
     L.total = off;
     return L;
@@ -313,7 +349,13 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
         if (pst != ESG_OK) return pst;
         esg_prof_count(1);   // features + network, one kernel
     }
+    // items longest first: a warp that takes a long search late would
+    // leave the others idle at the end of the launch
+    int32_t *order = (int32_t *)(scratch + L.order);
+    order_items_kernel<<<1, kOrderThreads, 0, stream>>>(pieces, ef_q, plan.ef, n_items, order);
+    ESG_CUDA_TRY(cudaGetLastError());
     SearchArgs a;
+    a.order = order;
     a.ef_q = ef_q; a.maxexp_q = maxexp_q;
     a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
     a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
@@ -330,7 +372,7 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     const cudaError_t ce = cudaGetLastError();
     esg_prof_end(pidx, stream);
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
-    esg_prof_count(3);  // prep, search, merge
+    esg_prof_count(4);  // prep, order, search, merge
     merge_kernel<<<ceil_div_i(s.nq, 128), 128, 0, stream>>>(
         s.nq, s.k_max, kq, res, res_cnt, res_status, res_stats, qs, ix->perm, pieces,
         s.out_ids, s.out_dist, s.out_count, s.out_status, s.out_stats);

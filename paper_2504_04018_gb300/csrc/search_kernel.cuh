@@ -331,6 +331,7 @@ struct SearchArgs {
     uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
     int G;
     unsigned long long *queue;  // atomic work counter
+    const int32_t *order = nullptr;  // optional: the counter's k-th value runs item order[k]
     Cand *res;             // [n_items, k_max]
     int32_t *res_cnt;      // [n_items]
     int32_t *res_status;   // [n_items]
@@ -374,6 +375,7 @@ search_kernel(SearchArgs a) {
         if (lane == 0) item = (int64_t)atomicAdd(a.queue, 1ULL);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.n_items) break;
+        if (a.order) item = a.order[item];
         unsigned long long t_start;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int64_t qi = item >> a.qshift;
