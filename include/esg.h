@@ -405,6 +405,34 @@ esg_status esg_bruteforce_filtered_knn(const float *base, int64_t n, int32_t d, 
                                        float *out_dist, int32_t *out_count, esg_stream_t stream);
 
 /*
+ * Host work plan of the tensor-core path of esg_bruteforce_filtered_knn
+ * (library-specific, no counterpart in the paper; for inspection and tests,
+ * no GPU work). The valid queries (0 <= l <= r < n) are sorted by
+ * (floor(log2(r - l + 1)), l, index) and tiled by 128; within each full query
+ * tile, sorted position s goes to row (s mod 4) * 32 + s / 4. Each query tile
+ * lists the 128-point tiles its ranges cover (ascending); these lists, query
+ * tile by query tile, form one sequence of covered tiles, cut into `ctas`
+ * contiguous shares (fewer when there are fewer covered tiles) of about equal
+ * estimated cost: tiles + 6.25 (2 / ceil(d / 64))^2 per (query, work item)
+ * pair in which the query covers one of the item's tiles; a share is split
+ * into work items at query-tile boundaries.
+ *  n, d       points and dimension of the search (d sets the cost weight);
+ *  l, r       host [nq] int64 inclusive ranges;
+ *  ctas       CTAs to plan for (the kernel uses one per SM);
+ *  sizes      host [4] out: valid queries V, covered tiles T, work items I, CTAs G;
+ *  order      host [V] out or NULL: query index at sorted-and-interleaved position;
+ *  tiles      host [T] out or NULL: the covered point tiles;
+ *  items      host [I, 4] out or NULL: (query tile, first position in tiles,
+ *             count, 0), in sequence order;
+ *  cta_first  host [G + 1] out or NULL: CTA c runs items [cta_first[c], cta_first[c + 1]).
+ * Call with NULL arrays to learn the sizes. ESG_ERR_UNSUPPORTED past 2^31
+ * covered tiles.
+ */
+esg_status esg_bruteforce_plan(int64_t n, int32_t d, const int64_t *l, const int64_t *r, int64_t nq,
+                               int32_t ctas, int64_t *sizes, int32_t *order, int32_t *tiles,
+                               int32_t *items, int32_t *cta_first);
+
+/*
  * Map attribute value ranges [lo, hi] to inclusive rank ranges [l, r] on the
  * host (binary search over the sorted attributes). A value range holding no
  * point yields l = r + 1. Host pointers, [nq] each.

@@ -18,7 +18,7 @@ from . import _build_lib
 
 __all__ = [
     "load_library", "Index", "esg_build", "esg_index_import", "esg_index_export", "esg_free",
-    "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
+    "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn", "esg_bruteforce_plan",
     "esg_attr_to_rank_range", "esg_save", "esg_load", "EsgError", "METRIC", "STORAGE",
     "PIECE_GRAPH", "PIECE_SCAN", "Q_INVALID", "Q_TRUNCATED", "Q_OVERFLOW",
 ]
@@ -31,7 +31,7 @@ Q_INVALID, Q_TRUNCATED, Q_OVERFLOW = 1, 2, 4
 EXPORTED = [
     "esg_build_params_default", "esg_search_params_default", "esg_build", "esg_index_import",
     "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
-    "esg_bruteforce_filtered_knn", "esg_attr_to_rank_range", "esg_save", "esg_load",
+    "esg_bruteforce_filtered_knn", "esg_bruteforce_plan", "esg_attr_to_rank_range", "esg_save", "esg_load",
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read", "esg_profile_tensor_work",
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
@@ -104,6 +104,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_bruteforce_filtered_knn.argtypes = [_P, _I64, _I32, _I32, _P, _I64, _P, _P, _I32, _P, _P,
                                                 _P, _P]
     lib.esg_attr_to_rank_range.argtypes = [_P, _P, _P, _I64, _P, _P]
+    lib.esg_bruteforce_plan.argtypes = [_I64, _I32, _P, _P, _I64, _I32, _P, _P, _P, _P, _P]
     lib.esg_save.argtypes = [_P, ctypes.c_char_p]
     lib.esg_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(_P)]
     lib.esg_profile_enable.argtypes = [_I32]
@@ -364,6 +365,24 @@ def esg_attr_to_rank_range(index: Index, lo: np.ndarray, hi: np.ndarray):
     _check(lib.esg_attr_to_rank_range(index.handle, _np_ptr(lo), _np_ptr(hi), lo.shape[0],
                                       _np_ptr(l), _np_ptr(r)), "esg_attr_to_rank_range")
     return l, r
+
+
+def esg_bruteforce_plan(n: int, d: int, l: np.ndarray, r: np.ndarray, ctas: int = 152):
+    """Host work plan of the tensor-core exact search (no GPU work): returns
+    (order [V], tiles [T], items [I, 4], cta_first [G + 1]) as int32 arrays."""
+    lib = load_library()
+    l = np.ascontiguousarray(l, dtype=np.int64)
+    r = np.ascontiguousarray(r, dtype=np.int64)
+    sizes = np.zeros(4, dtype=np.int64)
+    args = (n, d, _np_ptr(l), _np_ptr(r), l.shape[0], ctas)
+    _check(lib.esg_bruteforce_plan(*args, _np_ptr(sizes), None, None, None, None), "esg_bruteforce_plan")
+    order = np.empty(sizes[0], dtype=np.int32)
+    tiles = np.empty(sizes[1], dtype=np.int32)
+    items = np.empty((sizes[2], 4), dtype=np.int32)
+    cta_first = np.empty(sizes[3] + 1, dtype=np.int32)
+    _check(lib.esg_bruteforce_plan(*args, _np_ptr(sizes), _np_ptr(order), _np_ptr(tiles), _np_ptr(items),
+                                   _np_ptr(cta_first)), "esg_bruteforce_plan")
+    return order, tiles, items, cta_first
 
 
 def esg_save(index: Index, path: str):

@@ -950,12 +950,13 @@ static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n,
 // burst: the weight 6.25 (2 / nk)^2 tiles fits the best measured weights at
 // d = 128 (6.25) and d = 768 (0 to 0.5, where equal shares are as good).
 // Each cut inside a query tile costs the restarts of the lists of the queries
-// that span it. The shares are chosen greedily (each
-// CTA takes the remaining cost over the remaining CTAs); a second pass adds
-// the restart cost of the first pass's later cuts to the remaining cost, and
-// the pass with the smaller largest share is kept. `lt`/`rt` are the first
-// and last covered tile of each sorted query; `cut` receives G + 1 positions.
+// that span it. The shares are chosen greedily: each CTA takes about the
+// remaining cost over the remaining CTAs; every later pass adds the restart
+// cost of the previous pass's later cuts to the remaining cost, and the pass
+// with the smallest largest share is kept. `lt`/`rt` are the first and last
+// covered tile of each sorted query; `cut` receives G + 1 positions.
 constexpr double kRestart2 = 6.25;   // one list start, in tiles, at two K chunks
+constexpr int kSharePasses = 2;      // greedy passes (the first without restart look-ahead)
 
 static void bf2_shares(const std::vector<int32_t> &tiles, const std::vector<int64_t> &qt_first,
                        const std::vector<int32_t> &lt, const std::vector<int32_t> &rt, int64_t G,
@@ -1039,43 +1040,48 @@ static void bf2_shares(const std::vector<int32_t> &tiles, const std::vector<int6
         return worst;
     };
     std::vector<double> later(G, 0.0);
-    const double w0 = greedy(later, cut);
-    // restart cost of each cut of the first pass (the next share's head plus
-    // the query tile's cost up to the cut, minus the whole query tile),
-    // summed over the later cuts
-    for (int64_t c = G - 2; c >= 0; --c) {
-        const int64_t t = cut[c + 1];
-        double o = 0.0;
-        if (t < T) {
-            const int64_t qt = std::upper_bound(qt_first.begin(), qt_first.end(), t) - qt_first.begin() - 1;
-            if (t > qt_first[qt]) o = head[c + 1] + cost(qt, qt_first[qt], t) - (pre[qt + 1] - pre[qt]);
+    std::vector<int64_t> cur, nxt;
+    double best = greedy(later, cur);
+    cut = cur;
+    for (int pass = 1; pass < kSharePasses; ++pass) {
+        // restart cost of each cut of the previous pass (the next share's head
+        // plus the query tile's cost up to the cut, minus the whole query
+        // tile), summed over the later cuts
+        for (int64_t c = G - 2; c >= 0; --c) {
+            const int64_t t = cur[c + 1];
+            double o = 0.0;
+            if (t < T) {
+                const int64_t qt = std::upper_bound(qt_first.begin(), qt_first.end(), t) - qt_first.begin() - 1;
+                if (t > qt_first[qt]) o = head[c + 1] + cost(qt, qt_first[qt], t) - (pre[qt + 1] - pre[qt]);
+            }
+            later[c] = later[c + 1] + o;
         }
-        later[c] = later[c + 1] + o;
+        const double w = greedy(later, nxt);
+        if (w < best) { best = w; cut = nxt; }
+        cur.swap(nxt);
     }
-    std::vector<int64_t> cut1;
-    const double w1 = greedy(later, cut1);
-    if (w1 < w0) cut.swap(cut1);
 }
 
-static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
-                              const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
-                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
-    if (nq == 0) return ESG_OK;
-    const int nk = (d + TK - 1) / TK;
-    int dev = 0, max_smem = 0, sms = 0, S = 0, stream_a = 0;
-    size_t smem = 0;
-    ESG_CUDA_TRY(cudaGetDevice(&dev));
-    ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+// Host work plan of the pipelined kernel for the valid queries of host
+// ranges hl/hr over n points at dimension d, for `sms` CTAs: queries sorted
+// by (log2 width, l, index) and tiled by 128, the rows of each full query tile
+// interleaved over the four TMEM lane quarters, the point tiles each query
+// tile covers in one sequence, cut into `G` shares (bf2_shares) and into work
+// items at query-tile boundaries. ESG_ERR_UNSUPPORTED past 2^31 covered tiles.
+struct Bf2Plan {
+    std::vector<int32_t> order;        // sorted position -> caller's query index (valid queries)
+    std::vector<int32_t> tiles;        // covered point tiles, query tile by query tile
+    std::vector<int64_t> qt_first;     // [nqt + 1] first position of each query tile in `tiles`
+    std::vector<WorkItem> items;       // in query-tile order, each CTA's items contiguous
+    std::vector<int32_t> item_begin;   // [nqt + 1] first item of each query tile
+    std::vector<int32_t> cta_first;    // [G + 1] first item of each CTA
+    int64_t nv = 0, nqt = 0, total_tiles = 0, G = 0, largest = 0;
+};
 
-    // ---- host plan: sort queries by (log2 width, l), tile them, list the
-    // point tiles each query tile covers and cut the lists into work items
-    std::vector<int64_t> hl(nq), hr(nq);
-    ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
-    ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
-    ESG_CUDA_TRY(cudaStreamSynchronize(stream));
-    std::vector<int32_t> order;
+static esg_status bf2_plan(const int64_t *hl, const int64_t *hr, int64_t nq, int64_t n, int32_t d, int64_t sms,
+                           Bf2Plan &P) {
+    std::vector<int32_t> &order = P.order;
+    order.clear();
     order.reserve(nq);
     for (int64_t i = 0; i < nq; ++i)
         if (hl[i] >= 0 && hl[i] <= hr[i] && hr[i] < n) order.push_back((int32_t)i);
@@ -1088,6 +1094,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     });
     const int64_t nv = (int64_t)order.size();
     const int64_t nqt = (nv + TM - 1) / TM;
+    const int nk = (d + TK - 1) / TK;
     // the rows of each full query tile interleaved over the four TMEM lane
     // quarters (sorted position s -> row (s mod 4) * 32 + s / 4): queries
     // with nearby ranges take their insertions in the same point tiles, and
@@ -1117,9 +1124,11 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     // tile); CTA c runs the share [cut[c], cut[c + 1]) of it, shares of equal
     // estimated cost, cut into work items at query-tile boundaries (items in
     // query-tile order, each CTA's items contiguous)
-    std::vector<int32_t> tiles;
+    std::vector<int32_t> &tiles = P.tiles;
+    tiles.clear();
     tiles.reserve(total_tiles);
-    std::vector<int64_t> qt_first(nqt + 1, 0);
+    std::vector<int64_t> &qt_first = P.qt_first;
+    qt_first.assign(nqt + 1, 0);
     for (int64_t qt = 0; qt < nqt; ++qt) {
         qt_first[qt] = (int64_t)tiles.size();
         for (auto &x : spans[qt])
@@ -1133,8 +1142,11 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         for (int64_t s = 0; s < nv; ++s) { lt[s] = (int32_t)(hl[order[s]] / TN); rt[s] = (int32_t)(hr[order[s]] / TN); }
         bf2_shares(tiles, qt_first, lt, rt, G, kRestart2 * (2.0 / nk) * (2.0 / nk), cut);
     }
-    std::vector<WorkItem> items;
-    std::vector<int32_t> item_begin(nqt + 1, 0), cta_first(G + 1, 0);
+    std::vector<WorkItem> &items = P.items;
+    items.clear();
+    std::vector<int32_t> &item_begin = P.item_begin, &cta_first = P.cta_first;
+    item_begin.assign(nqt + 1, 0);
+    cta_first.assign(G + 1, 0);
     for (int64_t c = 0; c < G; ++c) {
         cta_first[c] = (int32_t)items.size();
         const int64_t t0 = cut[c], t1 = cut[c + 1];
@@ -1152,8 +1164,39 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
         while (i < (int64_t)items.size() && items[i].qtile < qt) ++i;
         item_begin[qt] = (int32_t)i;
     }
-    int64_t CH = 0;   // largest share
-    for (int64_t c = 0; c < G; ++c) CH = std::max(CH, cut[c + 1] - cut[c]);
+    P.largest = 0;
+    for (int64_t c = 0; c < G; ++c) P.largest = std::max(P.largest, cut[c + 1] - cut[c]);
+    P.nv = nv;
+    P.nqt = nqt;
+    P.total_tiles = total_tiles;
+    P.G = G;
+    return ESG_OK;
+}
+
+static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
+                              const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
+                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
+    if (nq == 0) return ESG_OK;
+    const int nk = (d + TK - 1) / TK;
+    int dev = 0, max_smem = 0, sms = 0, S = 0, stream_a = 0;
+    size_t smem = 0;
+    ESG_CUDA_TRY(cudaGetDevice(&dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+
+    // ---- host plan
+    std::vector<int64_t> hl(nq), hr(nq);
+    ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaStreamSynchronize(stream));
+    Bf2Plan P;
+    const esg_status pst = bf2_plan(hl.data(), hr.data(), nq, n, d, sms, P);
+    if (pst != ESG_OK) return pst;
+    const std::vector<int32_t> &order = P.order, &tiles = P.tiles, &item_begin = P.item_begin,
+                               &cta_first = P.cta_first;
+    const std::vector<WorkItem> &items = P.items;
+    const int64_t nv = P.nv, nqt = P.nqt, total_tiles = P.total_tiles, G = P.G, CH = P.largest;
     const int64_t n_items = (int64_t)items.size();
 
     // ---- query-side scratch
@@ -1289,4 +1332,38 @@ esg_status esg_bruteforce_tc(const float *base, int64_t n, int32_t d, int metric
                              int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
                              float *out_dist, int32_t *out_count, cudaStream_t stream) {
     return bruteforce_tc_v2(base, n, d, metric, queries, nq, l, r, k, out_ids, out_dist, out_count, stream);
+}
+
+esg_status esg_bruteforce_plan(int64_t n, int32_t d, const int64_t *l, const int64_t *r, int64_t nq,
+                               int32_t ctas, int64_t *sizes, int32_t *order, int32_t *tiles, int32_t *items,
+                               int32_t *cta_first) {
+    if (n < 1 || n >= ((int64_t)1 << 31) - 1 || d < 1 || nq < 0 || nq >= ((int64_t)1 << 31) || ctas < 1 ||
+        !sizes || (nq > 0 && (!l || !r))) {
+        esg_set_error("esg_bruteforce_plan: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    Bf2Plan P;
+    esg_status st = ESG_OK;
+    try {
+        st = bf2_plan(l, r, nq, n, d, ctas, P);
+    } catch (...) { st = ESG_ERR_OOM; }
+    if (st != ESG_OK) {
+        if (st == ESG_ERR_UNSUPPORTED) esg_set_error("esg_bruteforce_plan: more than 2^31 covered point tiles");
+        return st;
+    }
+    sizes[0] = P.nv;
+    sizes[1] = P.total_tiles;
+    sizes[2] = (int64_t)P.items.size();
+    sizes[3] = P.G;
+    if (order) std::copy(P.order.begin(), P.order.end(), order);
+    if (tiles) std::copy(P.tiles.begin(), P.tiles.end(), tiles);
+    if (items)
+        for (size_t i = 0; i < P.items.size(); ++i) {
+            items[4 * i] = P.items[i].qtile;
+            items[4 * i + 1] = P.items[i].off;
+            items[4 * i + 2] = P.items[i].cnt;
+            items[4 * i + 3] = 0;
+        }
+    if (cta_first) std::copy(P.cta_first.begin(), P.cta_first.end(), cta_first);
+    return ESG_OK;
 }
