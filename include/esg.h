@@ -241,7 +241,9 @@ esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, c
  *              traversal rows, out-of-range evaluations, FP32 re-rank rows,
  *              pieces, device latency in ns from the first of the query's
  *              pieces being taken by a warp to the last one finished,
- *              read from %globaltimer) or NULL.
+ *              read from %globaltimer; the items of a batch run longest
+ *              estimated search first, so a query's two pieces may run far
+ *              apart within the launch) or NULL.
  * Asynchronous on `stream`; temporary device memory is taken from and
  * returned to the stream-ordered allocator of that stream.
  */
