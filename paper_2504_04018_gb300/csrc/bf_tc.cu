@@ -1080,21 +1080,50 @@ struct Bf2Plan {
 
 static esg_status bf2_plan(const int64_t *hl, const int64_t *hr, int64_t nq, int64_t n, int32_t d, int64_t sms,
                            Bf2Plan &P) {
-    std::vector<int32_t> &order = P.order;
-    order.clear();
-    order.reserve(nq);
+    // sort key floor(log2 width) << 40 | l (l < 2^31), ties by query index:
+    // a stable LSD radix sort by bytes of the key over the valid queries in
+    // index order
+    struct Key { uint64_t k; int32_t i; };
+    std::vector<Key> keys, tmp;
+    keys.reserve(nq);
+    uint64_t kmax = 0;
     for (int64_t i = 0; i < nq; ++i)
-        if (hl[i] >= 0 && hl[i] <= hr[i] && hr[i] < n) order.push_back((int32_t)i);
-    auto wbits = [&](int32_t i) { return 63 - __builtin_clzll((unsigned long long)(hr[i] - hl[i] + 1)); };
-    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        const int wa = wbits(a), wb = wbits(b);
-        if (wa != wb) return wa < wb;
-        if (hl[a] != hl[b]) return hl[a] < hl[b];
-        return a < b;
-    });
+        if (hl[i] >= 0 && hl[i] <= hr[i] && hr[i] < n) {
+            const uint64_t wb = 63 - __builtin_clzll((unsigned long long)(hr[i] - hl[i] + 1));
+            keys.push_back(Key{(wb << 40) | (uint64_t)hl[i], (int32_t)i});
+            kmax = std::max(kmax, keys.back().k);
+        }
+    tmp.resize(keys.size());
+    for (int sh = 0; sh < 64 && (kmax >> sh) != 0; sh += 8) {
+        size_t cnt[257] = {0};
+        for (const Key &x : keys) ++cnt[((x.k >> sh) & 255) + 1];
+        for (int b = 0; b < 256; ++b) cnt[b + 1] += cnt[b];
+        for (const Key &x : keys) tmp[cnt[(x.k >> sh) & 255]++] = x;
+        keys.swap(tmp);
+    }
+    std::vector<int32_t> &order = P.order;
+    order.resize(keys.size());
+    for (size_t s = 0; s < keys.size(); ++s) order[s] = keys[s].i;
     const int64_t nv = (int64_t)order.size();
     const int64_t nqt = (nv + TM - 1) / TM;
     const int nk = (d + TK - 1) / TK;
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> spans(nqt);
+    int64_t total_tiles = 0;
+    std::vector<std::pair<int64_t, int64_t>> iv;
+    iv.reserve(TM);
+    for (int64_t qt = 0; qt < nqt; ++qt) {
+        iv.clear();
+        for (int64_t s = qt * TM; s < std::min(nv, (qt + 1) * TM); ++s)
+            iv.push_back({hl[order[s]] / TN, hr[order[s]] / TN});
+        if (!std::is_sorted(iv.begin(), iv.end())) std::sort(iv.begin(), iv.end());
+        for (auto &x : iv) {
+            if (!spans[qt].empty() && x.first <= spans[qt].back().second + 1)
+                spans[qt].back().second = std::max(spans[qt].back().second, x.second);
+            else
+                spans[qt].push_back(x);
+        }
+        for (auto &x : spans[qt]) total_tiles += x.second - x.first + 1;
+    }
     // the rows of each full query tile interleaved over the four TMEM lane
     // quarters (sorted position s -> row (s mod 4) * 32 + s / 4): queries
     // with nearby ranges take their insertions in the same point tiles, and
@@ -1104,37 +1133,22 @@ static esg_status bf2_plan(const int64_t *hl, const int64_t *hr, int64_t nq, int
         for (int i = 0; i < TM; ++i) rows[(i & 3) * 32 + (i >> 2)] = order[qt * TM + i];
         std::copy(rows, rows + TM, order.begin() + qt * TM);
     }
-    std::vector<std::vector<std::pair<int64_t, int64_t>>> spans(nqt);
-    int64_t total_tiles = 0;
-    for (int64_t qt = 0; qt < nqt; ++qt) {
-        std::vector<std::pair<int64_t, int64_t>> iv;
-        for (int64_t s = qt * TM; s < std::min(nv, (qt + 1) * TM); ++s)
-            iv.push_back({hl[order[s]] / TN, hr[order[s]] / TN});
-        std::sort(iv.begin(), iv.end());
-        for (auto &x : iv) {
-            if (!spans[qt].empty() && x.first <= spans[qt].back().second + 1)
-                spans[qt].back().second = std::max(spans[qt].back().second, x.second);
-            else
-                spans[qt].push_back(x);
-        }
-        for (auto &x : spans[qt]) total_tiles += x.second - x.first + 1;
-    }
     if (total_tiles >= ((int64_t)1 << 31)) return ESG_ERR_UNSUPPORTED;
     // the covered tiles of all query tiles in one sequence (query tile by query
     // tile); CTA c runs the share [cut[c], cut[c + 1]) of it, shares of equal
     // estimated cost, cut into work items at query-tile boundaries (items in
     // query-tile order, each CTA's items contiguous)
     std::vector<int32_t> &tiles = P.tiles;
-    tiles.clear();
-    tiles.reserve(total_tiles);
+    tiles.resize(total_tiles);
     std::vector<int64_t> &qt_first = P.qt_first;
     qt_first.assign(nqt + 1, 0);
+    int64_t pos = 0;
     for (int64_t qt = 0; qt < nqt; ++qt) {
-        qt_first[qt] = (int64_t)tiles.size();
+        qt_first[qt] = pos;
         for (auto &x : spans[qt])
-            for (int64_t t = x.first; t <= x.second; ++t) tiles.push_back((int32_t)t);
+            for (int64_t t = x.first; t <= x.second; ++t) tiles[pos++] = (int32_t)t;
     }
-    qt_first[nqt] = (int64_t)tiles.size();
+    qt_first[nqt] = pos;
     const int64_t G = std::max<int64_t>(1, std::min<int64_t>(sms, total_tiles));
     std::vector<int64_t> cut;
     {
