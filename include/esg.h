@@ -228,6 +228,9 @@ esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, c
 /*
  * Range-filtered approximate k-NN search (Algorithm 4 with Algorithm 1 +
  * POST on each graph piece, exact scan of leaf pieces, merge).
+ *  nq          0 .. 2^30 - 1 queries (this bound holds for every batched
+ *              search entry point: esg_search_batch_noalloc, max_nq of
+ *              esg_batch_create, esg_autotune, esg_train_predictor);
  *  queries     device [nq, d] float32;
  *  l, r        device [nq] int64 inclusive rank ranges;
  *  k           device [nq] int32 per-query k (1..k_max), or NULL for k_max;
@@ -282,8 +285,8 @@ esg_status esg_search_batch_noalloc(const esg_index *index, const float *queries
  * up to max_nq queries (inputs: queries [max_nq, d] f32, l, r [max_nq] int64,
  * k [max_nq] int32; outputs as in esg_search_batch, stats [max_nq, 6]) and the
  * search's scratch memory, all allocated at creation. esg_batch_run(nq)
- * replays the whole search (decomposition, persistent beam-search kernel over
- * an atomic queue of (query, piece) items, merge) for the first nq entries
+ * replays the whole search (decomposition, item order, persistent beam-search
+ * kernel over an atomic queue of (query, piece) items, merge) for the first nq entries
  * with a single cudaGraphLaunch on `stream`; the graph for a given nq is
  * captured on first use (on a private stream) and cached. The k buffer is
  * used only when use_k != 0. Runs on one batch must not overlap.

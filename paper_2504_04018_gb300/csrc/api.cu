@@ -304,7 +304,7 @@ esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t n
                             const esg_search_params *params, int64_t *out_ids, float *out_dist,
                             int32_t *out_count, int32_t *out_status, int64_t *out_stats,
                             esg_stream_t stream) {
-    if (!ix || nq < 0 || k_max < 1 || k_max > 1024 ||
+    if (!ix || nq < 0 || nq >= kMaxBatch || k_max < 1 || k_max > 1024 ||
         (nq > 0 && (!queries || !l || !r || !out_ids || !out_dist || !out_count))) {
         esg_set_error("esg_search_batch: bad argument");
         return ESG_ERR_INVALID_ARG;

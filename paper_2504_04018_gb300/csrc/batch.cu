@@ -51,7 +51,7 @@ esg_status esg_batch_create(const esg_index *ix, int64_t max_nq, int32_t k_max, 
                             const esg_search_params *params, esg_batch **out) {
     if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
     *out = nullptr;
-    if (!ix || max_nq < 1 || k_max < 1 || k_max > 1024) {
+    if (!ix || max_nq < 1 || max_nq >= kMaxBatch || k_max < 1 || k_max > 1024) {
         esg_set_error("esg_batch_create: bad argument");
         return ESG_ERR_INVALID_ARG;
     }
@@ -181,7 +181,7 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
                                    int32_t k_max, const int64_t *gt_ids, const int32_t *gt_count,
                                    float target_recall, const esg_search_params *base,
                                    esg_search_params *out, float *report, esg_stream_t stream_v) {
-    if (!ix || !queries || nq < 1 || !l || !r || k_max < 1 || k_max > 1024 || !gt_ids || !gt_count ||
+    if (!ix || !queries || nq < 1 || nq >= kMaxBatch || !l || !r || k_max < 1 || k_max > 1024 || !gt_ids || !gt_count ||
         !out || !(target_recall > 0.f && target_recall <= 1.f)) {
         esg_set_error("esg_autotune: bad argument");
         return ESG_ERR_INVALID_ARG;

@@ -17,6 +17,10 @@
 #define ESG_ITEM_STATS 6
 // per-query statistics returned by esg_search_batch (see esg.h)
 #define ESG_QUERY_STATS 6
+
+// Largest search batch: the (query, piece) items of a batch (two per query)
+// are numbered with int32 in the processing order.
+constexpr int64_t kMaxBatch = (int64_t)1 << 30;
 #define ESG_EXPANDED 0x80000000u
 #define ESG_ID_MASK 0x7FFFFFFFu
 

@@ -53,7 +53,7 @@ extern "C" esg_status esg_search_batch_noalloc(const esg_index *ix, const float 
                                                int64_t *out_ids, float *out_dist, int32_t *out_count,
                                                int32_t *out_status, int64_t *out_stats,
                                                esg_stream_t stream) {
-    if (!ix || nq < 0 || k_max < 1 || k_max > 1024 ||
+    if (!ix || nq < 0 || nq >= kMaxBatch || k_max < 1 || k_max > 1024 ||
         (nq > 0 && (!queries || !l || !r || !out_ids || !out_dist || !out_count))) {
         esg_set_error("esg_search_batch_noalloc: bad argument");
         return ESG_ERR_INVALID_ARG;

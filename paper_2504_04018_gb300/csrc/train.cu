@@ -51,7 +51,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
                                           int32_t k_max, const int64_t *gt_ids, const int32_t *gt_count,
                                           const esg_train_params *tp_in, float *report,
                                           esg_stream_t stream_v) {
-    if (!ix || !queries || nq < 16 || !l || !r || k_max < 1 || k_max > 1024 || !gt_ids || !gt_count) {
+    if (!ix || !queries || nq < 16 || nq >= kMaxBatch || !l || !r || k_max < 1 || k_max > 1024 || !gt_ids || !gt_count) {
         esg_set_error("esg_train_predictor: bad argument");
         return ESG_ERR_INVALID_ARG;
     }
