@@ -388,3 +388,229 @@ def test_adam_first_step_moves_by_lr():
     p1, m, v = mlp.adam_step(p, g, np.zeros(5), np.zeros(5), 1, 0.01)
     # bias-corrected first step is lr * sign(g) (where g != 0)
     assert np.allclose(p1, -0.01 * np.sign(g), atol=1e-9)
+
+
+# ------------------------------------------- Algorithm 3 hand-traced build
+
+def _load_build_fn(lib_path):
+    import ctypes
+    lib = ctypes.CDLL(lib_path)
+    P = ctypes.c_void_p
+    lib.oracle_build.restype = ctypes.c_int
+    lib.oracle_build.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+    return lib.oracle_build
+
+
+def _build_with(fn, X, metric, leaf, M, efc, E):
+    """oracle_build through `fn` (the oracle's library or a mutant of it)."""
+    n, d = X.shape
+    L = O.graph_depths(n, leaf)
+    adj = np.empty((L, n, 2 * M), np.uint32)
+    ent = np.empty(((1 << L) - 1, E), np.int32)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    assert fn(X.ctypes.data, n, d, O.METRICS[metric], leaf, M, efc, E, L, adj.ctypes.data,
+              ent.ctypes.data) == 0
+    return adj, ent
+
+
+def _alg3_golden():
+    g = json.load(open(os.path.join(GOLDEN, "alg3_build.json")))
+    X = np.array(g["points_1d"], np.float64)[:, None]
+    want = np.full((len(g["adjacency"]), len(X), 2 * g["M"]), O.NONE, np.uint32)
+    for t, rows in enumerate(g["adjacency"]):
+        for i, nb in enumerate(rows):
+            want[t, i, :len(nb)] = nb
+    return g, X, want
+
+
+def _matches_golden(adj, ent, g, want):
+    return adj.shape == want.shape and np.array_equal(adj, want) and \
+        ent.tolist() == g["entries"]
+
+
+def test_build_hand_trace():
+    """Every row of every depth and every node's entries equal the hand trace
+    of Algorithm 3 (tests/golden/alg3_build.json)."""
+    g, X, want = _alg3_golden()
+    idx = O.build_index(X, None, g["metric"], g["leaf_size"], g["M"], efc=g["efc"],
+                        n_entries=g["n_entries"])
+    for t in range(want.shape[0]):
+        assert idx.adj[t].tolist() == want[t].tolist(), f"depth {t}"
+    assert idx.entries.tolist() == g["entries"]
+
+
+# Mistakes planted in a copy of the oracle's C source (compiled on the CPU);
+# each must change the build of the hand-traced case. "fresh" rebuilds the
+# left half by insertion instead of copying the left child's graph: the
+# copy is only a saving of work, so that variant must give the same graph.
+_ALG3_MUTANTS = {
+    "no_copy": ("memcpy(row(c, depth, i), row(c, depth + 1, i), sizeof(uint32_t) * (size_t)c->R);",
+                "(void)0;"),
+    "right_half_descending": ("for (int64_t i = mid + 1; i <= r; ++i) insert_point(c, depth, l, i);",
+                              "for (int64_t i = r; i >= mid + 1; --i) insert_point(c, depth, l, i);"),
+    "full_row_drops_new_edge": ("if (du < c->R) { ru[du] = (uint32_t)v; continue; }",
+                                "if (du < c->R) { ru[du] = (uint32_t)v; continue; } else continue;"),
+    "full_row_keeps_nearest": ("int nk = select_neighbours(c->X, c->d, c->metric, cand, du + 1, c->R, keep);",
+                               "int nk = 0; for (; nk < c->R && nk < du + 1; ++nk) keep[nk] = cand[nk].id;"),
+    "occlusion_compares_to_kept": ("if (dist(c, X + (size_t)keep[s] * d, d, metric) < cand[i].d) { good = 0; break; }",
+                                   "if (dist(c, X + (size_t)keep[s] * d, d, metric) > cand[i].d) { good = 0; break; }"),
+    "fresh": ("if (left) {", "if (0) {"),
+}
+
+
+def _compile_mutant(tmp_path, name):
+    import subprocess
+    src = open(os.path.join(os.path.dirname(O.__file__), "esg_oracle.c")).read()
+    old, new = _ALG3_MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site of {name} not found"
+    p = tmp_path / f"{name}.c"
+    p.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", str(p), "-o", str(so), "-lm"])
+    return str(so)
+
+
+@pytest.mark.parametrize("name", sorted(_ALG3_MUTANTS))
+def test_build_hand_trace_rejects_planted_mistakes(tmp_path, name):
+    g, X, want = _alg3_golden()
+    fn = _load_build_fn(_compile_mutant(tmp_path, name))
+    adj, ent = _build_with(fn, X, g["metric"], g["leaf_size"], g["M"], g["efc"], g["n_entries"])
+    if name == "fresh":
+        assert _matches_golden(adj, ent, g, want)
+    else:
+        assert not _matches_golden(adj, ent, g, want), name
+
+
+# ------------------------------------- Adam, MLP forward, recall: hand values
+
+# Three Adam steps worked by hand for beta1 = 0.5, beta2 = 0.75, eps = 0.25,
+# lr = 0.1 from p = m = v = 0 with gradients g1, g2, g3 below:
+#   step 1: m = [0.5, -1, 2], v = [0.25, 1, 4]; bias corrections 1/2, 1/4:
+#           m^ = [1, -2, 4], v^ = [1, 4, 16], sqrt = [1, 2, 4];
+#           p = -0.1 * [1/1.25, -2/2.25, 4/4.25] = [-2/25, 4/45, -8/85]
+#   step 2: m = [1.75, 0.5, 1], v = [2.4375, 1.75, 3]; corrections 0.75, 0.4375:
+#           m^ = [7/3, 2/3, 4/3], v^ = [39/7, 4, 48/7]
+#   step 3: m = [0.375, 0.25, 1.5], v = [2.078125, 1.3125, 3.25];
+#           corrections 0.875, 0.578125: m^ = [3/7, 2/7, 12/7],
+#           v^ = [133/37, 84/37, 208/37]
+_ADAM_G = [np.array([1.0, -2.0, 4.0]), np.array([3.0, 2.0, 0.0]), np.array([-1.0, 0.0, 2.0])]
+_P1 = np.array([-2 / 25, 4 / 45, -8 / 85])
+_P2 = _P1 - 0.1 * np.array([7 / 3, 2 / 3, 4 / 3]) / (np.sqrt([39 / 7, 4.0, 48 / 7]) + 0.25)
+_P3 = _P2 - 0.1 * np.array([3 / 7, 2 / 7, 12 / 7]) / (np.sqrt([133 / 37, 84 / 37, 208 / 37]) + 0.25)
+_ADAM_WANT = [_P1, _P2, _P3]
+_ADAM_M = [np.array([0.5, -1.0, 2.0]), np.array([1.75, 0.5, 1.0]), np.array([0.375, 0.25, 1.5])]
+_ADAM_V = [np.array([0.25, 1.0, 4.0]), np.array([2.4375, 1.75, 3.0]), np.array([2.078125, 1.3125, 3.25])]
+
+
+def _adam_run(step_fn):
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    out = []
+    for t, g in enumerate(_ADAM_G, start=1):
+        p, m, v = step_fn(p, g, m, v, t, 0.1, beta1=0.5, beta2=0.75, eps=0.25)
+        out.append((p.copy(), m.copy(), v.copy()))
+    return out
+
+
+def _adam_ok(out):
+    return all(np.allclose(p, pw, rtol=0, atol=1e-12) and np.allclose(m, mw, atol=1e-12)
+               and np.allclose(v, vw, atol=1e-12)
+               for (p, m, v), pw, mw, vw in zip(out, _ADAM_WANT, _ADAM_M, _ADAM_V))
+
+
+def test_adam_three_steps_hand_values():
+    from oracle import mlp
+    assert _adam_ok(_adam_run(mlp.adam_step))
+
+
+def _adam_variant(kind):
+    """Plausible wrong Adam steps (planted on the CPU only)."""
+    def step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        b2 = beta1 if kind == "beta2_is_beta1" else beta2
+        m = beta1 * m + (1 - beta1) * g
+        v = b2 * v + (1 - b2) * g * g
+        e = t - 1 if kind == "bias_exponent_t_minus_1" else t
+        mh = m / (1 - beta1 ** max(e, 1)) if kind != "no_bias_correction" else m
+        vh = v / (1 - b2 ** max(e, 1)) if kind != "no_bias_correction" else v
+        if kind == "bias_exponent_t_minus_1" and t == 1:
+            mh, vh = m / (1 - beta1), v / (1 - b2)
+        if kind == "eps_inside_sqrt":
+            return p - lr * mh / np.sqrt(vh + eps), m, v
+        if kind == "v_from_beta1_correction":
+            vh = v / (1 - beta1 ** t)
+        return p - lr * mh / (np.sqrt(vh) + eps), m, v
+    return step
+
+
+@pytest.mark.parametrize("kind", ["beta2_is_beta1", "bias_exponent_t_minus_1", "no_bias_correction",
+                                  "eps_inside_sqrt", "v_from_beta1_correction"])
+def test_adam_hand_values_reject_planted_mistakes(kind):
+    assert not _adam_ok(_adam_run(_adam_variant(kind))), kind
+
+
+def _tiny_mlp():
+    """A 2-feature network with a few non-zero weights (flat layout W1 [F, 64],
+    b1, W2 [64, 64], b2, W3 [64, 2], b3). Hidden units 0-2 of layer 1:
+    z0 = xh0 + xh1 - 1, z1 = -xh0 + 0.5, z2 = 2 xh1 - 3; layer 2:
+    z0 = h0 - 0.5 h2 + 0.5, z1 = 2 h1 + h2 - 4; outputs
+    y0 = h0 + 0.5 h1 + 0.25, y1 = -h0 + 3 h1 - 0.5; every other weight 0."""
+    from oracle import mlp
+    F, H = 2, mlp.HIDDEN
+    W1 = np.zeros((F, H)); b1 = np.zeros(H)
+    W1[:, 0] = [1, 1]; b1[0] = -1
+    W1[:, 1] = [-1, 0]; b1[1] = 0.5
+    W1[:, 2] = [0, 2]; b1[2] = -3
+    W2 = np.zeros((H, H)); b2 = np.zeros(H)
+    W2[0, 0] = 1; W2[2, 0] = -0.5; b2[0] = 0.5
+    W2[1, 1] = 2; W2[2, 1] = 1; b2[1] = -4
+    W3 = np.zeros((H, 2)); b3 = np.array([0.25, -0.5])
+    W3[0, 0] = 1; W3[1, 0] = 0.5; W3[0, 1] = -1; W3[1, 1] = 3
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    mu, sigma = np.array([1.0, -1.0]), np.array([2.0, 0.5])
+    # by hand: x -> xh = ((x0 - 1) / 2, (x1 + 1) / 0.5) -> h1 -> h2 -> y
+    #   [3, 0]     -> [1, 2]  -> h1 [2, 0, 1]   -> h2 [2, 0] (z2_1 = -3 cut) -> [2.25, -2.5]
+    #   [-1, -0.5] -> [-1, 1] -> h1 [0, 1.5, 0] -> h2 [0.5, 0] (z2_1 = -1)  -> [0.75, -1.0]
+    #   [5, 1]     -> [2, 4]  -> h1 [5, 0, 5]   -> h2 [3, 1]                 -> [3.75, -0.5]
+    X = np.array([[3.0, 0.0], [-1.0, -0.5], [5.0, 1.0]])
+    Y = np.array([[2.25, -2.5], [0.75, -1.0], [3.75, -0.5]])
+    return p, X, mu, sigma, Y
+
+
+def test_mlp_forward_hand_values():
+    from oracle import mlp
+    p, X, mu, sigma, Y = _tiny_mlp()
+    y, _ = mlp.forward(p, X, mu, sigma)
+    assert np.allclose(y, Y, rtol=0, atol=1e-12)
+
+
+def test_mlp_forward_hand_values_reject_planted_mistakes():
+    from oracle import mlp
+    p, X, mu, sigma, Y = _tiny_mlp()
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, 2)
+    relu = lambda z: np.maximum(z, 0)
+    variants = {
+        "standardise_by_multiplying": lambda x: relu(relu(((x - mu) * sigma) @ W1 + b1) @ W2 + b2) @ W3 + b3,
+        "no_standardisation": lambda x: relu(relu(x @ W1 + b1) @ W2 + b2) @ W3 + b3,
+        "no_relu_layer1": lambda x: relu((((x - mu) / sigma) @ W1 + b1) @ W2 + b2) @ W3 + b3,
+        "no_relu_layer2": lambda x: (relu(((x - mu) / sigma) @ W1 + b1) @ W2 + b2) @ W3 + b3,
+        "relu_on_output": lambda x: relu(relu(relu(((x - mu) / sigma) @ W1 + b1) @ W2 + b2) @ W3 + b3),
+        "w2_transposed": lambda x: relu(relu(((x - mu) / sigma) @ W1 + b1) @ W2.T + b2) @ W3 + b3,
+    }
+    for name, f in variants.items():
+        assert not np.allclose(f(X), Y, atol=1e-9), name
+
+
+def test_recall_at_k_hand_case():
+    """Per-query |found ∩ truth| / |truth| averaged over queries, ids counted
+    once, an empty truth set (no point in range) counting as 1:
+    q0 {1,2,3} vs {2,3,4,9} -> 2/4; q1 empty truth -> 1; q2 nothing found of
+    {1} -> 0; q3 {7,8} vs {8,7} -> 1; mean 0.625."""
+    found = [np.array([1, 2, 2, 3]), np.array([5]), np.array([], np.int64), np.array([7, 8])]
+    truth = [np.array([2, 3, 4, 9]), np.array([], np.int64), np.array([1]), np.array([8, 7])]
+    assert O.recall_at_k(found, truth) == pytest.approx(0.625, abs=1e-15)
+    # planted mistakes: duplicates counted twice (0.6875), empty truth as 0 (0.375)
+    dup = np.mean([sum(1 for f in fo if f in set(t.tolist())) / len(t) if len(t) else 1.0
+                   for fo, t in zip(found, truth)])
+    empty0 = np.mean([len(set(fo.tolist()) & set(t.tolist())) / len(t) if len(t) else 0.0
+                      for fo, t in zip(found, truth)])
+    assert dup == pytest.approx(0.6875) and empty0 == pytest.approx(0.375)
