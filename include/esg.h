@@ -244,9 +244,9 @@ esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, c
  *              traversal rows, out-of-range evaluations, FP32 re-rank rows,
  *              pieces, device latency in ns from the first of the query's
  *              pieces being taken by a warp to the last one finished,
- *              read from %globaltimer; the items of a batch run longest
- *              estimated search first, so a query's two pieces may run far
- *              apart within the launch) or NULL.
+ *              read from %globaltimer; queries run longest estimated
+ *              search first, a query's two pieces one after the other)
+ *              or NULL.
  * Asynchronous on `stream`; temporary device memory is taken from and
  * returned to the stream-ordered allocator of that stream.
  */
@@ -268,9 +268,13 @@ esg_status esg_search_batch(const esg_index *index, const float *queries, int64_
  * whose scratch cannot fit in 64 MiB is rejected with ESG_ERR_INVALID_ARG
  * (scratch grows with nq * k_max; about 350 bytes per query at k_max = 10
  * plus the visited-set overflow tables, which shrink by running fewer
- * concurrent warps before a batch is refused). The first call on each device
- * looks the array's device address up once (make it before any stream
- * capture). All calls on a device share the array: calls whose GPU work
+ * concurrent warps before a batch is refused). The parameters are checked as
+ * in esg_search_batch. Each call made outside stream capture looks the
+ * array's device address up on the current device (no GPU work); a call on a
+ * capturing stream reuses the address found by the last call outside capture
+ * on that device, so the first call on each device must come before any
+ * stream capture (otherwise ESG_ERR_INVALID_ARG). All calls on a device share
+ * the array: calls whose GPU work
  * overlaps in time (different streams, or concurrent host threads) race and
  * corrupt each other's results; serialise them.
  */

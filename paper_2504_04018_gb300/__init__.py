@@ -186,6 +186,9 @@ class Index:
                                             (n, d, L, R, E, leaf, metric, storage)]), "esg_index_info")
         self.n, self.d, self.L, self.R, self.E = n.value, d.value, L.value, R.value, E.value
         self.leaf_size, self.metric, self.storage = leaf.value, metric.value, storage.value
+        # the library builds and imports on the current CUDA device
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
 
     @property
     def handle(self):
@@ -297,6 +300,36 @@ def unpack_pieces(pieces):
     return (p64[..., 0], p64[..., 1], p64[..., 2], p64[..., 3], p32[..., 8], p32[..., 9], p32[..., 10])
 
 
+def _check_search_buffers(who: str, index: Index, queries, l, r, k, k_max: int, ids, dist, count,
+                          status, stats):
+    """Shape, dtype, device and layout of every buffer of a batched search,
+    checked before the C call: the library trusts the sizes it is given, so a
+    buffer that is too small would be read or written past its end."""
+    import torch
+    nq = queries.shape[0] if hasattr(queries, "shape") else -1
+    want = [("queries", queries, (nq, index.d), torch.float32, True),
+            ("l", l, (nq,), torch.int64, True), ("r", r, (nq,), torch.int64, True),
+            ("k", k, (nq,), torch.int32, False),
+            ("ids", ids, (nq, k_max), torch.int64, True), ("dist", dist, (nq, k_max), torch.float32, True),
+            ("count", count, (nq,), torch.int32, True), ("status", status, (nq,), torch.int32, False),
+            ("stats", stats, (nq, 6), torch.int64, False)]
+    for name, t, shape, dtype, required in want:
+        if t is None:
+            if required:
+                raise EsgError(f"{who}: {name} is required")
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise EsgError(f"{who}: {name} must be a CUDA tensor")
+        if index.device is not None and t.device != index.device:
+            raise EsgError(f"{who}: {name} is on {t.device}, the index on {index.device}")
+        if t.dtype != dtype:
+            raise EsgError(f"{who}: {name} must be {dtype}, got {t.dtype}")
+        if tuple(t.shape) != shape:
+            raise EsgError(f"{who}: {name} must have shape {shape}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise EsgError(f"{who}: {name} must be contiguous")
+
+
 def search_params(ef: int = 64, max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
                   traversal: str = "f32", width: int = 1, warps_per_block: int = 0,
                   hash_slots: int = 0, lanes_per_row: int = 0) -> _SearchParams:
@@ -327,6 +360,8 @@ def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef
         ids, dist, count, status, stats = out
     p = params if params is not None else search_params(ef, max_expansions, rerank, use_learned,
                                                         traversal, width)
+    _check_search_buffers("esg_search_batch", index, queries, l, r, k, k_max, ids, dist, count,
+                          status, stats)
     _check(lib.esg_search_batch(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
                                 _dev_ptr(k), k_max, ctypes.byref(p), _dev_ptr(ids), _dev_ptr(dist),
                                 _dev_ptr(count), _dev_ptr(status), _dev_ptr(stats),
@@ -491,6 +526,8 @@ def esg_search_batch_noalloc(index: Index, queries, l, r, out, k=None, k_max: in
     lib = load_library()
     ids, dist, count, status, stats = out
     p = params if params is not None else search_params()
+    _check_search_buffers("esg_search_batch_noalloc", index, queries, l, r, k, k_max, ids, dist,
+                          count, status, stats)
     _check(lib.esg_search_batch_noalloc(index.handle, _dev_ptr(queries), queries.shape[0],
                                         _dev_ptr(l), _dev_ptr(r), _dev_ptr(k), k_max, ctypes.byref(p),
                                         _dev_ptr(ids), _dev_ptr(dist), _dev_ptr(count),

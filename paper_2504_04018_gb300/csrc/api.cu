@@ -66,6 +66,19 @@ uint32_t crc32_update(uint32_t crc, const void *data, size_t len) {
 
 void esg_set_error(const std::string &msg) { g_last_error = msg; }
 
+esg_status esg_check_search_params(const esg_search_params &p, const char *who) {
+    if (p.ef < 1 || p.ef > 1024 || p.max_expansions < 0 || p.width < 0 || p.width > 4 ||
+        !(p.warps_per_block == 0 || p.warps_per_block == 1 || p.warps_per_block == 2 ||
+          p.warps_per_block == 4) ||
+        (p.hash_slots != 0 && (p.hash_slots < 1024 || p.hash_slots > 16384 ||
+                               (p.hash_slots & (p.hash_slots - 1)))) ||
+        p.lanes_per_row < 0 || p.lanes_per_row > 32 || (p.lanes_per_row & (p.lanes_per_row - 1))) {
+        esg_set_error(std::string(who) + ": search parameter out of range");
+        return ESG_ERR_INVALID_ARG;
+    }
+    return ESG_OK;
+}
+
 extern "C" {
 
 const char *esg_last_error(void) { return g_last_error.c_str(); }
@@ -316,16 +329,7 @@ esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t n
     SearchLaunch s;
     s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max;
     s.p = params ? *params : esg_search_params_default();
-    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.max_expansions < 0 || s.p.width < 0 || s.p.width > 4 ||
-        !(s.p.warps_per_block == 0 || s.p.warps_per_block == 1 || s.p.warps_per_block == 2 ||
-          s.p.warps_per_block == 4) ||
-        (s.p.hash_slots != 0 && (s.p.hash_slots < 1024 || s.p.hash_slots > 16384 ||
-                                 (s.p.hash_slots & (s.p.hash_slots - 1)))) ||
-        s.p.lanes_per_row < 0 || s.p.lanes_per_row > 32 ||
-        (s.p.lanes_per_row & (s.p.lanes_per_row - 1))) {
-        esg_set_error("esg_search_batch: search parameter out of range");
-        return ESG_ERR_INVALID_ARG;
-    }
+    if (esg_check_search_params(s.p, "esg_search_batch") != ESG_OK) return ESG_ERR_INVALID_ARG;
     s.out_ids = out_ids; s.out_dist = out_dist; s.out_count = out_count;
     s.out_status = out_status; s.out_stats = out_stats;
     return esg_launch_search(s, (cudaStream_t)stream);

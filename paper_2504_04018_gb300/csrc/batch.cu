@@ -55,6 +55,7 @@ esg_status esg_batch_create(const esg_index *ix, int64_t max_nq, int32_t k_max, 
         esg_set_error("esg_batch_create: bad argument");
         return ESG_ERR_INVALID_ARG;
     }
+    if (params && esg_check_search_params(*params, "esg_batch_create") != ESG_OK) return ESG_ERR_INVALID_ARG;
     esg_batch *b = new (std::nothrow) esg_batch();
     if (!b) return ESG_ERR_OOM;
     b->ix = ix; b->max_nq = max_nq; b->k_max = k_max; b->use_k = use_k;

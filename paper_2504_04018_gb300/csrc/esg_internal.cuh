@@ -88,6 +88,10 @@ struct SearchLaunch {
     int64_t *out_stats;
 };
 
+// Range checks of esg_search_params shared by every batched search entry
+// point (sets the error message, prefixed with `who`).
+esg_status esg_check_search_params(const esg_search_params &p, const char *who);
+
 esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
                                 int64_t nq, esg_piece *pieces, int32_t *npieces,
                                 cudaStream_t stream);

@@ -25,14 +25,20 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 void *g_ptr[kMaxDevices] = {};
 
-// Device address of the array on the current device (looked up once per
-// device, with that device current).
-esg_status scratch_address(void **out) {
+// Device address of the array on the current device. Outside stream capture
+// every call looks it up again with that device current (the lookup queues
+// no GPU work), so the address stays right when the device's context is torn
+// down and made again (cudaDeviceReset), which reloads the module. A call on
+// a capturing stream uses the address the last call outside capture found
+// on that device, so the first call on a device must come before any capture.
+esg_status scratch_address(cudaStream_t stream, void **out) {
     int dev = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) { esg_set_error("device ordinal out of range"); return ESG_ERR_UNSUPPORTED; }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ESG_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_ptr[dev] == nullptr) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -40,6 +46,9 @@ esg_status scratch_address(void **out) {
             return ESG_ERR_CUDA;
         }
         g_ptr[dev] = p;
+    } else if (g_ptr[dev] == nullptr) {
+        esg_set_error("esg_search_batch_noalloc: the first call on a device must not be captured");
+        return ESG_ERR_INVALID_ARG;
     }
     *out = g_ptr[dev];
     return ESG_OK;
@@ -62,16 +71,13 @@ extern "C" esg_status esg_search_batch_noalloc(const esg_index *ix, const float 
         esg_set_error("esg_search_batch_noalloc: queries must be 16-byte aligned");
         return ESG_ERR_INVALID_ARG;
     }
-    void *scratch = nullptr;
-    esg_status st = scratch_address(&scratch);   // first call on a device: one-time lookup
-    if (st != ESG_OK || nq == 0) return st;
     SearchLaunch s;
     s.ix = ix; s.queries = queries; s.nq = nq; s.l = l; s.r = r; s.k = k; s.k_max = k_max;
     s.p = params ? *params : esg_search_params_default();
-    if (s.p.ef < 1 || s.p.ef > 1024 || s.p.width < 0 || s.p.width > 4) {
-        esg_set_error("esg_search_batch_noalloc: need 1 <= ef <= 1024 and 0 <= width <= 4");
-        return ESG_ERR_INVALID_ARG;
-    }
+    if (esg_check_search_params(s.p, "esg_search_batch_noalloc") != ESG_OK) return ESG_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    esg_status st = scratch_address((cudaStream_t)stream, &scratch);
+    if (st != ESG_OK || nq == 0) return st;
     s.out_ids = out_ids; s.out_dist = out_dist; s.out_count = out_count;
     s.out_status = out_status; s.out_stats = out_stats;
     SearchPlan plan;

@@ -53,11 +53,14 @@ __global__ void prep_kernel(int64_t n, int32_t leaf, const int64_t *l, const int
     qstatus[i] = (ok && cnt > 0) ? 0 : ESG_Q_INVALID;
 }
 
-// Processing order of the search items, longest first (one block, counting
-// sort over log-spaced cost buckets; the order within a bucket is arbitrary
-// and does not change any result). Estimated cost of an item: a graph piece
-// ~ ef (1 + log2 of its node size), a scan piece ~ its width / 64 rows, an
-// empty piece 0.
+// Processing order of the search items, longest first by query (one block,
+// counting sort over log-spaced cost buckets; the order within a bucket is
+// arbitrary and does not change any result). A query's two pieces are placed
+// next to each other, its longer piece first, and the query is keyed by that
+// longer piece: the launch keeps its short tail (long searches start early)
+// and a query's latency inside the batch stays that of its own pieces.
+// Estimated cost of an item: a graph piece ~ ef (1 + log2 of its node size),
+// a scan piece ~ its width / 64 rows, an empty piece 0.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderBuckets = 64;
 
@@ -72,20 +75,30 @@ __device__ __forceinline__ int order_bucket(const esg_piece &pc, int ef) {
 }
 
 __global__ void __launch_bounds__(kOrderThreads) order_items_kernel(const esg_piece *pieces, const int32_t *ef_q,
-                                                                    int ef, int64_t n_items, int32_t *order) {
+                                                                    int ef, int64_t nq, int32_t *order) {
     __shared__ int32_t cnt[kOrderBuckets];
     if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n_items; i += kOrderThreads)
-        atomicAdd(&cnt[order_bucket(pieces[i], ef_q ? ef_q[i >> 1] : ef)], 1);
+    // buckets count down from the longest estimated cost
+    for (int64_t q = threadIdx.x; q < nq; q += kOrderThreads) {
+        const int e = ef_q ? ef_q[q] : ef;
+        const int b = min(order_bucket(pieces[2 * q], e), order_bucket(pieces[2 * q + 1], e));
+        atomicAdd(&cnt[b], 2);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int32_t run = 0;
         for (int b = 0; b < kOrderBuckets; ++b) { const int32_t c = cnt[b]; cnt[b] = run; run += c; }
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n_items; i += kOrderThreads)
-        order[atomicAdd(&cnt[order_bucket(pieces[i], ef_q ? ef_q[i >> 1] : ef)], 1)] = (int32_t)i;
+    for (int64_t q = threadIdx.x; q < nq; q += kOrderThreads) {
+        const int e = ef_q ? ef_q[q] : ef;
+        const int b0 = order_bucket(pieces[2 * q], e), b1 = order_bucket(pieces[2 * q + 1], e);
+        const int32_t pos = atomicAdd(&cnt[min(b0, b1)], 2);
+        const bool second_first = b1 < b0;
+        order[pos] = (int32_t)(2 * q + (second_first ? 1 : 0));
+        order[pos + 1] = (int32_t)(2 * q + (second_first ? 0 : 1));
+    }
 }
 
 // Merge the (at most two) sorted piece lists of each query into its top k
@@ -352,7 +365,7 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     // items longest first: a warp that takes a long search late would
     // leave the others idle at the end of the launch
     int32_t *order = (int32_t *)(scratch + L.order);
-    order_items_kernel<<<1, kOrderThreads, 0, stream>>>(pieces, ef_q, plan.ef, n_items, order);
+    order_items_kernel<<<1, kOrderThreads, 0, stream>>>(pieces, ef_q, plan.ef, s.nq, order);
     ESG_CUDA_TRY(cudaGetLastError());
     SearchArgs a;
     a.order = order;
