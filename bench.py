@@ -1,28 +1,49 @@
 #!/usr/bin/env python
-"""Benchmark: range-filtered k-NN queries/sec at recall@10 >= 0.95 on GB300.
+"""Benchmark: range-filtered k-NN queries/sec at recall >= 0.95 on one GB300,
+learned + mixed-precision + batched ESG search against the plain FP32
+fixed-ef search.
 
-Workload (default): N = 1,000,000 points, d = 128 float32 drawn from a
-1,024-component Gaussian mixture (sigma 0.1), attribute = a random
-permutation of the ranks, 10,000 queries from the same mixture with range
-widths 2^-j N for j = 0..10 (equal share), k = 10, graph degree M = 32
-(row cap R = 64), leaf size 256, squared Euclidean distance. Synthetic data
-of the shape of the paper's 1M-point SIFT/DEEP workloads (Table 3).
+Default workload (the batching workload, the largest one that fits one GPU):
+N = 10,000,000 points, d = 96, unit-normalised 1,024-component Gaussian
+mixture, inner product, attribute = a random permutation of the ranks,
+100,000 queries from the same mixture with range widths log-uniform over
+0.01 %-100 % of N and k drawn uniformly from {1, 10, 100}; graph degree
+M = 32 (row cap 64), leaf size 256. Synthetic data shaped like the paper's
+DEEP workloads (Table 3) and its "mix" ranges (Section 5.1).
 
-One step = one esg_search_batch over the whole 10,000-query batch (all steps
-of the hot path: decomposition, beam search with the POST filter on graph
-pieces, leaf scans, merge) on device-resident inputs. The beam width is the
-smallest of an ef sweep whose recall@10 against the exact GPU brute force
-reaches 0.95. An L2 flush (a 512 MB write) separates timed steps, outside the
-per-step CUDA events.
+One step = one search of the whole 100,000-query batch (decomposition,
+beam search with the POST filter on graph pieces, leaf scans, merge) on
+device-resident inputs, with an L2 flush (a 512 MB write) between steps,
+outside the per-step CUDA events.
+
+Arms, each at the smallest setting whose recall reaches 0.95:
+  plain    FP32 rows, one fixed ef for every query (Algorithm 1 order),
+           default launch shape, direct esg_search_batch calls;
+  bf16     BF16 rows + FP32 re-rank, fixed ef (the precision lever alone);
+  learned  per-query ef and expansion budget from the trained predictor,
+           BF16 rows + FP32 re-rank, launch shape from the autotuner, the
+           whole batch replayed as one CUDA graph (the headline).
+Recall is checked against the exact answers of every query (GPU brute force,
+itself checked against the float64 oracle on a sample): recall@k over all
+queries (hits among each query's first min(k, width) exact ids, summed, over
+the summed denominators) and recall@10 over the queries with k >= 10; an arm
+qualifies when both reach 0.95.
+
+Other workloads (--workload): scale (1M x 128, L2, k = 10), precision
+(1M x 96 unit vectors, IP; FP32 / BF16 / FP8 rows), learned (1M x 768
+anisotropic, IP; 50k training queries). --mode bruteforce times only the
+exact filtered k-NN.
 
 `--impl reference` times the CPU oracle instead (exact float64 range-filtered
 k-NN, recall 1.0) on a bounded query sample per step, on the host cores.
 
-Prints one JSON line (rank 0).
+Prints one JSON line on stdout (rank 0); per-arm details go to stderr as one
+JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures
 import json
 import os
 import statistics
@@ -39,9 +60,36 @@ import numpy as np  # noqa: E402
 
 import synthetic  # noqa: E402
 
-METRIC_NAME = "RF-kNN queries/sec at recall@10 \u2265 0.95, 1 GB300: learned+mixed vs plain search"
-EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+METRIC_NAME = "RF-kNN queries/sec at recall@10 ≥ 0.95, 1 GB300: learned+mixed vs plain search"
 TARGET_RECALL = 0.95
+ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
+
+# per-workload settings: generator, graph parameters, beam-width sweep, the
+# learned budget's ef range and training set, the row type of the headline
+WORKLOADS = {
+    "batching": dict(gen=lambda a: synthetic.batching(n=a.n or 10_000_000, nq=a.nq or 100_000),
+                     desc="N={n}, d=96 unit-norm 1024-component mixture, inner product, {nq} queries, "
+                          "widths log-uniform 0.01%-100%, k in {{1,10,100}}, M=32, leaf 256",
+                     M=32, sweep=[16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512],
+                     ef_lo=8, ef_hi=256, n_train=30_000, trav="bf16", extra_storage=None),
+    "scale": dict(gen=lambda a: synthetic.scale(n=a.n or 1_000_000, nq=a.nq or 10_000),
+                  desc="N={n}, d=128 f32 1024-component mixture, {nq} queries, widths 2^-j N (j=0..10), "
+                       "k=10, M=32, leaf 256, L2",
+                  M=32, sweep=[16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512],
+                  ef_lo=8, ef_hi=64, n_train=20_000, trav="bf16", extra_storage="fp8"),
+    "precision": dict(gen=lambda a: synthetic.precision(n=a.n or 1_000_000, nq=a.nq or 10_000),
+                      desc="N={n}, d=96 unit-norm 1024-component mixture, inner product, {nq} queries, "
+                           "widths log-uniform 0.1%-100%, k=10, M=32, leaf 256",
+                      M=32, sweep=[16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512],
+                      ef_lo=8, ef_hi=128, n_train=20_000, trav="bf16", extra_storage="fp8"),
+    "learned": dict(gen=lambda a: synthetic.learned(n=a.n or 1_000_000, nq=a.nq or 10_000),
+                    desc="N={n}, d=768 anisotropic (power-law spectrum) unit vectors, inner product, "
+                         "{nq} held-out queries (50,000 training), widths log-uniform 0.1%-100%, k=10, M=32",
+                    M=32, sweep=[16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512],
+                    ef_lo=8, ef_hi=128, n_train=50_000, trav="bf16", extra_storage=None),
+}
+LEARNED_LABEL_RECALL = 0.9
+LEARNED_QUANTILE = 0.5
 
 
 def parse_args():
@@ -50,23 +98,15 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--nq", type=int, default=10_000)
-    ap.add_argument("--ef", type=int, default=0, help="fixed beam width (skip the sweep)")
+    ap.add_argument("--workload", default="batching", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=0, help="points (0: the workload's)")
+    ap.add_argument("--nq", type=int, default=0, help="queries (0: the workload's)")
+    ap.add_argument("--ef", type=int, default=0, help="fixed beam width of the fixed-ef arms (skip the sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--variants", default="", help="comma-separated subset of variant names")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget variant")
-    ap.add_argument("--learned-trav", default="bf16", choices=["auto", "f32", "bf16", "fp8"],
-                    help="row type of the learned variant; auto: the fastest fixed-ef variant's "
-                         "(BF16 and FP8 are within 1 %% there and flip between runs; with the "
-                         "learned budget BF16 measured 1.40 ms against 1.46 ms for FP8)")
-    ap.add_argument("--bf-workload", default="scale", choices=["scale", "learned"],
-                    help="workload of --mode bruteforce: the 128-d scale mixture or the 768-d "
-                         "anisotropic inner-product workload (its held-out queries)")
-    ap.add_argument("--mode", default="search", choices=["search", "bruteforce", "batching"],
-                    help="bruteforce: time only the exact filtered k-NN of the workload's queries; "
-                         "batching: the 10M-point, 100k-query workload in one CUDA-graph launch")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget arm")
+    ap.add_argument("--mode", default="search", choices=["search", "bruteforce"],
+                    help="bruteforce: time only the exact filtered k-NN of the workload's queries")
     return ap.parse_args()
 
 
@@ -77,18 +117,45 @@ def dist_env():
     return rank, world, local
 
 
-def workload(args):
-    return synthetic.scale(n=args.n, nq=args.nq)
+def make_workload(args):
+    w = WORKLOADS[args.workload]["gen"](args)
+    if args.workload == "learned":
+        # the first 50,000 queries are the training split, the rest held out
+        n_train = WORKLOADS["learned"]["n_train"]
+        w.train = (w.queries[:n_train], w.l[:n_train], w.r[:n_train], w.k[:n_train])
+        w.queries, w.l, w.r, w.k = w.queries[n_train:], w.l[n_train:], w.r[n_train:], w.k[n_train:]
+    return w
 
 
-def workload_config(args, extra=None):
-    cfg = {"workload": f"ESG range-filtered kNN, N={args.n}, d=128 f32 1024-component mixture, "
-                       f"{args.nq} queries, widths 2^-j N (j=0..10), k=10, M=32, leaf 256, L2",
-           "n": args.n, "d": 128, "nq": args.nq, "k": 10, "M": 32, "leaf_size": 256,
-           "l2_flush": True}
+def workload_config(args, w, extra=None):
+    cfg = {"workload": WORKLOADS[args.workload]["desc"].format(n=w.n, nq=len(w.l)),
+           "n": int(w.n), "d": int(w.d), "nq": int(len(w.l)), "k": sorted(set(int(x) for x in w.k)),
+           "M": WORKLOADS[args.workload]["M"], "leaf_size": 256, "metric": w.metric, "l2_flush": True}
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- float64 ground truth
+
+def fp64_exact(O, Xr, q, l, r, k, metric, chunk=1 << 20):
+    """The oracle's exact range-filtered k-NN (Definitions 1-2) over the
+    rank-ordered float32 rows Xr, promoted to float64 one chunk at a time.
+    Returns (ranks, float64 distances)."""
+    parts = []
+    q64 = np.asarray(q, np.float64)
+    for s in range(l, r + 1, chunk):
+        e = min(r, s + chunk - 1)
+        ids, dd = O.bruteforce(Xr[s:e + 1], q64, 0, e - s, k, metric)
+        parts.append((ids + s, dd))
+    return O.merge_topk(parts, k)
 
 
 # ---------------------------------------------------------------- reference arm
@@ -97,21 +164,20 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle as O
-    w = workload(args)
+    w = make_workload(args)
     perm = O.rerank(w.attr)
-    X = np.ascontiguousarray(w.base[perm].astype(np.float64))
-    per_step = 16
-    order = np.arange(len(w.queries))
-    times = []
+    Xr = np.ascontiguousarray(w.base[perm])
+    per_step = 8
     cursor = 0
+    times = []
 
     def step():
         nonlocal cursor
         t0 = time.perf_counter()
         for _ in range(per_step):
-            i = order[cursor % len(order)]
+            i = cursor % len(w.l)
             cursor += 1
-            O.bruteforce(X, w.queries[i].astype(np.float64), int(w.l[i]), int(w.r[i]), 10, w.metric)
+            fp64_exact(O, Xr, w.queries[i], int(w.l[i]), int(w.r[i]), int(w.k[i]), w.metric)
         return time.perf_counter() - t0
 
     for _ in range(args.warmup):
@@ -120,14 +186,14 @@ def run_reference(args, rank, world):
         times.append(step())
     total = sum(times)
     qps = per_step * args.steps / total
-    cores = 1
-    sample = f"{per_step} queries per step in workload order (exact float64 filtered k-NN, recall 1.0)"
+    sample = (f"{per_step} queries per step in workload order (exact float64 filtered k-NN by the oracle, "
+              f"recall 1.0, one host thread)")
     line = {"impl": "reference", "metric": METRIC_NAME, "value": qps, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, {"parallelism": "replicas"}),
-            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "config": workload_config(args, w, {"parallelism": "replicas"}),
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -186,48 +252,134 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- our arm
+# ---------------------------------------------------------------- recall
 
-def recall_at_10(ids, cnt, gt, gcnt):
-    tot = 0.0
+def recall(ids, cnt, gt, gc, k):
+    """(recall@k over all queries, recall@10 over the queries with k >= 10):
+    hits among each query's first min(k, |exact|) exact ids, summed over
+    queries, over the summed denominators."""
+    hits = tot = hits10 = tot10 = 0
     for i in range(len(ids)):
-        g = gt[i, :gcnt[i]]
-        if len(g) == 0:
-            tot += 1.0
-            continue
-        tot += len(np.intersect1d(ids[i, :cnt[i]], g, assume_unique=True)) / len(g)
-    return tot / len(ids)
+        c = min(int(k[i]), int(gc[i]))
+        found = set(ids[i, :min(int(cnt[i]), int(k[i]))].tolist())
+        hits += len(found & set(gt[i, :c].tolist()))
+        tot += c
+        if k[i] >= 10:
+            c10 = min(10, int(gc[i]))
+            f10 = set(ids[i, :min(int(cnt[i]), 10)].tolist())
+            hits10 += len(f10 & set(gt[i, :c10].tolist()))
+            tot10 += c10
+    return hits / max(tot, 1), (hits10 / tot10 if tot10 else None)
 
 
-def cpu_baseline(ix, w, ef, seconds):
+def qualifies(rec):
+    return rec[0] >= TARGET_RECALL and (rec[1] is None or rec[1] >= TARGET_RECALL)
+
+
+# ---------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(E, O, ix, w, Xr_host, ef, seconds, gt, gc, mem_budget=24 << 30):
     """The oracle's ESG search (Algorithm 4 + Algorithm 1 in plain C, float64)
-    on the same graph and ef, one host thread, bounded by `seconds`."""
-    import oracle as O
-    import paper_2504_04018_gb300 as E
-    adj, ent, perm = E.esg_index_export(ix)
-    X = np.ascontiguousarray(w.base[perm].astype(np.float64))
-    oi = O.OracleIndex(X, perm, adj, ent, ix.leaf_size, ix.R // 2, w.metric)
-    done = 0
-    t0 = time.perf_counter()
-    while done < len(w.queries) and time.perf_counter() - t0 < seconds:
-        i = done
-        O.search(oi, w.queries[i].astype(np.float64), int(w.l[i]), int(w.r[i]), 10, ef)
-        done += 1
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of {len(w.queries)} workload queries (all widths), "
-                      f"Algorithm 4 + Algorithm 1 in C float64 on the same graph, ef={ef}"}
+    on the GPU index's own graph at the plain arm's ef, on the first queries of
+    the workload (all widths): one host thread, then all host cores (a thread
+    pool over the pieces; the C search releases the interpreter lock).
+
+    Graph rows are exported node by node (a node's edges stay inside it) and
+    searched in place (row_base = the node's first rank) against one float64
+    copy of the rows. Nodes are taken in waves of at most `mem_budget` bytes of
+    exported rows, each wave timed on one thread and on all cores. The sample
+    size is set from a probe to about `seconds` of one-thread search. Also
+    returns the oracle's recall on the sample against the exact answers."""
+    X64 = Xr_host.astype(np.float64)
+    ent_all = E.esg_index_export_entries(ix)
+    perm = perm_of(ix, E)
+    inv = np.empty(w.n, np.int64)
+    inv[perm] = np.arange(w.n)
+
+    def pieces_of(i):
+        return O.decompose(w.n, ix.leaf_size, int(w.l[i]), int(w.r[i]))
+
+    def run_piece(i, p, rows):
+        q = w.queries[i]
+        k = int(w.k[i])
+        if p.kind == "scan":
+            return O.bruteforce(X64, q, p.pl, p.pr, k, w.metric)
+        ids, dd = O.graph_search_rows(X64[p.node_l:p.node_r + 1], rows, ent_all[p.heap], w.metric, q,
+                                      max(ef, k), p.pl, p.pr, row_base=p.node_l)
+        return ids[:k], dd[:k]
+
+    def run(queries):
+        """(parts per query, one-thread seconds, all-core seconds)."""
+        todo = {}
+        for i in queries:
+            for s_, p in enumerate(pieces_of(i)):
+                key = (p.depth, p.heap) if p.kind == "graph" else ("scan",)
+                todo.setdefault(key, []).append((i, s_, p))
+        parts = {i: {} for i in queries}
+        t1 = tall = 0.0
+        keys = sorted(todo, key=lambda k: (len(k), k))
+        cores = len(os.sched_getaffinity(0))
+        while keys:
+            wave, used = [], 0
+            while keys:
+                key = keys[0]
+                size = 0 if key == ("scan",) else (todo[key][0][2].node_r - todo[key][0][2].node_l + 1) * ix.R * 4
+                if wave and used + size > mem_budget:
+                    break
+                wave.append(key)
+                used += size
+                keys.pop(0)
+            rows = {key: None if key == ("scan",) else
+                    E.esg_index_export_rows(ix, key[0], todo[key][0][2].node_l,
+                                            todo[key][0][2].node_r - todo[key][0][2].node_l + 1)
+                    for key in wave}
+            jobs = [(i, s_, p, rows[key]) for key in wave for (i, s_, p) in todo[key]]
+            t0 = time.perf_counter()
+            for (i, s_, p, rw) in jobs:
+                parts[i][s_] = run_piece(i, p, rw)
+            t1 += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+                list(ex.map(lambda j: run_piece(j[0], j[2], j[3]), jobs))
+            tall += time.perf_counter() - t0
+            del rows, jobs
+        t0 = time.perf_counter()
+        merged = {i: O.merge_topk([parts[i][s_] for s_ in sorted(parts[i])], int(w.k[i]))[0] for i in queries}
+        tm = time.perf_counter() - t0
+        return merged, t1 + tm, tall + tm, cores
+
+    probe = list(range(min(len(w.l), 48)))
+    _, tp, _, _ = run(probe)
+    S = int(max(len(probe), min(len(w.l), seconds * len(probe) / max(tp, 1e-6))))
+    found, t1, tall, cores = run(list(range(S)))
+    hits = tot = 0
+    for i in range(S):
+        c = min(int(w.k[i]), int(gc[i]))
+        hits += len(set(found[i][:c].tolist()) & set(inv[gt[i, :c]].tolist()))
+        tot += c
+    return {"value": S / t1, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {S} of {len(w.l)} workload queries (all widths), Algorithm 4 + Algorithm 1 "
+                      f"in C float64 on the GPU index's graph (nodes exported from it), ef={ef}",
+            "all_cores": {"value": S / tall, "cores": cores},
+            "recall_at_k_same_graph": hits / max(tot, 1)}
 
 
-def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
+_PERM = {}
+
+
+def perm_of(ix, E):
+    if id(ix) not in _PERM:
+        _PERM[id(ix)] = E.esg_index_perm(ix)
+    return _PERM[id(ix)]
+
+
+# ---------------------------------------------------------------- brute force timing
+
+def bruteforce_timing(E, torch, Xr, Q, L, R, w, k=10):
     """Exact filtered k-NN of the benchmark queries: the tcgen05 path (whole
     call, and its MMA kernel alone with the MMA FLOPs it issued) against the
     SIMT FP32 kernel (CUDA events, median of 3)."""
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    pk = peaks()
     out = {}
     for name, env in (("tcgen05", "0"), ("simt", "1")):
         os.environ["ESG_BF_SIMT"] = env
@@ -235,58 +387,356 @@ def bruteforce_timing(E, torch, Xr, Q, L, R, w, args):
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10, w.metric)
+            E.esg_bruteforce_filtered_knn(Xr, Q, L, R, k, w.metric)
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         out[name + "_ms"] = round(sorted(ts)[1], 3)
     os.environ.pop("ESG_BF_SIMT", None)
-    # the MMA kernel alone
     E.esg_profile_enable(True)
-    E.esg_bruteforce_filtered_knn(Xr, Q, L, R, 10, w.metric)
+    E.esg_bruteforce_filtered_knn(Xr, Q, L, R, k, w.metric)
     torch.cuda.synchronize()
     kms, _, _ = E.esg_profile_read(reset=True)
     mma_flops = E.esg_profile_tensor_work(reset=True)
     E.esg_profile_enable(False)
     pairs = float(np.sum(w.r - w.l + 1))
-    useful = 2.0 * w.d * pairs                      # one dot product per in-range pair
-    peak = float(peaks.get("bf16_tflops", 1900.0))
+    useful = 2.0 * w.d * pairs
+    peak = float(pk.get("bf16_tflops", 1900.0))
     t = out["tcgen05_ms"] / 1e3
-    out.update({"queries": int(len(w.l)), "pairs": pairs,
+    out.update({"queries": int(len(w.l)), "k": k, "pairs": pairs,
                 "qps_tcgen05": len(w.l) / t, "qps_simt": len(w.l) / (out["simt_ms"] / 1e3),
                 "useful_tflops": useful / t / 1e12,
                 "mma_kernel_ms": round(kms, 4),
-                "mma_tflops_issued": mma_flops,
+                "mma_flops_issued": mma_flops,
+                "mma_flops_useful_bf16x3": 3 * useful,
                 "mma_kernel_tflops": (mma_flops / (kms / 1e3) / 1e12) if kms > 0 else None,
                 "mma_frac_of_bf16_peak": (mma_flops / (kms / 1e3) / 1e12 / peak) if kms > 0 else None,
                 "bf16_peak_tflops": peak,
-                "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"})
+                "peak_source": "measured" if "bf16_tflops" in pk else "fallback"})
     return out
 
 
-# (name, traversal rows, search width); "plain" is Algorithm 1's order on FP32 rows
-VARIANTS = [("plain", "f32", 1)] + [(f"{t}-w{wd}", t, wd) for t in ("f32", "bf16", "fp8")
-                                    for wd in (1, 2) if not (t == "f32" and wd == 1)]
-ESIZE = {"f32": 4, "bf16": 2, "fp8": 1}
-N_TRAIN = 20_000
-# largest beam width the learned budget may pick: the candidate list and the
-# visited table are sized for it, so a tight cap keeps more warps resident
-LEARNED_EF_HI = 64
-# labels = smallest ef reaching this per-query recall; median regression; the
-# calibrated margin then sets the mean recall (on the scale workload this beat
-# full-recall labels with quantile 0.9 by 5-8 % in kernel time at equal recall)
-LEARNED_LABEL_RECALL = 0.9
-LEARNED_QUANTILE = 0.5
+def run_bruteforce_only(args, local):
+    import torch
+    import paper_2504_04018_gb300 as E
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E.load_library()
+    w = make_workload(args)
+    perm = np.argsort(w.attr, kind="stable")
+    Xr = torch.as_tensor(w.base[perm], device=dev)
+    Q = torch.as_tensor(w.queries, device=dev)
+    L = torch.as_tensor(w.l, device=dev)
+    Rr = torch.as_tensor(w.r, device=dev)
+    info = bruteforce_timing(E, torch, Xr, Q, L, Rr, w)
+    print(json.dumps({"mode": "bruteforce", "metric": "exact RF-kNN queries/sec (k=10)",
+                      "value": info["qps_tcgen05"], "unit": "queries/s", "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "bf16x3+f32", "data": "synthetic",
+                      "config": workload_config(args, w), "bruteforce": info}), flush=True)
 
 
-def measured_traffic(variant, params):
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2504_04018_gb300 as E
+    import oracle as O
+    from paper_2504_04018_gb300 import replicas as RP
+
+    spec = WORKLOADS[args.workload]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    E.load_library()
+    t0 = time.perf_counter()
+    w = make_workload(args)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ix = E.esg_build(w.base, w.attr, M=spec["M"], leaf_size=256, n_entries=16, ef_construction=200,
+                     metric=w.metric, storage=spec["trav"])
+    if spec["extra_storage"]:
+        E.esg_index_add_storage(ix, spec["extra_storage"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    perm = perm_of(ix, E)
+    Xr_host = np.ascontiguousarray(w.base[perm])
+    Xr = torch.as_tensor(Xr_host, device=dev)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    nq = len(w.l)
+    k_max = int(w.k.max())
+    Q, L, Rr, K = t(w.queries), t(w.l), t(w.r), t(w.k.astype(np.int32))
+
+    def ground_truth(q, l, r, k):
+        """Exact answers (original ids, -1 padded to k_max) from the GPU brute
+        force, one call per distinct k."""
+        ids = np.full((len(l), k_max), -1, np.int64)
+        cnt = np.zeros(len(l), np.int32)
+        for kv in sorted(set(int(x) for x in k)):
+            sel = np.nonzero(k == kv)[0]
+            gi, _, gcnt = E.esg_bruteforce_filtered_knn(Xr, t(q[sel]), t(l[sel]), t(r[sel]), kv, w.metric)
+            torch.cuda.synchronize()
+            gi, gcnt = gi.cpu().numpy(), gcnt.cpu().numpy()
+            ids[sel, :kv] = np.where(gi >= 0, perm[np.maximum(gi, 0)], -1)
+            cnt[sel] = gcnt
+        return ids, cnt
+
+    t0 = time.perf_counter()
+    gt, gc = ground_truth(w.queries, w.l, w.r, w.k)
+    gt_s = time.perf_counter() - t0
+    # the GPU ground truth against the float64 oracle on sampled queries
+    rng = np.random.default_rng(7)
+    chk = rng.choice(nq, min(24, nq), replace=False)
+    same = 0
+    max_rel = 0.0
+    inv = np.empty(w.n, np.int64)
+    inv[perm] = np.arange(w.n)
+    for i in chk:
+        ranks, dd = fp64_exact(O, Xr_host, w.queries[i], int(w.l[i]), int(w.r[i]), int(w.k[i]), w.metric)
+        c = int(gc[i])
+        same += inv[gt[i, :c]].tolist() == ranks.tolist()
+        got = O.distances(Xr_host[inv[gt[i, :c]]], w.queries[i], w.metric)
+        max_rel = max(max_rel, float(np.max(np.abs(got - dd[:c]) / np.maximum(np.abs(dd[:c]), 1e-2 * np.abs(dd).max()))))
+    gt_check = {"sampled": int(len(chk)), "identical_id_lists": int(same), "max_rel_dist_err": max_rel}
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    outs = (torch.empty((nq, k_max), dtype=torch.int64, device=dev),
+            torch.empty((nq, k_max), dtype=torch.float32, device=dev),
+            torch.empty(nq, dtype=torch.int32, device=dev),
+            torch.empty(nq, dtype=torch.int32, device=dev),
+            torch.empty((nq, 6), dtype=torch.int64, device=dev))
+    clocks = ClockSampler(local)
+    clocks.start()
+    results = {}
+
+    def timed(step_fn, name):
+        for _ in range(args.warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        RP.barrier()
+        torch.cuda.nvtx.range_push(f"timed_{name}")
+        evs = [step_fn() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        total_ms = RP.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
+        RP.barrier()
+        return total_ms
+
+    def search_once(params):
+        E.esg_search_batch(ix, Q, L, Rr, K, k_max, params=params, out=outs)
+        torch.cuda.synchronize()
+        return outs[0].cpu().numpy(), outs[2].cpu().numpy(), outs[4].cpu().numpy()
+
+    def measure(name, params, trav):
+        """Recall, per-step time, search-kernel time and algorithmic bytes of
+        one parameter setting with direct esg_search_batch calls."""
+        ids, cnt, stats = search_once(params)
+        rec = recall(ids, cnt, gt, gc, w.k)
+        alg_bytes = float(stats[:, 1].sum() * ix.d * ESIZE[trav] + stats[:, 0].sum() * ix.R * 4
+                          + stats[:, 3].sum() * ix.d * 4)
+
+        def one_step():
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            E.esg_search_batch(ix, Q, L, Rr, K, k_max, params=params, out=outs)
+            ev1.record(stream)
+            return ev0, ev1
+
+        E.esg_profile_enable(True)
+        total_ms = timed(one_step, name)
+        kernel_ms, launches, nt = E.esg_profile_read(reset=True)
+        E.esg_profile_enable(False)
+        lat = stats[:, 5] / 1e3
+        return {"trav": trav, "params": params.as_dict(), "recall_at_k": round(rec[0], 5),
+                "recall_at_10_k_ge_10": None if rec[1] is None else round(rec[1], 5),
+                "qps": RP.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
+                "kernel_ms": kernel_ms / max(1, nt), "alg_bytes": alg_bytes,
+                "launches_per_step": launches // max(1, args.steps + args.warmup),
+                "evals_per_query": float(stats[:, 1].mean()),
+                "expansions_per_query": float(stats[:, 0].mean()),
+                "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}}
+
+    def sweep_arm(name, trav, width=1):
+        sweep, chosen = [], None
+        for ef in ([args.ef] if args.ef else spec["sweep"]):
+            ids, cnt, _ = search_once(E.search_params(ef=ef, traversal=trav, width=width))
+            rec = recall(ids, cnt, gt, gc, w.k)
+            sweep.append({"ef": ef, "recall_at_k": round(rec[0], 5),
+                          "recall_at_10_k_ge_10": None if rec[1] is None else round(rec[1], 5)})
+            chosen = ef
+            if qualifies(rec):
+                break
+        results[name] = measure(name, E.search_params(ef=chosen, traversal=trav, width=width), trav)
+        results[name]["sweep"] = sweep
+
+    sweep_arm("plain", "f32")
+    fixed_travs = ["bf16", "fp8"] if args.workload in ("precision", "scale") else [spec["trav"]]
+    for tv in fixed_travs:
+        sweep_arm(tv, tv)
+
+    learned_info = {}
+    if not args.no_learned:
+        trav = spec["trav"]
+        if hasattr(w, "train"):
+            tq, tl, tr, tk = w.train
+        else:
+            tq, tl, tr = synthetic.training_queries(w, spec["n_train"], 1024, seed=4000 + 7)
+            ks = np.array(sorted(set(int(x) for x in w.k)), np.int32)
+            tk = ks[np.random.default_rng(4001).integers(0, len(ks), len(tl))]
+        tgt, tgc = ground_truth(tq, tl, tr, tk)
+        TQ, TL, TR, TK = t(tq), t(tl), t(tr), t(tk.astype(np.int32))
+        t1 = time.perf_counter()
+        rep = E.esg_train_predictor(ix, TQ, TL, TR, t(tgt), t(tgc), k_max=k_max, k=TK,
+                                    target_recall=TARGET_RECALL + 0.005, ef_lo=spec["ef_lo"],
+                                    ef_hi=spec["ef_hi"], traversal=trav, epochs=40,
+                                    per_query_recall=LEARNED_LABEL_RECALL, quantile=LEARNED_QUANTILE)
+        train_s = time.perf_counter() - t1
+        base = E.search_params(ef=spec["ef_hi"], traversal=trav, use_learned=1)
+        m = min(nq, len(tl))
+        tuned, trec, tms = E.esg_autotune(ix, TQ[:m], TL[:m], TR[:m], t(tgt[:m]), t(tgc[:m]), k_max=k_max,
+                                          k=TK[:m], target_recall=TARGET_RECALL, base=base)
+        cands = []
+        for wd in (1, 2):
+            pw = E.search_params(**dict(tuned.as_dict(), width=wd))
+            nm = f"learned-{trav}" + ("" if wd == 1 else "-w2")
+            results[nm] = measure(nm, pw, trav)
+            cands.append((nm, pw))
+        ok = [c for c in cands if qualifies((results[c[0]]["recall_at_k"], results[c[0]]["recall_at_10_k_ge_10"]))]
+        name, tuned = max(ok or cands, key=lambda c: results[c[0]]["qps"])
+        # the chosen setting replayed as one CUDA graph per batch
+        b = E.Batch(ix, max_nq=nq, k_max=k_max, params=tuned, use_k=True)
+        b.view("queries", (nq, ix.d), torch.float32).copy_(Q)
+        b.view("l", (nq,), torch.int64).copy_(L)
+        b.view("r", (nq,), torch.int64).copy_(Rr)
+        b.view("k", (nq,), torch.int32).copy_(K)
+
+        def graph_step():
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.run(nq, stream=stream)
+            ev1.record(stream)
+            return ev0, ev1
+
+        total_ms = timed(graph_step, name + "-graph")
+        ids = b.view("ids", (nq, k_max), torch.int64).cpu().numpy()
+        cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
+        g = dict(results[name])
+        rec = recall(ids, cnt, gt, gc, w.k)
+        g.update({"recall_at_k": round(rec[0], 5),
+                  "recall_at_10_k_ge_10": None if rec[1] is None else round(rec[1], 5),
+                  "qps": RP.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
+                  "graph": True})
+        results[name + "-graph"] = g
+        learned_info = {"traversal": trav, "train_queries": int(len(tl)), "ef_range": [spec["ef_lo"], spec["ef_hi"]],
+                        "label_recall": LEARNED_LABEL_RECALL, "quantile": LEARNED_QUANTILE,
+                        "train_s": round(train_s, 2), "train_loss": float(rep[0]),
+                        "heldout_recall": float(rep[1]), "ef_margin_log2": float(rep[2]),
+                        "heldout_evals_per_query": float(rep[3]),
+                        "autotune": {"params": tuned.as_dict(), "recall": trec, "ms": tms}}
+    clk = clocks.stop()
+
+    ok = {k: v for k, v in results.items() if qualifies((v["recall_at_k"], v["recall_at_10_k_ge_10"]))}
+    opt = {k: v for k, v in ok.items() if k != "plain"}
+    head_name = max(opt, key=lambda k: opt[k]["qps"]) if opt else "plain"
+    head = results[head_name]
+
+    # end to end through the public API with pinned host buffers: the
+    # inputs copied in and the results copied out inside the timed region
+    Qh, Lh, Rh, Kh = (torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+                      for a in (w.queries, w.l, w.r, w.k.astype(np.int32)))
+    ids_h = torch.empty((nq, k_max), dtype=torch.int64).pin_memory()
+    dist_h = torch.empty((nq, k_max), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(nq, dtype=torch.int32).pin_memory()
+    head_params = E.search_params(**head["params"])
+    if head.get("graph"):
+        bq, bl, br, bk = (b.view("queries", (nq, ix.d), torch.float32), b.view("l", (nq,), torch.int64),
+                          b.view("r", (nq,), torch.int64), b.view("k", (nq,), torch.int32))
+        bi, bd, bc = (b.view("ids", (nq, k_max), torch.int64), b.view("dist", (nq, k_max), torch.float32),
+                      b.view("count", (nq,), torch.int32))
+    else:
+        bq, bl, br, bk = torch.empty_like(Q), torch.empty_like(L), torch.empty_like(Rr), torch.empty_like(K)
+        bi, bd, bc = outs[0], outs[1], outs[2]
+
+    def e2e_step():
+        flush.fill_(1.0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bq.copy_(Qh, non_blocking=True)
+        bl.copy_(Lh, non_blocking=True)
+        br.copy_(Rh, non_blocking=True)
+        bk.copy_(Kh, non_blocking=True)
+        if head.get("graph"):
+            b.run(nq, stream=stream)
+        else:
+            E.esg_search_batch(ix, bq, bl, br, bk, k_max, params=head_params, out=outs)
+        ids_h.copy_(bi, non_blocking=True)
+        dist_h.copy_(bd, non_blocking=True)
+        cnt_h.copy_(bc, non_blocking=True)
+        ev1.record(stream)
+        return ev0, ev1
+
+    e2e_ms = timed(e2e_step, "e2e")
+    h2d = Qh.numel() * 4 + Lh.numel() * 8 + Rh.numel() * 8 + Kh.numel() * 4
+    d2h = ids_h.numel() * 8 + dist_h.numel() * 4 + cnt_h.numel() * 4
+
+    pk = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved = head["alg_bytes"] / (head["kernel_ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": measured_traffic(f"{args.workload}:{head_name}", head["params"]),
+                "kernel": f"search_kernel ({head_name})", "kernel_ms_per_launch": round(head["kernel_ms"], 4),
+                "algorithmic_bytes_per_launch": head["alg_bytes"],
+                "peak_source": "measured" if "hbm_gbs" in pk else "fallback"}
+    details = {"variants": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
+                                if kk != "alg_bytes"} for k, v in results.items()},
+               "learned": learned_info, "gen_s": round(gen_s, 1), "build_s": round(build_s, 1),
+               "ground_truth_s": round(gt_s, 1), "ground_truth_check": gt_check}
+    if args.workload == "scale" and rank == 0:
+        details["bruteforce"] = bruteforce_timing(E, torch, Xr, Q, L, Rr, w)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(E, O, ix, w, Xr_host, results["plain"]["params"]["ef"], args.cpu_seconds, gt, gc)
+    plain = results["plain"]
+    line = {"metric": METRIC_NAME, "value": head["qps"], "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": head["trav"], "data": "synthetic",
+            "config": workload_config(args, w, {"parallelism": f"replicas{world}", "variant": head_name}),
+            "roofline": roofline, "clocks": clk,
+            "e2e": {"value": RP.job_rate(nq, world, args.steps, e2e_ms), "unit": "queries/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": head["launches_per_step"] * args.steps}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    # the comparison the metric names, last so that it survives a cut tail
+    line.update({"build_s": round(build_s, 1), "ground_truth_check": gt_check,
+                 "latency_us": head["latency_us"], "params": head["params"],
+                 "recall_at_k": head["recall_at_k"], "recall_at_10_k_ge_10": head["recall_at_10_k_ge_10"],
+                 "plain_fp32": {"qps": plain["qps"], "ef": plain["params"]["ef"],
+                                "recall_at_k": plain["recall_at_k"],
+                                "recall_at_10_k_ge_10": plain["recall_at_10_k_ge_10"],
+                                "kernel_ms": round(plain["kernel_ms"], 3)},
+                 "speedup_vs_plain": head["qps"] / plain["qps"]})
+    if rank == 0:
+        print(json.dumps(details), file=sys.stderr, flush=True)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measured_traffic(key, params):
     """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, when it was taken for this variant, these search parameters
-    (ef, budget, row type, width; not the launch shape) and the current
-    kernel sources (None otherwise)."""
+    summary, when it was taken for this "workload:variant" key, these search
+    parameters (ef, budget, row type, width; not the launch shape) and the
+    current kernel sources (None otherwise)."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")))[variant]
+        rec = json.load(open(os.path.join(ROOT, "profiles", "search_kernel_traffic.txt")))[key]
     except Exception:
         return None
     m = hashlib.sha256()
@@ -299,363 +749,6 @@ def measured_traffic(variant, params):
     return rec["traffic_bytes_per_launch"]
 
 
-def run_bruteforce_only(args, local):
-    """Exact filtered k-NN of the workload's queries over the rank-ordered
-    points, tcgen05 path against the SIMT kernel (no index is built)."""
-    import torch
-    import paper_2504_04018_gb300 as E
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    E.load_library()
-    if args.bf_workload == "learned":
-        w = synthetic.learned(n=args.n, nq=args.nq, n_train=0)
-    else:
-        w = workload(args)
-    perm = np.argsort(w.attr, kind="stable")      # rank order: attribute, ties by id
-    Xr = torch.as_tensor(w.base[perm], device=dev)
-    Q = torch.as_tensor(w.queries, device=dev)
-    L = torch.as_tensor(w.l, device=dev)
-    Rr = torch.as_tensor(w.r, device=dev)
-    info = bruteforce_timing(E, torch, Xr, Q, L, Rr, w, args)
-    print(json.dumps({"mode": "bruteforce", "metric": "exact RF-kNN queries/sec (k=10)",
-                      "value": info["qps_tcgen05"], "unit": "queries/s", "n_gpus": 1,
-                      "higher_is_better": True, "dtype": "bf16x3+f32", "data": "synthetic",
-                      "config": (workload_config(args) if args.bf_workload == "scale" else
-                                 {"workload": f"N={w.n}, d={w.d} anisotropic unit vectors, inner product, "
-                                              f"{len(w.l)} queries, widths log-uniform 0.1%-100%, k=10"}),
-                      "bruteforce": info}), flush=True)
-
-
-def run_batching(args, local):
-    """10M unit-norm 96-d points (inner product, BF16 rows + FP32 re-rank),
-    100,000 queries with widths 0.01%-100% and k in {1, 10, 100} replayed as
-    one CUDA graph per step; launch shape and beam width from the autotuner
-    on 2,000 training queries; recall on 3,000 sampled queries against the
-    exact GPU brute force; per-query device latency percentiles."""
-    import torch
-    import paper_2504_04018_gb300 as E
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    E.load_library()
-    w = synthetic.batching()
-    t0 = time.perf_counter()
-    ix = E.esg_build(w.base, w.attr, M=32, leaf_size=256, n_entries=16, metric="ip", storage="bf16")
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    _, _, perm = E.esg_index_export(ix)
-    Xr = torch.as_tensor(w.base[perm], device=dev)
-    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
-
-    def gt_of(q, l, r):
-        gi, _, gc = E.esg_bruteforce_filtered_knn(Xr, t(q), t(l), t(r), 100, "ip")
-        torch.cuda.synchronize()
-        gi, gc = gi.cpu().numpy(), gc.cpu().numpy()
-        return np.where(gi >= 0, perm[np.maximum(gi, 0)], -1), gc
-
-    tq, tl, tr = synthetic.training_queries(w, 2000, 1024, seed=4004)
-    tk = np.array([1, 10, 100], np.int32)[np.random.default_rng(4005).integers(0, 3, 2000)]
-    tgt, tgc = gt_of(tq, tl, tr)
-    params, trec, _ = E.esg_autotune(ix, t(tq), t(tl), t(tr), t(tgt), t(tgc), k_max=100, k=t(tk),
-                                     target_recall=0.955, base=E.search_params(ef=64, traversal="bf16"))
-    nq = len(w.l)
-    b = E.Batch(ix, max_nq=nq, k_max=100, params=params, use_k=True)
-    b.view("queries", (nq, ix.d), torch.float32).copy_(t(w.queries))
-    b.view("l", (nq,), torch.int64).copy_(t(w.l))
-    b.view("r", (nq,), torch.int64).copy_(t(w.r))
-    b.view("k", (nq,), torch.int32).copy_(t(w.k))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        b.run(nq, stream=stream)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    total = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        b.run(nq, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total += e0.elapsed_time(e1)
-    clk = clocks.stop()
-    stats = b.view("stats", (nq, 6), torch.int64).cpu().numpy()
-    ids = b.view("ids", (nq, 100), torch.int64).cpu().numpy()
-    cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
-    ev = np.random.default_rng(5).choice(nq, 3000, replace=False)
-    gt, gc = gt_of(w.queries[ev], w.l[ev], w.r[ev])
-    hits = tot = 0
-    for j, i in enumerate(ev):
-        c = min(int(w.k[i]), int(gc[j]))
-        hits += len(set(ids[i, :min(int(cnt[i]), c)].tolist()) & set(gt[j, :c].tolist()))
-        tot += c
-    lat = stats[:, 5] / 1e3
-    print(json.dumps({"mode": "batching", "metric": "RF-kNN queries/sec, 100k queries per CUDA-graph launch",
-                      "value": nq * args.steps / (total / 1e3), "unit": "queries/s", "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
-                      "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-                      "config": {"workload": "N=10,000,000, d=96 unit-norm 1024-component mixture, inner product, "
-                                             "100,000 queries, widths log-uniform 0.01%-100%, k in {1,10,100}, M=32",
-                                 "params": params.as_dict(), "l2_flush": True},
-                      "recall_sampled_3000": hits / tot, "autotune_train_recall": trec,
-                      "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                     "max": float(lat.max())},
-                      "build_s": round(build_s, 1), "clocks": clk}), flush=True)
-
-
-def run_ours(args, rank, world, local):
-    import torch
-    import paper_2504_04018_gb300 as E
-    from paper_2504_04018_gb300 import replicas as R
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    E.load_library()
-    w = workload(args)
-    t0 = time.perf_counter()
-    ix = E.esg_build(w.base, w.attr, M=32, leaf_size=256, n_entries=16, ef_construction=200,
-                     metric="l2", storage="bf16")
-    E.esg_index_add_storage(ix, "fp8")
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    _, _, perm = E.esg_index_export(ix)
-    Q = torch.as_tensor(w.queries, device=dev)
-    L = torch.as_tensor(w.l, device=dev)
-    Rr = torch.as_tensor(w.r, device=dev)
-    nq = Q.shape[0]
-    Xr = torch.as_tensor(w.base[perm], device=dev)
-
-    def ground_truth(q, l, r):
-        """Exact answers (original ids) from the GPU brute force over the
-        rank-ordered rows."""
-        gi, _, gc = E.esg_bruteforce_filtered_knn(Xr, q, l, r, 10)
-        torch.cuda.synchronize()
-        gi, gc = gi.cpu().numpy(), gc.cpu().numpy()
-        return np.where(gi >= 0, perm[np.maximum(gi, 0)], -1), gc
-
-    gt, gc = ground_truth(Q, L, Rr)
-    bf_info = bruteforce_timing(E, torch, Xr, Q, L, Rr, w, args)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    out = (torch.empty((nq, 10), dtype=torch.int64, device=dev),
-           torch.empty((nq, 10), dtype=torch.float32, device=dev),
-           torch.empty(nq, dtype=torch.int32, device=dev),
-           torch.empty(nq, dtype=torch.int32, device=dev), None)
-    stream = torch.cuda.current_stream()
-    clocks = ClockSampler(local)
-    clocks.start()
-    results = {}
-
-    def timed(step_fn, name):
-        for _ in range(args.warmup):
-            step_fn()
-        torch.cuda.synchronize()
-        R.barrier()
-        torch.cuda.nvtx.range_push(f"timed_{name}")
-        evs = [step_fn() for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        total_ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
-        R.barrier()
-        return total_ms
-
-    def measure(name, params, trav):
-        """Recall, per-step time, kernel time and algorithmic bytes of one
-        parameter setting with direct esg_search_batch calls."""
-        ids, dist, cnt, st, stats = E.esg_search_batch(ix, Q, L, Rr, None, 10, params=params,
-                                                       want_stats=True)
-        torch.cuda.synchronize()
-        rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
-        stats = stats.cpu().numpy()
-        alg_bytes = float(stats[:, 1].sum() * ix.d * ESIZE[trav] + stats[:, 0].sum() * ix.R * 4
-                          + stats[:, 3].sum() * ix.d * 4)
-
-        def one_step():
-            flush.fill_(1.0)
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            E.esg_search_batch(ix, Q, L, Rr, None, 10, params=params, out=out)
-            ev1.record(stream)
-            return ev0, ev1
-
-        E.esg_profile_enable(True)
-        total_ms = timed(one_step, name)
-        kernel_ms, launches, nt = E.esg_profile_read(reset=True)
-        E.esg_profile_enable(False)
-        launches_per_step = launches // max(1, args.steps + args.warmup)
-        return {"trav": trav, "params": params.as_dict(), "recall": round(rec, 5),
-                "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
-                "kernel_ms": kernel_ms / max(1, nt), "alg_bytes": alg_bytes,
-                "launches": launches_per_step * args.steps,
-                "evals_per_query": float(stats[:, 1].mean()),
-                "expansions_per_query": float(stats[:, 0].mean()),
-                # per-query device latency inside the batch (first piece taken
-                # by a warp to last piece finished), from the kernel's timer
-                "latency_us": {"p50": float(np.percentile(stats[:, 5], 50) / 1e3),
-                               "p99": float(np.percentile(stats[:, 5], 99) / 1e3)}}
-
-    sweeps = {}
-    chosen_variants = [v for v in VARIANTS if not args.variants or v[0] in args.variants.split(",")]
-    if not any(v[0] == "plain" for v in chosen_variants):
-        chosen_variants = [VARIANTS[0]] + chosen_variants
-    for name, trav, width in chosen_variants:
-        sweep, chosen = [], args.ef
-        for ef in ([args.ef] if args.ef else EF_SWEEP):
-            ids, _, cnt, _, _ = E.esg_search_batch(ix, Q, L, Rr, None, 10, ef=ef, traversal=trav,
-                                                   width=width)
-            torch.cuda.synchronize()
-            rec = recall_at_10(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc)
-            sweep.append({"ef": ef, "recall": round(rec, 5)})
-            if not args.ef and rec >= TARGET_RECALL:
-                chosen = ef
-                break
-        sweeps[name] = sweep
-        results[name] = measure(name, E.search_params(ef=chosen or EF_SWEEP[-1], traversal=trav,
-                                                      width=width), trav)
-
-    # learned budget + low-precision rows + autotuned launch shape + CUDA graph
-    learned_info = {}
-    if not args.no_learned:
-        mixed = {k: v for k, v in results.items() if k != "plain" and v["recall"] >= TARGET_RECALL
-                 and v["params"]["width"] == 1}
-        trav = results[max(mixed, key=lambda k: mixed[k]["qps"])]["trav"] if mixed else "f32"
-        if args.learned_trav != "auto":
-            trav = args.learned_trav
-        tq, tl, tr = synthetic.training_queries(w, N_TRAIN, 1024, seed=4002)
-        TQ, TL, TR = (torch.as_tensor(a, device=dev) for a in (tq, tl, tr))
-        tgt, tgc = ground_truth(TQ, TL, TR)
-        t1 = time.perf_counter()
-        rep = E.esg_train_predictor(ix, TQ, TL, TR, torch.as_tensor(tgt, device=dev),
-                                    torch.as_tensor(tgc, device=dev), k_max=10,
-                                    target_recall=TARGET_RECALL + 0.005, ef_lo=8, ef_hi=LEARNED_EF_HI,
-                                    traversal=trav, epochs=40, per_query_recall=LEARNED_LABEL_RECALL,
-                                    quantile=LEARNED_QUANTILE)
-        train_s = time.perf_counter() - t1
-        base = E.search_params(ef=LEARNED_EF_HI, traversal=trav, use_learned=1)
-        # launch shape timed on training batches of the benchmark's batch size
-        tuned, trec, tms = E.esg_autotune(ix, TQ[:nq], TL[:nq], TR[:nq], torch.as_tensor(tgt[:nq], device=dev),
-                                          torch.as_tensor(tgc[:nq], device=dev), k_max=10,
-                                          target_recall=TARGET_RECALL, base=base)
-        # both search widths with the tuned launch shape, like the fixed-ef
-        # variants; the faster one that meets the recall target is replayed
-        # as a graph
-        cands = []
-        for wd in (1, 2):
-            pw = E.search_params(**dict(tuned.as_dict(), width=wd))
-            nm = f"learned-{trav}" + ("" if wd == 1 else "-w2")
-            results[nm] = measure(nm, pw, trav)
-            cands.append((nm, pw))
-        ok = [c for c in cands if results[c[0]]["recall"] >= TARGET_RECALL] or cands
-        name, tuned = max(ok, key=lambda c: results[c[0]]["qps"])
-        # the chosen setting replayed as one CUDA graph per batch
-        b = E.Batch(ix, max_nq=nq, k_max=10, params=tuned)
-        b.view("queries", (nq, ix.d), torch.float32).copy_(Q)
-        b.view("l", (nq,), torch.int64).copy_(L)
-        b.view("r", (nq,), torch.int64).copy_(Rr)
-
-        def graph_step():
-            flush.fill_(1.0)
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            b.run(nq, stream=stream)
-            ev1.record(stream)
-            return ev0, ev1
-
-        E.esg_profile_enable(True)
-        total_ms = timed(graph_step, name + "-graph")
-        _, launches, _ = E.esg_profile_read(reset=True)
-        E.esg_profile_enable(False)
-        ids = b.view("ids", (nq, 10), torch.int64).cpu().numpy()
-        cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
-        g = dict(results[name])
-        g.update({"recall": round(recall_at_10(ids, cnt, gt, gc), 5),
-                  "qps": R.job_rate(nq, world, args.steps, total_ms), "ms_per_step": total_ms / args.steps,
-                  "launches": launches // max(1, args.steps + args.warmup) * args.steps, "graph": True})
-        results[name + "-graph"] = g
-        learned_info = {"traversal": trav, "train_queries": N_TRAIN, "ef_hi": LEARNED_EF_HI,
-                        "label_recall": LEARNED_LABEL_RECALL, "quantile": LEARNED_QUANTILE, "train_s": round(train_s, 2),
-                        "train_loss": float(rep[0]), "heldout_recall": float(rep[1]),
-                        "ef_margin_log2": float(rep[2]), "heldout_evals_per_query": float(rep[3]),
-                        "autotune": {"params": tuned.as_dict(), "recall": trec, "ms": tms}}
-    clk = clocks.stop()
-    ok = {k: v for k, v in results.items() if v["recall"] >= TARGET_RECALL}
-    opt = {k: v for k, v in ok.items() if k != "plain"}
-    head_name = max(opt, key=lambda k: opt[k]["qps"]) if opt else "plain"
-    head = results[head_name]
-
-    # end to end through the public call with host buffers (headline setting)
-    Qh = torch.as_tensor(w.queries).pin_memory()
-    Lh = torch.as_tensor(w.l).pin_memory()
-    Rh = torch.as_tensor(w.r).pin_memory()
-    ids_h = torch.empty((nq, 10), dtype=torch.int64).pin_memory()
-    dist_h = torch.empty((nq, 10), dtype=torch.float32).pin_memory()
-    cnt_h = torch.empty(nq, dtype=torch.int32).pin_memory()
-    Qd, Ld, Rd = torch.empty_like(Q), torch.empty_like(L), torch.empty_like(Rr)
-    head_params = E.search_params(**head["params"])
-
-    def e2e_step():
-        flush.fill_(1.0)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        Qd.copy_(Qh, non_blocking=True)
-        Ld.copy_(Lh, non_blocking=True)
-        Rd.copy_(Rh, non_blocking=True)
-        E.esg_search_batch(ix, Qd, Ld, Rd, None, 10, params=head_params, out=out)
-        ids_h.copy_(out[0], non_blocking=True)
-        dist_h.copy_(out[1], non_blocking=True)
-        cnt_h.copy_(out[2], non_blocking=True)
-        ev1.record(stream)
-        return ev0, ev1
-
-    e2e_ms = timed(e2e_step, "e2e")
-    h2d = Qh.numel() * 4 + Lh.numel() * 8 + Rh.numel() * 8
-    d2h = ids_h.numel() * 8 + dist_h.numel() * 4 + cnt_h.numel() * 4
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = head["alg_bytes"] / (head["kernel_ms"] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": measured_traffic(head_name, head["params"]),
-                "kernel": f"search_kernel ({head_name})",
-                "kernel_ms_per_launch": round(head["kernel_ms"], 4),
-                "algorithmic_bytes_per_launch": head["alg_bytes"],
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    variants = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
-                    if kk not in ("alg_bytes",)} for k, v in results.items()}
-    line = {"metric": METRIC_NAME, "value": head["qps"], "unit": "queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": head["trav"], "data": "synthetic",
-            "config": workload_config(args, {"parallelism": f"replicas{world}",
-                                             "variant": head_name, "params": head["params"]}),
-            "recall_at_10": head["recall"],
-            "plain_fp32": {"qps": results["plain"]["qps"], "ef": results["plain"]["params"]["ef"],
-                           "recall_at_10": results["plain"]["recall"]},
-            "speedup_vs_plain": head["qps"] / results["plain"]["qps"],
-            "variants": variants, "ef_sweeps": sweeps, "learned": learned_info,
-            "build_s": round(build_s, 2), "roofline": roofline, "clocks": clk,
-            "bruteforce": bf_info,
-            "e2e": {"value": R.job_rate(nq, world, args.steps, e2e_ms), "unit": "queries/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": head["launches"]}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(ix, w, results["plain"]["params"]["ef"], args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-
-
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -665,10 +758,6 @@ def main():
     if args.mode == "bruteforce":
         if rank == 0:
             run_bruteforce_only(args, local)
-        return
-    if args.mode == "batching":
-        if rank == 0:
-            run_batching(args, local)
         return
     run_ours(args, rank, world, local)
 

@@ -194,6 +194,17 @@ esg_status esg_index_export(const esg_index *index, uint32_t *adj, int32_t *entr
                             int64_t *perm);
 
 /*
+ * Copy rows row0 .. row0 + nrows - 1 of graph level `level` (depth of the
+ * tree) to a host buffer adj [nrows, R] uint32, in the esg_index_export
+ * layout: for one node [node_l, node_r] of that depth, rows node_l..node_r
+ * are the node's whole graph (its edges never leave the node). Lets a caller
+ * read one node of a large index without copying every level.
+ * Synchronous.
+ */
+esg_status esg_index_export_rows(const esg_index *index, int32_t level, int64_t row0, int64_t nrows,
+                                 uint32_t *adj);
+
+/*
  * Copy the index's low-precision traversal rows of type `dtype` to host
  * buffers (rank order): ESG_BF16: rows = [n, d] uint16 bit patterns;
  * ESG_FP8E4M3: rows = [n, d] uint8 E4M3 codes and scale = [n] float32 per-row
@@ -394,6 +405,16 @@ esg_status esg_mlp_adam_step(float *params, const float *grad, float *m, float *
 esg_status esg_query_features(const esg_index *index, const float *queries, int64_t nq,
                               const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
                               float *features, esg_stream_t stream);
+
+/* The per-query search budget the trained predictor gives, exactly as a
+ * search with use_learned = 1 and ef = ef_fixed applies it: ef_out [nq] int32
+ * (the beam width of every piece of the query, at least its k) and
+ * maxexp_out [nq] int32 (the expansion cap of each piece; 0 = the default
+ * cap 16 ef_fixed + 256, used when the network's output is not finite).
+ * Device pointers; asynchronous. ESG_ERR_INVALID_ARG without a predictor. */
+esg_status esg_query_budget(const esg_index *index, const float *queries, int64_t nq, const int64_t *l,
+                            const int64_t *r, const int32_t *k, int32_t k_max, int32_t ef_fixed,
+                            int32_t *ef_out, int32_t *maxexp_out, esg_stream_t stream);
 
 /*
  * Exact range-filtered k-NN by brute force (Definitions 1 and 2): for each

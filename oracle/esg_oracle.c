@@ -102,15 +102,23 @@ static int cmp_item(const void *a, const void *b) {
  *  - Q is trimmed back to ef after each insertion.
  * Passing pl = 0, pr = n - 1 gives the unfiltered search used by the build.
  *
+ * max_exp > 0 caps the expansions (a search budget, not part of Algorithm
+ * 1): when the stop test has not fired but max_exp expansions were made, the
+ * search ends there and counters[2] is incremented; 0 = no cap.
+ *
+ * Rows: X, adj and visited hold the ranks base, base + 1, ... (rank u is
+ * row u - base), so a caller may pass only one node's rows; ids in and out
+ * are ranks.
+ *
  * visited: caller-provided array of n bytes, all zero on entry; it is left
  * zeroed on return. Returns the number of results written (<= ef) in
  * ascending (distance, rank) order. counters[0] += expansions,
- * counters[1] += distance evaluations.
+ * counters[1] += distance evaluations (counters holds 3 entries).
  */
 static int graph_search(const double *X, int d, int metric, const uint32_t *adj, int R,
                         const uint32_t *entries, int n_entries, const double *q, int ef,
                         uint32_t pl, uint32_t pr, uint8_t *visited, item *out,
-                        int64_t *counters) {
+                        int64_t *counters, uint32_t base, int64_t max_exp) {
     heap P, Q;
     heap_init(&P, 4 * ef + 16, 0);
     heap_init(&Q, ef + 2, 1);
@@ -120,11 +128,11 @@ static int graph_search(const double *X, int d, int metric, const uint32_t *adj,
 
     for (int e = 0; e < n_entries; ++e) {
         uint32_t ep = entries[e];
-        if (ep == NONE || visited[ep]) continue;
-        visited[ep] = 1;
+        if (ep == NONE || visited[ep - base]) continue;
+        visited[ep - base] = 1;
         if (n_vis == vis_cap) { vis_cap *= 2; vis_list = (uint32_t *)realloc(vis_list, sizeof(uint32_t) * (size_t)vis_cap); }
         vis_list[n_vis++] = ep;
-        item it = { dist(q, X + (size_t)ep * d, d, metric), ep };
+        item it = { dist(q, X + (size_t)(ep - base) * d, d, metric), ep };
         ++evals;
         heap_push(&P, it);
         if (ep >= pl && ep <= pr) {
@@ -135,16 +143,20 @@ static int graph_search(const double *X, int d, int metric, const uint32_t *adj,
     while (P.n > 0) {
         item u = heap_pop(&P);
         if (Q.n == ef && item_less(Q.v[0], u)) break;      /* u farther than Q.top() */
+        if (max_exp > 0 && expansions >= max_exp) {        /* expansion budget spent */
+            if (counters) counters[2] += 1;
+            break;
+        }
         ++expansions;
-        const uint32_t *nb = adj + (size_t)u.id * R;
+        const uint32_t *nb = adj + (size_t)(u.id - base) * R;
         for (int j = 0; j < R; ++j) {
             uint32_t v = nb[j];
             if (v == NONE) continue;
-            if (visited[v]) continue;
-            visited[v] = 1;
+            if (visited[v - base]) continue;
+            visited[v - base] = 1;
             if (n_vis == vis_cap) { vis_cap *= 2; vis_list = (uint32_t *)realloc(vis_list, sizeof(uint32_t) * (size_t)vis_cap); }
             vis_list[n_vis++] = v;
-            item it = { dist(q, X + (size_t)v * d, d, metric), v };
+            item it = { dist(q, X + (size_t)(v - base) * d, d, metric), v };
             ++evals;
             if (Q.n < ef || item_less(it, Q.v[0])) {
                 heap_push(&P, it);                           /* P <- P u {v} */
@@ -157,22 +169,25 @@ static int graph_search(const double *X, int d, int metric, const uint32_t *adj,
     }
     int cnt = Q.n;
     for (int i = cnt - 1; i >= 0; --i) out[i] = heap_pop(&Q);
-    for (int i = 0; i < n_vis; ++i) visited[vis_list[i]] = 0;
+    for (int i = 0; i < n_vis; ++i) visited[vis_list[i] - base] = 0;
     free(vis_list);
     heap_free(&P); heap_free(&Q);
     if (counters) { counters[0] += expansions; counters[1] += evals; }
     return cnt;
 }
 
-/* Exported search: one graph level, one query. */
+/* Exported search: one graph, one query; X and adj_level hold the n rows of
+ * ranks row_base .. row_base + n - 1 (a whole level with row_base = 0, or
+ * one node's rows: its edges never leave it). */
 int oracle_graph_search(const double *X, int64_t n, int d, int metric, const uint32_t *adj_level,
                         int R, const uint32_t *entries, int n_entries, const double *q, int ef,
                         int64_t pl, int64_t pr, uint32_t *out_ids, double *out_dist,
-                        int64_t *counters) {
+                        int64_t *counters, int64_t row_base, int64_t max_exp) {
     uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
     item *out = (item *)malloc(sizeof(item) * (size_t)(ef > 0 ? ef : 1));
     int cnt = graph_search(X, d, metric, adj_level, R, entries, n_entries, q, ef,
-                           (uint32_t)pl, (uint32_t)pr, visited, out, counters);
+                           (uint32_t)pl, (uint32_t)pr, visited, out, counters, (uint32_t)row_base,
+                           max_exp);
     for (int i = 0; i < cnt; ++i) { out_ids[i] = out[i].id; out_dist[i] = out[i].d; }
     free(out); free(visited);
     return cnt;
@@ -237,7 +252,7 @@ static void insert_point(build_ctx *c, int depth, int64_t l, int64_t v) {
     uint32_t ep = (uint32_t)l;
     item *W = c->buf;
     int nw = graph_search(c->X, c->d, c->metric, row(c, depth, 0), c->R, &ep, 1, xv, c->efc,
-                          0, (uint32_t)(c->n - 1), c->visited, W, NULL);
+                          0, (uint32_t)(c->n - 1), c->visited, W, NULL, 0, 0);
     uint32_t sel[1024];
     int ns = select_neighbours(c->X, c->d, c->metric, W, nw, c->M, sel);
     for (int s = 0; s < ns; ++s) rv[s] = sel[s];

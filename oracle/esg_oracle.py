@@ -31,7 +31,7 @@ METRICS = {"l2": 0, "ip": 1}
 
 __all__ = [
     "build_c", "rerank", "is_leaf", "split", "Piece", "decompose", "graph_depths",
-    "bruteforce", "merge_topk", "OracleIndex", "build_index", "graph_search",
+    "bruteforce", "merge_topk", "OracleIndex", "build_index", "graph_search", "graph_search_rows",
     "search", "recall_at_k", "distances", "METRICS", "NONE", "bf16_round", "bf16_to_float",
     "fp8_e4m3_grid", "fp8_quantize_rows", "fp8_to_float", "traversal_rows",
 ]
@@ -60,7 +60,8 @@ def _c():
         lib.oracle_graph_search.restype = ctypes.c_int
         lib.oracle_graph_search.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, P,
                                             ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
-                                            ctypes.c_int64, ctypes.c_int64, P, P, P]
+                                            ctypes.c_int64, ctypes.c_int64, P, P, P, ctypes.c_int64,
+                                            ctypes.c_int64]
         lib.oracle_build.restype = ctypes.c_int
         lib.oracle_build.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
@@ -336,28 +337,47 @@ def build_index(base: np.ndarray, attr: Optional[np.ndarray], metric: str, leaf_
 
 def graph_search(index: OracleIndex, depth: int, heap: int, q: np.ndarray, ef: int,
                  pl: int, pr: int, counters: Optional[np.ndarray] = None,
-                 X: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray]:
+                 X: Optional[np.ndarray] = None, max_expansions: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Algorithm 1 with POST filtering to [pl, pr] on the graph of heap node
     `heap` (at `depth`), from that node's entry points, over the rows X
     (default: the index's float64 rows). Returns up to ef (ranks, distances)
-    ascending."""
+    ascending. max_expansions > 0 caps the expansions (a search budget)."""
     X = index.X if X is None else np.ascontiguousarray(X, dtype=np.float64)
+    return graph_search_rows(X, index.adj[depth], index.entries[heap], index.metric, q, ef, pl, pr,
+                             counters, max_expansions=max_expansions)
+
+
+def graph_search_rows(X: np.ndarray, adj: np.ndarray, entries: np.ndarray, metric: str, q: np.ndarray,
+                      ef: int, pl: int, pr: int, counters: Optional[np.ndarray] = None,
+                      row_base: int = 0, max_expansions: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """Algorithm 1 with POST filtering to [pl, pr] on one graph given by its
+    rows: X float64 and adj uint32 [rows, R] hold the ranks row_base,
+    row_base + 1, ... (a whole level, or one node's rows, whose edges stay
+    inside the node); entries are ranks (-1 padded). Returns up to ef
+    (ranks, distances) ascending. counters (int64, 2 or 3 entries)
+    accumulates expansions, distance evaluations and searches ended by the
+    max_expansions cap (0 = no cap)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    adj = np.ascontiguousarray(adj, dtype=np.uint32)
     q64 = np.ascontiguousarray(q, dtype=np.float64)
-    ent = np.ascontiguousarray(index.entries[heap].astype(np.uint32))
-    ent_n = int(np.sum(index.entries[heap] >= 0))
-    adj = np.ascontiguousarray(index.adj[depth])
+    entries = np.asarray(entries)
+    ent = np.ascontiguousarray(entries[entries >= 0].astype(np.uint32))
     ids = np.empty(ef, dtype=np.uint32)
     dd = np.empty(ef, dtype=np.float64)
-    cnt_arr = counters if counters is not None else np.zeros(2, dtype=np.int64)
-    cnt = _c().oracle_graph_search(_ptr(X), X.shape[0], X.shape[1], METRICS[index.metric],
-                                   _ptr(adj), index.R, _ptr(ent), ent_n, _ptr(q64), ef,
-                                   pl, pr, _ptr(ids), _ptr(dd), _ptr(cnt_arr))
+    cnt_arr = np.zeros(3, dtype=np.int64)
+    cnt = _c().oracle_graph_search(_ptr(X), X.shape[0], X.shape[1], METRICS[metric],
+                                   _ptr(adj), adj.shape[1], _ptr(ent) if len(ent) else None, len(ent),
+                                   _ptr(q64), ef, pl, pr, _ptr(ids), _ptr(dd), _ptr(cnt_arr), row_base,
+                                   max_expansions)
+    if counters is not None:
+        m = min(len(counters), 3)
+        counters[:m] += cnt_arr[:m]
     return ids[:cnt].astype(np.int64), dd[:cnt].copy()
 
 
 def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
-           counters: Optional[np.ndarray] = None, trav_X: Optional[np.ndarray] = None
-           ) -> Tuple[np.ndarray, np.ndarray]:
+           counters: Optional[np.ndarray] = None, trav_X: Optional[np.ndarray] = None,
+           max_expansions: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Query-2D-Index (Algorithm 4): decompose [lq, rq]; answer scan pieces
     exactly and graph pieces with Algorithm 1 + POST at beam width
     max(ef, k); merge into the top k by (distance, rank). Returns ranks.
@@ -365,7 +385,7 @@ def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
     With `trav_X` (rows as stored in low precision, see traversal_rows) the
     traversal and scans use those rows, each piece keeps its best max(ef, k)
     in-range candidates, and these are re-ranked with the exact rows before
-    the merge."""
+    the merge. max_expansions > 0 caps each graph piece's expansions."""
     parts = []
     w = max(ef, k)
     for p in decompose(index.n, index.leaf_size, lq, rq):
@@ -373,13 +393,15 @@ def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
             if p.kind == "scan":
                 parts.append(bruteforce(index.X, q, p.pl, p.pr, k, index.metric))
             else:
-                ids, dd = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters)
+                ids, dd = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters,
+                                       max_expansions=max_expansions)
                 parts.append((ids[:k], dd[:k]))
             continue
         if p.kind == "scan":
             ids, _ = bruteforce(trav_X, q, p.pl, p.pr, w, index.metric)
         else:
-            ids, _ = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters, X=trav_X)
+            ids, _ = graph_search(index, p.depth, p.heap, q, w, p.pl, p.pr, counters, X=trav_X,
+                                  max_expansions=max_expansions)
         exact = distances(index.X[ids], q, index.metric)
         order = np.lexsort((ids, exact))[:k]
         parts.append((ids[order], exact[order]))

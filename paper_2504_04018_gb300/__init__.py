@@ -37,7 +37,7 @@ EXPORTED = [
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
     "esg_train_params_default", "esg_train_predictor", "esg_predictor_set", "esg_predictor_get",
     "esg_mlp_num_params", "esg_mlp_num_features", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
-    "esg_query_features",
+    "esg_query_features", "esg_query_budget", "esg_index_export_rows",
 ]
 
 
@@ -94,6 +94,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                      ctypes.POINTER(_P)]
     lib.esg_index_info.argtypes = [_P] + [_P] * 8
     lib.esg_index_export.argtypes = [_P, _P, _P, _P]
+    lib.esg_index_export_rows.argtypes = [_P, _I32, _I64, _I64, _P]
     lib.esg_index_export_storage.argtypes = [_P, _I32, _P, _P]
     lib.esg_index_add_storage.argtypes = [_P, _I32]
     lib.esg_free.argtypes = [_P]
@@ -121,6 +122,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_mlp_loss_grad.argtypes = [_P, _P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]
     lib.esg_mlp_adam_step.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_float, _P]
     lib.esg_query_features.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _P, _P]
+    lib.esg_query_budget.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, _I32, _P, _P, _P]
     lib.esg_search_batch_noalloc.argtypes = [_P, _P, _I64, _P, _P, _P, _I32,
                                              ctypes.POINTER(_SearchParams), _P, _P, _P, _P, _P, _P]
     lib.esg_batch_create.argtypes = [_P, _I64, _I32, _I32, ctypes.POINTER(_SearchParams), ctypes.POINTER(_P)]
@@ -133,14 +135,14 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_status_str.restype = ctypes.c_char_p
     lib.esg_status_str.argtypes = [_I32]
     lib.esg_last_error.restype = ctypes.c_char_p
-    for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export",
+    for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export", "esg_index_export_rows",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
                  "esg_profile_read", "esg_profile_tensor_work", "esg_index_export_storage", "esg_index_add_storage",
                  "esg_batch_create", "esg_batch_buffers", "esg_batch_run", "esg_autotune",
                  "esg_search_batch_noalloc", "esg_train_predictor", "esg_predictor_set",
                  "esg_predictor_get", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
-                 "esg_query_features"]:
+                 "esg_query_features", "esg_query_budget"]:
         getattr(lib, name).restype = _I32
     _lib = lib
     return lib
@@ -253,6 +255,30 @@ def esg_index_export(index: Index) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
                                 _np_ptr(ent) if ent.size else None, _np_ptr(perm)),
            "esg_index_export")
     return adj, ent, perm
+
+
+def esg_index_export_entries(index: Index) -> np.ndarray:
+    """Entry ranks per graph node: int32 [nodes, E], -1 padded."""
+    ent = np.empty(((1 << index.L) - 1, index.E), dtype=np.int32)
+    _check(load_library().esg_index_export(index.handle, None, _np_ptr(ent) if ent.size else None, None),
+           "esg_index_export")
+    return ent
+
+
+def esg_index_perm(index: Index) -> np.ndarray:
+    """Original id of each rank: int64 [n]."""
+    perm = np.empty(index.n, dtype=np.int64)
+    _check(load_library().esg_index_export(index.handle, None, None, _np_ptr(perm)), "esg_index_export")
+    return perm
+
+
+def esg_index_export_rows(index: Index, level: int, row0: int, nrows: int) -> np.ndarray:
+    """Rows row0 .. row0 + nrows - 1 of one graph level: uint32 [nrows, R]."""
+    adj = np.empty((nrows, index.R), dtype=np.uint32)
+    _check(load_library().esg_index_export_rows(index.handle, level, row0, nrows,
+                                                _np_ptr(adj) if adj.size else None),
+           "esg_index_export_rows")
+    return adj
 
 
 def esg_index_export_storage(index: Index, dtype: str):
@@ -607,3 +633,16 @@ def esg_query_features(index: Index, queries, l, r, k=None, k_max: int = 10, str
                                              _dev_ptr(l), _dev_ptr(r), _dev_ptr(k), k_max, _dev_ptr(f),
                                              _stream_ptr(stream)), "esg_query_features")
     return f
+
+
+def esg_query_budget(index: Index, queries, l, r, k=None, k_max: int = 10, ef_fixed: int = 64, stream=None):
+    """Per-query (ef, expansion cap) the trained predictor gives, as CUDA
+    int32 tensors [nq] (cap 0 = the default 16 ef_fixed + 256)."""
+    import torch
+    nq = queries.shape[0]
+    ef = torch.empty(nq, dtype=torch.int32, device=queries.device)
+    mx = torch.empty(nq, dtype=torch.int32, device=queries.device)
+    _check(load_library().esg_query_budget(index.handle, _dev_ptr(queries), nq, _dev_ptr(l), _dev_ptr(r),
+                                           _dev_ptr(k), k_max, ef_fixed, _dev_ptr(ef), _dev_ptr(mx),
+                                           _stream_ptr(stream)), "esg_query_budget")
+    return ef, mx

@@ -268,6 +268,18 @@ esg_status esg_index_export(const esg_index *ix, uint32_t *adj, int32_t *entries
     return ESG_OK;
 }
 
+esg_status esg_index_export_rows(const esg_index *ix, int32_t level, int64_t row0, int64_t nrows,
+                                 uint32_t *adj) {
+    if (!ix || (!adj && nrows > 0) || level < 0 || level >= ix->L || row0 < 0 || nrows < 0 || row0 + nrows > ix->n) {
+        esg_set_error("esg_index_export_rows: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (nrows > 0)
+        ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj + ((size_t)level * ix->n + row0) * ix->R,
+                                sizeof(uint32_t) * nrows * ix->R, cudaMemcpyDeviceToHost));
+    return ESG_OK;
+}
+
 esg_status esg_index_export_storage(const esg_index *ix, esg_dtype dtype, void *rows, float *scale) {
     if (!ix || !rows) { esg_set_error("esg_index_export_storage: bad argument"); return ESG_ERR_INVALID_ARG; }
     const size_t count = (size_t)ix->n * ix->d;

@@ -394,6 +394,26 @@ esg_status esg_query_features(const esg_index *ix, const float *queries, int64_t
     return ESG_OK;
 }
 
+esg_status esg_query_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+                            const int64_t *r, const int32_t *k, int32_t k_max, int32_t ef_fixed,
+                            int32_t *ef_out, int32_t *maxexp_out, esg_stream_t stream_v) {
+    if (!ix || nq < 0 || nq >= kMaxBatch || k_max < 1 || k_max > 1024 || ef_fixed < 1 || ef_fixed > 1024 ||
+        (nq > 0 && (!queries || !l || !r || !ef_out || !maxexp_out))) {
+        esg_set_error("esg_query_budget: bad argument");
+        return ESG_ERR_INVALID_ARG;
+    }
+    if (!ix->mlp_ready) { esg_set_error("esg_query_budget: no trained predictor"); return ESG_ERR_INVALID_ARG; }
+    if (nq == 0) return ESG_OK;
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    float *feat = nullptr;
+    ESG_CUDA_TRY(cudaMallocAsync((void **)&feat, sizeof(float) * nq * kF, stream));
+    esg_status st = esg_predict_budget(ix, queries, nq, l, r, k, k_max, ef_fixed, feat, ef_out, maxexp_out,
+                                       stream);
+    const cudaError_t fe = cudaFreeAsync(feat, stream);
+    if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }
+    return st;
+}
+
 esg_status esg_predictor_set(esg_index *ix, const float *blob_host, int32_t ef_lo, int32_t ef_hi) {
     if (!ix || !blob_host || ef_lo < 1 || ef_hi < ef_lo || ef_hi > 1024) { esg_set_error("esg_predictor_set: bad argument"); return ESG_ERR_INVALID_ARG; }
     const size_t n = (size_t)kP + 2 * kF + 2;

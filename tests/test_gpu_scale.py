@@ -124,3 +124,90 @@ def test_precision_workload(dtype):
     print(f"precision {dtype}: recall@10 {rec:.4f}, max |distance error| {max(errs):.2e}")
     assert max(errs) <= 1e-5        # re-ranked (or FP32) distances are exact to FP32 rounding
     assert rec >= 0.95
+
+
+# ------------------------------------------ parity with the oracle at 1M points
+
+PARITY_Q = 1000          # the first queries of the workload: every width 2^-j N
+
+
+@pytest.fixture(scope="module")
+def scale_oracle(scale_index):
+    """The oracle's view of the GPU-built 1M index: the same graphs (exported),
+    the same rank-ordered rows in float64."""
+    w, ix, perm = scale_index
+    adj, ent, _ = E.esg_index_export(ix)
+    X32 = np.ascontiguousarray(w.base[perm])
+    oi = O.OracleIndex(X32.astype(np.float64), perm, adj, ent, ix.leaf_size, ix.R // 2, "l2")
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    gi, _, gc = E.esg_bruteforce_filtered_knn(_t(X32), q, l, r, 10)
+    torch.cuda.synchronize()
+    return oi, X32, gi.cpu().numpy(), gc.cpu().numpy()
+
+
+def _parity(w, ix, perm, oi, ids, cnt, gi, gc, ef_of, trav_X, cap_of):
+    """GPU results of the first PARITY_Q queries against the oracle's
+    Algorithm 4 + Algorithm 1 on the same graph, beam width and expansion
+    cap: recall@10 (against the exact answers) within 0.5 points, and at
+    least 95 % of the queries with identical result lists."""
+    inv = np.empty(len(perm), np.int64)
+    inv[perm] = np.arange(len(perm))
+    same = hg = hc = tot = 0
+    for i in range(PARITY_Q):
+        l, r = int(w.l[i]), int(w.r[i])
+        gpu = inv[ids[i, :cnt[i]]]
+        cpu, _ = O.search(oi, w.queries[i], l, r, 10, ef_of(i), trav_X=trav_X, max_expansions=cap_of(i))
+        exact = set(gi[i, :gc[i]].tolist())
+        hg += len(set(gpu.tolist()) & exact)
+        hc += len(set(cpu.tolist()) & exact)
+        tot += int(gc[i])
+        same += gpu.tolist() == cpu.tolist()
+    rg, rc = hg / tot, hc / tot
+    print(f"parity: GPU recall {rg:.4f}, oracle recall {rc:.4f}, identical {same}/{PARITY_Q}")
+    assert abs(rg - rc) <= 0.005, (rg, rc)
+    assert same >= 0.95 * PARITY_Q, same
+
+
+@pytest.mark.parametrize("variant", ["f32", "bf16", "fp8", "f32-bench-shape"])
+def test_scale_parity_with_oracle_algorithm1(scale_index, scale_oracle, variant):
+    """The GPU search on the GPU-built 1M index against the oracle's
+    Algorithm 1 on the same exported graph at ef 24: FP32 rows, BF16 and FP8
+    rows (the oracle traverses the same decoded values and re-ranks exactly),
+    and the launch shape of the benchmark (4 warps per block, 2,048 shared
+    visited slots so that searches spill into the global overflow table,
+    4 lanes per row)."""
+    w, ix, perm = scale_index
+    oi, X32, gi, gc = scale_oracle
+    trav = variant.split("-")[0]
+    kw = dict(warps_per_block=4, hash_slots=2048, lanes_per_row=4) if variant.endswith("shape") else {}
+    params = E.search_params(ef=24, traversal=trav, **kw)
+    q, l, r = (_t(a[:PARITY_Q]) for a in (w.queries, w.l, w.r))
+    ids, _, cnt, st, _ = E.esg_search_batch(ix, q, l, r, None, 10, params=params)
+    torch.cuda.synchronize()
+    trav_X = None if trav == "f32" else O.traversal_rows(X32, trav)
+    _parity(w, ix, perm, oi, ids.cpu().numpy(), cnt.cpu().numpy(), gi, gc, lambda i: 24, trav_X,
+            lambda i: 16 * 24 + 256)
+
+
+def test_scale_parity_learned_budget(scale_index, scale_oracle):
+    """The learned budget on BF16 rows: the oracle runs each query at the beam
+    width and expansion cap the predictor gave it (esg_query_budget)."""
+    w, ix, perm = scale_index
+    oi, X32, gi, gc = scale_oracle
+    tq, tl, tr = synthetic.training_queries(w, 8000, 1024, seed=4100)
+    gtq, _, gtc = E.esg_bruteforce_filtered_knn(_t(X32), _t(tq), _t(tl), _t(tr), 10)
+    torch.cuda.synchronize()
+    gtq = torch.as_tensor(np.where(gtq.cpu().numpy() >= 0, perm[np.maximum(gtq.cpu().numpy(), 0)], -1),
+                          device=DEV)
+    E.esg_train_predictor(ix, _t(tq), _t(tl), _t(tr), gtq, gtc, k_max=10, target_recall=0.955,
+                          ef_lo=8, ef_hi=64, traversal="bf16", epochs=20)
+    q, l, r = (_t(a[:PARITY_Q]) for a in (w.queries, w.l, w.r))
+    params = E.search_params(ef=64, traversal="bf16", use_learned=1)
+    ids, _, cnt, st, _ = E.esg_search_batch(ix, q, l, r, None, 10, params=params)
+    ef_q, mx_q = E.esg_query_budget(ix, q, l, r, None, 10, ef_fixed=64)
+    torch.cuda.synchronize()
+    ef_q, mx_q = ef_q.cpu().numpy(), mx_q.cpu().numpy()
+    assert np.all((ef_q >= 10) & (ef_q <= 64))
+    print(f"learned budget: ef {np.percentile(ef_q, [5, 50, 95])}, cap {np.percentile(mx_q, [5, 50, 95])}")
+    _parity(w, ix, perm, oi, ids.cpu().numpy(), cnt.cpu().numpy(), gi, gc, lambda i: int(ef_q[i]),
+            O.traversal_rows(X32, "bf16"), lambda i: int(mx_q[i]) if mx_q[i] > 0 else 16 * 64 + 256)

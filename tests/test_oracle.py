@@ -614,3 +614,38 @@ def test_recall_at_k_hand_case():
     empty0 = np.mean([len(set(fo.tolist()) & set(t.tolist())) / len(t) if len(t) else 0.0
                       for fo, t in zip(found, truth)])
     assert dup == pytest.approx(0.6875) and empty0 == pytest.approx(0.375)
+
+
+def test_node_rows_search_equals_level_search(small_index):
+    """Searching one node from its own rows (row_base = the node's first rank)
+    gives the same answer as searching it inside the whole level: a node's
+    edges never leave it."""
+    w, idx = small_index
+    for i in range(30):
+        for p in O.decompose(idx.n, idx.leaf_size, int(w.l[i]), int(w.r[i])):
+            if p.kind != "graph":
+                continue
+            a = O.graph_search(idx, p.depth, p.heap, w.queries[i], 12, p.pl, p.pr)
+            rows = slice(p.node_l, p.node_r + 1)
+            b = O.graph_search_rows(idx.X[rows], idx.adj[p.depth][rows], idx.entries[p.heap], w.metric,
+                                    w.queries[i], 12, p.pl, p.pr, row_base=p.node_l)
+            assert a[0].tolist() == b[0].tolist() and np.array_equal(a[1], b[1])
+
+
+def test_graph_search_expansion_cap_hand_trace():
+    """The first hand trace of tests/golden/alg1_traces.json (q = 5.2, entry 0,
+    ef = 2, full range) with at most 3 expansions: expanding 0, 1, 2 reaches
+    1, 2, 3 (Q = {3, 2}); rank 3 is popped, passes the stop test (Q's worst
+    is 2 at 10.24 > 4.84) and the budget ends the search: result [3, 2],
+    3 expansions, 4 distance evaluations, one capped search. A cap of 7 or
+    more does not change the uncapped trace."""
+    g = json.load(open(os.path.join(GOLDEN, "alg1_traces.json")))
+    c = g["cases"][0]
+    idx = _path_index(g["points_1d"], g["adjacency"], c["entries"], g["metric"])
+    cnt = np.zeros(3, np.int64)
+    ids, dd = O.graph_search(idx, 0, 0, np.array([c["q"]]), c["ef"], 0, 7, cnt, max_expansions=3)
+    assert ids.tolist() == [3, 2] and np.allclose(dd, [4.84, 10.24], atol=1e-12)
+    assert cnt.tolist() == [3, 4, 1]
+    cnt = np.zeros(3, np.int64)
+    ids, _ = O.graph_search(idx, 0, 0, np.array([c["q"]]), c["ef"], 0, 7, cnt, max_expansions=7)
+    assert ids.tolist() == c["result_ranks"] and cnt.tolist() == [7, 8, 0]

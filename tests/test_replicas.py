@@ -100,7 +100,7 @@ def test_roofline_traffic_only_for_unchanged_kernel(tmp_path, monkeypatch):
     name, r = next(iter(rec.items()))
     params = dict(r["params"], max_expansions=0, rerank=1, warps_per_block=1, hash_slots=0,
                   lanes_per_row=4)
-    assert bench.measured_traffic("some-other-variant", params) is None
+    assert bench.measured_traffic("scale:some-other-variant", params) is None
     assert bench.measured_traffic(name, dict(params, ef=params["ef"] + 1)) is None
     # a copy of the tree whose kernel source differs by one byte
     root = tmp_path / "tree"
