@@ -1,6 +1,7 @@
 /*
- * ESG CPU oracle: graph search (Algorithm 1 with the POST principle) and the
- * general-range index build (Algorithm 3), in plain single-threaded C with
+ * ESG CPU oracle: graph search (Algorithm 1 with the POST principle), the
+ * general-range index build (Algorithm 3, any fanout) and the half-bounded
+ * index build (Algorithm 2, any base), in plain single-threaded C with
  * float64 arithmetic.
  *
  * TEST INFRASTRUCTURE ONLY. This file is the slow, obviously-correct reference
@@ -215,19 +216,20 @@ static int select_neighbours(const double *X, int d, int metric, const item *can
     return kept;
 }
 
-/* ------------------------------------------------------ Algorithm 3 build */
+/* ------------------------------------------------- Algorithms 2 and 3 build */
 
 typedef struct {
-    const double *X; int d, metric, leaf, M, R, efc, E, L;
+    const double *X; int d, metric, leaf, M, R, efc, E, L, f;
     int64_t n;
-    uint32_t *adj;        /* [L][n][R] */
-    int32_t *entries;     /* [2^L - 1][E] */
+    uint32_t *adj;           /* the rows of every level */
+    const int64_t *row_off;  /* rank i of level t is row row_off[t] + i of adj */
+    int32_t *entries;        /* [graph nodes][E] */
     uint8_t *visited;
-    item *buf;            /* scratch, efc + R + 1 items */
+    item *buf;               /* scratch, efc + R + 1 items */
 } build_ctx;
 
-static uint32_t *row(build_ctx *c, int depth, int64_t i) {
-    return c->adj + ((size_t)depth * (size_t)c->n + (size_t)i) * (size_t)c->R;
+static uint32_t *row(build_ctx *c, int level, int64_t i) {
+    return c->adj + ((size_t)c->row_off[level] + (size_t)i) * (size_t)c->R;
 }
 
 static int degree(const uint32_t *r, int R) {
@@ -282,48 +284,115 @@ static void set_entries(build_ctx *c, int64_t h, int64_t l, int64_t r) {
     for (int i = 0; i < cnt; ++i) e[i] = (int32_t)(l + (int64_t)i * n / cnt);
 }
 
+/* First rank of child j of node [l, r] in a tree of fanout f:
+ * l + ceil(j * len / f); child j is [child_lo(j), child_lo(j + 1) - 1], empty
+ * when the node has fewer than f points. For f = 2, child 0 is [l, mid]. */
+static int64_t child_lo(int64_t l, int64_t r, int f, int j) {
+    int64_t len = r - l + 1;
+    return l + ((int64_t)j * len + f - 1) / f;
+}
+
 /*
  * Build-2D-Index (Algorithm 3) for the node with heap number h covering
- * [l, r] at `depth`. Returns 1 when the node got a graph, 0 for a leaf
- * (r - l < leaf: no graph). The graph of [l, r] is a copy of the left child's
- * graph (built from scratch over [l, mid] when the left child is a leaf)
- * with the points mid+1..r inserted in increasing rank order; the left
- * child's stored graph is left untouched (memory snapshot).
+ * [l, r] at `depth`, in a tree of fanout f (children of heap node h are
+ * f h + 1 + j). Returns 1 when the node got a graph, 0 for a leaf
+ * (r - l < leaf: no graph). The graph of [l, r] is a copy of its first
+ * child's graph (built from scratch over that child when the child is a leaf)
+ * with the remaining points of [l, r] inserted in increasing rank order; the
+ * child's stored graph is left untouched (memory snapshot). With f = 2 this
+ * is Algorithm 3 as printed; larger f is the extension of Section 4.2.
  */
 static int build_node(build_ctx *c, int64_t h, int depth, int64_t l, int64_t r) {
     if (r - l < c->leaf) return 0;
-    int64_t mid = (l + r) / 2;
-    int left = build_node(c, 2 * h + 1, depth + 1, l, mid);
-    build_node(c, 2 * h + 2, depth + 1, mid + 1, r);
-    if (left) {
-        for (int64_t i = l; i <= mid; ++i)
+    int first = 0;
+    for (int j = 0; j < c->f; ++j) {
+        int64_t a = child_lo(l, r, c->f, j), b = child_lo(l, r, c->f, j + 1) - 1;
+        if (a > b) continue;
+        int g = build_node(c, (int64_t)c->f * h + 1 + j, depth + 1, a, b);
+        if (j == 0) first = g;
+    }
+    int64_t b1 = child_lo(l, r, c->f, 1);
+    if (first) {
+        for (int64_t i = l; i < b1; ++i)
             memcpy(row(c, depth, i), row(c, depth + 1, i), sizeof(uint32_t) * (size_t)c->R);
     } else {
-        for (int64_t i = l; i <= mid; ++i) insert_point(c, depth, l, i);
+        for (int64_t i = l; i < b1; ++i) insert_point(c, depth, l, i);
     }
-    for (int64_t i = mid + 1; i <= r; ++i) insert_point(c, depth, l, i);
+    for (int64_t i = b1; i <= r; ++i) insert_point(c, depth, l, i);
     set_entries(c, h, l, r);
     return 1;
 }
 
+static int64_t tree_nodes(int L, int f) {
+    int64_t total = 0, w = 1;
+    for (int t = 0; t < L; ++t) { total += w; w *= f; }
+    return total;
+}
+
 /*
- * Exported build. X: [n, d] float64, rank order. adj: [L][n][R] output
- * (filled with NONE for rows that belong to leaves at a depth). entries:
- * [2^L - 1][E] output (-1 where a node has no graph). L must be the number of
- * depths that contain at least one graph node. Returns 0 on success.
+ * Exported build of the segment tree (ESG-2D). X: [n, d] float64, rank
+ * order. adj: [L][n][R] output (NONE for rows that belong to leaves at a
+ * depth). entries: [(f^L - 1) / (f - 1)][E] output (-1 where a node has no
+ * graph). L must be the number of depths that contain at least one graph
+ * node for this fanout. Returns 0 on success.
  */
 int oracle_build(const double *X, int64_t n, int d, int metric, int leaf, int M, int efc, int E,
-                 int L, uint32_t *adj, int32_t *entries) {
-    if (n <= 0 || d <= 0 || M <= 0 || efc <= 0 || E <= 0 || L < 0) return 1;
+                 int L, uint32_t *adj, int32_t *entries, int fanout) {
+    if (n <= 0 || d <= 0 || M <= 0 || efc <= 0 || E <= 0 || L < 0 || fanout < 2) return 1;
     build_ctx c;
     c.X = X; c.n = n; c.d = d; c.metric = metric; c.leaf = leaf; c.M = M; c.R = 2 * M;
-    c.efc = efc; c.E = E; c.L = L; c.adj = adj; c.entries = entries;
+    c.efc = efc; c.E = E; c.L = L; c.f = fanout; c.adj = adj; c.entries = entries;
     if (c.R > 1024 || M > 1024) return 1;
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(L > 0 ? L : 1));
+    for (int t = 0; t < L; ++t) off[t] = (int64_t)t * n;
+    c.row_off = off;
     memset(adj, 0xFF, sizeof(uint32_t) * (size_t)L * (size_t)n * (size_t)c.R);
-    for (int64_t i = 0; i < (((int64_t)1 << L) - 1) * (int64_t)E; ++i) entries[i] = -1;
+    for (int64_t i = 0; i < tree_nodes(L, fanout) * (int64_t)E; ++i) entries[i] = -1;
     c.visited = (uint8_t *)calloc((size_t)n, 1);
     c.buf = (item *)malloc(sizeof(item) * (size_t)(efc + c.R + 2));
     if (L > 0) build_node(&c, 0, 0, 0, n - 1);
-    free(c.visited); free(c.buf);
+    free(c.visited); free(c.buf); free(off);
+    return 0;
+}
+
+/*
+ * Build-1D-Index (Algorithm 2; base B, the extension of Section 4.1): graphs
+ * over the prefixes [0, n_i - 1], n_i = floor(n / B^i), for i = 0..L-1 with
+ * every n_i >= 1. The points are inserted into one graph in increasing rank
+ * order (Algorithm 2's loop, reading "insert v_i, i in (pre, cur]"), and the
+ * graph is copied out (snapshot) each time it holds exactly n_i points.
+ * Level i's rows sit at row offset n_0 + ... + n_{i-1} of adj (total rows
+ * the sum of the n_i); level 0, the whole graph, is the working graph.
+ * Insertion searches start from rank 0. entries: [L][E], E ranks evenly
+ * spaced over each prefix. Returns 0 on success.
+ */
+int oracle_build_prefix(const double *X, int64_t n, int d, int metric, int B, int M, int efc, int E,
+                        int L, uint32_t *adj, int32_t *entries) {
+    if (n <= 0 || d <= 0 || M <= 0 || efc <= 0 || E <= 0 || L <= 0 || B < 2) return 1;
+    build_ctx c;
+    c.X = X; c.n = n; c.d = d; c.metric = metric; c.leaf = 0; c.M = M; c.R = 2 * M;
+    c.efc = efc; c.E = E; c.L = L; c.f = B; c.adj = adj; c.entries = entries;
+    if (c.R > 1024 || M > 1024) return 1;
+    int64_t *size = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)L);
+    int64_t total = 0, m = n;
+    for (int i = 0; i < L; ++i) { size[i] = m; off[i] = total; total += m; m /= B; }
+    if (size[L - 1] < 1 || m >= 1) { free(size); free(off); return 1; }   /* L must cover every n_i >= 1 */
+    c.row_off = off;
+    memset(adj, 0xFF, sizeof(uint32_t) * (size_t)total * (size_t)c.R);
+    for (int64_t i = 0; i < (int64_t)L * E; ++i) entries[i] = -1;
+    c.visited = (uint8_t *)calloc((size_t)n, 1);
+    c.buf = (item *)malloc(sizeof(item) * (size_t)(efc + c.R + 2));
+    int lev = L - 1;                                  /* next snapshot: the smallest prefix */
+    for (int64_t v = 0; v < n; ++v) {
+        insert_point(&c, 0, 0, v);
+        while (lev >= 1 && v + 1 == size[lev]) {
+            for (int64_t i = 0; i < size[lev]; ++i)
+                memcpy(row(&c, lev, i), row(&c, 0, i), sizeof(uint32_t) * (size_t)c.R);
+            --lev;
+        }
+    }
+    for (int i = 0; i < L; ++i) set_entries(&c, i, 0, size[i] - 1);
+    free(c.visited); free(c.buf); free(size); free(off);
     return 0;
 }

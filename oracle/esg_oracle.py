@@ -30,7 +30,9 @@ NONE = 0xFFFFFFFF
 METRICS = {"l2": 0, "ip": 1}
 
 __all__ = [
-    "build_c", "rerank", "is_leaf", "split", "Piece", "decompose", "graph_depths",
+    "build_c", "rerank", "is_leaf", "split", "children", "Piece", "decompose", "graph_depths",
+    "tree_nodes", "prefix_sizes", "decompose_prefix", "decompose_root", "pieces_of",
+    "build_prefix_index",
     "bruteforce", "merge_topk", "OracleIndex", "build_index", "graph_search", "graph_search_rows",
     "search", "recall_at_k", "distances", "METRICS", "NONE", "bf16_round", "bf16_to_float",
     "fp8_e4m3_grid", "fp8_quantize_rows", "fp8_to_float", "traversal_rows",
@@ -64,7 +66,11 @@ def _c():
                                             ctypes.c_int64]
         lib.oracle_build.restype = ctypes.c_int
         lib.oracle_build.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
+                                     ctypes.c_int]
+        lib.oracle_build_prefix.restype = ctypes.c_int
+        lib.oracle_build_prefix.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
         _lib = lib
     return _lib
 
@@ -97,14 +103,27 @@ def split(l: int, r: int) -> int:
     return (l + r) // 2
 
 
+def children(l: int, r: int, fanout: int = 2) -> List[Tuple[int, int, int]]:
+    """The non-empty children (a, b, j) of node [l, r] in a tree of fanout f:
+    child j = [b_j, b_{j+1} - 1] with b_j = l + ceil(j * len / f), len = r - l + 1
+    (the paper leaves the split points of a larger fanout open; this reading
+    gives Algorithm 3's [l, mid], [mid + 1, r] for f = 2). Child j of heap
+    node h is heap node f h + 1 + j."""
+    n = r - l + 1
+    b = [l + -(-j * n // fanout) for j in range(fanout + 1)]
+    return [(b[j], b[j + 1] - 1, j) for j in range(fanout) if b[j] <= b[j + 1] - 1]
+
+
 @dataclasses.dataclass(frozen=True)
 class Piece:
     """One subrange chosen by Algorithm 4.
 
     kind: "graph" (search the graph of node [node_l, node_r]) or "scan"
     (linear scan). [pl, pr] is the part of the query range it answers.
-    heap: the node's heap number (root 0, children 2h+1 and 2h+2); depth:
-    its depth (root 0).
+    heap: the node's heap number (root 0; children of h are f h + 1 .. f h + f
+    in a tree of fanout f; for a prefix index, the prefix graph's number);
+    depth: its depth (root 0; for a prefix index, the level of the prefix
+    graph).
     """
     kind: str
     node_l: int
@@ -122,8 +141,9 @@ def decompose(n: int, leaf_size: int, lq: int, rq: int, fanout: int = 2) -> List
     by a linear scan of its part of the query; a node that contains the query
     part with |[lq, rq]| / |[l, r]| >= c (c = 1/fanout, tested in integers as
     fanout * |[lq, rq]| >= |[l, r]|) is answered by its graph; otherwise the
-    node is split at mid and the query part is clipped to each child it
-    overlaps (left first). Lemma 3 bounds the result to two pieces.
+    query part is clipped to each child it overlaps (left first) and each is
+    resolved the same way. Lemma 3 (fanout 2) and Lemma 4 (fanout f with
+    c = 1/f) bound the result to two pieces.
     """
     if not (0 <= lq <= rq <= n - 1):
         raise ValueError("need 0 <= lq <= rq <= n-1")
@@ -136,17 +156,15 @@ def decompose(n: int, leaf_size: int, lq: int, rq: int, fanout: int = 2) -> List
         if l <= a and b <= r and fanout * (b - a + 1) >= (r - l + 1):
             out.append(Piece("graph", l, r, a, b, h, depth))
             return
-        mid = split(l, r)
-        if a <= mid:
-            rec(l, mid, a, min(mid, b), 2 * h + 1, depth + 1)
-        if b > mid:
-            rec(mid + 1, r, max(mid + 1, a), b, 2 * h + 2, depth + 1)
+        for (ca, cb, j) in children(l, r, fanout):
+            if a <= cb and b >= ca:
+                rec(ca, cb, max(a, ca), min(b, cb), fanout * h + 1 + j, depth + 1)
 
     rec(0, n - 1, lq, rq, 0, 0)
     return out
 
 
-def graph_depths(n: int, leaf_size: int) -> int:
+def graph_depths(n: int, leaf_size: int, fanout: int = 2) -> int:
     """Number of depths of the tree that hold at least one graph node."""
     L = 0
     frontier = [(0, n - 1)]
@@ -156,13 +174,51 @@ def graph_depths(n: int, leaf_size: int) -> int:
         for (l, r) in frontier:
             if not is_leaf(l, r, leaf_size):
                 any_graph = True
-                m = split(l, r)
-                nxt += [(l, m), (m + 1, r)]
+                nxt += [(a, b) for (a, b, _) in children(l, r, fanout)]
         if not any_graph:
             break
         L += 1
         frontier = nxt
     return L
+
+
+def tree_nodes(L: int, fanout: int = 2) -> int:
+    """Heap slots of the depths 0..L-1: 1 + f + ... + f^(L-1)."""
+    return sum(fanout ** t for t in range(L))
+
+
+def prefix_sizes(n: int, base: int = 2) -> List[int]:
+    """Sizes of the prefix graphs of the half-bounded index (ESG-1D, Section
+    4.1): n_i = floor(n / B^i) for i = 0, 1, ... while n_i >= 1 (B = 2 in the
+    paper's definition; base B is its extension)."""
+    out, m = [], n
+    while m >= 1:
+        out.append(m)
+        m //= base
+    return out
+
+
+def decompose_prefix(n: int, base: int, lq: int, rq: int) -> List[Piece]:
+    """Query processing of the half-bounded index (Section 4.1, Lemma 2): a
+    query [0, rq] is answered by the smallest prefix graph [0, n_i - 1] that
+    contains it, i.e. the largest i with n_i = floor(n / B^i) >= rq + 1. Then
+    |[0, rq]| / n_i > 1/B. (Lemma 2 as printed picks [1, N / 2^ceil(log r)],
+    which is [1, 1] for r = N; this reading is the one its two claims,
+    containment and ratio >= 1/2, fix.) Only prefix ranges are supported."""
+    if not (lq == 0 and 0 <= rq <= n - 1):
+        raise ValueError("the half-bounded index answers ranges [0, r] with 0 <= r <= n-1")
+    sizes = prefix_sizes(n, base)
+    i = max(j for j, m in enumerate(sizes) if m >= rq + 1)
+    return [Piece("graph", 0, sizes[i] - 1, 0, rq, i, i)]
+
+
+def decompose_root(n: int, leaf_size: int, lq: int, rq: int) -> List[Piece]:
+    """POST on the root graph alone (the baseline of Section 3.1): every
+    query is one piece of the root [0, n-1], scanned when the root is a leaf."""
+    if not (0 <= lq <= rq <= n - 1):
+        raise ValueError("need 0 <= lq <= rq <= n-1")
+    kind = "scan" if is_leaf(0, n - 1, leaf_size) else "graph"
+    return [Piece(kind, 0, n - 1, lq, rq, 0, 0)]
 
 
 # ------------------------------------------------------------ exact k-NN
@@ -286,12 +342,16 @@ def traversal_rows(X32: np.ndarray, dtype: str) -> np.ndarray:
 
 @dataclasses.dataclass
 class OracleIndex:
-    """Graphs of the segment tree in the layout the GPU library imports.
+    """Graphs of an ESG index in the layout the GPU library imports.
 
-    X: float64 [n, d] in rank order. adj: uint32 [L, n, R]; row i of depth t
-    lists the neighbour ranks of point i in the graph of the depth-t node
-    that contains i (NONE-padded). entries: int32 [2^L - 1, E] entry ranks
-    per heap node (-1 padded; all -1 for leaves). perm: rank -> original row.
+    X: float64 [n, d] in rank order; perm: rank -> original row.
+    kind "tree" (ESG-2D, Algorithm 3; fanout f): adj uint32 [L, n, R]; row i of
+    depth t lists the neighbour ranks of point i in the graph of the depth-t
+    node that contains i (NONE-padded); entries int32 [(f^L - 1)/(f - 1), E]
+    entry ranks per heap node (-1 padded; all -1 for leaves).
+    kind "prefix" (ESG-1D, Algorithm 2; base B = fanout): adj uint32
+    [sum of n_i, R], the rows of prefix graph i (ranks 0..n_i - 1) starting at
+    row n_0 + ... + n_{i-1}; entries int32 [L, E].
     """
     X: np.ndarray
     perm: np.ndarray
@@ -300,6 +360,8 @@ class OracleIndex:
     leaf_size: int
     M: int
     metric: str
+    kind: str = "tree"
+    fanout: int = 2
 
     @property
     def n(self) -> int:
@@ -307,30 +369,68 @@ class OracleIndex:
 
     @property
     def R(self) -> int:
-        return self.adj.shape[2]
+        return self.adj.shape[-1]
 
     @property
     def L(self) -> int:
-        return self.adj.shape[0]
+        return self.adj.shape[0] if self.kind == "tree" else len(prefix_sizes(self.n, self.fanout))
+
+    def level(self, t: int) -> np.ndarray:
+        """Rows of graph level t, indexed by rank."""
+        if self.kind == "tree":
+            return self.adj[t]
+        sizes = prefix_sizes(self.n, self.fanout)
+        off = sum(sizes[:t])
+        return self.adj[off:off + sizes[t]]
 
 
 def build_index(base: np.ndarray, attr: Optional[np.ndarray], metric: str, leaf_size: int,
-                M: int, efc: int = 200, n_entries: int = 16) -> OracleIndex:
-    """Re-rank the points, then Build-2D-Index (Algorithm 3) with HNSW-style
-    insertion into flat graphs (out-degree cap R = 2M, M neighbours chosen
-    per insertion by edge occlusion, efc = construction beam width)."""
+                M: int, efc: int = 200, n_entries: int = 16, fanout: int = 2) -> OracleIndex:
+    """Re-rank the points, then Build-2D-Index (Algorithm 3; fanout f, the
+    extension of Section 4.2 for f > 2) with HNSW-style insertion into flat
+    graphs (out-degree cap R = 2M, M neighbours chosen per insertion by edge
+    occlusion, efc = construction beam width)."""
     n, d = base.shape
     perm = rerank(attr) if attr is not None else np.arange(n, dtype=np.int64)
     X = np.ascontiguousarray(base[perm].astype(np.float64))
-    L = graph_depths(n, leaf_size)
+    L = graph_depths(n, leaf_size, fanout)
     R = 2 * M
     adj = np.empty((max(L, 0), n, R), dtype=np.uint32)
-    entries = np.empty(((1 << L) - 1 if L > 0 else 0, n_entries), dtype=np.int32)
+    entries = np.empty((tree_nodes(L, fanout), n_entries), dtype=np.int32)
     rc = _c().oracle_build(_ptr(X), n, d, METRICS[metric], leaf_size, M, efc, n_entries, L,
-                           _ptr(adj), _ptr(entries) if entries.size else None)
+                           _ptr(adj), _ptr(entries) if entries.size else None, fanout)
     if rc != 0:
         raise RuntimeError("oracle_build failed")
-    return OracleIndex(X, perm, adj, entries, leaf_size, M, metric)
+    return OracleIndex(X, perm, adj, entries, leaf_size, M, metric, "tree", fanout)
+
+
+def build_prefix_index(base: np.ndarray, attr: Optional[np.ndarray], metric: str, M: int,
+                       efc: int = 200, n_entries: int = 16, base_b: int = 2) -> OracleIndex:
+    """Re-rank the points, then Build-1D-Index (Algorithm 2; base B, the
+    extension of Section 4.1): prefix graphs of sizes floor(n / B^i), each a
+    snapshot of one graph grown by inserting the points in rank order."""
+    n, d = base.shape
+    perm = rerank(attr) if attr is not None else np.arange(n, dtype=np.int64)
+    X = np.ascontiguousarray(base[perm].astype(np.float64))
+    sizes = prefix_sizes(n, base_b)
+    R = 2 * M
+    adj = np.empty((sum(sizes), R), dtype=np.uint32)
+    entries = np.empty((len(sizes), n_entries), dtype=np.int32)
+    rc = _c().oracle_build_prefix(_ptr(X), n, d, METRICS[metric], base_b, M, efc, n_entries, len(sizes),
+                                  _ptr(adj), _ptr(entries))
+    if rc != 0:
+        raise RuntimeError("oracle_build_prefix failed")
+    return OracleIndex(X, perm, adj, entries, 0, M, metric, "prefix", base_b)
+
+
+def pieces_of(index: OracleIndex, lq: int, rq: int, mode: str = "elastic") -> List[Piece]:
+    """The pieces a query range is answered by: the elastic choice of the
+    index's kind (Algorithm 4 / Lemma 2), or POST on the root graph alone."""
+    if mode == "root":
+        return decompose_root(index.n, index.leaf_size, lq, rq)
+    if index.kind == "prefix":
+        return decompose_prefix(index.n, index.fanout, lq, rq)
+    return decompose(index.n, index.leaf_size, lq, rq, index.fanout)
 
 
 # -------------------------------------------------------------- search
@@ -343,7 +443,7 @@ def graph_search(index: OracleIndex, depth: int, heap: int, q: np.ndarray, ef: i
     (default: the index's float64 rows). Returns up to ef (ranks, distances)
     ascending. max_expansions > 0 caps the expansions (a search budget)."""
     X = index.X if X is None else np.ascontiguousarray(X, dtype=np.float64)
-    return graph_search_rows(X, index.adj[depth], index.entries[heap], index.metric, q, ef, pl, pr,
+    return graph_search_rows(X, index.level(depth), index.entries[heap], index.metric, q, ef, pl, pr,
                              counters, max_expansions=max_expansions)
 
 
@@ -377,7 +477,7 @@ def graph_search_rows(X: np.ndarray, adj: np.ndarray, entries: np.ndarray, metri
 
 def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
            counters: Optional[np.ndarray] = None, trav_X: Optional[np.ndarray] = None,
-           max_expansions: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+           max_expansions: int = 0, mode: str = "elastic") -> Tuple[np.ndarray, np.ndarray]:
     """Query-2D-Index (Algorithm 4): decompose [lq, rq]; answer scan pieces
     exactly and graph pieces with Algorithm 1 + POST at beam width
     max(ef, k); merge into the top k by (distance, rank). Returns ranks.
@@ -385,10 +485,11 @@ def search(index: OracleIndex, q: np.ndarray, lq: int, rq: int, k: int, ef: int,
     With `trav_X` (rows as stored in low precision, see traversal_rows) the
     traversal and scans use those rows, each piece keeps its best max(ef, k)
     in-range candidates, and these are re-ranked with the exact rows before
-    the merge. max_expansions > 0 caps each graph piece's expansions."""
+    the merge. max_expansions > 0 caps each graph piece's expansions.
+    mode "root" answers every query by POST on the root graph alone."""
     parts = []
     w = max(ef, k)
-    for p in decompose(index.n, index.leaf_size, lq, rq):
+    for p in pieces_of(index, lq, rq, mode):
         if trav_X is None:
             if p.kind == "scan":
                 parts.append(bruteforce(index.X, q, p.pl, p.pr, k, index.metric))

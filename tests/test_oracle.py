@@ -398,19 +398,20 @@ def _load_build_fn(lib_path):
     P = ctypes.c_void_p
     lib.oracle_build.restype = ctypes.c_int
     lib.oracle_build.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
+                                 ctypes.c_int]
     return lib.oracle_build
 
 
-def _build_with(fn, X, metric, leaf, M, efc, E):
+def _build_with(fn, X, metric, leaf, M, efc, E, fanout=2):
     """oracle_build through `fn` (the oracle's library or a mutant of it)."""
     n, d = X.shape
-    L = O.graph_depths(n, leaf)
+    L = O.graph_depths(n, leaf, fanout)
     adj = np.empty((L, n, 2 * M), np.uint32)
-    ent = np.empty(((1 << L) - 1, E), np.int32)
+    ent = np.empty((O.tree_nodes(L, fanout), E), np.int32)
     X = np.ascontiguousarray(X, dtype=np.float64)
     assert fn(X.ctypes.data, n, d, O.METRICS[metric], leaf, M, efc, E, L, adj.ctypes.data,
-              ent.ctypes.data) == 0
+              ent.ctypes.data, fanout) == 0
     return adj, ent
 
 
@@ -447,15 +448,15 @@ def test_build_hand_trace():
 _ALG3_MUTANTS = {
     "no_copy": ("memcpy(row(c, depth, i), row(c, depth + 1, i), sizeof(uint32_t) * (size_t)c->R);",
                 "(void)0;"),
-    "right_half_descending": ("for (int64_t i = mid + 1; i <= r; ++i) insert_point(c, depth, l, i);",
-                              "for (int64_t i = r; i >= mid + 1; --i) insert_point(c, depth, l, i);"),
+    "right_half_descending": ("for (int64_t i = b1; i <= r; ++i) insert_point(c, depth, l, i);",
+                              "for (int64_t i = r; i >= b1; --i) insert_point(c, depth, l, i);"),
     "full_row_drops_new_edge": ("if (du < c->R) { ru[du] = (uint32_t)v; continue; }",
                                 "if (du < c->R) { ru[du] = (uint32_t)v; continue; } else continue;"),
     "full_row_keeps_nearest": ("int nk = select_neighbours(c->X, c->d, c->metric, cand, du + 1, c->R, keep);",
                                "int nk = 0; for (; nk < c->R && nk < du + 1; ++nk) keep[nk] = cand[nk].id;"),
     "occlusion_compares_to_kept": ("if (dist(c, X + (size_t)keep[s] * d, d, metric) < cand[i].d) { good = 0; break; }",
                                    "if (dist(c, X + (size_t)keep[s] * d, d, metric) > cand[i].d) { good = 0; break; }"),
-    "fresh": ("if (left) {", "if (0) {"),
+    "fresh": ("if (first) {", "if (0) {"),
 }
 
 
@@ -649,3 +650,239 @@ def test_graph_search_expansion_cap_hand_trace():
     cnt = np.zeros(3, np.int64)
     ids, _ = O.graph_search(idx, 0, 0, np.array([c["q"]]), c["ef"], 0, 7, cnt, max_expansions=7)
     assert ids.tolist() == c["result_ranks"] and cnt.tolist() == [7, 8, 0]
+
+
+# ------------------------------ larger fanout (Lemma 4), ESG-1D (Lemma 2), root
+
+def _all_nodes_f(n, leaf, f):
+    """Every node of the fanout-f tree as (l, r, depth, heap), breadth first,
+    with child bounds l + ceil(j len / f) computed in exact integers."""
+    out, frontier, depth = [], [(0, n - 1, 0)], 0
+    while frontier:
+        nxt = []
+        for (l, r, h) in frontier:
+            out.append((l, r, depth, h))
+            if r - l >= leaf:
+                ln = r - l + 1
+                for j in range(f):
+                    a = l + (j * ln + f - 1) // f
+                    b = l + ((j + 1) * ln + f - 1) // f - 1
+                    if a <= b:
+                        nxt.append((a, b, f * h + 1 + j))
+        frontier, depth = nxt, depth + 1
+    return out
+
+
+def _closed_form_f(nodes, leaf, f, lq, rq):
+    """Independent statement of the fanout-f choice: along the chain of nodes
+    containing the query, the shallowest that is a leaf or holds it with
+    f |q| >= |node|; if none, the deepest containing node's children the query
+    overlaps (at most two, Lemma 4) each resolved the same way along their own
+    chains."""
+    def chain(a, b):
+        return sorted([nd for nd in nodes if nd[0] <= a and b <= nd[1]], key=lambda t: t[2])
+
+    def accept(nd, a, b):
+        return (nd[1] - nd[0] < leaf) or (f * (b - a + 1) >= nd[1] - nd[0] + 1)
+
+    def resolve(a, b):
+        for nd in chain(a, b):
+            if accept(nd, a, b):
+                return ("scan" if nd[1] - nd[0] < leaf else "graph", nd[0], nd[1], a, b, nd[3], nd[2])
+        raise AssertionError("unreachable")
+
+    ch = chain(lq, rq)
+    for nd in ch:
+        if accept(nd, lq, rq):
+            return [resolve(lq, rq)]
+    deepest = ch[-1]
+    kids = [nd for nd in nodes if nd[2] == deepest[2] + 1 and deepest[0] <= nd[0] and nd[1] <= deepest[1]
+            and nd[0] <= rq and nd[1] >= lq]
+    assert len(kids) <= 2                                             # Lemma 4
+    return [resolve(max(lq, nd[0]), min(rq, nd[1])) for nd in sorted(kids)]
+
+
+@pytest.mark.parametrize("n,leaf,f", [(1, 1, 4), (10, 1, 3), (37, 1, 4), (64, 2, 4), (100, 3, 8),
+                                      (130, 1, 16), (90, 5, 5), (257, 16, 16)])
+def test_decompose_fanout_matches_closed_form_exhaustive(n, leaf, f):
+    nodes = _all_nodes_f(n, leaf, f)
+    for lq in range(n):
+        for rq in range(lq, n):
+            got = [(p.kind, p.node_l, p.node_r, p.pl, p.pr, p.heap, p.depth)
+                   for p in O.decompose(n, leaf, lq, rq, f)]
+            assert got == _closed_form_f(nodes, leaf, f, lq, rq), (n, leaf, f, lq, rq)
+
+
+@pytest.mark.parametrize("f", [2, 3, 4, 8, 16])
+def test_decompose_fanout_lemma4_invariants(f):
+    """At most two pieces that partition the range, each inside its node, and
+    every graph piece covers at least 1/f of its node (Lemma 4)."""
+    rng = np.random.default_rng(f)
+    for n, leaf in [(1000, 16), (4096, 64), (10_000_000, 256)]:
+        for _ in range(2000):
+            a, b = sorted(rng.integers(0, n, size=2).tolist())
+            ps = O.decompose(n, leaf, a, b, f)
+            assert 1 <= len(ps) <= 2 and ps[0].pl == a and ps[-1].pr == b
+            for x, y in zip(ps, ps[1:]):
+                assert y.pl == x.pr + 1
+            for p in ps:
+                assert p.node_l <= p.pl <= p.pr <= p.node_r
+                size = p.node_r - p.node_l + 1
+                if p.kind == "graph":
+                    assert f * (p.pr - p.pl + 1) >= size and size - 1 >= leaf
+                else:
+                    assert size - 1 < leaf
+
+
+def test_fanout2_children_are_algorithm3_halves():
+    for l, r in [(0, 0), (0, 1), (3, 10), (5, 1000), (0, 999_999)]:
+        kids = O.children(l, r, 2)
+        mid = (l + r) // 2
+        want = [(l, mid, 0)] + ([(mid + 1, r, 1)] if mid + 1 <= r else [])
+        assert kids == want
+
+
+@pytest.mark.parametrize("n,B", [(1, 2), (2, 2), (7, 2), (100, 2), (100, 3), (1000, 4), (1023, 10), (4096, 16)])
+def test_decompose_prefix_exhaustive(n, B):
+    """Lemma 2 with base B: the chosen prefix graph contains [0, r] and covers
+    more than 1/B of it is covered by the query; the level is the largest i
+    with B^i (r + 1) <= n (exact integer powers, a different computation)."""
+    sizes = O.prefix_sizes(n, B)
+    assert sizes[0] == n and sizes[-1] >= 1 and sizes[-1] // B == 0
+    assert all(sizes[i + 1] == n // B ** (i + 1) for i in range(len(sizes) - 1))
+    for r in range(n):
+        (p,) = O.decompose_prefix(n, B, 0, r)
+        i = 0
+        while B ** (i + 1) * (r + 1) <= n:
+            i += 1
+        assert (p.kind, p.node_l, p.node_r, p.pl, p.pr, p.heap, p.depth) == \
+            ("graph", 0, n // B ** i - 1, 0, r, i, i)
+        size = p.node_r + 1
+        assert size >= r + 1 and B * (r + 1) > size            # containment, ratio > 1/B
+    with pytest.raises(ValueError):
+        O.decompose_prefix(n, B, 1, n - 1) if n > 1 else O.decompose_prefix(n, B, 0, 1)
+
+
+def test_decompose_root_mode():
+    assert O.decompose_root(1000, 16, 5, 7) == [O.Piece("graph", 0, 999, 5, 7, 0, 0)]
+    assert O.decompose_root(10, 16, 2, 3) == [O.Piece("scan", 0, 9, 2, 3, 0, 0)]
+
+
+def _golden_f4():
+    g = json.load(open(os.path.join(GOLDEN, "alg3_build_fanout4.json")))
+    X = np.array(g["points_1d"], np.float64)[:, None]
+    want = np.full((len(g["adjacency"]), len(X), 2 * g["M"]), O.NONE, np.uint32)
+    for t, rows in enumerate(g["adjacency"]):
+        for i, nb in enumerate(rows):
+            want[t, i, :len(nb)] = nb
+    return g, X, want
+
+
+def test_build_fanout4_hand_trace():
+    g, X, want = _golden_f4()
+    idx = O.build_index(X, None, g["metric"], g["leaf_size"], g["M"], efc=g["efc"],
+                        n_entries=g["n_entries"], fanout=g["fanout"])
+    assert idx.L == 2 and idx.adj.tolist() == want.tolist()
+    assert idx.entries.tolist() == g["entries"]
+
+
+def test_build_fanout4_hand_trace_rejects_floor_split(tmp_path):
+    """Child bounds l + floor(j len / f) instead of the ceiling change the
+    nodes of this 10-point tree, and so the graphs."""
+    import subprocess
+    src = open(os.path.join(os.path.dirname(O.__file__), "esg_oracle.c")).read()
+    old = "return l + ((int64_t)j * len + f - 1) / f;"
+    assert src.count(old) == 1
+    p = tmp_path / "floor.c"
+    p.write_text(src.replace(old, "return l + ((int64_t)j * len) / f;"))
+    so = tmp_path / "floor.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", str(p), "-o", str(so), "-lm"])
+    g, X, want = _golden_f4()
+    adj, ent = _build_with(_load_build_fn(str(so)), X, g["metric"], g["leaf_size"], g["M"], g["efc"],
+                           g["n_entries"], fanout=4)
+    assert not (np.array_equal(adj, want) and ent.tolist() == g["entries"])
+
+
+def _check_prefix_golden(build):
+    g = json.load(open(os.path.join(GOLDEN, "alg2_build.json")))
+    X = np.array(g["points_1d"], np.float64)[:, None]
+    ok = True
+    for c in g["cases"]:
+        idx = build(X, g, c["base"])
+        ok &= O.prefix_sizes(len(X), c["base"]) == c["sizes"]
+        for i, rows in enumerate(c["levels"]):
+            lev = idx.level(i)
+            ok &= len(lev) == len(rows)
+            for row, nb in zip(lev, rows):
+                ok &= row[row != O.NONE].tolist() == nb and bool(np.all(row[len(nb):] == O.NONE))
+        ok &= idx.entries.tolist() == c["entries"]
+    return ok
+
+
+def test_build_prefix_hand_trace():
+    assert _check_prefix_golden(lambda X, g, B: O.build_prefix_index(
+        X, None, g["metric"], g["M"], efc=g["efc"], n_entries=g["n_entries"], base_b=B))
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("snapshot_one_point_late", "while (lev >= 1 && v + 1 == size[lev]) {", "while (lev >= 1 && v == size[lev]) {"),
+    ("no_snapshot", "memcpy(row(&c, lev, i), row(&c, 0, i), sizeof(uint32_t) * (size_t)c.R);", "(void)0;"),
+    ("descending_insertion", "insert_point(&c, 0, 0, v);", "insert_point(&c, 0, 0, n - 1 - v);"),
+])
+def test_build_prefix_hand_trace_rejects_planted_mistakes(tmp_path, name, old, new):
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(O.__file__), "esg_oracle.c")).read()
+    assert src.count(old) == 1, name
+    p = tmp_path / f"{name}.c"
+    p.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", str(p), "-o", str(so), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    P = ctypes.c_void_p
+    lib.oracle_build_prefix.argtypes = [P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+
+    def build(X, g, B):
+        sizes = O.prefix_sizes(len(X), B)
+        adj = np.empty((sum(sizes), 2 * g["M"]), np.uint32)
+        ent = np.empty((len(sizes), g["n_entries"]), np.int32)
+        Xc = np.ascontiguousarray(X)
+        lib.oracle_build_prefix(Xc.ctypes.data, len(X), 1, 0, B, g["M"], g["efc"], g["n_entries"],
+                                len(sizes), adj.ctypes.data, ent.ctypes.data)
+        return O.OracleIndex(Xc, np.arange(len(X)), adj, ent, 0, g["M"], g["metric"], "prefix", B)
+
+    assert not _check_prefix_golden(build), name
+
+
+def test_prefix_search_is_exact_when_ef_covers_the_prefix():
+    """A prefix query searched with ef >= the prefix graph's size visits every
+    point reachable from the entries: the exact k-NN of those points."""
+    w = synthetic.small_mixture(700, 16, 40, n_comp=8, seed=12, M=6)
+    idx = O.build_prefix_index(w.base, w.attr, w.metric, w.M, efc=40, n_entries=4, base_b=2)
+    for i in range(len(w.queries)):
+        r = int(w.r[i])
+        ids, dd = O.search(idx, w.queries[i], 0, r, 10, ef=idx.n)
+        (p,) = O.decompose_prefix(idx.n, 2, 0, r)
+        lev = idx.level(p.depth)
+        seen = set(int(e) for e in idx.entries[p.heap] if e >= 0)
+        stack = list(seen)
+        while stack:
+            u = stack.pop()
+            for v in lev[u]:
+                if v != O.NONE and int(v) not in seen:
+                    seen.add(int(v)); stack.append(int(v))
+        cand = np.array(sorted(c for c in seen if c <= r), np.int64)
+        dist = O.distances(idx.X[cand], w.queries[i], w.metric)
+        order = np.lexsort((cand, dist))[:10]
+        assert ids.tolist() == cand[order].tolist()
+        assert len(seen) >= 0.99 * lev.shape[0]
+
+
+def test_root_mode_search_is_root_graph_search(small_index):
+    w, idx = small_index
+    for i in range(10):
+        l, r = int(w.l[i]), int(w.r[i])
+        a, _ = O.search(idx, w.queries[i], l, r, 10, 16, mode="root")
+        b, _ = O.graph_search(idx, 0, 0, w.queries[i], 16, l, r)
+        assert a.tolist() == b[:10].tolist()
