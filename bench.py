@@ -105,8 +105,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-budget arm")
-    ap.add_argument("--mode", default="search", choices=["search", "bruteforce"],
-                    help="bruteforce: time only the exact filtered k-NN of the workload's queries")
+    ap.add_argument("--mode", default="search", choices=["search", "bruteforce", "layouts"],
+                    help="bruteforce: time only the exact filtered k-NN of the workload's queries; "
+                         "layouts: fanout 2/4/8/16 trees, the prefix index and POST on the root "
+                         "on the scale workload")
     return ap.parse_args()
 
 
@@ -749,6 +751,91 @@ def measured_traffic(key, params):
     return rec["traffic_bytes_per_launch"]
 
 
+def run_layouts(args, local):
+    """Index layouts on the scale workload (1M x 128, L2, k = 10): for the
+    segment tree of fanout f in {2, 4, 8, 16} (Lemma 4) the graph bytes,
+    build time and the plain FP32 search's queries/s at the smallest ef of the
+    sweep with recall@10 >= 0.95; POST on the root graph alone at the same
+    sweep (the baseline the elastic graphs improve on); and on half-bounded
+    queries [0, r] (r + 1 = the workload's widths) the prefix index (ESG-1D,
+    B = 2) against the binary tree."""
+    import torch
+    import paper_2504_04018_gb300 as E
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E.load_library()
+    args.workload = "scale"
+    w = make_workload(args)
+    nq = len(w.l)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    Q = t(w.queries)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    perm = np.argsort(w.attr, kind="stable")
+    Xr = t(w.base[perm])
+
+    def truth(l, r):
+        gi, _, gc = E.esg_bruteforce_filtered_knn(Xr, Q, t(l), t(r), 10, w.metric)
+        torch.cuda.synchronize()
+        gi, gc = gi.cpu().numpy(), gc.cpu().numpy()
+        return np.where(gi >= 0, perm[np.maximum(gi, 0)], -1), gc
+
+    def arm(ix, l, r, gt, gc, post_root=0):
+        L_, R_ = t(l), t(r)
+        sweep, best = [], None
+        for ef in WORKLOADS["scale"]["sweep"]:
+            p = E.search_params(ef=ef, post_root=post_root)
+            ids, _, cnt, _, _ = E.esg_search_batch(ix, Q, L_, R_, None, 10, params=p)
+            torch.cuda.synchronize()
+            rec = recall(ids.cpu().numpy(), cnt.cpu().numpy(), gt, gc, w.k)[0]
+            sweep.append({"ef": ef, "recall": round(rec, 4)})
+            best = (ef, p, rec)
+            if rec >= TARGET_RECALL:
+                break
+        ef, p, rec = best
+        for _ in range(args.warmup):
+            E.esg_search_batch(ix, Q, L_, R_, None, 10, params=p)
+        ms = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E.esg_search_batch(ix, Q, L_, R_, None, 10, params=p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return {"ef": ef, "recall_at_10": round(rec, 4), "qps": nq / (statistics.median(ms) / 1e3),
+                "ms_per_batch": round(statistics.median(ms), 3), "reached_target": rec >= TARGET_RECALL,
+                "sweep": sweep}
+
+    gt, gc = truth(w.l, w.r)
+    rp = w.r - w.l                                   # half-bounded queries [0, r]
+    lp = np.zeros_like(rp)
+    gtp, gcp = truth(lp, rp)
+    out = {"tree": {}, "prefix": {}}
+    for f in (2, 4, 8, 16):
+        t0 = time.perf_counter()
+        ix = E.esg_build(w.base, w.attr, M=32, leaf_size=256, n_entries=16, metric=w.metric, fanout=f)
+        torch.cuda.synchronize()
+        rec = {"build_s": round(time.perf_counter() - t0, 1), "levels": ix.L,
+               "graph_bytes": ix.adj_rows * ix.R * 4 + ix.nodes * ix.E * 4,
+               "general": arm(ix, w.l, w.r, gt, gc)}
+        if f == 2:
+            rec["half_bounded"] = arm(ix, lp, rp, gtp, gcp)
+            rec["post_root"] = arm(ix, w.l, w.r, gt, gc, post_root=1)
+        out["tree"][f] = rec
+        del ix
+    t0 = time.perf_counter()
+    ix = E.esg_build(w.base, w.attr, M=32, n_entries=16, metric=w.metric, fanout=2, layout="prefix")
+    torch.cuda.synchronize()
+    out["prefix"] = {"base": 2, "build_s": round(time.perf_counter() - t0, 1), "levels": ix.L,
+                     "graph_bytes": ix.adj_rows * ix.R * 4 + ix.nodes * ix.E * 4,
+                     "half_bounded": arm(ix, lp, rp, gtp, gcp)}
+    print(json.dumps({"mode": "layouts", "metric": "RF-kNN queries/sec at recall@10 >= 0.95 per index layout",
+                      "unit": "queries/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": workload_config(args, w), "layouts": out}), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -758,6 +845,10 @@ def main():
     if args.mode == "bruteforce":
         if rank == 0:
             run_bruteforce_only(args, local)
+        return
+    if args.mode == "layouts":
+        if rank == 0:
+            run_layouts(args, local)
         return
     run_ours(args, rank, world, local)
 

@@ -17,6 +17,12 @@
  * beam search (Algorithm 1) that walks out-of-range points but only admits
  * in-range points to the result queue (the POST principle, Section 2.2);
  * leaf pieces are scanned. The piece results are merged into the top k.
+ * The tree may have a larger fanout f with elastic factor 1/f (the extension
+ * of Section 4.2, Lemma 4: still at most two pieces). For half-bounded
+ * ranges [0, r] the index may instead hold only prefix graphs (ESG-1D,
+ * Section 4.1, Algorithm 2, Lemma 2: one piece). A search may also skip the
+ * decomposition and answer every query by POST on the root graph (the
+ * baseline of Section 3.1).
  *
  * Conventions for every call:
  *  - ranks and ranges are 0-based and inclusive (the paper counts from 1);
@@ -63,7 +69,8 @@ typedef enum { ESG_F32 = 0, ESG_BF16 = 1, ESG_FP8E4M3 = 2 } esg_dtype;
 /* Per-query status codes written by esg_search_batch. */
 enum {
     ESG_Q_OK = 0,
-    ESG_Q_INVALID = 1,   /* l > r, r >= N, l < 0, k < 1 or k > k_max: count = 0 */
+    ESG_Q_INVALID = 1,   /* l > r, r >= N, l < 0, k < 1 or k > k_max, or l > 0 on a
+                            prefix-layout index without post_root: count = 0 */
     ESG_Q_TRUNCATED = 2, /* a beam search hit its expansion cap; results are partial */
     ESG_Q_OVERFLOW = 4   /* the candidate list or visited set overflowed (results valid) */
 };
@@ -72,10 +79,27 @@ enum {
 enum { ESG_PIECE_NONE = 0, ESG_PIECE_GRAPH = 1, ESG_PIECE_SCAN = 2 };
 
 /*
- * One subrange chosen by Algorithm 4: the tree node [node_l, node_r] (heap
- * number `heap`: root 0, children 2h+1 and 2h+2; `depth` from the root)
- * answers the query part [pl, pr]. kind is ESG_PIECE_GRAPH (beam search on
- * the node's graph) or ESG_PIECE_SCAN (linear scan of a leaf).
+ * Index layouts.
+ *  ESG_LAYOUT_TREE    the segment tree of Algorithm 3 (ESG-2D) with fanout f:
+ *                     the children of node [l, r] are [b_j, b_{j+1} - 1],
+ *                     b_j = l + ceil(j (r - l + 1) / f), j = 0..f-1 (empty ones
+ *                     skipped; f = 2 gives [l, mid], [mid + 1, r]); graph
+ *                     levels are the depths that hold a graph node; heap
+ *                     numbers: root 0, children of h are f h + 1 + j.
+ *  ESG_LAYOUT_PREFIX  the half-bounded index of Algorithm 2 (ESG-1D) with
+ *                     base B: graphs over the prefixes [0, n_i - 1],
+ *                     n_i = floor(n / B^i), for every i with n_i >= 1; level
+ *                     and node number i. Answers ranges [0, r] only (a
+ *                     range [l, n - 1] is a prefix of the reversed order:
+ *                     build on negated attributes).
+ */
+typedef enum { ESG_LAYOUT_TREE = 0, ESG_LAYOUT_PREFIX = 1 } esg_layout;
+
+/*
+ * One subrange chosen by the decomposition: the graph node [node_l, node_r]
+ * (node number `heap`, graph level `depth`, both as in esg_layout) answers
+ * the query part [pl, pr]. kind is ESG_PIECE_GRAPH (beam search on the
+ * node's graph) or ESG_PIECE_SCAN (linear scan of a leaf).
  */
 typedef struct {
     int64_t node_l, node_r, pl, pr;
@@ -96,7 +120,11 @@ typedef struct esg_index esg_index; /* opaque; owned by the library */
  *  ef_construction  beam width of the insertion searches (Section 5.1: 200);
  *  batch_div        points inserted concurrently per node and round are at
  *                   most 1/batch_div of the points already in its graph;
- *  storage          traversal precision kept on the device besides FP32.
+ *  fanout           tree fanout f, 2..16 (elastic factor 1/f); for the prefix
+ *                   layout the base B, 2..16; 0 = 2;
+ *  storage          traversal precision kept on the device besides FP32;
+ *  layout           ESG_LAYOUT_TREE (default) or ESG_LAYOUT_PREFIX (the
+ *                   leaf size is not used: every prefix has a graph).
  */
 typedef struct {
     int32_t M;
@@ -104,9 +132,11 @@ typedef struct {
     int32_t n_entries;
     int32_t ef_construction;
     int32_t batch_div;
-    int32_t reserved;
+    int32_t fanout;
     esg_metric metric;
     esg_dtype storage;
+    esg_layout layout;
+    int32_t reserved;
 } esg_build_params;
 
 /*
@@ -131,7 +161,11 @@ typedef struct {
  *                  CTA (1, 2 or 4), shared visited-table slots (power of two,
  *                  1024..16384) and lanes that share one row gather (1..32,
  *                  a power of two dividing the row's 16-byte vectors); 0 =
- *                  automatic. esg_autotune picks them.
+ *                  automatic. esg_autotune picks them;
+ *  post_root       0 = the elastic decomposition of the index's layout;
+ *                  1 = every query is one piece: POST on the root graph alone
+ *                  (a scan when the root is a leaf), the baseline the elastic
+ *                  graphs improve on (Section 3.1).
  */
 typedef struct {
     int32_t ef;
@@ -143,7 +177,7 @@ typedef struct {
     int32_t warps_per_block;
     int32_t hash_slots;
     int32_t lanes_per_row;
-    int32_t reserved;
+    int32_t post_root;
 } esg_search_params;
 
 esg_build_params esg_build_params_default(void);
@@ -168,38 +202,49 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
  * reference build), in the layout the library stores:
  *  vectors  host [n, d] float32 in RANK order (row i = rank i);
  *  perm     host [n] int64: original id of rank i (NULL = identity);
- *  adj      host [L, n, R] uint32: row i of depth t lists the neighbour ranks
- *           of point i in the graph of the depth-t node containing i, padded
- *           with 0xFFFFFFFF; R <= 128;
- *  entries  host [2^L - 1, n_entries] int32 entry ranks per heap node, -1
- *           padded; n_entries <= 32.
- * L must equal the number of depths holding graph nodes for (n, leaf_size).
+ *  layout, fanout  as in esg_build_params (fanout 2..16);
+ *  adj      host uint32 rows of R neighbour ranks, 0xFFFFFFFF padded, R <= 128:
+ *           tree: [L, n, R], row i of depth t lists the neighbours of point i
+ *           in the graph of the depth-t node containing i; prefix: the
+ *           levels' rows one after the other (level i holds ranks
+ *           0..n_i - 1), [n_0 + ... + n_{L-1}, R];
+ *  entries  host [nodes, n_entries] int32 entry ranks per graph node, -1
+ *           padded, n_entries <= 32; nodes = (f^L - 1) / (f - 1) for the
+ *           tree, L for the prefix layout.
+ * L must equal the number of graph levels of (n, leaf_size, layout, fanout).
  */
 esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n, int32_t d,
-                            esg_metric metric, int32_t leaf_size, const uint32_t *adj,
-                            int32_t L, int32_t R, const int32_t *entries, int32_t n_entries,
-                            esg_dtype storage, esg_index **out);
+                            esg_metric metric, int32_t leaf_size, esg_layout layout, int32_t fanout,
+                            const uint32_t *adj, int32_t L, int32_t R, const int32_t *entries,
+                            int32_t n_entries, esg_dtype storage, esg_index **out);
 
 /* Shape of an index: any output pointer may be NULL. */
 esg_status esg_index_info(const esg_index *index, int64_t *n, int32_t *d, int32_t *L,
                           int32_t *R, int32_t *n_entries, int32_t *leaf_size,
                           int32_t *metric, int32_t *storage);
 
+/* Layout of an index: layout, fanout (or base), graph nodes (rows of the
+ * entries array) and adjacency rows (rows of the adj array, for all levels);
+ * any output pointer may be NULL. */
+esg_status esg_index_layout(const esg_index *index, int32_t *layout, int32_t *fanout,
+                            int64_t *nodes, int64_t *adj_rows);
+
 /*
  * Copy the index's graphs to host buffers of the esg_index_import layout:
- * adj [L, n, R] uint32, entries [2^L - 1, n_entries] int32, perm [n] int64.
- * Any pointer may be NULL to skip it. Synchronous.
+ * adj [adj_rows, R] uint32, entries [nodes, n_entries] int32 (see
+ * esg_index_layout), perm [n] int64. Any pointer may be NULL to skip it.
+ * Synchronous.
  */
 esg_status esg_index_export(const esg_index *index, uint32_t *adj, int32_t *entries,
                             int64_t *perm);
 
 /*
- * Copy rows row0 .. row0 + nrows - 1 of graph level `level` (depth of the
- * tree) to a host buffer adj [nrows, R] uint32, in the esg_index_export
- * layout: for one node [node_l, node_r] of that depth, rows node_l..node_r
- * are the node's whole graph (its edges never leave the node). Lets a caller
- * read one node of a large index without copying every level.
- * Synchronous.
+ * Copy the rows of ranks row0 .. row0 + nrows - 1 of graph level `level` (a
+ * depth of the tree, or prefix graph `level`) to a host buffer
+ * adj [nrows, R] uint32, in the esg_index_export layout: for one node
+ * [node_l, node_r] of that level, ranks node_l..node_r are the node's whole
+ * graph (its edges never leave the node). Lets a caller read one node of a
+ * large index without copying every level. Synchronous.
  */
 esg_status esg_index_export_rows(const esg_index *index, int32_t level, int64_t row0, int64_t nrows,
                                  uint32_t *adj);
@@ -224,17 +269,23 @@ esg_status esg_index_add_storage(esg_index *index, esg_dtype dtype);
 void esg_free(esg_index *index);
 
 /*
- * Elastic decomposition (Algorithm 4's choice of subranges; at most two
- * pieces by Lemma 3) of nq query ranges over the tree of n points with the
- * given leaf size (fanout 2, elastic factor 1/2).
+ * Decomposition of nq query ranges into the pieces a search answers them by,
+ * for an index of n points with the given leaf size, layout and fanout:
+ *  tree    Algorithm 4's choice of elastic subranges, a node accepted when it
+ *          holds the query part and f |part| >= |node| (at most two pieces:
+ *          Lemma 3 for f = 2, Lemma 4 for fanout f);
+ *  prefix  the prefix graph n_i = floor(n / B^i) with the largest i such that
+ *          n_i >= r + 1 (Lemma 2 with base B: contains [0, r], more than 1/B
+ *          of it in range); only ranges with l = 0 are valid;
+ *  post_root = 1: one piece on the root graph (any valid range).
  *  l, r         device [nq] int64 inclusive rank ranges;
  *  out_pieces   device [nq, 2] esg_piece (unused slot: kind ESG_PIECE_NONE);
  *  out_npieces  device [nq] int32: number of pieces, 0 for an invalid range.
  * Asynchronous on `stream`. Integer-only and exact.
  */
-esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
-                               int64_t nq, esg_piece *out_pieces, int32_t *out_npieces,
-                               esg_stream_t stream);
+esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, esg_layout layout, int32_t fanout,
+                               int32_t post_root, const int64_t *l, const int64_t *r, int64_t nq,
+                               esg_piece *out_pieces, int32_t *out_npieces, esg_stream_t stream);
 
 /*
  * Range-filtered approximate k-NN search (Algorithm 4 with Algorithm 1 +

@@ -25,12 +25,13 @@ __all__ = [
 
 METRIC = {"l2": 0, "ip": 1}
 STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
+LAYOUT = {"tree": 0, "prefix": 1}
 PIECE_NONE, PIECE_GRAPH, PIECE_SCAN = 0, 1, 2
 Q_INVALID, Q_TRUNCATED, Q_OVERFLOW = 1, 2, 4
 
 EXPORTED = [
     "esg_build_params_default", "esg_search_params_default", "esg_build", "esg_index_import",
-    "esg_index_info", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
+    "esg_index_info", "esg_index_layout", "esg_index_export", "esg_free", "esg_decompose_batch", "esg_search_batch",
     "esg_bruteforce_filtered_knn", "esg_bruteforce_plan", "esg_attr_to_rank_range", "esg_save", "esg_load",
     "esg_status_str", "esg_last_error", "esg_profile_enable", "esg_profile_read", "esg_profile_tensor_work",
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
@@ -48,8 +49,8 @@ class EsgError(RuntimeError):
 class _BuildParams(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("n_entries", ctypes.c_int32),
                 ("ef_construction", ctypes.c_int32), ("batch_div", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("metric", ctypes.c_int32),
-                ("storage", ctypes.c_int32)]
+                ("fanout", ctypes.c_int32), ("metric", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _TrainParams(ctypes.Structure):
@@ -64,10 +65,10 @@ class _SearchParams(ctypes.Structure):
                 ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("traversal", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("post_root", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None
@@ -90,16 +91,17 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_build_params_default.restype = _BuildParams
     lib.esg_search_params_default.restype = _SearchParams
     lib.esg_build.argtypes = [_P, _I64, _I32, _P, ctypes.POINTER(_BuildParams), ctypes.POINTER(_P)]
-    lib.esg_index_import.argtypes = [_P, _P, _I64, _I32, _I32, _I32, _P, _I32, _I32, _P, _I32, _I32,
-                                     ctypes.POINTER(_P)]
+    lib.esg_index_import.argtypes = [_P, _P, _I64, _I32, _I32, _I32, _I32, _I32, _P, _I32, _I32, _P, _I32,
+                                     _I32, ctypes.POINTER(_P)]
     lib.esg_index_info.argtypes = [_P] + [_P] * 8
+    lib.esg_index_layout.argtypes = [_P] + [_P] * 4
     lib.esg_index_export.argtypes = [_P, _P, _P, _P]
     lib.esg_index_export_rows.argtypes = [_P, _I32, _I64, _I64, _P]
     lib.esg_index_export_storage.argtypes = [_P, _I32, _P, _P]
     lib.esg_index_add_storage.argtypes = [_P, _I32]
     lib.esg_free.argtypes = [_P]
     lib.esg_free.restype = None
-    lib.esg_decompose_batch.argtypes = [_I64, _I32, _P, _P, _I64, _P, _P, _P]
+    lib.esg_decompose_batch.argtypes = [_I64, _I32, _I32, _I32, _I32, _P, _P, _I64, _P, _P, _P]
     lib.esg_search_batch.argtypes = [_P, _P, _I64, _P, _P, _P, _I32, ctypes.POINTER(_SearchParams),
                                      _P, _P, _P, _P, _P, _P]
     lib.esg_bruteforce_filtered_knn.argtypes = [_P, _I64, _I32, _I32, _P, _I64, _P, _P, _I32, _P, _P,
@@ -135,7 +137,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_status_str.restype = ctypes.c_char_p
     lib.esg_status_str.argtypes = [_I32]
     lib.esg_last_error.restype = ctypes.c_char_p
-    for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_export", "esg_index_export_rows",
+    for name in ["esg_build", "esg_index_import", "esg_index_info", "esg_index_layout", "esg_index_export",
+                 "esg_index_export_rows",
                  "esg_decompose_batch", "esg_search_batch", "esg_bruteforce_filtered_knn",
                  "esg_attr_to_rank_range", "esg_save", "esg_load", "esg_profile_enable",
                  "esg_profile_read", "esg_profile_tensor_work", "esg_index_export_storage", "esg_index_add_storage",
@@ -188,6 +191,11 @@ class Index:
                                             (n, d, L, R, E, leaf, metric, storage)]), "esg_index_info")
         self.n, self.d, self.L, self.R, self.E = n.value, d.value, L.value, R.value, E.value
         self.leaf_size, self.metric, self.storage = leaf.value, metric.value, storage.value
+        layout, fanout, nodes, rows = _I32(), _I32(), _I64(), _I64()
+        _check(lib.esg_index_layout(handle, *[ctypes.byref(x) for x in (layout, fanout, nodes, rows)]),
+               "esg_index_layout")
+        self.layout = {v: k for k, v in LAYOUT.items()}[layout.value]
+        self.fanout, self.nodes, self.adj_rows = fanout.value, nodes.value, rows.value
         # the library builds and imports on the current CUDA device
         import torch
         self.device = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
@@ -212,14 +220,17 @@ class Index:
 
 def esg_build(vectors: np.ndarray, attr: Optional[np.ndarray] = None, *, M: int = 16,
               leaf_size: int = 256, n_entries: int = 16, ef_construction: int = 200,
-              batch_div: int = 8, metric: str = "l2", storage: str = "f32") -> Index:
+              batch_div: int = 8, metric: str = "l2", storage: str = "f32", fanout: int = 2,
+              layout: str = "tree") -> Index:
     """Build an index on the current CUDA device from host float32 vectors
-    [n, d] (original order) and optional float64 attributes [n]."""
+    [n, d] (original order) and optional float64 attributes [n]: the segment
+    tree of fanout f (layout "tree") or the prefix graphs of base `fanout`
+    (layout "prefix", half-bounded ranges [0, r])."""
     lib = load_library()
     v = np.ascontiguousarray(vectors, dtype=np.float32)
     a = None if attr is None else np.ascontiguousarray(attr, dtype=np.float64)
-    p = _BuildParams(M, leaf_size, n_entries, ef_construction, batch_div, 0, METRIC[metric],
-                     STORAGE[storage])
+    p = _BuildParams(M, leaf_size, n_entries, ef_construction, batch_div, fanout, METRIC[metric],
+                     STORAGE[storage], LAYOUT[layout], 0)
     h = _P()
     _check(lib.esg_build(_np_ptr(v), v.shape[0], v.shape[1], _np_ptr(a), ctypes.byref(p),
                          ctypes.byref(h)), "esg_build")
@@ -228,28 +239,34 @@ def esg_build(vectors: np.ndarray, attr: Optional[np.ndarray] = None, *, M: int 
 
 def esg_index_import(vectors_ranked: np.ndarray, perm: Optional[np.ndarray], metric: str,
                      leaf_size: int, adj: np.ndarray, entries: np.ndarray,
-                     storage: str = "f32") -> Index:
+                     storage: str = "f32", layout: str = "tree", fanout: int = 2) -> Index:
     """Create an index from host graphs in the stored layout (vectors in rank
-    order, adj [L, n, R] uint32, entries [2^L - 1, E] int32)."""
+    order; tree: adj [L, n, R] uint32, entries [(f^L - 1)/(f - 1), E] int32;
+    prefix: adj [sum of n_i, R], entries [L, E])."""
     lib = load_library()
     v = np.ascontiguousarray(vectors_ranked, dtype=np.float32)
     pm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
     ent = np.ascontiguousarray(entries, dtype=np.int32)
-    L, _, R = adj.shape if adj.ndim == 3 else (0, 0, 1)
+    if layout == "tree":
+        L, _, R = adj.shape if adj.ndim == 3 else (0, 0, 1)
+    else:
+        L, R = ent.shape[0], adj.shape[1]
     h = _P()
     _check(lib.esg_index_import(_np_ptr(v), _np_ptr(pm), v.shape[0], v.shape[1], METRIC[metric],
-                                leaf_size, _np_ptr(adj) if L else None, L, R,
+                                leaf_size, LAYOUT[layout], fanout, _np_ptr(adj) if L else None, L, R,
                                 _np_ptr(ent) if L else None, ent.shape[1] if ent.ndim == 2 else 1,
                                 STORAGE[storage], ctypes.byref(h)), "esg_index_import")
     return Index(h)
 
 
 def esg_index_export(index: Index) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """(adj [L, n, R] uint32, entries [2^L-1, E] int32, perm [n] int64)."""
+    """(adj uint32: tree [L, n, R], prefix [sum of n_i, R]; entries [nodes, E]
+    int32; perm [n] int64)."""
     lib = load_library()
-    adj = np.empty((index.L, index.n, index.R), dtype=np.uint32)
-    ent = np.empty(((1 << index.L) - 1, index.E), dtype=np.int32)
+    shape = (index.L, index.n, index.R) if index.layout == "tree" else (index.adj_rows, index.R)
+    adj = np.empty(shape, dtype=np.uint32)
+    ent = np.empty((index.nodes, index.E), dtype=np.int32)
     perm = np.empty(index.n, dtype=np.int64)
     _check(lib.esg_index_export(index.handle, _np_ptr(adj) if adj.size else None,
                                 _np_ptr(ent) if ent.size else None, _np_ptr(perm)),
@@ -259,7 +276,7 @@ def esg_index_export(index: Index) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
 
 def esg_index_export_entries(index: Index) -> np.ndarray:
     """Entry ranks per graph node: int32 [nodes, E], -1 padded."""
-    ent = np.empty(((1 << index.L) - 1, index.E), dtype=np.int32)
+    ent = np.empty((index.nodes, index.E), dtype=np.int32)
     _check(load_library().esg_index_export(index.handle, None, _np_ptr(ent) if ent.size else None, None),
            "esg_index_export")
     return ent
@@ -306,16 +323,20 @@ def esg_free(index: Index):
     index.close()
 
 
-def esg_decompose_batch(n: int, leaf_size: int, l, r, stream=None):
-    """Elastic decomposition on the device. l, r: CUDA int64 [nq]. Returns
-    (pieces int64 [nq, 2, 6] raw esg_piece records, npieces int32 [nq])."""
+def esg_decompose_batch(n: int, leaf_size: int, l, r, stream=None, fanout: int = 2, layout: str = "tree",
+                        post_root: int = 0):
+    """Decomposition of query ranges on the device (elastic subranges of the
+    fanout-f tree, the prefix graph of the prefix layout, or the root alone).
+    l, r: CUDA int64 [nq]. Returns (pieces int64 [nq, 2, 6] raw esg_piece
+    records, npieces int32 [nq])."""
     import torch
     lib = load_library()
     nq = l.numel()
     pieces = torch.empty((nq, 2, 6), dtype=torch.int64, device=l.device)
     npieces = torch.empty(nq, dtype=torch.int32, device=l.device)
-    _check(lib.esg_decompose_batch(n, leaf_size, _dev_ptr(l), _dev_ptr(r), nq, _dev_ptr(pieces),
-                                   _dev_ptr(npieces), _stream_ptr(stream)), "esg_decompose_batch")
+    _check(lib.esg_decompose_batch(n, leaf_size, LAYOUT[layout], fanout, post_root, _dev_ptr(l), _dev_ptr(r),
+                                   nq, _dev_ptr(pieces), _dev_ptr(npieces), _stream_ptr(stream)),
+           "esg_decompose_batch")
     return pieces, npieces
 
 
@@ -358,11 +379,11 @@ def _check_search_buffers(who: str, index: Index, queries, l, r, k, k_max: int, 
 
 def search_params(ef: int = 64, max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
                   traversal: str = "f32", width: int = 1, warps_per_block: int = 0,
-                  hash_slots: int = 0, lanes_per_row: int = 0) -> _SearchParams:
+                  hash_slots: int = 0, lanes_per_row: int = 0, post_root: int = 0) -> _SearchParams:
     """An esg_search_params record."""
     return _SearchParams(ef, max_expansions, rerank, use_learned,
                          STORAGE[traversal] if isinstance(traversal, str) else traversal, width,
-                         warps_per_block, hash_slots, lanes_per_row, 0)
+                         warps_per_block, hash_slots, lanes_per_row, post_root)
 
 
 def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,

@@ -30,19 +30,25 @@ void free_index_memory(esg_index *ix) {
     if (!ix) return;
     cudaFree(ix->X); cudaFree(ix->Xb); cudaFree(ix->X8); cudaFree(ix->scale8);
     cudaFree(ix->adj); cudaFree(ix->entries); cudaFree(ix->perm); cudaFree(ix->mlp);
+    cudaFree(ix->row_off);
     ix->X = nullptr; ix->Xb = nullptr; ix->X8 = nullptr; ix->scale8 = nullptr;
     ix->adj = nullptr; ix->entries = nullptr; ix->perm = nullptr; ix->mlp = nullptr;
+    ix->row_off = nullptr;
 }
 
 bool dim_ok(int32_t d) { return d >= 4 && d <= 1024 && d % 4 == 0; }
 
-// Common tail of build/import/load: allocate device arrays for the shape.
+// Common tail of build/import/load: allocate device arrays for the shape
+// (esg_set_layout first) and copy the level offsets.
 esg_status alloc_index(esg_index *ix) {
     esg_status s;
     if ((s = dev_alloc(&ix->X, (size_t)ix->n * ix->d)) != ESG_OK) return s;
-    if ((s = dev_alloc(&ix->adj, (size_t)ix->L * ix->n * ix->R)) != ESG_OK) return s;
+    if ((s = dev_alloc(&ix->adj, (size_t)ix->adj_rows * ix->R)) != ESG_OK) return s;
     if ((s = dev_alloc(&ix->entries, (size_t)ix->n_heap * ix->E)) != ESG_OK) return s;
     if ((s = dev_alloc(&ix->perm, (size_t)ix->n)) != ESG_OK) return s;
+    if ((s = dev_alloc(&ix->row_off, (size_t)std::max(ix->L, 1))) != ESG_OK) return s;
+    if (ix->L > 0)
+        ESG_CUDA_TRY(cudaMemcpy(ix->row_off, ix->level_off.data(), sizeof(int64_t) * ix->L, cudaMemcpyHostToDevice));
     return ESG_OK;
 }
 
@@ -104,9 +110,11 @@ esg_build_params esg_build_params_default(void) {
     p.n_entries = 16;
     p.ef_construction = 200;
     p.batch_div = 8;
-    p.reserved = 0;
+    p.fanout = 2;
     p.metric = ESG_L2SQ;
     p.storage = ESG_F32;
+    p.layout = ESG_LAYOUT_TREE;
+    p.reserved = 0;
     return p;
 }
 
@@ -121,7 +129,7 @@ esg_search_params esg_search_params_default(void) {
     p.warps_per_block = 0;
     p.hash_slots = 0;
     p.lanes_per_row = 0;
-    p.reserved = 0;
+    p.post_root = 0;
     return p;
 }
 
@@ -150,8 +158,10 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
         return ESG_ERR_INVALID_ARG;
     }
     esg_build_params p = params ? *params : esg_build_params_default();
+    if (p.fanout == 0) p.fanout = 2;
     if (p.M < 1 || 2 * p.M > 128 || p.leaf_size < 1 || p.n_entries < 1 || p.n_entries > 32 ||
         p.ef_construction < 1 || p.ef_construction > 1024 || p.batch_div < 1 ||
+        p.fanout < 2 || p.fanout > 16 || (p.layout != ESG_LAYOUT_TREE && p.layout != ESG_LAYOUT_PREFIX) ||
         (p.metric != ESG_L2SQ && p.metric != ESG_IP) ||
         (p.storage != ESG_F32 && p.storage != ESG_BF16 && p.storage != ESG_FP8E4M3)) {
         esg_set_error("esg_build: parameter out of range");
@@ -165,9 +175,11 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
     if (!ix) return ESG_ERR_OOM;
     ix->n = n; ix->d = d; ix->metric = p.metric; ix->storage = p.storage;
     ix->leaf_size = p.leaf_size; ix->M = p.M; ix->R = 2 * p.M; ix->E = p.n_entries;
-    ix->L = esg_graph_depths(n, p.leaf_size);
-    if (ix->L > 30) { delete ix; esg_set_error("tree too deep (leaf_size too small)"); return ESG_ERR_UNSUPPORTED; }
-    ix->n_heap = ((int64_t)1 << ix->L) - 1;
+    ix->layout = p.layout; ix->fanout = p.fanout;
+    {
+        esg_status ls = esg_set_layout(ix);
+        if (ls != ESG_OK) { delete ix; return ls; }
+    }
     cudaGetDevice(&ix->device);
     // re-ranking: rank i = i-th smallest attribute, ties by row
     ix->perm_host.resize(n);
@@ -194,7 +206,7 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
             std::memcpy(&ranked[(size_t)i * d], vectors + (size_t)ix->perm_host[i] * d, sizeof(float) * d);
         cudaError_t e = cudaMemcpyAsync(ix->X, ranked.data(), sizeof(float) * n * d, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ix->perm, ix->perm_host.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess && ix->L > 0) e = cudaMemsetAsync(ix->adj, 0xFF, sizeof(uint32_t) * ix->L * n * ix->R, stream);
+        if (e == cudaSuccess && ix->L > 0) e = cudaMemsetAsync(ix->adj, 0xFF, sizeof(uint32_t) * ix->adj_rows * ix->R, stream);
         if (e == cudaSuccess && ix->n_heap > 0) e = cudaMemsetAsync(ix->entries, 0xFF, sizeof(int32_t) * ix->n_heap * ix->E, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); s = ESG_ERR_CUDA; }
@@ -208,9 +220,9 @@ esg_status esg_build(const float *vectors, int64_t n, int32_t d, const double *a
 }
 
 esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n, int32_t d,
-                            esg_metric metric, int32_t leaf_size, const uint32_t *adj, int32_t L,
-                            int32_t R, const int32_t *entries, int32_t n_entries, esg_dtype storage,
-                            esg_index **out) {
+                            esg_metric metric, int32_t leaf_size, esg_layout layout, int32_t fanout,
+                            const uint32_t *adj, int32_t L, int32_t R, const int32_t *entries,
+                            int32_t n_entries, esg_dtype storage, esg_index **out) {
     if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!vectors || n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) || leaf_size < 1 ||
@@ -219,14 +231,34 @@ esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n
         esg_set_error("esg_index_import: argument out of range");
         return ESG_ERR_INVALID_ARG;
     }
-    if (L != esg_graph_depths(n, leaf_size)) {
-        esg_set_error("esg_index_import: L does not match (n, leaf_size)");
-        return ESG_ERR_INVALID_ARG;
-    }
     esg_index *ix = new (std::nothrow) esg_index();
     if (!ix) return ESG_ERR_OOM;
     ix->n = n; ix->d = d; ix->metric = metric; ix->storage = storage; ix->leaf_size = leaf_size;
-    ix->L = L; ix->R = R; ix->M = R / 2; ix->E = n_entries; ix->n_heap = ((int64_t)1 << L) - 1;
+    ix->layout = layout; ix->fanout = fanout; ix->R = R; ix->M = R / 2; ix->E = n_entries;
+    {
+        esg_status ls = esg_set_layout(ix);
+        if (ls == ESG_OK && L != ix->L) {
+            esg_set_error("esg_index_import: L does not match (n, leaf_size, layout, fanout)");
+            ls = ESG_ERR_INVALID_ARG;
+        }
+        // every id must name a row of its level, every entry a rank of its node's level
+        for (int t = 0; ls == ESG_OK && t < ix->L; ++t) {
+            const uint32_t *a = adj + (size_t)ix->level_off[t] * R;
+            for (size_t i = 0; i < (size_t)ix->level_rows[t] * R; ++i)
+                if (a[i] != ESG_NONE && (int64_t)a[i] >= ix->level_rows[t]) { ls = ESG_ERR_INVALID_ARG; break; }
+        }
+        for (int64_t h = 0; ls == ESG_OK && h < ix->n_heap; ++h) {
+            const int64_t lim = layout == ESG_LAYOUT_PREFIX ? ix->level_rows[h] : n;
+            for (int e = 0; e < n_entries; ++e)
+                if (entries[h * n_entries + e] >= lim) { ls = ESG_ERR_INVALID_ARG; break; }
+        }
+        if (ls != ESG_OK) {
+            if (ls == ESG_ERR_INVALID_ARG && L == ix->L)
+                esg_set_error("esg_index_import: an adjacency id or entry lies outside its level");
+            delete ix;
+            return ls;
+        }
+    }
     cudaGetDevice(&ix->device);
     ix->perm_host.resize(n);
     if (perm) std::memcpy(ix->perm_host.data(), perm, sizeof(int64_t) * n);
@@ -235,7 +267,7 @@ esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n
     if (s == ESG_OK) {
         cudaError_t e = cudaMemcpy(ix->X, vectors, sizeof(float) * n * d, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(ix->perm, ix->perm_host.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && L > 0) e = cudaMemcpy(ix->adj, adj, sizeof(uint32_t) * L * n * R, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && L > 0) e = cudaMemcpy(ix->adj, adj, sizeof(uint32_t) * ix->adj_rows * R, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && L > 0) e = cudaMemcpy(ix->entries, entries, sizeof(int32_t) * ix->n_heap * n_entries, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); s = ESG_ERR_CUDA; }
     }
@@ -260,9 +292,19 @@ esg_status esg_index_info(const esg_index *ix, int64_t *n, int32_t *d, int32_t *
     return ESG_OK;
 }
 
+esg_status esg_index_layout(const esg_index *ix, int32_t *layout, int32_t *fanout, int64_t *nodes,
+                            int64_t *adj_rows) {
+    if (!ix) { esg_set_error("index is NULL"); return ESG_ERR_INVALID_ARG; }
+    if (layout) *layout = ix->layout;
+    if (fanout) *fanout = ix->fanout;
+    if (nodes) *nodes = ix->n_heap;
+    if (adj_rows) *adj_rows = ix->adj_rows;
+    return ESG_OK;
+}
+
 esg_status esg_index_export(const esg_index *ix, uint32_t *adj, int32_t *entries, int64_t *perm) {
     if (!ix) { esg_set_error("index is NULL"); return ESG_ERR_INVALID_ARG; }
-    if (adj && ix->L > 0) ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj, sizeof(uint32_t) * ix->L * ix->n * ix->R, cudaMemcpyDeviceToHost));
+    if (adj && ix->L > 0) ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj, sizeof(uint32_t) * ix->adj_rows * ix->R, cudaMemcpyDeviceToHost));
     if (entries && ix->n_heap > 0) ESG_CUDA_TRY(cudaMemcpy(entries, ix->entries, sizeof(int32_t) * ix->n_heap * ix->E, cudaMemcpyDeviceToHost));
     if (perm) std::memcpy(perm, ix->perm_host.data(), sizeof(int64_t) * ix->n);
     return ESG_OK;
@@ -270,12 +312,13 @@ esg_status esg_index_export(const esg_index *ix, uint32_t *adj, int32_t *entries
 
 esg_status esg_index_export_rows(const esg_index *ix, int32_t level, int64_t row0, int64_t nrows,
                                  uint32_t *adj) {
-    if (!ix || (!adj && nrows > 0) || level < 0 || level >= ix->L || row0 < 0 || nrows < 0 || row0 + nrows > ix->n) {
+    if (!ix || (!adj && nrows > 0) || level < 0 || level >= ix->L || row0 < 0 || nrows < 0 ||
+        row0 + nrows > ix->level_rows[level]) {
         esg_set_error("esg_index_export_rows: bad argument");
         return ESG_ERR_INVALID_ARG;
     }
     if (nrows > 0)
-        ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj + ((size_t)level * ix->n + row0) * ix->R,
+        ESG_CUDA_TRY(cudaMemcpy(adj, ix->adj + ((size_t)ix->level_off[level] + row0) * ix->R,
                                 sizeof(uint32_t) * nrows * ix->R, cudaMemcpyDeviceToHost));
     return ESG_OK;
 }
@@ -314,14 +357,17 @@ void esg_free(esg_index *ix) {
     delete ix;
 }
 
-esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
-                               int64_t nq, esg_piece *out_pieces, int32_t *out_npieces,
-                               esg_stream_t stream) {
-    if (n < 1 || leaf_size < 1 || nq < 0 || (nq > 0 && (!l || !r || !out_pieces || !out_npieces))) {
+esg_status esg_decompose_batch(int64_t n, int32_t leaf_size, esg_layout layout, int32_t fanout,
+                               int32_t post_root, const int64_t *l, const int64_t *r, int64_t nq,
+                               esg_piece *out_pieces, int32_t *out_npieces, esg_stream_t stream) {
+    if (n < 1 || leaf_size < 1 || nq < 0 || fanout < 2 || fanout > 16 ||
+        (layout != ESG_LAYOUT_TREE && layout != ESG_LAYOUT_PREFIX) ||
+        (nq > 0 && (!l || !r || !out_pieces || !out_npieces))) {
         esg_set_error("esg_decompose_batch: bad argument");
         return ESG_ERR_INVALID_ARG;
     }
-    return esg_launch_decompose(n, leaf_size, l, r, nq, out_pieces, out_npieces, (cudaStream_t)stream);
+    const DecomposeSpec spec{n, leaf_size, fanout, (int32_t)layout, post_root ? 1 : 0};
+    return esg_launch_decompose(spec, l, r, nq, out_pieces, out_npieces, (cudaStream_t)stream);
 }
 
 esg_status esg_search_batch(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
@@ -393,7 +439,7 @@ esg_status esg_attr_to_rank_range(const esg_index *ix, const double *lo, const d
 
 namespace {
 const char kMagic[8] = {'E', 'S', 'G', 'G', 'B', '3', '0', '0'};
-const uint32_t kVersion = 3;
+const uint32_t kVersion = 4;
 
 struct FileHeader {
     char magic[8];
@@ -405,7 +451,10 @@ struct FileHeader {
     uint64_t mlp_count;       // floats of the learned predictor's blob (0: none)
     int32_t mlp_ef_lo, mlp_ef_hi;
     int32_t storage_mask;     // bit t: rows of esg_dtype t are held (low-precision copies are rebuilt on load)
+    int32_t layout;           // esg_layout
+    int32_t fanout;           // tree fanout or prefix base
     int32_t reserved;
+    int64_t adj_rows;         // rows of the adjacency section
 };
 
 bool write_section(FILE *f, const void *data, size_t bytes) {
@@ -430,7 +479,7 @@ esg_status read_section(FILE *f, void *data, size_t bytes) {
 esg_status esg_save(const esg_index *ix, const char *path) {
     if (!ix || !path) { esg_set_error("esg_save: bad argument"); return ESG_ERR_INVALID_ARG; }
     std::vector<float> X((size_t)ix->n * ix->d);
-    std::vector<uint32_t> adj((size_t)ix->L * ix->n * ix->R);
+    std::vector<uint32_t> adj((size_t)ix->adj_rows * ix->R);
     std::vector<int32_t> ent((size_t)ix->n_heap * ix->E);
     ESG_CUDA_TRY(cudaMemcpy(X.data(), ix->X, sizeof(float) * X.size(), cudaMemcpyDeviceToHost));
     if (!adj.empty()) ESG_CUDA_TRY(cudaMemcpy(adj.data(), ix->adj, sizeof(uint32_t) * adj.size(), cudaMemcpyDeviceToHost));
@@ -443,6 +492,7 @@ esg_status esg_save(const esg_index *ix, const char *path) {
     h.version = kVersion; h.d = ix->d; h.metric = ix->metric; h.storage = ix->storage;
     h.leaf_size = ix->leaf_size; h.L = ix->L; h.R = ix->R; h.E = ix->E; h.M = ix->M; h.n = ix->n;
     h.n_heap = ix->n_heap; h.attr_count = ix->attr_sorted.size();
+    h.layout = ix->layout; h.fanout = ix->fanout; h.adj_rows = ix->adj_rows;
     h.mlp_count = ix->mlp_ready ? ix->mlp_host.size() : 0;
     h.mlp_ef_lo = ix->mlp_ef_lo; h.mlp_ef_hi = ix->mlp_ef_hi;
     h.storage_mask = (1 << ESG_F32) | (ix->Xb ? 1 << ESG_BF16 : 0) | (ix->X8 ? 1 << ESG_FP8E4M3 : 0);
@@ -464,10 +514,13 @@ esg_status esg_load(const char *path, esg_index **out) {
     if (!f) { esg_set_error(std::string("esg_load: cannot open ") + path); return ESG_ERR_IO; }
     FileHeader h;
     esg_status s = read_section(f, &h, sizeof(h));
+    esg_index shape;   // the layout the header's parameters imply
+    shape.n = h.n; shape.leaf_size = h.leaf_size; shape.layout = h.layout; shape.fanout = h.fanout;
     if (s == ESG_OK && (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion || h.n < 1 ||
-                        !dim_ok(h.d) || h.L < 0 || h.L > 30 || h.R < 1 || h.R > 128 || h.E < 1 ||
-                        h.E > 32 || h.n_heap != (((int64_t)1 << h.L) - 1) ||
-                        h.L != esg_graph_depths(h.n, h.leaf_size) ||
+                        h.leaf_size < 1 || esg_set_layout(&shape) != ESG_OK))
+        s = ESG_ERR_CORRUPT;
+    if (s == ESG_OK && (!dim_ok(h.d) || h.R < 1 || h.R > 128 || h.E < 1 ||
+                        h.E > 32 || h.n_heap != shape.n_heap || h.L != shape.L || h.adj_rows != shape.adj_rows ||
                         (h.attr_count != 0 && h.attr_count != (uint64_t)h.n) ||
                         (h.mlp_count != 0 && h.mlp_count != (uint64_t)esg_mlp_param_count() + 2 * ESG_MLP_FEATURES + 2)))
         s = ESG_ERR_CORRUPT;
@@ -479,7 +532,7 @@ esg_status esg_load(const char *path, esg_index **out) {
     std::vector<float> mlp;
     if (s == ESG_OK) {
         try {
-            X.resize((size_t)h.n * h.d); perm.resize(h.n); adj.resize((size_t)h.L * h.n * h.R);
+            X.resize((size_t)h.n * h.d); perm.resize(h.n); adj.resize((size_t)h.adj_rows * h.R);
             ent.resize((size_t)h.n_heap * h.E); attr.resize(h.attr_count); mlp.resize(h.mlp_count);
         } catch (...) { s = ESG_ERR_OOM; }
     }
@@ -496,7 +549,8 @@ esg_status esg_load(const char *path, esg_index **out) {
     }
     esg_index *ix = nullptr;
     s = esg_index_import(X.data(), perm.data(), h.n, h.d, (esg_metric)h.metric, h.leaf_size,
-                         adj.data(), h.L, h.R, ent.data(), h.E, (esg_dtype)h.storage, &ix);
+                         (esg_layout)h.layout, h.fanout, adj.data(), h.L, h.R, ent.data(), h.E,
+                         (esg_dtype)h.storage, &ix);
     if (s != ESG_OK) return s;
     ix->M = h.M;
     ix->attr_sorted.swap(attr);

@@ -45,17 +45,23 @@ struct esg_index {
     int32_t metric = 0;
     int32_t storage = 0;
     int32_t leaf_size = 0;
-    int32_t L = 0;           // depths holding graph nodes
+    int32_t layout = ESG_LAYOUT_TREE;
+    int32_t fanout = 2;      // tree fanout f, or the prefix layout's base B
+    int32_t L = 0;           // graph levels: depths holding graph nodes, or prefix graphs
     int32_t R = 0;           // row width of the adjacency
     int32_t E = 0;           // entry points per node
     int32_t M = 0;
-    int64_t n_heap = 0;      // 2^L - 1 heap slots with entries
+    int64_t n_heap = 0;      // graph nodes with entries: (f^L - 1) / (f - 1), or L
+    int64_t adj_rows = 0;    // rows of adj over all levels
+    std::vector<int64_t> level_off;   // first adj row of each level (rank i of level t: row level_off[t] + i)
+    std::vector<int64_t> level_rows;  // ranks 0..level_rows[t] - 1 have rows at level t
+    int64_t *row_off = nullptr;       // level_off on the device
     int device = 0;
     float *X = nullptr;              // [n, d] fp32, rank order
     __nv_bfloat16 *Xb = nullptr;     // [n, d] bf16 (storage BF16)
     __nv_fp8_e4m3 *X8 = nullptr;     // [n, d] fp8 (storage FP8)
     float *scale8 = nullptr;         // [n] per-row fp8 scale
-    uint32_t *adj = nullptr;         // [L, n, R]
+    uint32_t *adj = nullptr;         // [adj_rows, R]
     int32_t *entries = nullptr;      // [n_heap, E]
     int64_t *perm = nullptr;         // [n] rank -> original id (device)
     std::vector<int64_t> perm_host;  // same on the host
@@ -68,8 +74,25 @@ struct esg_index {
     int32_t mlp_ef_lo = 8, mlp_ef_hi = 128;
 };
 
-// Number of depths that hold at least one graph node.
-int esg_graph_depths(int64_t n, int32_t leaf_size);
+// Number of graph levels: depths of the fanout-f tree that hold at least
+// one graph node, or prefix graphs floor(n / B^i) >= 1 of the prefix layout.
+int esg_graph_depths(int64_t n, int32_t leaf_size, int32_t layout, int32_t fanout);
+// Fill the layout fields of `ix` (L, n_heap, adj_rows, level_off,
+// level_rows) from n, leaf_size, layout and fanout; ESG_ERR_UNSUPPORTED when
+// the node table would not fit int32 node numbers.
+esg_status esg_set_layout(esg_index *ix);
+
+// What a search decomposes its query ranges by (see decompose.cuh).
+struct DecomposeSpec {
+    int64_t n;
+    int32_t leaf;       // leaf size of the tree layout
+    int32_t fanout;     // tree fanout f, or prefix base B
+    int32_t layout;     // esg_layout
+    int32_t post_root;  // 1: one piece on the root graph
+};
+inline DecomposeSpec esg_spec_of(const esg_index *ix, int post_root) {
+    return DecomposeSpec{ix->n, ix->leaf_size, ix->fanout, ix->layout, post_root};
+}
 
 // --------------------------------------------------------- launch helpers
 
@@ -92,7 +115,7 @@ struct SearchLaunch {
 // point (sets the error message, prefixed with `who`).
 esg_status esg_check_search_params(const esg_search_params &p, const char *who);
 
-esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
+esg_status esg_launch_decompose(const DecomposeSpec &spec, const int64_t *l, const int64_t *r,
                                 int64_t nq, esg_piece *pieces, int32_t *npieces,
                                 cudaStream_t stream);
 esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream);
@@ -127,7 +150,7 @@ esg_status esg_make_storage(esg_index *ix, cudaStream_t stream);
 
 // learned predictor (mlp.cu): features + per-query ef and expansion budget
 int esg_mlp_param_count();
-esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+esg_status esg_predict_budget(const esg_index *ix, int post_root, const float *queries, int64_t nq, const int64_t *l,
                               const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
                               float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream);
 // per-query hits of returned ids against exact ids (batch.cu)

@@ -175,7 +175,7 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
 // writes the query's ef and expansion budget; invalid predictions fall back
 // to the fixed beam width.
 template <bool PREDICT>
-__global__ void features_kernel(const float *X, int d, int metric, int64_t n, int32_t leaf,
+__global__ void features_kernel(const float *X, int d, int metric, DecomposeSpec spec,
                                 const int32_t *entries, int E, const float *queries, int64_t nq,
                                 const int64_t *l, const int64_t *r, const int32_t *k, int32_t k_max,
                                 float *feat, const float *blob, int ef_fixed, int ef_lo, int ef_hi,
@@ -190,7 +190,8 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
     if (qi >= nq) return;
     esg_piece pc[2];
     const int64_t lq = l[qi], rq = r[qi];
-    const int np = esg_decompose_one(n, leaf, lq, rq, pc);
+    const int np = esg_decompose_one(spec, lq, rq, pc);
+    const int64_t n = spec.n;
     const int kk = k ? k[qi] : k_max;
     float f[kF];
     for (int i = 0; i < kF; ++i) f[i] = 0.f;
@@ -316,12 +317,12 @@ __global__ void features_kernel(const float *X, int d, int metric, int64_t n, in
 // Shapes shared with the host code of the search and the ABI.
 int esg_mlp_param_count() { return kP; }
 
-esg_status esg_predict_budget(const esg_index *ix, const float *queries, int64_t nq, const int64_t *l,
+esg_status esg_predict_budget(const esg_index *ix, int post_root, const float *queries, int64_t nq, const int64_t *l,
                               const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
                               float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream) {
     features_kernel<true><<<ceil_div_i(nq, 4), 128, 0, stream>>>(
-        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat,
-        ix->mlp, ef_fixed, ix->mlp_ef_lo, ix->mlp_ef_hi, ef_q, maxexp_q);
+        ix->X, ix->d, ix->metric, esg_spec_of(ix, post_root), ix->entries, ix->E, queries, nq, l, r, k, k_max,
+        feat, ix->mlp, ef_fixed, ix->mlp_ef_lo, ix->mlp_ef_hi, ef_q, maxexp_q);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }
@@ -388,7 +389,7 @@ esg_status esg_query_features(const esg_index *ix, const float *queries, int64_t
     if (!ix || nq < 0 || (nq > 0 && (!queries || !l || !r || !feat))) { esg_set_error("esg_query_features: bad argument"); return ESG_ERR_INVALID_ARG; }
     if (nq == 0) return ESG_OK;
     features_kernel<false><<<ceil_div_i(nq, 4), 128, 0, (cudaStream_t)stream>>>(
-        ix->X, ix->d, ix->metric, ix->n, ix->leaf_size, ix->entries, ix->E, queries, nq, l, r, k, k_max, feat,
+        ix->X, ix->d, ix->metric, esg_spec_of(ix, 0), ix->entries, ix->E, queries, nq, l, r, k, k_max, feat,
         nullptr, 0, 0, 0, nullptr, nullptr);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
@@ -407,7 +408,7 @@ esg_status esg_query_budget(const esg_index *ix, const float *queries, int64_t n
     cudaStream_t stream = (cudaStream_t)stream_v;
     float *feat = nullptr;
     ESG_CUDA_TRY(cudaMallocAsync((void **)&feat, sizeof(float) * nq * kF, stream));
-    esg_status st = esg_predict_budget(ix, queries, nq, l, r, k, k_max, ef_fixed, feat, ef_out, maxexp_out,
+    esg_status st = esg_predict_budget(ix, 0, queries, nq, l, r, k, k_max, ef_fixed, feat, ef_out, maxexp_out,
                                        stream);
     const cudaError_t fe = cudaFreeAsync(feat, stream);
     if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }

@@ -32,7 +32,7 @@ using esg_sk::SearchFn;
 namespace {
 
 // Validate queries and decompose their ranges (one thread per query).
-__global__ void prep_kernel(int64_t n, int32_t leaf, const int64_t *l, const int64_t *r,
+__global__ void prep_kernel(DecomposeSpec spec, const int64_t *l, const int64_t *r,
                             const int32_t *k, int32_t k_max, int64_t nq, esg_piece *pieces,
                             int32_t *kq, int32_t *qstatus) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -41,8 +41,8 @@ __global__ void prep_kernel(int64_t n, int32_t leaf, const int64_t *l, const int
     int kk = k ? k[i] : k_max;
     esg_piece pcs[2];
     int cnt = 0;
-    bool ok = kk >= 1 && kk <= k_max && lq >= 0 && lq <= rq && rq < n;
-    if (ok) cnt = esg_decompose_one(n, leaf, lq, rq, pcs);
+    bool ok = kk >= 1 && kk <= k_max && lq >= 0 && lq <= rq && rq < spec.n;
+    if (ok) cnt = esg_decompose_one(spec, lq, rq, pcs);
     if (!ok || cnt <= 0) {
         pcs[0].kind = ESG_PIECE_NONE; pcs[1].kind = ESG_PIECE_NONE;
         kk = 0;
@@ -149,12 +149,12 @@ __global__ void merge_kernel(int64_t nq, int32_t k_max, const int32_t *kq, const
     }
 }
 
-__global__ void decompose_kernel(int64_t n, int32_t leaf, const int64_t *l, const int64_t *r,
+__global__ void decompose_kernel(DecomposeSpec spec, const int64_t *l, const int64_t *r,
                                  int64_t nq, esg_piece *out, int32_t *npieces) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nq) return;
     esg_piece p[2];
-    int c = esg_decompose_one(n, leaf, l[i], r[i], p);
+    int c = esg_decompose_one(spec, l[i], r[i], p);
     out[2 * i] = p[0];
     out[2 * i + 1] = p[1];
     npieces[i] = c < 0 ? 0 : c;
@@ -255,10 +255,10 @@ int esg_vpl_for_lpr(int nvec, int lpr) {
     return (v == 1 || v == 2 || v == 3 || v == 4 || v == 6 || v == 8) ? v : 0;
 }
 
-esg_status esg_launch_decompose(int64_t n, int32_t leaf_size, const int64_t *l, const int64_t *r,
+esg_status esg_launch_decompose(const DecomposeSpec &spec, const int64_t *l, const int64_t *r,
                                 int64_t nq, esg_piece *pieces, int32_t *npieces, cudaStream_t stream) {
     if (nq == 0) return ESG_OK;
-    decompose_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(n, leaf_size, l, r, nq, pieces, npieces);
+    decompose_kernel<<<ceil_div_i(nq, 256), 256, 0, stream>>>(spec, l, r, nq, pieces, npieces);
     ESG_CUDA_TRY(cudaGetLastError());
     return ESG_OK;
 }
@@ -350,15 +350,15 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
 
     ESG_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
     ESG_CUDA_TRY(cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream));
-    prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(ix->n, ix->leaf_size, s.l, s.r, s.k,
+    prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(esg_spec_of(ix, s.p.post_root), s.l, s.r, s.k,
                                                            s.k_max, s.nq, pieces, kq, qs);
     ESG_CUDA_TRY(cudaGetLastError());
     int32_t *ef_q = nullptr, *maxexp_q = nullptr;
     if (plan.learned) {
         ef_q = (int32_t *)(scratch + L.efq);
         maxexp_q = (int32_t *)(scratch + L.mxq);
-        esg_status pst = esg_predict_budget(ix, s.queries, s.nq, s.l, s.r, s.k, s.k_max, plan.ef,
-                                            (float *)(scratch + L.feat), ef_q, maxexp_q, stream);
+        esg_status pst = esg_predict_budget(ix, s.p.post_root, s.queries, s.nq, s.l, s.r, s.k, s.k_max,
+                                            plan.ef, (float *)(scratch + L.feat), ef_q, maxexp_q, stream);
         if (pst != ESG_OK) return pst;
         esg_prof_count(1);   // features + network, one kernel
     }
@@ -370,7 +370,7 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     SearchArgs a;
     a.order = order;
     a.ef_q = ef_q; a.maxexp_q = maxexp_q;
-    a.X = ix->X; a.adj = ix->adj; a.entries = ix->entries; a.queries = s.queries;
+    a.X = ix->X; a.adj = ix->adj; a.row_off = ix->row_off; a.entries = ix->entries; a.queries = s.queries;
     a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
     a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
     a.d = ix->d; a.nvec = plan.nvec; a.R = ix->R; a.E = ix->E;
@@ -408,11 +408,12 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
 
 // Beam search over prepared work items (graph construction): item i searches
 // the piece pieces[i] for the row qidx[i] of X, keeping the best k results in
-// res[i * k ..]. Entry points come from `entries` (E per heap node).
+// res[i * k ..]. Entry points come from `entries` (E per node); the rows of
+// rank p at level t are adj[(row_off[t] + p) * R ..].
 esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, const uint32_t *adj,
-                                int R, const int32_t *entries, int E, const int64_t *qidx,
-                                const esg_piece *pieces, int64_t n_items, int ef, int k,
-                                int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
+                                const int64_t *row_off, int R, const int32_t *entries, int E,
+                                const int64_t *qidx, const esg_piece *pieces, int64_t n_items, int ef,
+                                int k, int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
     SearchPlan plan;
@@ -428,7 +429,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
     if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream);
     if (ce == cudaSuccess) {
         SearchArgs a;
-        a.X = X; a.adj = adj; a.entries = entries; a.queries = X; a.qidx = qidx;
+        a.X = X; a.adj = adj; a.row_off = row_off; a.entries = entries; a.queries = X; a.qidx = qidx;
         a.pieces = pieces; a.kq = nullptr; a.kconst = k; a.qshift = 0;
         a.ef_q = nullptr; a.maxexp_q = nullptr;
         a.n = n; a.n_items = n_items; a.d = d; a.nvec = plan.nvec; a.LPR = plan.lpr; a.R = R; a.E = E;

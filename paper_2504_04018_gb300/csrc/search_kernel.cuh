@@ -312,6 +312,7 @@ struct SearchArgs {
     const float *scale8;   // FP8 per-row scales
     int rerank;
     const uint32_t *adj;
+    const int64_t *row_off;  // first adj row of each graph level (rank p of level t: row row_off[t] + p)
     const int32_t *entries;
     const float *queries;
     const int64_t *qidx;   // optional: query row of an item (build: the inserted point)
@@ -434,7 +435,7 @@ search_kernel(SearchArgs a) {
             if (lane == 0) { w.hcount[0] = 0; w.hcount[1] = 0; }
             __syncwarp();
             bool used_g = false;
-            const uint32_t *adj = a.adj + (size_t)pc.depth * (size_t)a.n * a.R;
+            const uint32_t *adj = a.adj + (size_t)a.row_off[pc.depth] * a.R;
             // entry points: into P, and into Q when in range
             {
                 uint32_t e = ESG_NONE;

@@ -51,7 +51,17 @@ def test_invalid_arguments_rejected_on_host():
     import numpy as np
     v = np.zeros((4, 12), np.float32)
     assert lib.esg_build(v.ctypes.data_as(ctypes.c_void_p), 4, 12, None, None, ctypes.byref(h)) == 1
-    assert lib.esg_decompose_batch(0, 16, None, None, 1, None, None, None) == 1
+    assert lib.esg_decompose_batch(0, 16, 0, 2, 0, None, None, 1, None, None, None) == 1
+    assert lib.esg_decompose_batch(100, 16, 0, 17, 0, None, None, 0, None, None, None) == 1   # fanout > 16
+    assert lib.esg_decompose_batch(100, 16, 2, 2, 0, None, None, 0, None, None, None) == 1    # no such layout
+    # build parameters: fanout outside 2..16, unknown layout
+    v16 = np.zeros((40, 16), np.float32)
+    p = lib.esg_build_params_default()
+    assert p.fanout == 2 and p.layout == 0
+    p.fanout = 17
+    assert lib.esg_build(v16.ctypes.data_as(ctypes.c_void_p), 40, 16, None, ctypes.byref(p), ctypes.byref(h)) == 1
+    p.fanout, p.layout = 4, 3
+    assert lib.esg_build(v16.ctypes.data_as(ctypes.c_void_p), 40, 16, None, ctypes.byref(p), ctypes.byref(h)) == 1
     assert lib.esg_search_batch(None, None, 1, None, None, None, 10, None, None, None, None, None,
                                 None, None) == 1
     assert lib.esg_bruteforce_filtered_knn(None, 10, 16, 0, None, 1, None, None, 0, None, None,
