@@ -225,7 +225,8 @@ esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n
                             int32_t n_entries, esg_dtype storage, esg_index **out) {
     if (!out) { esg_set_error("out is NULL"); return ESG_ERR_INVALID_ARG; }
     *out = nullptr;
-    if (!vectors || n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) || leaf_size < 1 ||
+    if (!vectors || n < 1 || n >= ((int64_t)1 << 31) - 1 || !dim_ok(d) ||
+        (layout == ESG_LAYOUT_TREE && leaf_size < 1) ||
         R < 1 || R > 128 || n_entries < 1 || n_entries > 32 || (L > 0 && (!adj || !entries)) ||
         (metric != ESG_L2SQ && metric != ESG_IP)) {
         esg_set_error("esg_index_import: argument out of range");
@@ -233,7 +234,9 @@ esg_status esg_index_import(const float *vectors, const int64_t *perm, int64_t n
     }
     esg_index *ix = new (std::nothrow) esg_index();
     if (!ix) return ESG_ERR_OOM;
-    ix->n = n; ix->d = d; ix->metric = metric; ix->storage = storage; ix->leaf_size = leaf_size;
+    // the prefix layout has no leaves; its leaf size is kept at 1
+    ix->n = n; ix->d = d; ix->metric = metric; ix->storage = storage;
+    ix->leaf_size = std::max<int32_t>(leaf_size, 1);
     ix->layout = layout; ix->fanout = fanout; ix->R = R; ix->M = R / 2; ix->E = n_entries;
     {
         esg_status ls = esg_set_layout(ix);

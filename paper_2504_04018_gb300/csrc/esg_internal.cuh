@@ -120,14 +120,29 @@ esg_status esg_launch_decompose(const DecomposeSpec &spec, const int64_t *l, con
                                 cudaStream_t stream);
 esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream);
 
-// Launch plan of one search call (kernel, shape, shared memory, scratch).
-struct SearchPlan {
+// One launch of the beam-search kernel: kernel, shape, shared memory.
+struct KernelPlan {
     void *fn;
-    const void *Xt;       // traversal rows
-    int vpl, lpr, C, H, G, wpb, nvec, width, BB, ef, efk;
-    bool learned;         // per-query ef and expansion budget from the predictor
+    int vpl, lpr, C, H, G, wpb, nvec, width, BB, efk;
     size_t smem;
-    int64_t grid, n_items;
+    int64_t grid;
+};
+// Largest per-query beam width (max(ef, k)) of the small budget class
+// (environment ESG_SMALL_CLASS_EF overrides it; 0 keeps one class).
+constexpr int kSmallClassEf = 64;
+// Launch plan of one search call. The queries may be split into two budget
+// classes by max(ef_q, k): class 0 (at most kSmallClassEf) and class 1, each
+// searched by its own launch whose lists and visited tables are sized for
+// that class, so that the narrow beams of most queries are not run at the
+// occupancy of the widest one.
+struct SearchPlan {
+    const void *Xt;       // traversal rows
+    int ef, efk;
+    bool learned;         // per-query ef and expansion budget from the predictor
+    int nclass;           // 1: every query in cls[0]; 2: cls[0] small, cls[1] large
+    int small_ef;         // class bound when nclass == 2, else 0
+    KernelPlan cls[2];
+    int64_t n_items;
     size_t scratch_bytes;
 };
 // Validate and plan a search; scratch_bytes tells how much device scratch

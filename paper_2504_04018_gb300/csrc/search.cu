@@ -74,27 +74,39 @@ __device__ __forceinline__ int order_bucket(const esg_piece &pc, int ef) {
     return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
 }
 
+// With split_ef > 0 the queries are also split into the budget classes of
+// SearchPlan (class 1 when max(ef_q, k) > split_ef): class 0's items come
+// first, and range[2c], range[2c + 1] receive the first and one-past-last
+// position of class c.
 __global__ void __launch_bounds__(kOrderThreads) order_items_kernel(const esg_piece *pieces, const int32_t *ef_q,
-                                                                    int ef, int64_t nq, int32_t *order) {
-    __shared__ int32_t cnt[kOrderBuckets];
-    if (threadIdx.x < kOrderBuckets) cnt[threadIdx.x] = 0;
+                                                                    const int32_t *kq, int ef, int split_ef,
+                                                                    int64_t nq, int32_t *order, int32_t *range) {
+    __shared__ int32_t cnt[2 * kOrderBuckets];
+    if (threadIdx.x < 2 * kOrderBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    // buckets count down from the longest estimated cost
+    // buckets count down from the longest estimated cost, class 0 first
     for (int64_t q = threadIdx.x; q < nq; q += kOrderThreads) {
         const int e = ef_q ? ef_q[q] : ef;
+        const int cls = split_ef > 0 && max(e, kq[q]) > split_ef ? 1 : 0;
         const int b = min(order_bucket(pieces[2 * q], e), order_bucket(pieces[2 * q + 1], e));
-        atomicAdd(&cnt[b], 2);
+        atomicAdd(&cnt[cls * kOrderBuckets + b], 2);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         int32_t run = 0;
-        for (int b = 0; b < kOrderBuckets; ++b) { const int32_t c = cnt[b]; cnt[b] = run; run += c; }
+        for (int b = 0; b < 2 * kOrderBuckets; ++b) {
+            if (b == kOrderBuckets) { range[1] = run; range[2] = run; }
+            const int32_t c = cnt[b]; cnt[b] = run; run += c;
+        }
+        range[0] = 0;
+        range[3] = run;
     }
     __syncthreads();
     for (int64_t q = threadIdx.x; q < nq; q += kOrderThreads) {
         const int e = ef_q ? ef_q[q] : ef;
+        const int cls = split_ef > 0 && max(e, kq[q]) > split_ef ? 1 : 0;
         const int b0 = order_bucket(pieces[2 * q], e), b1 = order_bucket(pieces[2 * q + 1], e);
-        const int32_t pos = atomicAdd(&cnt[min(b0, b1)], 2);
+        const int32_t pos = atomicAdd(&cnt[cls * kOrderBuckets + min(b0, b1)], 2);
         const bool second_first = b1 < b0;
         order[pos] = (int32_t)(2 * q + (second_first ? 1 : 0));
         order[pos + 1] = (int32_t)(2 * q + (second_first ? 0 : 1));
@@ -181,7 +193,7 @@ namespace {
 // Kernel, launch shape and shared memory for a search (or construction)
 // call; knobs left at 0 are chosen automatically.
 esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, int wpb_req,
-                     int hash_req, int lpr_req, SearchPlan &pl) {
+                     int hash_req, int lpr_req, KernelPlan &pl) {
     pl.width = std::max(1, std::min(width, 4));
     pl.BB = 64;
     while (pl.BB < pl.width * R) pl.BB <<= 1;
@@ -199,7 +211,11 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     SearchFn fn = pick_search(st, pl.vpl);
     if (fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
     pl.fn = (void *)fn;
-    pl.C = ((std::max(4 * efk, 256) + 31) / 32) * 32;
+    // candidate list: Q (at most ef in-range items) interleaved with the
+    // unexpanded out-of-range candidates closer than its worst, LPE ef items
+    // (at least 2: the in-place FP32 re-rank sorts a power of two >= ef in it)
+    const int lpe = std::max(2, std::min(8, env_int("ESG_LIST_PER_EF", 4)));
+    pl.C = ((std::max(lpe * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
     // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
     // the global overflow table takes what does not fit
@@ -215,7 +231,7 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
     pl.wpb = wpb_req > 0 ? wpb_req : 2;
-    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 16 + (size_t)pl.BB * 12 + 32 * 8 + 16 +
+    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 8 + (size_t)pl.BB * 12 + 32 * 8 + 16 +
                (((size_t)d * 4 + 15) & ~(size_t)15)) * pl.wpb;
     int dev = 0, sms = 0, per_sm = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
@@ -226,7 +242,7 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
     pl.grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + pl.wpb - 1) / pl.wpb);
     if (pl.grid < 1) pl.grid = 1;
-    pl.n_items = n_items;
+    pl.efk = efk;
     return ESG_OK;
 }
 
@@ -270,6 +286,13 @@ struct ScratchLayout {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+size_t hash_bytes(const SearchPlan &plan) {
+    size_t b = 0;
+    for (int c = 0; c < plan.nclass; ++c)
+        b = std::max(b, (size_t)plan.cls[c].grid * plan.cls[c].wpb * plan.cls[c].G * 4);
+    return b;
+}
+
 ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) {
     const int64_t n_items = 2 * nq;
     ScratchLayout L;
@@ -280,12 +303,13 @@ ScratchLayout scratch_layout(int64_t nq, int32_t k_max, const SearchPlan &plan) 
     L.res = off; off += al256(sizeof(Cand) * n_items * k_max);
     L.cnt = off; off += al256(sizeof(int32_t) * n_items * 2);
     L.stats = off; off += al256(sizeof(int64_t) * n_items * ESG_ITEM_STATS);
-    L.hash = off; off += al256((size_t)plan.grid * plan.wpb * plan.G * 4);
+    // the class launches run one after the other and share the overflow tables
+    L.hash = off; off += al256(hash_bytes(plan));
     L.feat = off; off += plan.learned ? al256(sizeof(float) * nq * ESG_MLP_FEATURES) : 0;
     L.efq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
     L.mxq = off; off += plan.learned ? al256(sizeof(int32_t) * nq) : 0;
     L.order = off; off += al256(sizeof(int32_t) * n_items);
-    L.queue = off; off += 256;
+    L.queue = off; off += 256;   // a work counter and an item range per class
     L.total = off;
     return L;
 }
@@ -304,9 +328,20 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     else if (st_trav == ESG_FP8E4M3) Xt = ix->X8;
     else if (st_trav != ESG_F32) { esg_set_error("unknown traversal type"); return ESG_ERR_INVALID_ARG; }
     if (Xt == nullptr) { esg_set_error("index has no rows of the requested traversal type (build with that storage)"); return ESG_ERR_INVALID_ARG; }
-    esg_status pst = make_plan(ix->d, ix->R, efk, 2 * std::max<int64_t>(s.nq, 1), st_trav, s.p.width,
-                               s.p.warps_per_block, s.p.hash_slots, s.p.lanes_per_row, plan);
-    if (pst != ESG_OK) return pst;
+    // two budget classes when some queries may need a beam wider than the
+    // small class's and others may not: the learned budget, or a fixed ef
+    // below the class bound with a larger k_max
+    const int64_t n_items = 2 * std::max<int64_t>(s.nq, 1);
+    const int small_ef = env_int("ESG_SMALL_CLASS_EF", kSmallClassEf);
+    plan.nclass = (small_ef > 0 && efk > small_ef && (learned || ef <= small_ef)) ? 2 : 1;
+    plan.small_ef = plan.nclass == 2 ? small_ef : 0;
+    const int ef_cls[2] = {plan.nclass == 2 ? small_ef : efk, efk};
+    for (int c = 0; c < plan.nclass; ++c) {
+        esg_status pst = make_plan(ix->d, ix->R, ef_cls[c], n_items, st_trav, s.p.width, s.p.warps_per_block,
+                                   s.p.hash_slots, s.p.lanes_per_row, plan.cls[c]);
+        if (pst != ESG_OK) return pst;
+    }
+    plan.n_items = n_items;
     plan.Xt = Xt;
     plan.learned = learned;
     plan.ef = ef;
@@ -319,8 +354,12 @@ esg_status esg_search_prepare_capped(const SearchLaunch &s, size_t max_scratch, 
     esg_status st = esg_search_prepare(s, plan);
     if (st != ESG_OK) return st;
     const int64_t nq = std::max<int64_t>(s.nq, 1);
-    while (plan.scratch_bytes > max_scratch && plan.grid > 1) {
-        plan.grid = std::max<int64_t>(1, plan.grid / 2);
+    auto grid_above_one = [&]() {
+        for (int c = 0; c < plan.nclass; ++c) if (plan.cls[c].grid > 1) return true;
+        return false;
+    };
+    while (plan.scratch_bytes > max_scratch && grid_above_one()) {
+        for (int c = 0; c < plan.nclass; ++c) plan.cls[c].grid = std::max<int64_t>(1, plan.cls[c].grid / 2);
         plan.scratch_bytes = scratch_layout(nq, s.k_max, plan).total;
     }
     if (plan.scratch_bytes > max_scratch) {
@@ -345,10 +384,11 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     int32_t *res_status = res_cnt + n_items;
     int64_t *res_stats = (int64_t *)(scratch + L.stats);
     uint32_t *ghash = (uint32_t *)(scratch + L.hash);
-    unsigned long long *queue = (unsigned long long *)(scratch + L.queue);
-    const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
+    unsigned long long *queue = (unsigned long long *)(scratch + L.queue);   // [2] work counters
+    int32_t *range = (int32_t *)(scratch + L.queue + 64);                     // [2][2] item ranges
+    const size_t bytes_hash = hash_bytes(plan);
 
-    ESG_CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream));
+    ESG_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), stream));
     ESG_CUDA_TRY(cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream));
     prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(esg_spec_of(ix, s.p.post_root), s.l, s.r, s.k,
                                                            s.k_max, s.nq, pieces, kq, qs);
@@ -365,7 +405,8 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     // items longest first: a warp that takes a long search late would
     // leave the others idle at the end of the launch
     int32_t *order = (int32_t *)(scratch + L.order);
-    order_items_kernel<<<1, kOrderThreads, 0, stream>>>(pieces, ef_q, plan.ef, s.nq, order);
+    order_items_kernel<<<1, kOrderThreads, 0, stream>>>(pieces, ef_q, kq, plan.ef, plan.small_ef, s.nq, order,
+                                                        range);
     ESG_CUDA_TRY(cudaGetLastError());
     SearchArgs a;
     a.order = order;
@@ -373,19 +414,26 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     a.X = ix->X; a.adj = ix->adj; a.row_off = ix->row_off; a.entries = ix->entries; a.queries = s.queries;
     a.qidx = nullptr; a.kconst = 0; a.qshift = 1;
     a.pieces = pieces; a.kq = kq; a.n = ix->n; a.n_items = n_items;
-    a.d = ix->d; a.nvec = plan.nvec; a.R = ix->R; a.E = ix->E;
+    a.d = ix->d; a.R = ix->R; a.E = ix->E;
     a.Xv = reinterpret_cast<const uint4 *>(plan.Xt); a.scale8 = ix->scale8; a.rerank = s.p.rerank;
-    a.width = plan.width; a.BB = plan.BB; a.LPR = plan.lpr;
     a.metric = ix->metric; a.ef = plan.ef;
     a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * plan.ef + 256;
-    a.k_max = s.k_max; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
+    a.k_max = s.k_max; a.ghash = ghash;
     a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
-    const int pidx = esg_prof_begin(stream);
-    ((SearchFn)plan.fn)<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
-    const cudaError_t ce = cudaGetLastError();
-    esg_prof_end(pidx, stream);
-    if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
-    esg_prof_count(4);  // prep, order, search, merge
+    // the large class first: its items are the longest
+    for (int c = plan.nclass - 1; c >= 0; --c) {
+        const KernelPlan &kp = plan.cls[c];
+        a.nvec = kp.nvec; a.width = kp.width; a.BB = kp.BB; a.LPR = kp.lpr;
+        a.H = kp.H; a.C = kp.C; a.G = kp.G;
+        a.queue = queue + c;
+        a.range = range + 2 * c;
+        const int pidx = esg_prof_begin(stream);
+        ((SearchFn)kp.fn)<<<(unsigned)kp.grid, kp.wpb * 32, kp.smem, stream>>>(a);
+        const cudaError_t ce = cudaGetLastError();
+        esg_prof_end(pidx, stream);
+        if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); return ESG_ERR_CUDA; }
+    }
+    esg_prof_count(3 + plan.nclass);  // prep, order, search per class, merge
     merge_kernel<<<ceil_div_i(s.nq, 128), 128, 0, stream>>>(
         s.nq, s.k_max, kq, res, res_cnt, res_status, res_stats, qs, ix->perm, pieces,
         s.out_ids, s.out_dist, s.out_count, s.out_status, s.out_stats);
@@ -416,7 +464,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
                                 int k, int max_exp, Cand *res, int32_t *res_cnt, int32_t *res_status,
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
-    SearchPlan plan;
+    KernelPlan plan;
     esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, 1, 0, 0, 0, plan);
     if (pst != ESG_OK) return pst;
     const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;

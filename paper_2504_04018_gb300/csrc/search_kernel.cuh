@@ -11,7 +11,6 @@ constexpr int kBatch = 64;  // neighbours handled per expansion (R <= 64 per pas
 struct WarpSmem {
     uint32_t *hash;
     Cand *list;
-    Cand *list2;
     Cand *batch;
     uint32_t *nbuf;
     int *hcount;
@@ -203,20 +202,34 @@ __device__ __forceinline__ void eval_rows_fp32(const float *__restrict__ X, int 
     __syncwarp();
 }
 
-// Merge the sorted, duplicate-free batch B[0..b) into the sorted list
-// A[0..a), writing O (capacity C). Returns the new length min(a + b, C).
-__device__ __forceinline__ int warp_merge(const Cand *A, int a, const Cand *B, int b, Cand *O, int C) {
+// Merge the sorted batch B[0..b) into the sorted list A[0..a) in place
+// (capacity C; no item of B equals one of A). An item's final position is its
+// index plus the number of items of the other sequence before it. The batch
+// positions are found first, against the unchanged list, and parked in
+// `pos` (b entries); the list items then move right, 32 at a time from the
+// end, every lane reading before any lane writes, so that no item is
+// overwritten before it is read (a list item never moves left); last the
+// batch items are written. Items whose position reaches C are dropped.
+// Returns the new length min(a + b, C).
+__device__ __forceinline__ int warp_merge_inplace(Cand *A, int a, const Cand *B, int b, uint32_t *pos,
+                                                  int C) {
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i < a; i += 32) {
-        Cand x = A[i];
-        int pos = i + lower_rank(B, b, x);
-        if (pos < C) O[pos] = x;
+    for (int j = lane; j < b; j += 32) pos[j] = (uint32_t)(j + lower_rank(A, a, B[j]));
+    __syncwarp();
+    for (int i0 = ((a - 1) >> 5) << 5; i0 >= 0; i0 -= 32) {
+        const int i = i0 + lane;
+        Cand x;
+        int p = C;
+        if (i < a) {
+            x = A[i];
+            p = i + lower_rank(B, b, x);
+        }
+        __syncwarp();
+        if (p < C) A[p] = x;
+        __syncwarp();
     }
-    for (int j = lane; j < b; j += 32) {
-        Cand x = B[j];
-        int pos = j + lower_rank(A, a, x);
-        if (pos < C) O[pos] = x;
-    }
+    for (int j = lane; j < b; j += 32)
+        if (pos[j] < (uint32_t)C) A[pos[j]] = B[j];
     __syncwarp();
     return min(a + b, C);
 }
@@ -266,16 +279,16 @@ __device__ __forceinline__ void truncate_list(const Cand *list, ListState &st, i
 }
 
 // Admitted candidates sit in batch[0..BB) (BB a multiple of 64 and a power
-// of two; rejected slots hold +inf). Sort them and merge them into `list`,
-// returning the merged list (list or list2) after truncation. Batches of at
-// most 32 are sorted in registers.
-__device__ __forceinline__ Cand *admit_batch(Cand *batch, int BB, Cand *cbuf, Cand *list, Cand *list2,
-                                             ListState &st, int ef, int C, uint32_t pl, uint32_t pr,
-                                             int &status) {
+// of two; rejected slots hold +inf). Sort them and merge them into `list` in
+// place (nbuf, BB entries, is scratch), then truncate. Batches of at most 32
+// are sorted in registers. Returns false when nothing was admitted.
+__device__ __forceinline__ bool admit_batch(Cand *batch, int BB, Cand *cbuf, Cand *list, uint32_t *nbuf,
+                                            ListState &st, int ef, int C, uint32_t pl, uint32_t pr,
+                                            int &status) {
     const int lane = threadIdx.x & 31;
     int b = 0;
     for (int c = 0; c < BB; c += 32) b += __popc(__ballot_sync(0xffffffffu, batch[c + lane].id != ESG_NONE));
-    if (b == 0) return list;
+    if (b == 0) return false;
     const Cand *B;
     if (b <= 32) {
         const unsigned below = (1u << lane) - 1;
@@ -301,9 +314,9 @@ __device__ __forceinline__ Cand *admit_batch(Cand *batch, int BB, Cand *cbuf, Ca
         B = batch;
     }
     if (st.len + b > C) status |= ESG_Q_OVERFLOW;
-    st.len = warp_merge(list, st.len, B, b, list2, C);
-    truncate_list(list2, st, ef, pl, pr);
-    return list2;
+    st.len = warp_merge_inplace(list, st.len, B, b, nbuf, C);
+    truncate_list(list, st, ef, pl, pr);
+    return true;
 }
 
 struct SearchArgs {
@@ -332,7 +345,8 @@ struct SearchArgs {
     uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
     int G;
     unsigned long long *queue;  // atomic work counter
-    const int32_t *order = nullptr;  // optional: the counter's k-th value runs item order[k]
+    const int32_t *order = nullptr;  // optional: the counter's k-th value runs item order[range[0] + k]
+    const int32_t *range = nullptr;  // optional, device: [first, end) of this launch's part of order
     Cand *res;             // [n_items, k_max]
     int32_t *res_cnt;      // [n_items]
     int32_t *res_status;   // [n_items]
@@ -347,13 +361,12 @@ search_kernel(SearchArgs a) {
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     const size_t qbytes = ((size_t)a.d * 4 + 15) & ~(size_t)15;
-    const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 * 2 + (size_t)a.BB * 12 + 32 * 8 +
+    const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 + (size_t)a.BB * 12 + 32 * 8 +
                             16 + qbytes;
     unsigned char *base = smem_raw + per_warp * wib;
     WarpSmem w;
     size_t off = 0;
     w.list = (Cand *)(base + off); off += (size_t)a.C * 8;
-    w.list2 = (Cand *)(base + off); off += (size_t)a.C * 8;
     w.batch = (Cand *)(base + off); off += (size_t)a.BB * 8;
     Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
     w.nbuf = (uint32_t *)(base + off); off += (size_t)a.BB * 4;
@@ -371,12 +384,14 @@ search_kernel(SearchArgs a) {
     vis.gcount = w.hcount + 1;
     vis.glimit = (a.G * 3) / 4;
 
+    const int64_t first = a.range ? (int64_t)a.range[0] : 0;
+    const int64_t count = a.range ? (int64_t)a.range[1] - first : a.n_items;
     for (;;) {
         int64_t item = 0;
         if (lane == 0) item = (int64_t)atomicAdd(a.queue, 1ULL);
         item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= a.n_items) break;
-        if (a.order) item = a.order[item];
+        if (item >= count) break;
+        if (a.order) item = a.order[first + item];
         unsigned long long t_start;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
         const int64_t qi = item >> a.qshift;
@@ -407,7 +422,7 @@ search_kernel(SearchArgs a) {
             __syncwarp();
         }
         ListState st{0, 0, Cand{INFINITY, ESG_NONE}, -1};
-        Cand *list = w.list, *list2 = w.list2;
+        Cand *list = w.list;
         bool saturated = false;
 
         if (!is_graph) {
@@ -423,8 +438,7 @@ search_kernel(SearchArgs a) {
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
-                if (nl != list) { list2 = list; list = nl; }
+                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status);
             }
         } else {
             // Graph piece: Algorithm 1 with POST filtering to [pl, pr].
@@ -455,8 +469,7 @@ search_kernel(SearchArgs a) {
                     else n_oor += (w.batch[j].id < pl || w.batch[j].id > pr);
                 }
                 __syncwarp();
-                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
-                if (nl != list) { list2 = list; list = nl; }
+                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status);
             }
             // all items before `hint` are expanded
             int hint = st.first < 0 ? st.len : st.first;
@@ -537,11 +550,8 @@ search_kernel(SearchArgs a) {
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                Cand *nl = admit_batch(w.batch, a.BB, cbuf, list, list2, st, ef, a.C, pl, pr, status);
-                if (nl != list) {
-                    list2 = list; list = nl;
+                if (admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status))
                     hint = st.first < 0 ? st.len : st.first;
-                }
             }
             if (__any_sync(0xffffffffu, saturated)) status |= ESG_Q_OVERFLOW;
             if (__any_sync(0xffffffffu, used_g)) {
@@ -550,33 +560,36 @@ search_kernel(SearchArgs a) {
                 __syncwarp();
             }
         }
-        // FP32 re-rank of the final in-range candidates found on low-precision rows
+        // FP32 re-rank of the final in-range candidates found on low-precision
+        // rows, in place: the first ef in-range items are moved to the front
+        // (an item never moves right, and each chunk is read before it is
+        // written), their exact distances computed, then sorted (the list
+        // holds at least 4 ef items, so the power-of-two sort fits)
         if (do_rerank && st.len > 0) {
             int cnt = 0;
-            for (int b0 = 0; b0 < st.len; b0 += 32) {
+            for (int b0 = 0; b0 < st.len && cnt < ef; b0 += 32) {
                 const int i = b0 + lane;
                 const uint32_t id = i < st.len ? (list[i].id & ESG_ID_MASK) : ESG_NONE;
                 const bool inr = i < st.len && id >= pl && id <= pr;
                 const unsigned bal = __ballot_sync(0xffffffffu, inr);
                 const int pos = cnt + __popc(bal & ((1u << lane) - 1));
-                if (inr && pos < ef) list2[pos] = Cand{0.f, id};
+                __syncwarp();
+                if (inr && pos < ef) list[pos] = Cand{0.f, id};
+                __syncwarp();
                 cnt += __popc(bal);
-                if (cnt >= ef) break;
             }
             cnt = min(cnt, ef);
-            __syncwarp();
             for (int c0 = 0; c0 < cnt; c0 += kBatch) {
                 const int m = min(kBatch, cnt - c0);
-                for (int j = lane; j < m; j += 32) w.nbuf[j] = list2[c0 + j].id;
+                for (int j = lane; j < m; j += 32) w.nbuf[j] = list[c0 + j].id;
                 __syncwarp();
-                eval_rows_fp32(a.X, a.d, qs, w.nbuf, m, list2 + c0, a.metric);
+                eval_rows_fp32(a.X, a.d, qs, w.nbuf, m, list + c0, a.metric);
             }
             n_rr += cnt;
             const int P = next_pow2_int(max(cnt, 2));
-            for (int j = cnt + lane; j < P; j += 32) list2[j] = Cand{INFINITY, ESG_NONE};
+            for (int j = cnt + lane; j < P; j += 32) list[j] = Cand{INFINITY, ESG_NONE};
             __syncwarp();
-            warp_sort_pow2(list2, P);
-            Cand *t = list; list = list2; list2 = t;
+            warp_sort_pow2(list, P);
             st.len = cnt;
         }
         // emit the first min(k, |Q|) in-range items

@@ -80,3 +80,42 @@ def test_autotune_meets_target(setup):
     ids, _, cnt = _search(gix, t, params)
     hits = sum(len(set(ids[i, :cnt[i]].tolist()) & set(gt[i, :gc[i]].tolist())) for i in range(len(gc)))
     assert hits / gc.sum() >= 0.97
+
+
+def test_budget_classes_do_not_change_results(monkeypatch):
+    """With a learned budget whose ef range reaches past the small class
+    (ef_hi 128), the queries run in two launches sized for their classes;
+    with the split switched off, in one. Results and counters are the same
+    for every query whose candidate list did not overflow in either run."""
+    import synthetic
+    w = synthetic.small_mixture(20000, 32, 600, n_comp=16, seed=41, M=12, leaf_size=64)
+    gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
+    nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
+    blob = np.zeros(nparam + 2 * F + 2, np.float32)
+    # log2 ef = 4 + 0.6 * (standardised log2 width): beams from 16 to the cap
+    blob[0 * 64 + 0] = 1.0                      # W1[0, 0]: hidden unit 0 reads log2 width
+    blob[F * 64 + 64 + 0] = 1.0                 # W2[0, 0]: passed on by layer 2
+    blob[F * 64 + 64 + 64 * 64 + 64 + 0] = 0.6  # W3[0, 0]: log2 ef = 4 + 0.6 log2 width
+    blob[nparam - 2] = 4.0
+    blob[nparam - 1] = 20.0
+    blob[nparam:nparam + F] = 0.0
+    blob[nparam + F:nparam + 2 * F] = 1.0
+    E.esg_predictor_set(gix, blob, 8, 128)
+    dev = torch.device("cuda:0")
+    q, l, r = (torch.as_tensor(a, device=dev) for a in (w.queries, w.l, w.r))
+    k = torch.as_tensor(np.array([1, 10, 100] * 200, np.int32), device=dev)
+    p = E.search_params(ef=64, use_learned=1)
+    outs = []
+    for split in ("64", "0"):
+        monkeypatch.setenv("ESG_SMALL_CLASS_EF", split)
+        o = E.esg_search_batch(gix, q, l, r, k, 100, params=p, want_stats=True)
+        torch.cuda.synchronize()
+        outs.append([x.cpu().numpy() for x in o])
+    (ia, da, ca, sa, ta), (ib, db, cb, sb, tb) = outs
+    ok = ((sa & E.Q_OVERFLOW) == 0) & ((sb & E.Q_OVERFLOW) == 0)
+    assert ok.sum() >= 0.9 * len(ok)
+    ef_q, _ = E.esg_query_budget(gix, q, l, r, k, 100, ef_fixed=64)
+    ef_q = ef_q.cpu().numpy()
+    assert np.any(ef_q <= 64) and np.any(ef_q > 64)          # both classes are used
+    assert np.array_equal(ia[ok], ib[ok]) and np.array_equal(ca[ok], cb[ok])
+    assert np.array_equal(ta[ok, :5], tb[ok, :5])
