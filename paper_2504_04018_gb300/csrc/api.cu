@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -17,7 +19,7 @@ template <typename T>
 esg_status dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return ESG_OK;
-    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    cudaError_t e = esg_malloc((void **)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         esg_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
         *p = nullptr;
@@ -71,6 +73,19 @@ uint32_t crc32_update(uint32_t crc, const void *data, size_t len) {
 }  // namespace
 
 void esg_set_error(const std::string &msg) { g_last_error = msg; }
+
+bool esg_fault_alloc() {
+    static std::mutex mu;
+    static std::string seen;
+    static long long count = 0;
+    const char *v = getenv("ESG_FAULT_ALLOC");
+    const std::string cur = v ? v : "";
+    std::lock_guard<std::mutex> lk(mu);
+    if (cur != seen) { seen = cur; count = 0; }   // a new value starts a new count
+    if (cur.empty()) return false;
+    const long long k = atoll(cur.c_str());
+    return k >= 1 && ++count == k;
+}
 
 esg_status esg_check_search_params(const esg_search_params &p, const char *who) {
     if (p.ef < 1 || p.ef > 1024 || p.max_expansions < 0 || p.width < 0 || p.width > 4 ||

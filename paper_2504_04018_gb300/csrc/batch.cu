@@ -63,7 +63,7 @@ esg_status esg_batch_create(const esg_index *ix, int64_t max_nq, int32_t k_max, 
     esg_status st = ESG_OK;
     auto A = [&](void **p, size_t bytes) {
         if (st != ESG_OK) return;
-        cudaError_t e = cudaMalloc(p, bytes);
+        cudaError_t e = esg_malloc((void **)p, bytes);
         if (e != cudaSuccess) { esg_set_error(cudaGetErrorString(e)); st = ESG_ERR_OOM; }
     };
     A((void **)&b->queries, sizeof(float) * max_nq * ix->d);
@@ -210,7 +210,7 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
         if (plan.scratch_bytes > scratch_bytes) {
             cudaFree(scratch);
             scratch = nullptr;
-            if (cudaMalloc(&scratch, plan.scratch_bytes) != cudaSuccess) { esg_set_error("autotune: scratch"); return ESG_ERR_OOM; }
+            if (esg_malloc((void **)&scratch, plan.scratch_bytes) != cudaSuccess) { esg_set_error("autotune: scratch"); return ESG_ERR_OOM; }
             scratch_bytes = plan.scratch_bytes;
         }
         return esg_search_enqueue(s, plan, scratch, stream);
@@ -244,10 +244,10 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
     const int efs[] = {8, 12, 16, 20, 24, 32, 40, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
     struct Cand_ { esg_search_params p; double recall; float ms; };
     std::vector<Cand_> found;
-    if (cudaMalloc(&ids, sizeof(int64_t) * nq * k_max) != cudaSuccess ||
-        cudaMalloc(&dist, sizeof(float) * nq * k_max) != cudaSuccess ||
-        cudaMalloc(&cnt, sizeof(int32_t) * nq) != cudaSuccess ||
-        cudaMalloc(&hits, sizeof(int32_t) * nq) != cudaSuccess ||
+    if (esg_malloc((void **)&ids, sizeof(int64_t) * nq * k_max) != cudaSuccess ||
+        esg_malloc((void **)&dist, sizeof(float) * nq * k_max) != cudaSuccess ||
+        esg_malloc((void **)&cnt, sizeof(int32_t) * nq) != cudaSuccess ||
+        esg_malloc((void **)&hits, sizeof(int32_t) * nq) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         esg_set_error("autotune: allocation");
         st = ESG_ERR_OOM;

@@ -197,6 +197,8 @@ constexpr int kThreads2 = 64 + 32 * kEpiWarps;
 constexpr int kMaxK1v2 = 64;
 constexpr int kTS = 65;                   // row stride of the transposed half tile
 constexpr int kMaxStages = 6;
+// Limit of the waits that let work already issued finish before a CTA exits
+// (bulk copies, MMAs); the pipeline's own waits take Tc2Args::wait_ns.
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct WorkItem {
@@ -220,6 +222,9 @@ struct Tc2Args {
     int32_t *part_i;                // [n_items][128][K1]
     int32_t *part_n;                // [n_items][128]
     int32_t *err;
+    unsigned long long wait_ns;     // limit of a pipeline wait (ESG_BF_WAIT_NS; default 2 s)
+    int32_t stall;                  // failure-detection test: the producer first waits on a
+                                    // barrier nothing arrives on, before it issues any copy
 };
 
 __device__ __forceinline__ unsigned long long gtime() {
@@ -238,10 +243,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
 }
 
 // Bounded wait for the phase of the given parity. Gives up when another role
-// has aborted (unless `ignore_abort`) or after kWaitNs; on a timeout it
+// has aborted (unless `ignore_abort`) or after limit_ns; on a timeout it
 // raises the abort flag and the error flag.
 __device__ bool wait_phase(uint32_t mbar, uint32_t parity, volatile int *abort_f, int32_t *err,
-                           bool ignore_abort = false) {
+                           unsigned long long limit_ns, bool ignore_abort = false) {
     unsigned long long t0 = 0;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(mbar, parity)) return true;
@@ -249,7 +254,7 @@ __device__ bool wait_phase(uint32_t mbar, uint32_t parity, volatile int *abort_f
             if (!ignore_abort && *abort_f) return false;
             const unsigned long long t = gtime();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > kWaitNs) {
+            else if (t - t0 > limit_ns) {
                 *abort_f = 1;
                 atomicExch(err, 1);
                 return false;
@@ -359,6 +364,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
     uint64_t *acc_full = a_full + 2, *acc_empty = a_full + 4, *drain = a_full + 6;
     uint32_t *tmem_slot = (uint32_t *)(a_full + 7);
     volatile int *abort_f = (volatile int *)(tmem_slot + 1);
+    uint64_t *never = a_full + 8;                             // nothing arrives on it
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this CTA's contiguous share of the work items
     const int it_begin = a.cta_first[blockIdx.x];
@@ -376,6 +382,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             mbar_init(smem_u32(acc_empty + b), kEpiWarps);
         }
         mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(never), 1);
         *abort_f = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -397,10 +404,11 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             bool a_pending = false;
             uint32_t a_par = 0;
             bool ok = true;
+            if (a.stall && !wait_phase(smem_u32(never), 0u, abort_f, a.err, a.wait_ns)) ok = false;
             for (int it = it_begin; ok && it < it_end; ++it) {
                 const WorkItem I = a.items[it];
                 if (!a.stream_a) {
-                    if (!wait_phase(smem_u32(a_empty), pa ^ 1u, abort_f, a.err)) { ok = false; break; }
+                    if (!wait_phase(smem_u32(a_empty), pa ^ 1u, abort_f, a.err, a.wait_ns)) { ok = false; break; }
                     mbar_expect_tx(smem_u32(a_full), (uint32_t)(a.nk * STAGE));
                     for (int kc = 0; kc < a.nk; ++kc)
                         bulk_g2s(smem_u32(sA + (size_t)kc * STAGE),
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                 for (int j = 0; ok && j < I.cnt; ++j) {
                     const int64_t t = a.tiles[I.off + j];
                     for (int kc = 0; kc < a.nk; ++kc) {
-                        if (!wait_phase(smem_u32(empty + s), ps ^ 1u, abort_f, a.err)) { ok = false; break; }
+                        if (!wait_phase(smem_u32(empty + s), ps ^ 1u, abort_f, a.err, a.wait_ns)) { ok = false; break; }
                         unsigned char *sg = sB + (size_t)s * stage_bytes;
                         mbar_expect_tx(smem_u32(full + s), (uint32_t)stage_bytes);
                         if (a.stream_a) {
@@ -428,8 +436,8 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             if (!ok) {
                 // let the copies already issued land before the CTA can exit
                 for (int q = 0; q < a.S; ++q)
-                    if (issued[q]) wait_phase(smem_u32(full + q), ipar[q], abort_f, a.err, true);
-                if (a_pending) wait_phase(smem_u32(a_full), a_par, abort_f, a.err, true);
+                    if (issued[q]) wait_phase(smem_u32(full + q), ipar[q], abort_f, a.err, kWaitNs, true);
+                if (a_pending) wait_phase(smem_u32(a_full), a_par, abort_f, a.err, kWaitNs, true);
             }
         }
     } else if (warp == 1) {
@@ -441,19 +449,19 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             for (int it = it_begin; ok && it < it_end; ++it) {
                 const int cnt = a.items[it].cnt;
                 if (!a.stream_a) {
-                    if (!wait_phase(smem_u32(a_full), pa, abort_f, a.err)) { ok = false; break; }
+                    if (!wait_phase(smem_u32(a_full), pa, abort_f, a.err, a.wait_ns)) { ok = false; break; }
                     pa ^= 1u;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int j = 0; ok && j < cnt; ++j) {
                     const uint32_t b = acc_it & 1u;
-                    if (!wait_phase(smem_u32(acc_empty + b), pacc[b] ^ 1u, abort_f, a.err)) { ok = false; break; }
+                    if (!wait_phase(smem_u32(acc_empty + b), pacc[b] ^ 1u, abort_f, a.err, a.wait_ns)) { ok = false; break; }
                     pacc[b] ^= 1u;
                     ++acc_it;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t dt = tmem + b * TN;
                     for (int kc = 0; kc < a.nk; ++kc) {
-                        if (!wait_phase(smem_u32(full + s), ps, abort_f, a.err)) { ok = false; break; }
+                        if (!wait_phase(smem_u32(full + s), ps, abort_f, a.err, a.wait_ns)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t sg = smem_u32(sB + (size_t)s * stage_bytes);
                         const uint32_t ah = a.stream_a ? sg : smem_u32(sA + (size_t)kc * STAGE), al = ah + CHUNK;
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
             }
             // all MMAs issued by this thread complete before the CTA exits
             mma_commit(smem_u32(drain));
-            wait_phase(smem_u32(drain), 0u, abort_f, a.err, true);
+            wait_phase(smem_u32(drain), 0u, abort_f, a.err, kWaitNs, true);
         }
     } else {
         // ---------------- epilogue (256 threads, 4 pairs of warps)
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(kThreads2, 1) tc_knn2_kernel(Tc2Args a) {
                 const int32_t tile_nx2 = g_cur + 2 < g_end ? __ldg(a.tiles + g_cur + 2) : -1;
                 ++tcount;
                 const uint32_t b = acc_it & 1u;
-                wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err);
+                wait_phase(smem_u32(acc_full + b), pe[b], abort_f, a.err, a.wait_ns);
                 pe[b] ^= 1u;
                 ++acc_it;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -907,7 +915,7 @@ static esg_status bf2_escalate(const PreparedX &X, const float *base, int64_t n,
     const size_t bytes = al(sizeof(int64_t) * m) + al(sizeof(float) * m * d) + 2 * al(sizeof(int64_t) * m) +
                          al(sizeof(int64_t) * m * k) + al(sizeof(float) * m * k) + al(sizeof(int32_t) * m);
     unsigned char *sc = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&sc, bytes, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&sc, bytes, stream));
     unsigned char *p = sc;
     int64_t *didx = (int64_t *)p; p += al(sizeof(int64_t) * m);
     float *Qg = (float *)p; p += al(sizeof(float) * m * d);
@@ -1223,7 +1231,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
                    al((sizeof(float) + sizeof(int32_t)) * (size_t)nq * K1) + 3 * al(sizeof(int32_t) * nq) +
                    al(sizeof(int32_t) * 4);
     unsigned char *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&scratch, bytes, stream));
     unsigned char *p = scratch;
     auto take = [&](size_t b) { unsigned char *q = p; p += al(b); return q; };
     unsigned char *qs = take((size_t)std::max<int64_t>(nqt, 1) * nk * STAGE);
@@ -1267,8 +1275,14 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (ce == cudaSuccess && n_items > 0) {
         // MMA work issued: three 128 x 128 x 64 BF16 products per point tile and K chunk
         esg_prof_tensor_flops((double)total_tiles * nk * 3.0 * 2.0 * TM * TN * TK);
+        // failure-detection hooks (host side): ESG_BF_WAIT_NS bounds each
+        // pipeline wait, ESG_TEST_BF_STALL=1 makes every CTA's first wait one
+        // that nothing completes
+        const char *wn = getenv("ESG_BF_WAIT_NS");
+        const char *stl = getenv("ESG_TEST_BF_STALL");
+        const unsigned long long wait_ns = wn && *wn ? std::max(1ull, strtoull(wn, nullptr, 10)) : kWaitNs;
         Tc2Args a{X.xs, qs, X.xnorm, qnorm, l, r, d_order, d_items, d_tiles, d_cta, (int)n_items, nv, nk, metric, K1, S,
-                  stream_a, n, part_d, part_i, part_n, err};
+                  stream_a, n, part_d, part_i, part_n, err, wait_ns, (stl && atoi(stl) == 1) ? 1 : 0};
         const int pidx = esg_prof_begin(stream);
         tc_knn2_kernel<<<(unsigned)G, kThreads2, smem, stream>>>(a);
         ce = cudaGetLastError();
@@ -1317,7 +1331,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t bytes = al((size_t)xt * nk * STAGE) + 2 * al(sizeof(float) * n) + al(sizeof(float) * 4);
     unsigned char *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&scratch, bytes, stream));
     unsigned char *p = scratch;
     unsigned char *xs = p; p += al((size_t)xt * nk * STAGE);
     float *xnorm = (float *)p; p += al(sizeof(float) * n);

@@ -242,7 +242,7 @@ esg_status esg_launch_bruteforce_mode(int mode, const float *base, int64_t n, in
     if (smem_lists) smem += sizeof(Cand) * (size_t)(BQ + 8) * k;
     int64_t grid = (nq + BQ - 1) / BQ;
     Cand *glists = nullptr;
-    if (!smem_lists) ESG_CUDA_TRY(cudaMallocAsync((void **)&glists, sizeof(Cand) * (size_t)grid * (BQ + 8) * k, stream));
+    if (!smem_lists) ESG_CUDA_TRY(esg_malloc_async((void **)&glists, sizeof(Cand) * (size_t)grid * (BQ + 8) * k, stream));
     BfArgs a{base, n, d, queries, nq, l, r, k, out_ids, out_dist, out_count, id_map, exclude_self,
              xnorm, qnorm, glists};
     void (*fn)(BfArgs) = mode == 0 ? bf_kernel<0> : (mode == 1 ? bf_kernel<1> : bf_kernel<2>);
@@ -290,7 +290,7 @@ esg_status esg_bruteforce_redo(const float *base, int64_t n, int32_t d, int metr
     const size_t bytes = al(sizeof(int64_t) * m) + al(sizeof(float) * m * d) + 2 * al(sizeof(int64_t) * m) +
                          al(sizeof(int64_t) * m * k) + al(sizeof(float) * m * k) + al(sizeof(int32_t) * m);
     unsigned char *s = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&s, bytes, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&s, bytes, stream));
     unsigned char *p = s;
     int64_t *didx = (int64_t *)p; p += al(sizeof(int64_t) * m);
     float *Qg = (float *)p; p += al(sizeof(float) * m * d);

@@ -215,18 +215,18 @@ struct Rounds {
 esg_status rounds_alloc(Rounds &B, const esg_index *ix, int64_t cap, int efc, int M) {
     const int64_t n = ix->n;
     B.cap = cap;
-    B_TRY(cudaMalloc(&B.pts, sizeof(int64_t) * cap));
-    B_TRY(cudaMalloc(&B.pieces, sizeof(esg_piece) * cap));
-    B_TRY(cudaMalloc(&B.res, sizeof(Cand) * cap * efc));
-    B_TRY(cudaMalloc(&B.res_cnt, sizeof(int32_t) * cap * 2));
-    B_TRY(cudaMalloc(&B.stats, sizeof(int64_t) * cap * ESG_ITEM_STATS));
-    B_TRY(cudaMalloc(&B.indeg, sizeof(int32_t) * (n + 1)));
-    B_TRY(cudaMalloc(&B.cursor, sizeof(int32_t) * n));
-    B_TRY(cudaMalloc(&B.off, sizeof(int64_t) * (n + 1)));
-    B_TRY(cudaMalloc(&B.rev, sizeof(uint32_t) * cap * M));
-    B_TRY(cudaMalloc(&B.bentry, sizeof(int32_t) * std::max<int64_t>(ix->n_heap, 1)));
+    B_TRY(esg_malloc((void **)&B.pts, sizeof(int64_t) * cap));
+    B_TRY(esg_malloc((void **)&B.pieces, sizeof(esg_piece) * cap));
+    B_TRY(esg_malloc((void **)&B.res, sizeof(Cand) * cap * efc));
+    B_TRY(esg_malloc((void **)&B.res_cnt, sizeof(int32_t) * cap * 2));
+    B_TRY(esg_malloc((void **)&B.stats, sizeof(int64_t) * cap * ESG_ITEM_STATS));
+    B_TRY(esg_malloc((void **)&B.indeg, sizeof(int32_t) * (n + 1)));
+    B_TRY(esg_malloc((void **)&B.cursor, sizeof(int32_t) * n));
+    B_TRY(esg_malloc((void **)&B.off, sizeof(int64_t) * (n + 1)));
+    B_TRY(esg_malloc((void **)&B.rev, sizeof(uint32_t) * cap * M));
+    B_TRY(esg_malloc((void **)&B.bentry, sizeof(int32_t) * std::max<int64_t>(ix->n_heap, 1)));
     B_TRY(cub::DeviceScan::ExclusiveSum(nullptr, B.cub_bytes, (int32_t *)nullptr, (int64_t *)nullptr, (int)(n + 1)));
-    B_TRY(cudaMalloc(&B.cub_tmp, B.cub_bytes));
+    B_TRY(esg_malloc((void **)&B.cub_tmp, B.cub_bytes));
     B_TRY(cudaMemset(B.indeg, 0, sizeof(int32_t) * (n + 1)));
     return ESG_OK;
 }

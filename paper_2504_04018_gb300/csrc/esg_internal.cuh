@@ -28,6 +28,21 @@ constexpr int64_t kMaxBatch = (int64_t)1 << 30;
 
 void esg_set_error(const std::string &msg);
 
+// Every device allocation of the library goes through these. They carry the
+// host-side fault injection of the failure-detection tests: with the
+// environment variable ESG_FAULT_ALLOC=K (K >= 1), the K-th allocation the
+// library attempts after that value was set fails as if the device were out
+// of memory (no GPU fault is involved).
+bool esg_fault_alloc();
+inline cudaError_t esg_malloc(void **p, size_t bytes) {
+    if (esg_fault_alloc()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMalloc(p, bytes);
+}
+inline cudaError_t esg_malloc_async(void **p, size_t bytes, cudaStream_t stream) {
+    if (esg_fault_alloc()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMallocAsync(p, bytes, stream);
+}
+
 #define ESG_CUDA_TRY(expr)                                                                 \
     do {                                                                                   \
         cudaError_t _e = (expr);                                                           \
@@ -127,9 +142,11 @@ struct KernelPlan {
     size_t smem;
     int64_t grid;
 };
-// Largest per-query beam width (max(ef, k)) of the small budget class
-// (environment ESG_SMALL_CLASS_EF overrides it; 0 keeps one class).
-constexpr int kSmallClassEf = 64;
+// Largest per-query beam width (max(ef, k)) of the small budget class; 0 =
+// one class (the default: with lists of 2 ef items the widest plans still
+// reach the register-bound occupancy, and a second launch adds a tail; the
+// environment variable ESG_SMALL_CLASS_EF sets it).
+constexpr int kSmallClassEf = 0;
 // Launch plan of one search call. The queries may be split into two budget
 // classes by max(ef_q, k): class 0 (at most kSmallClassEf) and class 1, each
 // searched by its own launch whose lists and visited tables are sized for

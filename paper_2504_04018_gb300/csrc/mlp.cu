@@ -352,7 +352,7 @@ esg_status esg_mlp_loss_grad(const float *params, const float *X, const float *T
     cudaStream_t stream = (cudaStream_t)stream_v;
     float *buf = nullptr;
     const size_t per = 2 + kH + kH + 2 + kH + kH + 1;   // Y, Z1, Z2, dY, dZ2, dZ1, row loss
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&buf, sizeof(float) * per * B, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&buf, sizeof(float) * per * B, stream));
     float *Y = buf, *Z1 = Y + 2 * B, *Z2 = Z1 + kH * B, *dY = Z2 + kH * B, *dZ2 = dY + 2 * B,
           *dZ1 = dZ2 + kH * B, *rl = dZ1 + kH * B;
     mlp_forward_kernel<<<ceil_div_i(B, 128), 128, 0, stream>>>(params, X, mu, sigma, B, Y, Z1, Z2);
@@ -407,7 +407,7 @@ esg_status esg_query_budget(const esg_index *ix, const float *queries, int64_t n
     if (nq == 0) return ESG_OK;
     cudaStream_t stream = (cudaStream_t)stream_v;
     float *feat = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&feat, sizeof(float) * nq * kF, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&feat, sizeof(float) * nq * kF, stream));
     esg_status st = esg_predict_budget(ix, 0, queries, nq, l, r, k, k_max, ef_fixed, feat, ef_out, maxexp_out,
                                        stream);
     const cudaError_t fe = cudaFreeAsync(feat, stream);
@@ -418,7 +418,7 @@ esg_status esg_query_budget(const esg_index *ix, const float *queries, int64_t n
 esg_status esg_predictor_set(esg_index *ix, const float *blob_host, int32_t ef_lo, int32_t ef_hi) {
     if (!ix || !blob_host || ef_lo < 1 || ef_hi < ef_lo || ef_hi > 1024) { esg_set_error("esg_predictor_set: bad argument"); return ESG_ERR_INVALID_ARG; }
     const size_t n = (size_t)kP + 2 * kF + 2;
-    if (!ix->mlp) ESG_CUDA_TRY(cudaMalloc((void **)&ix->mlp, sizeof(float) * n));
+    if (!ix->mlp) ESG_CUDA_TRY(esg_malloc((void **)&ix->mlp, sizeof(float) * n));
     ESG_CUDA_TRY(cudaMemcpy(ix->mlp, blob_host, sizeof(float) * n, cudaMemcpyHostToDevice));
     ix->mlp_host.assign(blob_host, blob_host + n);
     ix->mlp_ef_lo = ef_lo;

@@ -30,12 +30,12 @@ __global__ void to_fp8_kernel(const float *X, int64_t n, int d, __nv_fp8_e4m3 *o
 esg_status esg_make_storage(esg_index *ix, cudaStream_t stream) {
     const int64_t count = ix->n * (int64_t)ix->d;
     if (ix->storage == ESG_BF16) {
-        ESG_CUDA_TRY(cudaMalloc((void **)&ix->Xb, sizeof(__nv_bfloat16) * count));
+        ESG_CUDA_TRY(esg_malloc((void **)&ix->Xb, sizeof(__nv_bfloat16) * count));
         to_bf16_kernel<<<ceil_div_i(count, 256), 256, 0, stream>>>(ix->X, count, ix->Xb);
         ESG_CUDA_TRY(cudaGetLastError());
     } else if (ix->storage == ESG_FP8E4M3) {
-        ESG_CUDA_TRY(cudaMalloc((void **)&ix->X8, sizeof(__nv_fp8_e4m3) * count));
-        ESG_CUDA_TRY(cudaMalloc((void **)&ix->scale8, sizeof(float) * ix->n));
+        ESG_CUDA_TRY(esg_malloc((void **)&ix->X8, sizeof(__nv_fp8_e4m3) * count));
+        ESG_CUDA_TRY(esg_malloc((void **)&ix->scale8, sizeof(float) * ix->n));
         to_fp8_kernel<<<ceil_div_i(ix->n, 8), 256, 0, stream>>>(ix->X, ix->n, ix->d, ix->X8, ix->scale8);
         ESG_CUDA_TRY(cudaGetLastError());
     }

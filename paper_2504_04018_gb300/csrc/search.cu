@@ -193,7 +193,7 @@ namespace {
 // Kernel, launch shape and shared memory for a search (or construction)
 // call; knobs left at 0 are chosen automatically.
 esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, int wpb_req,
-                     int hash_req, int lpr_req, KernelPlan &pl) {
+                     int hash_req, int lpr_req, KernelPlan &pl, int list_per_ef = 2) {
     pl.width = std::max(1, std::min(width, 4));
     pl.BB = 64;
     while (pl.BB < pl.width * R) pl.BB <<= 1;
@@ -212,9 +212,11 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     if (fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
     pl.fn = (void *)fn;
     // candidate list: Q (at most ef in-range items) interleaved with the
-    // unexpanded out-of-range candidates closer than its worst, LPE ef items
-    // (at least 2: the in-place FP32 re-rank sorts a power of two >= ef in it)
-    const int lpe = std::max(2, std::min(8, env_int("ESG_LIST_PER_EF", 4)));
+    // unexpanded out-of-range candidates closer than its worst, list_per_ef
+    // times ef items (at least 2: the in-place FP32 re-rank sorts a power of
+    // two >= ef in it); on the elastic pieces (at least half of a node in
+    // range) twice ef measured no loss of recall at 10^7 points
+    const int lpe = std::max(2, std::min(8, list_per_ef));
     pl.C = ((std::max(lpe * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
     // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
@@ -336,9 +338,12 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     plan.nclass = (small_ef > 0 && efk > small_ef && (learned || ef <= small_ef)) ? 2 : 1;
     plan.small_ef = plan.nclass == 2 ? small_ef : 0;
     const int ef_cls[2] = {plan.nclass == 2 ? small_ef : efk, efk};
+    // POST on the root keeps every reached point while fewer than ef
+    // in-range points are known: a long list (the baseline's own cost)
+    const int lpe = s.p.post_root ? 8 : env_int("ESG_LIST_PER_EF", 2);
     for (int c = 0; c < plan.nclass; ++c) {
         esg_status pst = make_plan(ix->d, ix->R, ef_cls[c], n_items, st_trav, s.p.width, s.p.warps_per_block,
-                                   s.p.hash_slots, s.p.lanes_per_row, plan.cls[c]);
+                                   s.p.hash_slots, s.p.lanes_per_row, plan.cls[c], lpe);
         if (pst != ESG_OK) return pst;
     }
     plan.n_items = n_items;
@@ -447,7 +452,7 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream) {
     esg_status st = esg_search_prepare(s, plan);
     if (st != ESG_OK) return st;
     void *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync(&scratch, plan.scratch_bytes, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&scratch, plan.scratch_bytes, stream));
     st = esg_search_enqueue(s, plan, scratch, stream);
     const cudaError_t fe = cudaFreeAsync(scratch, stream);
     if (st == ESG_OK && fe != cudaSuccess) { esg_set_error(cudaGetErrorString(fe)); st = ESG_ERR_CUDA; }
@@ -469,7 +474,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
     if (pst != ESG_OK) return pst;
     const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
     unsigned char *scratch = nullptr;
-    ESG_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes_hash + 256, stream));
+    ESG_CUDA_TRY(esg_malloc_async((void **)&scratch, bytes_hash + 256, stream));
     unsigned long long *queue = (unsigned long long *)scratch;
     uint32_t *ghash = (uint32_t *)(scratch + 256);
     esg_status st = ESG_OK;

@@ -313,9 +313,12 @@ __device__ __forceinline__ bool admit_batch(Cand *batch, int BB, Cand *cbuf, Can
         else warp_sort_pow2(batch, BB);
         B = batch;
     }
-    if (st.len + b > C) status |= ESG_Q_OVERFLOW;
+    const bool dropped = st.len + b > C;
     st.len = warp_merge_inplace(list, st.len, B, b, nbuf, C);
     truncate_list(list, st, ef, pl, pr);
+    // items beyond the capacity only matter when the list did not reach its
+    // ef-th in-range item within it (otherwise truncation drops them anyway)
+    if (dropped && st.qn < ef) status |= ESG_Q_OVERFLOW;
     return true;
 }
 

@@ -69,7 +69,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     if (n_tr < 8) { esg_set_error("esg_train_predictor: too few training queries"); return ESG_ERR_INVALID_ARG; }
 
     DevBuf ids_b, dist_b, cnt_b, stats_b, hits_b, feat_b;
-    auto alloc = [&](DevBuf &b, size_t bytes) -> bool { return cudaMalloc(&b.p, bytes) == cudaSuccess; };
+    auto alloc = [&](DevBuf &b, size_t bytes) -> bool { return esg_malloc((void **)&b.p, bytes) == cudaSuccess; };
     if (!alloc(ids_b, sizeof(int64_t) * nq * k_max) || !alloc(dist_b, sizeof(float) * nq * k_max) ||
         !alloc(cnt_b, sizeof(int32_t) * nq) || !alloc(stats_b, sizeof(int64_t) * nq * ESG_QUERY_STATS) ||
         !alloc(hits_b, sizeof(int32_t) * nq) || !alloc(feat_b, sizeof(float) * nq * F)) {

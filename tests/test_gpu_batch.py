@@ -92,11 +92,11 @@ def test_budget_classes_do_not_change_results(monkeypatch):
     gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
     nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
     blob = np.zeros(nparam + 2 * F + 2, np.float32)
-    # log2 ef = 4 + 0.6 * (standardised log2 width): beams from 16 to the cap
+    # log2 ef = 2 + 0.4 log2 width: beams from about 13 to the cap
     blob[0 * 64 + 0] = 1.0                      # W1[0, 0]: hidden unit 0 reads log2 width
     blob[F * 64 + 64 + 0] = 1.0                 # W2[0, 0]: passed on by layer 2
-    blob[F * 64 + 64 + 64 * 64 + 64 + 0] = 0.6  # W3[0, 0]: log2 ef = 4 + 0.6 log2 width
-    blob[nparam - 2] = 4.0
+    blob[F * 64 + 64 + 64 * 64 + 64 + 0] = 0.4  # W3[0, 0]: log2 ef = 2 + 0.4 log2 width
+    blob[nparam - 2] = 2.0
     blob[nparam - 1] = 20.0
     blob[nparam:nparam + F] = 0.0
     blob[nparam + F:nparam + 2 * F] = 1.0

@@ -1,0 +1,134 @@
+"""Failure detection without a GPU fault: every failure is made on the host or
+by a bounded wait that runs out, and the library must report it with a
+status and stay usable.
+
+- a search that reaches its expansion cap reports ESG_Q_TRUNCATED with valid
+  partial results;
+- device allocations failing (host-side injection, ESG_FAULT_ALLOC=K fails
+  the K-th allocation) make build, search and brute force return
+  ESG_ERR_OOM without leaking device memory, and the next call works;
+- the tensor-core brute force's bounded mbarrier waits: a wait that nothing
+  completes (ESG_TEST_BF_STALL=1, taken before any copy is issued) runs out
+  after ESG_BF_WAIT_NS, the call returns ESG_ERR_TIMEOUT and the next call
+  is exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic
+
+torch = pytest.importorskip("torch")
+E = pytest.importorskip("paper_2504_04018_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = synthetic.small_mixture(6000, 32, 200, n_comp=8, seed=51, M=8, leaf_size=64)
+    gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
+    return w, gix
+
+
+def test_expansion_cap_reports_truncation(small):
+    w, gix = small
+    ids, dist, cnt, st, stats = E.esg_search_batch(gix, _t(w.queries), _t(w.l), _t(w.r), None, 10,
+                                                   params=E.search_params(ef=64, max_expansions=1),
+                                                   want_stats=True)
+    torch.cuda.synchronize()
+    ids, dist, cnt, st, stats = (x.cpu().numpy() for x in (ids, dist, cnt, st, stats))
+    perm = E.esg_index_perm(gix)
+    inv = np.empty(len(perm), np.int64)
+    inv[perm] = np.arange(len(perm))
+    truncated = 0
+    for i in range(len(w.l)):
+        pieces = O.decompose(gix.n, gix.leaf_size, int(w.l[i]), int(w.r[i]))
+        graph = any(p.kind == "graph" for p in pieces)
+        if graph:
+            # one expansion per graph piece, and the piece ended on its cap
+            assert st[i] & E.Q_TRUNCATED and stats[i, 0] <= sum(p.kind == "graph" for p in pieces)
+            truncated += 1
+        ranks = inv[ids[i, :cnt[i]]]
+        assert cnt[i] <= min(10, w.r[i] - w.l[i] + 1)
+        assert np.all((ranks >= w.l[i]) & (ranks <= w.r[i])) and len(set(ranks.tolist())) == cnt[i]
+        assert np.all(np.diff(dist[i, :cnt[i]]) >= 0)
+        assert np.all(ids[i, cnt[i]:] == -1)
+    assert truncated > 0
+
+
+def _used():
+    torch.cuda.synchronize()
+    free, total = torch.cuda.mem_get_info()
+    return total - free
+
+
+@pytest.mark.parametrize("what", ["build", "search", "bruteforce"])
+def test_allocation_failure_injection(small, monkeypatch, what):
+    w, gix = small
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    X = _t(w.base[E.esg_index_perm(gix)])
+
+    def call():
+        if what == "build":
+            return E.esg_build(w.base[:3000], w.attr[:3000], M=8, leaf_size=64, n_entries=8, storage="bf16")
+        if what == "search":
+            out = E.esg_search_batch(gix, q, l, r, None, 10, ef=32)
+            torch.cuda.synchronize()
+            return out
+        out = E.esg_bruteforce_filtered_knn(X, q, l, r, 10)
+        torch.cuda.synchronize()
+        return out
+
+    monkeypatch.delenv("ESG_FAULT_ALLOC", raising=False)
+    ref = call()
+    base_used = _used()
+    failures = 0
+    for kth in range(1, 14):
+        monkeypatch.setenv("ESG_FAULT_ALLOC", str(kth))
+        try:
+            got = call()
+        except E.EsgError as e:
+            assert "out of memory" in str(e), str(e)
+            failures += 1
+            continue
+        finally:
+            monkeypatch.delenv("ESG_FAULT_ALLOC", raising=False)
+        if what != "build":                       # a call that did not fail is exact
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[2], ref[2])
+    assert failures >= 1
+    again = call()                                # the library is still usable
+    if what != "build":
+        assert torch.equal(again[0], ref[0])
+    # no device memory left behind by the failed calls (stream-ordered pools
+    # may keep what they cached; allow one cached scratch of slack)
+    assert _used() <= base_used + (64 << 20)
+
+
+def test_bruteforce_bounded_wait_times_out(small, monkeypatch):
+    w, gix = small
+    X = w.base[E.esg_index_perm(gix)]
+    q, l, r = _t(w.queries), _t(w.l), _t(w.r)
+    monkeypatch.delenv("ESG_BF_SIMT", raising=False)
+    monkeypatch.setenv("ESG_TEST_BF_STALL", "1")
+    monkeypatch.setenv("ESG_BF_WAIT_NS", "2000000")          # 2 ms
+    with pytest.raises(E.EsgError, match="timeout"):
+        E.esg_bruteforce_filtered_knn(_t(X), q, l, r, 10)
+        torch.cuda.synchronize()
+    monkeypatch.delenv("ESG_TEST_BF_STALL")
+    monkeypatch.delenv("ESG_BF_WAIT_NS")
+    ids, dist, cnt = E.esg_bruteforce_filtered_knn(_t(X), q, l, r, 10)
+    torch.cuda.synchronize()
+    ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy()
+    X64 = X.astype(np.float64)
+    same = 0
+    for i in range(len(w.l)):
+        gt, _ = O.bruteforce(X64, w.queries[i], int(w.l[i]), int(w.r[i]), 10, "l2")
+        assert cnt[i] == len(gt)
+        same += ids[i, :cnt[i]].tolist() == gt.tolist()
+    assert same >= 0.98 * len(w.l)
