@@ -425,7 +425,6 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     a.max_exp = s.p.max_expansions > 0 ? s.p.max_expansions : 16 * plan.ef + 256;
     a.k_max = s.k_max; a.ghash = ghash;
     a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
-    a.prefetch = env_int("ESG_PREFETCH_ROWS", 0);
     // the large class first: its items are the longest
     for (int c = plan.nclass - 1; c >= 0; --c) {
         const KernelPlan &kp = plan.cls[c];

@@ -119,22 +119,14 @@ __device__ __forceinline__ float accum_vec(const uint4 &raw, const float *qs, fl
     return acc;
 }
 
-// Bulk prefetch of `bytes` (a multiple of 16) at a 16-byte aligned global
-// address into L2 (no registers held, no completion to wait for).
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
-}
-
 // Distances from the query (FP32, staged in shared memory `qs`) to the rows
 // listed in nbuf[0..m), written to batch[0..m). Rows are nvec 16-byte
 // vectors; LPR lanes share a row, each loading VPL vectors, and the loads of
-// U passes are all issued before any reduction. With `prefetch`, every row
-// past the first pass is first fetched into L2 by one bulk prefetch, so that
-// the later passes wait on L2 instead of DRAM.
+// U passes are all issued before any reduction.
 template <int ST, int VPL>
 __device__ __forceinline__ void eval_rows(const uint4 *__restrict__ Xv, const float *__restrict__ scale8,
                                           int nvec, int LPR, const float *qs, const uint32_t *nbuf,
-                                          int m, Cand *batch, int metric, int prefetch = 0) {
+                                          int m, Cand *batch, int metric) {
     constexpr int EPV = Store<ST>::EPV;
     const int lane = threadIdx.x & 31;
     const int s = lane & (LPR - 1);
@@ -145,9 +137,6 @@ __device__ __forceinline__ void eval_rows(const uint4 *__restrict__ Xv, const fl
     constexpr int W = ST == ESG_F32 ? 1 : (ST == ESG_BF16 ? 2 : 4);
     constexpr int U0 = 16 / (VPL * W);
     constexpr int U = U0 < 1 ? 1 : (U0 > 8 ? 8 : U0);
-    if (prefetch)
-        for (int row = rows_per_pass * U + lane; row < m; row += 32)
-            prefetch_l2(Xv + (size_t)nbuf[row] * nvec, (uint32_t)nvec * 16u);
     for (int base = 0; base < m; base += rows_per_pass * U) {
         uint4 xv[U][VPL];
         uint32_t id[U];
@@ -354,7 +343,6 @@ struct SearchArgs {
     int d, nvec, LPR, R, E, metric;
     int ef, max_exp, k_max;
     int width;             // candidates expanded per iteration (1 = Algorithm 1 order)
-    int prefetch = 0;      // L2 bulk prefetch of the neighbour rows beyond the first gather pass
     int BB;                // batch capacity: width * R rounded up to 64
     int H, C;
     uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
@@ -546,7 +534,7 @@ search_kernel(SearchArgs a) {
                 }
                 __syncwarp();
                 if (m == 0) continue;
-                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric, a.prefetch);
+                eval_rows<ST, VPL>(a.Xv, a.scale8, a.nvec, a.LPR, qs, w.nbuf, m, w.batch, a.metric);
                 n_eval += m;
                 // Algorithm 1's admission test, then de-duplication against
                 // the list (only needed once the visited set saturates)
