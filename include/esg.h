@@ -407,7 +407,9 @@ esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq
  * expansions it used; trains the MLP with a pinball loss at `quantile` using
  * the library's GPU forward/backward/Adam kernels (epochs, batch, lr, seed);
  * then calibrates a margin on the last val_fraction of the queries so their
- * mean recall reaches target_recall. report (may be NULL) receives
+ * mean recall reaches target_recall, and an offset to it for every class of
+ * k (floor(log2 k)) with at least 64 of those queries so that the class's
+ * own recall reaches target_recall. report (may be NULL) receives
  * [final training loss, held-out recall, ef margin (log2), held-out distance
  * evaluations per query]. Synchronous. ESG_ERR_UNSUPPORTED if no margin
  * reaches the target.
@@ -432,9 +434,14 @@ esg_status esg_train_predictor(esg_index *index, const float *queries, int64_t n
                                const esg_train_params *params, float *report, esg_stream_t stream);
 
 /* Trained predictor as a host blob [params, mu[F], sigma[F], margin_ef,
- * margin_expansions] (F = esg_mlp_num_features(); esg_mlp_num_params() + 2 F + 2
- * floats) with its ef range;
+ * margin_expansions, offset[12]] of esg_mlp_blob_size() floats
+ * (F = esg_mlp_num_features(); esg_mlp_num_params() + 2 F + 14) with its ef
+ * range. A query's predicted log2 ef gets margin_ef plus offset[c], c =
+ * floor(log2 k) capped at 11 (esg_train_predictor calibrates one margin, then
+ * an offset per class of k so that each class reaches the target recall on
+ * its own); its log2 expansion budget gets margin_expansions.
  * set installs one (e.g. a saved one), get reads it back. */
+int32_t esg_mlp_blob_size(void);
 esg_status esg_predictor_set(esg_index *index, const float *blob, int32_t ef_lo, int32_t ef_hi);
 esg_status esg_predictor_get(const esg_index *index, float *blob, int32_t *ef_lo, int32_t *ef_hi);
 

@@ -37,7 +37,7 @@ EXPORTED = [
     "esg_index_export_storage", "esg_index_add_storage", "esg_batch_create", "esg_batch_buffers",
     "esg_batch_run", "esg_batch_free", "esg_autotune", "esg_search_batch_noalloc",
     "esg_train_params_default", "esg_train_predictor", "esg_predictor_set", "esg_predictor_get",
-    "esg_mlp_num_params", "esg_mlp_num_features", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
+    "esg_mlp_num_params", "esg_mlp_num_features", "esg_mlp_blob_size", "esg_mlp_forward", "esg_mlp_loss_grad", "esg_mlp_adam_step",
     "esg_query_features", "esg_query_budget", "esg_index_export_rows",
 ]
 
@@ -120,6 +120,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.esg_predictor_get.argtypes = [_P, _P, _P, _P]
     lib.esg_mlp_num_params.restype = _I32
     lib.esg_mlp_num_features.restype = _I32
+    lib.esg_mlp_blob_size.restype = _I32
     lib.esg_mlp_forward.argtypes = [_P, _P, _P, _P, _I64, _P, _P]
     lib.esg_mlp_loss_grad.argtypes = [_P, _P, _P, _P, _P, _I64, ctypes.c_float, _P, _P, _P]
     lib.esg_mlp_adam_step.argtypes = [_P, _P, _P, _P, _I32, ctypes.c_float, _P]
@@ -602,7 +603,7 @@ def esg_train_predictor(index: Index, queries, l, r, gt_ids, gt_count, k_max: in
 
 def esg_predictor_get(index: Index):
     lib = load_library()
-    blob = np.empty(lib.esg_mlp_num_params() + 2 * lib.esg_mlp_num_features() + 2, dtype=np.float32)
+    blob = np.empty(lib.esg_mlp_blob_size(), dtype=np.float32)
     lo, hi = _I32(), _I32()
     _check(lib.esg_predictor_get(index.handle, _np_ptr(blob), ctypes.byref(lo), ctypes.byref(hi)),
            "esg_predictor_get")
@@ -621,6 +622,11 @@ def esg_mlp_num_params() -> int:
 
 def esg_mlp_num_features() -> int:
     return int(load_library().esg_mlp_num_features())
+
+
+def esg_mlp_blob_size() -> int:
+    """Floats of a predictor blob (esg_predictor_get / esg_predictor_set)."""
+    return int(load_library().esg_mlp_blob_size())
 
 
 def esg_mlp_forward(params, X, mu, sigma, stream=None):

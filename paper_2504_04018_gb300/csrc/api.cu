@@ -457,7 +457,7 @@ esg_status esg_attr_to_rank_range(const esg_index *ix, const double *lo, const d
 
 namespace {
 const char kMagic[8] = {'E', 'S', 'G', 'G', 'B', '3', '0', '0'};
-const uint32_t kVersion = 4;
+const uint32_t kVersion = 5;
 
 struct FileHeader {
     char magic[8];
@@ -540,7 +540,7 @@ esg_status esg_load(const char *path, esg_index **out) {
     if (s == ESG_OK && (!dim_ok(h.d) || h.R < 1 || h.R > 128 || h.E < 1 ||
                         h.E > 32 || h.n_heap != shape.n_heap || h.L != shape.L || h.adj_rows != shape.adj_rows ||
                         (h.attr_count != 0 && h.attr_count != (uint64_t)h.n) ||
-                        (h.mlp_count != 0 && h.mlp_count != (uint64_t)esg_mlp_param_count() + 2 * ESG_MLP_FEATURES + 2)))
+                        (h.mlp_count != 0 && h.mlp_count != (uint64_t)esg_mlp_blob_floats())))
         s = ESG_ERR_CORRUPT;
     std::vector<float> X;
     std::vector<int64_t> perm;

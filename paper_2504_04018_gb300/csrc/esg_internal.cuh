@@ -12,6 +12,8 @@
 
 #define ESG_NONE 0xFFFFFFFFu
 #define ESG_MLP_FEATURES 9
+// classes of k (floor(log2 k), capped) with their own beam-width margin
+#define ESG_MLP_KBUCKETS 12
 // per-item search statistics: expansions, evaluations, out-of-range
 // evaluations, re-ranked rows, start and end time (ns, %globaltimer)
 #define ESG_ITEM_STATS 6
@@ -182,6 +184,14 @@ esg_status esg_make_storage(esg_index *ix, cudaStream_t stream);
 
 // learned predictor (mlp.cu): features + per-query ef and expansion budget
 int esg_mlp_param_count();
+// floats of the predictor blob: params, mu, sigma, the ef and expansion
+// margins, one ef margin offset per class of k
+inline int esg_mlp_blob_floats() { return esg_mlp_param_count() + 2 * ESG_MLP_FEATURES + 2 + ESG_MLP_KBUCKETS; }
+__host__ __device__ inline int esg_k_bucket(int k) {
+    int b = 0;
+    while (b + 1 < ESG_MLP_KBUCKETS && (k >> (b + 1)) > 0) ++b;   // floor(log2 k), capped
+    return b;
+}
 esg_status esg_predict_budget(const esg_index *ix, int post_root, const float *queries, int64_t nq, const int64_t *l,
                               const int64_t *r, const int32_t *k, int32_t k_max, int ef_fixed,
                               float *feat, int32_t *ef_q, int32_t *maxexp_q, cudaStream_t stream);

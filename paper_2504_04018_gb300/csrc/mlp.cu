@@ -301,7 +301,8 @@ __global__ void features_kernel(const float *X, int d, int metric, DecomposeSpec
     if (lane == 0) {
         int ef = ef_fixed, mx = 0;
         if (isfinite(y0) && isfinite(y1)) {
-            const float e = exp2f(fminf(fmaxf(y0 + margin[0], 0.f), 12.f));
+            // the ef margin plus the offset of the query's class of k
+            const float e = exp2f(fminf(fmaxf(y0 + margin[0] + margin[2 + esg_k_bucket(kk)], 0.f), 12.f));
             ef = (int)ceilf(e);
             ef = max(ef_lo, min(ef, ef_hi));
             const float x = exp2f(fminf(fmaxf(y1 + margin[1], 0.f), 20.f));
@@ -417,7 +418,7 @@ esg_status esg_query_budget(const esg_index *ix, const float *queries, int64_t n
 
 esg_status esg_predictor_set(esg_index *ix, const float *blob_host, int32_t ef_lo, int32_t ef_hi) {
     if (!ix || !blob_host || ef_lo < 1 || ef_hi < ef_lo || ef_hi > 1024) { esg_set_error("esg_predictor_set: bad argument"); return ESG_ERR_INVALID_ARG; }
-    const size_t n = (size_t)kP + 2 * kF + 2;
+    const size_t n = (size_t)esg_mlp_blob_floats();
     if (!ix->mlp) ESG_CUDA_TRY(esg_malloc((void **)&ix->mlp, sizeof(float) * n));
     ESG_CUDA_TRY(cudaMemcpy(ix->mlp, blob_host, sizeof(float) * n, cudaMemcpyHostToDevice));
     ix->mlp_host.assign(blob_host, blob_host + n);
@@ -426,6 +427,8 @@ esg_status esg_predictor_set(esg_index *ix, const float *blob_host, int32_t ef_l
     ix->mlp_ready = 1;
     return ESG_OK;
 }
+
+int32_t esg_mlp_blob_size(void) { return esg_mlp_blob_floats(); }
 
 esg_status esg_predictor_get(const esg_index *ix, float *blob_host, int32_t *ef_lo, int32_t *ef_hi) {
     if (!ix) { esg_set_error("esg_predictor_get: bad argument"); return ESG_ERR_INVALID_ARG; }

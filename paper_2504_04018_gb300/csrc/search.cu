@@ -219,16 +219,12 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     const int lpe = std::max(2, std::min(8, list_per_ef));
     pl.C = ((std::max(lpe * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
-    // shared visited table: ~64 slots per unit of beam width, 2K..8K slots;
-    // the global overflow table takes what does not fit
-    if (hash_req > 0) {
-        pl.H = hash_req;
-    } else {
-        const int per_ef = env_int("ESG_HASH_PER_EF", 64);
-        const int hmax = env_int("ESG_HASH_MAX", 8192);
-        pl.H = 2048;
-        while (pl.H < per_ef * efk && pl.H < hmax) pl.H <<= 1;
-    }
+    // shared visited table: 2,048 slots unless asked otherwise; the global
+    // overflow table takes what does not fit. A table sized for the widest
+    // beam (up to 8K slots) cost more warps per SM than its overflow probes
+    // save: at 10^7 points, ef 128, k up to 100, 185 vs 125 ms per
+    // 100k-query call (FP32 rows)
+    pl.H = hash_req > 0 ? hash_req : env_int("ESG_HASH_DEFAULT", 2048);
     while (pl.H < 4 * R) pl.H <<= 1;
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
@@ -251,12 +247,13 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
 }  // namespace
 
 // Lanes per row (LPR) and float4 per lane (VPL) for rows of d floats: prefer
-// 8 lanes per row (4 rows per warp instruction, short shuffle reductions);
-// wider rows use 16 or 32 lanes.
+// 4 lanes per row (8 rows per warp instruction, two shuffle steps per
+// reduction; 5-7 % faster than 8 lanes on FP32 rows of 96 dimensions), then
+// 8; wider rows use 16 or 32 lanes.
 int esg_pick_vpl(int d, int *lpr) {
     if (d % 4) return 0;
     const int nvec = d / 4;
-    const int lprs[] = {8, 4, 2, 1, 16, 32};
+    const int lprs[] = {4, 8, 2, 1, 16, 32};
     for (int L : lprs) {
         if (nvec % L) continue;
         const int v = nvec / L;

@@ -207,16 +207,19 @@ __device__ __forceinline__ void eval_rows_fp32(const float *__restrict__ X, int 
 // index plus the number of items of the other sequence before it. The batch
 // positions are found first, against the unchanged list, and parked in
 // `pos` (b entries); the list items then move right, 32 at a time from the
-// end, every lane reading before any lane writes, so that no item is
-// overwritten before it is read (a list item never moves left); last the
-// batch items are written. Items whose position reaches C are dropped.
+// end down to the first batch item's position (items before it stay), every
+// lane reading before any lane writes, so that no item is overwritten before
+// it is read (a list item never moves left); last the batch items are
+// written. Items whose position reaches C are dropped.
 // Returns the new length min(a + b, C).
 __device__ __forceinline__ int warp_merge_inplace(Cand *A, int a, const Cand *B, int b, uint32_t *pos,
                                                   int C) {
     const int lane = threadIdx.x & 31;
     for (int j = lane; j < b; j += 32) pos[j] = (uint32_t)(j + lower_rank(A, a, B[j]));
     __syncwarp();
-    for (int i0 = ((a - 1) >> 5) << 5; i0 >= 0; i0 -= 32) {
+    // list items before the first batch item's position do not move
+    const int first = b > 0 ? (int)pos[0] : a;
+    for (int i0 = ((a - 1) >> 5) << 5; i0 >= (first & ~31); i0 -= 32) {
         const int i = i0 + lane;
         Cand x;
         int p = C;

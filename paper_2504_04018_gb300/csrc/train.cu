@@ -196,17 +196,36 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     }
     ESG_CUDA_TRY(cudaMemcpyAsync(params.data(), p_b.p, sizeof(float) * P, cudaMemcpyDeviceToHost, stream));
     ESG_CUDA_TRY(cudaStreamSynchronize(stream));
-    // 5. calibrate the ef margin on the held-out split (bisection in log2 units)
-    std::vector<float> blob(P + 2 * F + 2);
+    // 5. calibrate the ef margin on the held-out split (bisection in log2
+    // units), first one margin for all queries, then an offset per class of
+    // k (floor(log2 k)) so that each class reaches the target on its own:
+    // the classes with large k dominate the pooled recall, and one margin
+    // set by them widens the beams of the small-k queries for nothing
+    const int KB = ESG_MLP_KBUCKETS;
+    std::vector<float> blob(esg_mlp_blob_floats(), 0.f);
     std::memcpy(blob.data(), params.data(), sizeof(float) * P);
     std::memcpy(blob.data() + P, mu.data(), sizeof(float) * F);
     std::memcpy(blob.data() + P + F, sigma.data(), sizeof(float) * F);
+    float *margins = blob.data() + P + 2 * F;   // [ef, expansions, ef offset per class of k]
     const float exp_margin = 1.0f;   // expansion budget: twice the predicted expansions
+    std::vector<int> vb(n_val);
+    std::vector<double> gv_b(KB, 0.0);
+    std::vector<int64_t> nv_b(KB, 0);
     double gv = 0;
-    for (int64_t i = n_tr; i < nq; ++i) gv += gc[i];
-    auto val_recall = [&](float margin, double &rec, double &mean_ef) -> esg_status {
-        blob[P + 2 * F] = margin;
-        blob[P + 2 * F + 1] = exp_margin;
+    {
+        std::vector<int32_t> hk(nq, k_max);
+        if (k) ESG_CUDA_TRY(cudaMemcpy(hk.data(), k, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
+        for (int64_t i = n_tr; i < nq; ++i) {
+            const int b = esg_k_bucket(std::max(1, std::min(hk[i], k_max)));
+            vb[i - n_tr] = b;
+            gv_b[b] += gc[i];
+            ++nv_b[b];
+            gv += gc[i];
+        }
+    }
+    std::vector<double> rec_b(KB, 1.0);
+    auto val_recall = [&](double &rec, double &mean_ef) -> esg_status {
+        margins[1] = exp_margin;
         esg_status st = esg_predictor_set(ix, blob.data(), tp.ef_lo, tp.ef_hi);
         if (st != ESG_OK) return st;
         esg_search_params q = sp;
@@ -223,30 +242,59 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         ESG_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), stats, sizeof(int64_t) * n_val * ESG_QUERY_STATS, cudaMemcpyDeviceToHost, stream));
         ESG_CUDA_TRY(cudaStreamSynchronize(stream));
         double h = 0, ev = 0;
-        for (int64_t i = 0; i < n_val; ++i) { h += h_hits[i]; ev += h_stats[i * ESG_QUERY_STATS + 1]; }
+        std::vector<double> h_b(KB, 0.0);
+        for (int64_t i = 0; i < n_val; ++i) {
+            h += h_hits[i];
+            h_b[vb[i]] += h_hits[i];
+            ev += h_stats[i * ESG_QUERY_STATS + 1];
+        }
         rec = gv > 0 ? h / gv : 1.0;
+        for (int b = 0; b < KB; ++b) rec_b[b] = gv_b[b] > 0 ? h_b[b] / gv_b[b] : 1.0;
         mean_ef = ev / n_val;   // distance evaluations per query
         return ESG_OK;
     };
     float lo = -4.f, hi = 4.f;
     double rec_hi = 0, cost_hi = 0;
-    esg_status st = val_recall(hi, rec_hi, cost_hi);
+    margins[0] = hi;
+    esg_status st = val_recall(rec_hi, cost_hi);
     if (st != ESG_OK) return st;
     if (rec_hi < tp.target_recall) {
         ix->mlp_ready = 0;
         esg_set_error("esg_train_predictor: even the largest margin misses the target recall");
         return ESG_ERR_UNSUPPORTED;
     }
-    double rec_best = rec_hi, cost_best = cost_hi;
     for (int it = 0; it < 10; ++it) {
         const float mid = 0.5f * (lo + hi);
         double rec = 0, cost = 0;
-        st = val_recall(mid, rec, cost);
+        margins[0] = mid;
+        st = val_recall(rec, cost);
         if (st != ESG_OK) return st;
-        if (rec >= tp.target_recall) { hi = mid; rec_best = rec; cost_best = cost; } else lo = mid;
+        if (rec >= tp.target_recall) hi = mid; else lo = mid;
+    }
+    margins[0] = hi;
+    // per-class offsets, all classes bisected together (a search serves all
+    // of them); a class with too few held-out queries keeps offset 0, and a
+    // class whose widest offset misses the target keeps that widest offset
+    const int64_t kMinClass = 64;
+    std::vector<float> olo(KB, -4.f), ohi(KB, 4.f);
+    bool any = false;
+    for (int b = 0; b < KB; ++b) if (nv_b[b] >= kMinClass) any = true;
+    if (any) {
+        for (int it = 0; it < 10; ++it) {
+            for (int b = 0; b < KB; ++b) margins[2 + b] = nv_b[b] >= kMinClass ? 0.5f * (olo[b] + ohi[b]) : 0.f;
+            double rec = 0, cost = 0;
+            st = val_recall(rec, cost);
+            if (st != ESG_OK) return st;
+            for (int b = 0; b < KB; ++b) {
+                if (nv_b[b] < kMinClass) continue;
+                const float mid = margins[2 + b];
+                if (rec_b[b] >= tp.target_recall) ohi[b] = mid; else olo[b] = mid;
+            }
+        }
+        for (int b = 0; b < KB; ++b) margins[2 + b] = nv_b[b] >= kMinClass ? ohi[b] : 0.f;
     }
     double rec_f = 0, cost_f = 0;
-    st = val_recall(hi, rec_f, cost_f);
+    st = val_recall(rec_f, cost_f);
     if (st != ESG_OK) return st;
     if (report) {
         report[0] = last_loss;
@@ -254,6 +302,5 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
         report[2] = hi;
         report[3] = (float)cost_f;
     }
-    (void)rec_best; (void)cost_best;
     return ESG_OK;
 }

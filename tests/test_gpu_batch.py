@@ -91,7 +91,7 @@ def test_budget_classes_do_not_change_results(monkeypatch):
     w = synthetic.small_mixture(20000, 32, 600, n_comp=16, seed=41, M=12, leaf_size=64)
     gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8)
     nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
-    blob = np.zeros(nparam + 2 * F + 2, np.float32)
+    blob = np.zeros(E.esg_mlp_blob_size(), np.float32)
     # log2 ef = 2 + 0.4 log2 width: beams from about 13 to the cap
     blob[0 * 64 + 0] = 1.0                      # W1[0, 0]: hidden unit 0 reads log2 width
     blob[F * 64 + 64 + 0] = 1.0                 # W2[0, 0]: passed on by layer 2

@@ -185,7 +185,7 @@ def test_constant_predictor_equals_fixed_ef(learned_setup):
     saved = E.esg_predictor_get(gix)
     try:
         nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
-        blob = np.zeros(nparam + 2 * F + 2, np.float32)
+        blob = np.zeros(E.esg_mlp_blob_size(), np.float32)
         blob[nparam - 2] = 5.0          # b3[0]: log2 ef
         blob[nparam - 1] = 20.0         # b3[1]: log2 expansion budget (clamped to 16 ef + 256)
         blob[nparam + F:nparam + 2 * F] = 1.0   # feature standard deviations

@@ -113,7 +113,7 @@ def test_noalloc_bf16_traversal_and_learned_budget(bf16_index):
     k = torch.as_tensor(np.array([1, 10, 20] * 1000, np.int32), device=dev)
     _compare(gix, q, l, r, k, 20, E.search_params(ef=32, traversal="bf16"), dev)
     nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
-    blob = np.zeros(nparam + 2 * F + 2, np.float32)
+    blob = np.zeros(E.esg_mlp_blob_size(), np.float32)
     blob[nparam - 2] = 5.0                      # b3[0]: log2 ef
     blob[nparam - 1] = 20.0                     # b3[1]: log2 expansion budget (clamped)
     blob[nparam + F:nparam + 2 * F] = 1.0       # feature standard deviations
