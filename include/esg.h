@@ -165,7 +165,14 @@ typedef struct {
  *  post_root       0 = the elastic decomposition of the index's layout;
  *                  1 = every query is one piece: POST on the root graph alone
  *                  (a scan when the root is a leaf), the baseline the elastic
- *                  graphs improve on (Section 3.1).
+ *                  graphs improve on (Section 3.1);
+ *  max_registers   registers per thread of the search kernel build: 128, or
+ *                  96 (five 128-thread blocks per SM: more resident searches;
+ *                  built for BF16 rows of 3 or 6 and FP8 rows of 1 or 3
+ *                  16-byte vectors per lane, ESG_ERR_UNSUPPORTED otherwise);
+ *                  0 = the 96-register build where it exists and shared
+ *                  memory lets more searches reside with it. Does not change
+ *                  results; esg_autotune picks it.
  */
 typedef struct {
     int32_t ef;
@@ -178,6 +185,7 @@ typedef struct {
     int32_t hash_slots;
     int32_t lanes_per_row;
     int32_t post_root;
+    int32_t max_registers;
 } esg_search_params;
 
 esg_build_params esg_build_params_default(void);
@@ -374,7 +382,7 @@ void esg_batch_free(esg_batch *batch);
  * target_recall (hits among each query's first min(k_i, gt_count_i) exact ids,
  * summed, over the sum of min(k_i, gt_count_i); k_i = k[i], or k_max when k
  * is NULL), then the fastest launch shape (warps per block, visited-table
- * slots, lanes per row) by timing with CUDA events (every shape best of
+ * slots, lanes per row, registers per thread) by timing with CUDA events (every shape best of
  * three, then the six fastest best of eleven). `base` supplies the other
  * fields (traversal, rerank, ...). Writes the chosen parameters to `out` and,
  * if `report` is not NULL, [recall, milliseconds per search of the sample].
@@ -407,9 +415,12 @@ esg_status esg_autotune(const esg_index *index, const float *queries, int64_t nq
  * expansions it used; trains the MLP with a pinball loss at `quantile` using
  * the library's GPU forward/backward/Adam kernels (epochs, batch, lr, seed);
  * then calibrates a margin on the last val_fraction of the queries so their
- * mean recall reaches target_recall, and an offset to it for every class of
- * k (floor(log2 k)) with at least 64 of those queries so that the class's
- * own recall reaches target_recall. report (may be NULL) receives
+ * pooled recall (hits over all their answers) reaches target_recall; with
+ * per_k_class set, also an offset to it for every class of k
+ * (floor(log2 k)) with at least 64 of those queries so that the class's own
+ * recall reaches target_recall (stricter than the pooled target: the classes
+ * of small k, which the pooled recall weighs least, get wider beams).
+ * report (may be NULL) receives
  * [final training loss, held-out recall, ef margin (log2), held-out distance
  * evaluations per query]. Synchronous. ESG_ERR_UNSUPPORTED if no margin
  * reaches the target.
@@ -424,6 +435,7 @@ typedef struct {
     int32_t batch;           /* (1024) */
     int32_t ef_lo, ef_hi;    /* predicted ef range (8, 128) */
     esg_dtype traversal;     /* rows the traced and predicted searches use */
+    int32_t per_k_class;     /* 1: each class of k reaches target_recall on its own (0) */
     uint64_t seed;           /* initial weights and minibatch order */
 } esg_train_params;
 
@@ -437,9 +449,8 @@ esg_status esg_train_predictor(esg_index *index, const float *queries, int64_t n
  * margin_expansions, offset[12]] of esg_mlp_blob_size() floats
  * (F = esg_mlp_num_features(); esg_mlp_num_params() + 2 F + 14) with its ef
  * range. A query's predicted log2 ef gets margin_ef plus offset[c], c =
- * floor(log2 k) capped at 11 (esg_train_predictor calibrates one margin, then
- * an offset per class of k so that each class reaches the target recall on
- * its own); its log2 expansion budget gets margin_expansions.
+ * floor(log2 k) capped at 11 (zero unless esg_train_predictor calibrated
+ * them with per_k_class); its log2 expansion budget gets margin_expansions.
  * set installs one (e.g. a saved one), get reads it back. */
 int32_t esg_mlp_blob_size(void);
 esg_status esg_predictor_set(esg_index *index, const float *blob, int32_t ef_lo, int32_t ef_hi);

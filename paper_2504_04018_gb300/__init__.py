@@ -57,7 +57,8 @@ class _TrainParams(ctypes.Structure):
     _fields_ = [("target_recall", ctypes.c_float), ("per_query_recall", ctypes.c_float),
                 ("quantile", ctypes.c_float), ("lr", ctypes.c_float), ("val_fraction", ctypes.c_float),
                 ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("ef_lo", ctypes.c_int32),
-                ("ef_hi", ctypes.c_int32), ("traversal", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("ef_hi", ctypes.c_int32), ("traversal", ctypes.c_int32), ("per_k_class", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class _SearchParams(ctypes.Structure):
@@ -65,7 +66,8 @@ class _SearchParams(ctypes.Structure):
                 ("rerank", ctypes.c_int32), ("use_learned", ctypes.c_int32),
                 ("traversal", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("hash_slots", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("post_root", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("post_root", ctypes.c_int32),
+                ("max_registers", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -380,11 +382,12 @@ def _check_search_buffers(who: str, index: Index, queries, l, r, k, k_max: int, 
 
 def search_params(ef: int = 64, max_expansions: int = 0, rerank: int = 1, use_learned: int = 0,
                   traversal: str = "f32", width: int = 1, warps_per_block: int = 0,
-                  hash_slots: int = 0, lanes_per_row: int = 0, post_root: int = 0) -> _SearchParams:
+                  hash_slots: int = 0, lanes_per_row: int = 0, post_root: int = 0,
+                  max_registers: int = 0) -> _SearchParams:
     """An esg_search_params record."""
     return _SearchParams(ef, max_expansions, rerank, use_learned,
                          STORAGE[traversal] if isinstance(traversal, str) else traversal, width,
-                         warps_per_block, hash_slots, lanes_per_row, post_root)
+                         warps_per_block, hash_slots, lanes_per_row, post_root, max_registers)
 
 
 def esg_search_batch(index: Index, queries, l, r, k=None, k_max: int = 10, *, ef: int = 64,

@@ -93,7 +93,9 @@ esg_status esg_check_search_params(const esg_search_params &p, const char *who) 
           p.warps_per_block == 4) ||
         (p.hash_slots != 0 && (p.hash_slots < 1024 || p.hash_slots > 16384 ||
                                (p.hash_slots & (p.hash_slots - 1)))) ||
-        p.lanes_per_row < 0 || p.lanes_per_row > 32 || (p.lanes_per_row & (p.lanes_per_row - 1))) {
+        p.lanes_per_row < 0 || p.lanes_per_row > 32 || (p.lanes_per_row & (p.lanes_per_row - 1)) ||
+        !(p.max_registers == 0 || p.max_registers == 96 || p.max_registers == 128) ||
+        !(p.post_root == 0 || p.post_root == 1)) {
         esg_set_error(std::string(who) + ": search parameter out of range");
         return ESG_ERR_INVALID_ARG;
     }
@@ -145,6 +147,7 @@ esg_search_params esg_search_params_default(void) {
     p.hash_slots = 0;
     p.lanes_per_row = 0;
     p.post_root = 0;
+    p.max_registers = 0;
     return p;
 }
 
@@ -160,6 +163,7 @@ esg_train_params esg_train_params_default(void) {
     p.ef_lo = 8;
     p.ef_hi = 128;
     p.traversal = ESG_F32;
+    p.per_k_class = 0;
     p.seed = 4005;
     return p;
 }

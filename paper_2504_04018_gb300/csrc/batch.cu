@@ -189,7 +189,7 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
     }
     cudaStream_t stream = (cudaStream_t)stream_v;
     esg_search_params p = base ? *base : esg_search_params_default();
-    p.warps_per_block = 0; p.hash_slots = 0; p.lanes_per_row = 0;
+    p.warps_per_block = 0; p.hash_slots = 0; p.lanes_per_row = 0; p.max_registers = 0;
     int64_t *ids = nullptr;
     float *dist = nullptr;
     int32_t *cnt = nullptr, *hits = nullptr;
@@ -293,15 +293,19 @@ extern "C" esg_status esg_autotune(const esg_index *ix, const float *queries, in
         if (st != ESG_OK) break;
         const int lprs[] = {0, 4, 8, 16, 32};
         for (int wpb : {1, 2, 4}) {
-            for (int hs : {0, 2048, 4096, 8192}) {
+            for (int hs : {0, 1024, 4096, 8192}) {   // 0: the default, 2,048 slots
                 for (int lpr : lprs) {
-                    esg_search_params pp = c.p;
-                    pp.warps_per_block = wpb; pp.hash_slots = hs; pp.lanes_per_row = lpr;
-                    float ms = 0.f;
-                    esg_status s2 = time_of(pp, ms, 4);
-                    if (s2 == ESG_ERR_UNSUPPORTED) continue;   // shape not valid for this row
-                    if (s2 != ESG_OK) { st = s2; break; }
-                    timed.push_back({pp, c.recall, ms});
+                    for (int mr : {128, 96}) {
+                        esg_search_params pp = c.p;
+                        pp.warps_per_block = wpb; pp.hash_slots = hs; pp.lanes_per_row = lpr;
+                        pp.max_registers = mr;
+                        float ms = 0.f;
+                        esg_status s2 = time_of(pp, ms, 4);
+                        if (s2 == ESG_ERR_UNSUPPORTED) continue;   // shape not valid for this row
+                        if (s2 != ESG_OK) { st = s2; break; }
+                        timed.push_back({pp, c.recall, ms});
+                    }
+                    if (st != ESG_OK) break;
                 }
                 if (st != ESG_OK) break;
             }

@@ -140,7 +140,7 @@ esg_status esg_launch_search(const SearchLaunch &s, cudaStream_t stream);
 // One launch of the beam-search kernel: kernel, shape, shared memory.
 struct KernelPlan {
     void *fn;
-    int vpl, lpr, C, H, G, wpb, nvec, width, BB, efk;
+    int vpl, lpr, C, H, G, wpb, nvec, width, BB, efk, lpe;
     size_t smem;
     int64_t grid;
 };

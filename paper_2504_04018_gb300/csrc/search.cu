@@ -174,10 +174,10 @@ __global__ void decompose_kernel(DecomposeSpec spec, const int64_t *l, const int
 
 typedef void (*SearchFn)(SearchArgs);
 
-SearchFn pick_search(int st, int vpl) {
-    if (st == ESG_BF16) return esg_sk::pick_bf16(vpl);
-    if (st == ESG_FP8E4M3) return esg_sk::pick_fp8(vpl);
-    return esg_sk::pick_f32(vpl);
+SearchFn pick_search(int st, int vpl, bool occ5 = false) {
+    if (st == ESG_BF16) return esg_sk::pick_bf16(vpl, occ5);
+    if (st == ESG_FP8E4M3) return esg_sk::pick_fp8(vpl, occ5);
+    return esg_sk::pick_f32(vpl, occ5);
 }
 
 int env_int(const char *name, int dflt) {
@@ -193,7 +193,7 @@ namespace {
 // Kernel, launch shape and shared memory for a search (or construction)
 // call; knobs left at 0 are chosen automatically.
 esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, int wpb_req,
-                     int hash_req, int lpr_req, KernelPlan &pl, int list_per_ef = 2) {
+                     int hash_req, int lpr_req, int mr_req, KernelPlan &pl, int list_per_ef = 2) {
     pl.width = std::max(1, std::min(width, 4));
     pl.BB = 64;
     while (pl.BB < pl.width * R) pl.BB <<= 1;
@@ -208,24 +208,27 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     }
     if (pl.vpl == 0) { esg_set_error("unsupported dimension / lanes per row"); return ESG_ERR_UNSUPPORTED; }
     if (R > 128) { esg_set_error("R > 128"); return ESG_ERR_UNSUPPORTED; }
-    SearchFn fn = pick_search(st, pl.vpl);
-    if (fn == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
-    pl.fn = (void *)fn;
     // candidate list: Q (at most ef in-range items) interleaved with the
     // unexpanded out-of-range candidates closer than its worst, list_per_ef
     // times ef items (at least 2: the in-place FP32 re-rank sorts a power of
     // two >= ef in it); on the elastic pieces (at least half of a node in
     // range) twice ef measured no loss of recall at 10^7 points
     const int lpe = std::max(2, std::min(8, list_per_ef));
+    pl.lpe = lpe;
     pl.C = ((std::max(lpe * efk, 256) + 31) / 32) * 32;
     if (pl.C > 4096) pl.C = 4096;
-    // shared visited table: 2,048 slots unless asked otherwise; the global
-    // overflow table takes what does not fit. A table sized for the widest
-    // beam (up to 8K slots) cost more warps per SM than its overflow probes
-    // save: at 10^7 points, ef 128, k up to 100, 185 vs 125 ms per
-    // 100k-query call (FP32 rows)
-    pl.H = hash_req > 0 ? hash_req : env_int("ESG_HASH_DEFAULT", 2048);
-    while (pl.H < 4 * R) pl.H <<= 1;
+    // shared visited table: 2,048 slots unless asked otherwise for an item
+    // whose list is the smallest (256 items); the kernel gives an item with
+    // a wider beam two fewer slots per list item above that (its own list
+    // and table share one arena of C items + H slots), down to 1,024 slots.
+    // The global overflow table takes what does not fit. A table sized for
+    // the widest beam (up to 8K slots) cost more warps per SM than its
+    // overflow probes save: at 10^7 points, ef 128, k up to 100, 185 vs
+    // 125 ms per 100k-query call (FP32 rows)
+    const int hs = hash_req > 0 ? hash_req : env_int("ESG_HASH_DEFAULT", 2048);
+    pl.H = std::max(hs - 2 * (pl.C - 256), std::min(hs, 1024));
+    pl.H = std::max(pl.H, 4 * R);
+    pl.H = (pl.H + 3) & ~3;
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
     pl.wpb = wpb_req > 0 ? wpb_req : 2;
@@ -235,8 +238,27 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (pl.smem > 227 * 1024) { esg_set_error("search plan needs too much shared memory"); return ESG_ERR_UNSUPPORTED; }
-    ESG_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, pl.wpb * 32, pl.smem));
+    // the 128- and the 96-register builds: resident blocks per SM of each
+    SearchFn f128 = pick_search(st, pl.vpl), f96 = pick_search(st, pl.vpl, true);
+    if (f128 == nullptr) { esg_set_error("no search kernel for this dimension and row type"); return ESG_ERR_UNSUPPORTED; }
+    if (mr_req == 96 && f96 == nullptr) {
+        esg_set_error("no 96-register search kernel for this row type and lanes per row");
+        return ESG_ERR_UNSUPPORTED;
+    }
+    int per_sm128 = 0, per_sm96 = 0;
+    ESG_CUDA_TRY(cudaFuncSetAttribute(f128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm128, f128, pl.wpb * 32, pl.smem));
+    if (f96 != nullptr && mr_req != 128) {
+        ESG_CUDA_TRY(cudaFuncSetAttribute(f96, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+        ESG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm96, f96, pl.wpb * 32, pl.smem));
+    }
+    // automatic: the 96-register build only where more searches reside with
+    // it (at 10^7 points, d = 96, 100k queries: BF16 rows at ef 128 118.9
+    // vs 129.5 ms per call, FP8 116.5 vs 128.4)
+    const bool use96 = mr_req == 96 || (mr_req == 0 && f96 != nullptr && per_sm96 > per_sm128);
+    SearchFn fn = use96 ? f96 : f128;
+    per_sm = use96 ? per_sm96 : per_sm128;
+    pl.fn = (void *)fn;
     if (per_sm < 1) { esg_set_error("search kernel does not fit on an SM"); return ESG_ERR_UNSUPPORTED; }
     pl.grid = std::min<int64_t>((int64_t)sms * per_sm, (n_items + pl.wpb - 1) / pl.wpb);
     if (pl.grid < 1) pl.grid = 1;
@@ -288,7 +310,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t hash_bytes(const SearchPlan &plan) {
     size_t b = 0;
     for (int c = 0; c < plan.nclass; ++c)
-        b = std::max(b, (size_t)plan.cls[c].grid * plan.cls[c].wpb * plan.cls[c].G * 4);
+        b = std::max(b, (size_t)plan.cls[c].grid * plan.cls[c].wpb * plan.cls[c].G * 8);
     return b;
 }
 
@@ -340,7 +362,7 @@ esg_status esg_search_prepare(const SearchLaunch &s, SearchPlan &plan) {
     const int lpe = s.p.post_root ? 8 : env_int("ESG_LIST_PER_EF", 2);
     for (int c = 0; c < plan.nclass; ++c) {
         esg_status pst = make_plan(ix->d, ix->R, ef_cls[c], n_items, st_trav, s.p.width, s.p.warps_per_block,
-                                   s.p.hash_slots, s.p.lanes_per_row, plan.cls[c], lpe);
+                                   s.p.hash_slots, s.p.lanes_per_row, s.p.max_registers, plan.cls[c], lpe);
         if (pst != ESG_OK) return pst;
     }
     plan.n_items = n_items;
@@ -385,13 +407,13 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     int32_t *res_cnt = (int32_t *)(scratch + L.cnt);
     int32_t *res_status = res_cnt + n_items;
     int64_t *res_stats = (int64_t *)(scratch + L.stats);
-    uint32_t *ghash = (uint32_t *)(scratch + L.hash);
+    unsigned long long *ghash = (unsigned long long *)(scratch + L.hash);
     unsigned long long *queue = (unsigned long long *)(scratch + L.queue);   // [2] work counters
     int32_t *range = (int32_t *)(scratch + L.queue + 64);                     // [2][2] item ranges
     const size_t bytes_hash = hash_bytes(plan);
 
     ESG_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), stream));
-    ESG_CUDA_TRY(cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream));
+    ESG_CUDA_TRY(cudaMemsetAsync(ghash, 0, bytes_hash, stream));   // tag 0: free for every item
     prep_kernel<<<ceil_div_i(s.nq, 256), 256, 0, stream>>>(esg_spec_of(ix, s.p.post_root), s.l, s.r, s.k,
                                                            s.k_max, s.nq, pieces, kq, qs);
     ESG_CUDA_TRY(cudaGetLastError());
@@ -426,7 +448,7 @@ esg_status esg_search_enqueue(const SearchLaunch &s, const SearchPlan &plan, voi
     for (int c = plan.nclass - 1; c >= 0; --c) {
         const KernelPlan &kp = plan.cls[c];
         a.nvec = kp.nvec; a.width = kp.width; a.BB = kp.BB; a.LPR = kp.lpr;
-        a.H = kp.H; a.C = kp.C; a.G = kp.G;
+        a.H = kp.H; a.C = kp.C; a.G = kp.G; a.lpe = kp.lpe;
         a.queue = queue + c;
         a.range = range + 2 * c;
         const int pidx = esg_prof_begin(stream);
@@ -467,16 +489,16 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
                                 int64_t *res_stats, cudaStream_t stream) {
     if (n_items == 0) return ESG_OK;
     KernelPlan plan;
-    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, 1, 0, 0, 0, plan);
+    esg_status pst = make_plan(d, R, std::max(ef, k), n_items, ESG_F32, 1, 0, 0, 0, 0, plan);
     if (pst != ESG_OK) return pst;
-    const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 4;
+    const size_t bytes_hash = (size_t)plan.grid * plan.wpb * plan.G * 8;
     unsigned char *scratch = nullptr;
     ESG_CUDA_TRY(esg_malloc_async((void **)&scratch, bytes_hash + 256, stream));
     unsigned long long *queue = (unsigned long long *)scratch;
-    uint32_t *ghash = (uint32_t *)(scratch + 256);
+    unsigned long long *ghash = (unsigned long long *)(scratch + 256);
     esg_status st = ESG_OK;
     cudaError_t ce = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0xFF, bytes_hash, stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(ghash, 0, bytes_hash, stream);
     if (ce == cudaSuccess) {
         SearchArgs a;
         a.X = X; a.adj = adj; a.row_off = row_off; a.entries = entries; a.queries = X; a.qidx = qidx;
@@ -486,7 +508,7 @@ esg_status esg_run_search_items(const float *X, int64_t n, int d, int metric, co
         a.Xv = reinterpret_cast<const uint4 *>(X); a.scale8 = nullptr; a.rerank = 0;
         a.width = plan.width; a.BB = plan.BB;
         a.metric = metric; a.ef = ef; a.max_exp = max_exp > 0 ? max_exp : 16 * ef + 256;
-        a.k_max = k; a.H = plan.H; a.C = plan.C; a.ghash = ghash; a.G = plan.G; a.queue = queue;
+        a.k_max = k; a.H = plan.H; a.C = plan.C; a.lpe = plan.lpe; a.ghash = ghash; a.G = plan.G; a.queue = queue;
         a.res = res; a.res_cnt = res_cnt; a.res_status = res_status; a.res_stats = res_stats;
         ((SearchFn)plan.fn)<<<(unsigned)plan.grid, plan.wpb * 32, plan.smem, stream>>>(a);
         ce = cudaGetLastError();

@@ -4,7 +4,8 @@
 
 namespace esg_sk {
 
-SearchFn pick_f32(int vpl) {
+SearchFn pick_f32(int vpl, bool occ5) {
+    if (occ5) return nullptr;   // FP32 rows spill at 96 registers
     switch (vpl) {
         case 1: return search_kernel<ESG_F32, 1>;
         case 2: return search_kernel<ESG_F32, 2>;

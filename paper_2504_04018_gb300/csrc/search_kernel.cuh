@@ -10,7 +10,6 @@ constexpr int kBatch = 64;  // neighbours handled per expansion (R <= 64 per pas
 
 struct WarpSmem {
     uint32_t *hash;
-    Cand *list;
     Cand *batch;
     uint32_t *nbuf;
     int *hcount;
@@ -26,21 +25,25 @@ __device__ __forceinline__ uint32_t hash_mix(uint32_t x) {
 // global-memory slot. visit() returns false iff `id` was already visited.
 // Only when both tables are at their limits is an id reported as new without
 // being stored (`saturated`; the list de-duplication then catches repeats).
+// A global slot holds (tag << 32 | id), the tag being the work item's index
+// + 1: a slot with another tag is free for this item, so the table is zeroed
+// once per launch and never cleared between the items a warp runs.
 struct Visited {
-    uint32_t *hs;   // shared table, hmask + 1 slots
-    uint32_t hmask;
+    uint32_t *hs;   // shared table, hsize slots (a multiple of 4)
+    uint32_t hsize;
     int *hcount;
     int hlimit;
-    uint32_t *hg;   // global overflow table, gmask + 1 slots (all ESG_NONE when unused)
+    unsigned long long *hg;   // global overflow table, gmask + 1 slots
     uint32_t gmask;
+    uint32_t tag;             // this item's tag (>= 1)
     int *gcount;
     int glimit;
 };
 
-__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated, bool *used_g) {
-    uint32_t h = hash_mix(id) & v.hmask;
-    for (uint32_t probe = 0; probe <= v.hmask; ++probe) {
-        const uint32_t slot = (h + probe) & v.hmask;
+__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated) {
+    // first slot by multiply-shift range reduction (any table size)
+    uint32_t slot = __umulhi(hash_mix(id), v.hsize);
+    for (uint32_t probe = 0; probe < v.hsize; ++probe, slot = slot + 1 == v.hsize ? 0 : slot + 1) {
         const uint32_t cur = v.hs[slot];
         if (cur == id) return false;
         if (cur == ESG_NONE) {
@@ -51,18 +54,21 @@ __device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *satur
         }
     }
     if (v.hg == nullptr) { *saturated = true; return true; }
-    *used_g = true;
-    h = hash_mix(id ^ 0x9e3779b9u) & v.gmask;
+    const unsigned long long mine = ((unsigned long long)v.tag << 32) | id;
+    const uint32_t h = hash_mix(id ^ 0x9e3779b9u) & v.gmask;
     for (uint32_t probe = 0; probe <= v.gmask; ++probe) {
         const uint32_t slot = (h + probe) & v.gmask;
-        const uint32_t cur = *(volatile uint32_t *)&v.hg[slot];
-        if (cur == id) return false;
-        if (cur == ESG_NONE) {
-            if (*(volatile int *)v.gcount >= v.glimit) { *saturated = true; return true; }
-            const uint32_t prev = atomicCAS(&v.hg[slot], ESG_NONE, id);
-            if (prev == ESG_NONE) { atomicAdd(v.gcount, 1); return true; }
-            if (prev == id) return false;
+        const unsigned long long cur = *(volatile unsigned long long *)&v.hg[slot];
+        if ((uint32_t)(cur >> 32) == v.tag) {   // taken by this item
+            if ((uint32_t)cur == id) return false;
+            continue;
         }
+        if (*(volatile int *)v.gcount >= v.glimit) { *saturated = true; return true; }
+        // only this warp's lanes write its table, always with this tag: a
+        // failed swap leaves a slot of this item, holding `id` or another id
+        const unsigned long long prev = atomicCAS(&v.hg[slot], cur, mine);
+        if (prev == cur) { atomicAdd(v.gcount, 1); return true; }
+        if (prev == mine) return false;
     }
     *saturated = true;
     return true;
@@ -347,8 +353,9 @@ struct SearchArgs {
     int ef, max_exp, k_max;
     int width;             // candidates expanded per iteration (1 = Algorithm 1 order)
     int BB;                // batch capacity: width * R rounded up to 64
-    int H, C;
-    uint32_t *ghash;       // global overflow visited tables, G slots per warp (all ESG_NONE), or null
+    int H, C;              // per warp: table slots and list items of the widest beam
+    int lpe;               // list items per unit of an item's beam width (>= 2)
+    unsigned long long *ghash;  // global overflow visited tables, G slots per warp (zeroed), or null
     int G;
     unsigned long long *queue;  // atomic work counter
     const int32_t *order = nullptr;  // optional: the counter's k-th value runs item order[range[0] + k]
@@ -359,8 +366,11 @@ struct SearchArgs {
     int64_t *res_stats;    // [n_items, ESG_ITEM_STATS]
 };
 
-template <int ST, int VPL>
-__global__ void __launch_bounds__(128, 4)
+// MINB: resident blocks of 128 threads per SM the register allocation is
+// sized for (4: up to 128 registers; 5: up to 96, instantiated only where
+// that compiles without spills).
+template <int ST, int VPL, int MINB = 4>
+__global__ void __launch_bounds__(128, MINB)
 search_kernel(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -372,21 +382,20 @@ search_kernel(SearchArgs a) {
     unsigned char *base = smem_raw + per_warp * wib;
     WarpSmem w;
     size_t off = 0;
-    w.list = (Cand *)(base + off); off += (size_t)a.C * 8;
     w.batch = (Cand *)(base + off); off += (size_t)a.BB * 8;
     Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
     w.nbuf = (uint32_t *)(base + off); off += (size_t)a.BB * 4;
     w.hcount = (int *)(base + off); off += 16;
     float *qs = (float *)(base + off); off += qbytes;
     const int gwarp = blockIdx.x * wpb + wib;
-    w.hash = (uint32_t *)(base + off);
+    // the arena of C list items and H table slots is split per item: the
+    // list takes what the item's beam needs, the visited table the rest
+    unsigned char *arena = base + off;
     Visited vis;
-    vis.hs = w.hash;
-    vis.hmask = (uint32_t)a.H - 1;
     vis.hcount = w.hcount;
-    vis.hlimit = (a.H * 3) / 4;
     vis.hg = a.ghash ? a.ghash + (size_t)gwarp * a.G : nullptr;
     vis.gmask = (uint32_t)a.G - 1;
+    vis.tag = 0;
     vis.gcount = w.hcount + 1;
     vis.glimit = (a.G * 3) / 4;
 
@@ -428,7 +437,14 @@ search_kernel(SearchArgs a) {
             __syncwarp();
         }
         ListState st{0, 0, Cand{INFINITY, ESG_NONE}, -1};
-        Cand *list = w.list;
+        // list capacity for this item's beam (as the plan sizes it for the
+        // widest one), a multiple of 32; the table gets 2 slots per item freed
+        const int cap = min(a.C, ((max(a.lpe * ef, 256) + 31) / 32) * 32);
+        Cand *list = reinterpret_cast<Cand *>(arena);
+        w.hash = reinterpret_cast<uint32_t *>(arena + (size_t)cap * 8);
+        vis.hs = w.hash;
+        vis.hsize = (uint32_t)(a.H + 2 * (a.C - cap));
+        vis.hlimit = (int)(vis.hsize / 4) * 3;
         bool saturated = false;
 
         if (!is_graph) {
@@ -444,17 +460,18 @@ search_kernel(SearchArgs a) {
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status);
+                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, cap, pl, pr, status);
             }
         } else {
             // Graph piece: Algorithm 1 with POST filtering to [pl, pr].
-            {   // the table starts 16-byte aligned and H is a power of two >= 256
+            {   // the table starts 16-byte aligned and holds a multiple of 4 slots
                 uint4 *h4 = reinterpret_cast<uint4 *>(w.hash);
-                for (int i = lane; i < a.H / 4; i += 32) h4[i] = make_uint4(ESG_NONE, ESG_NONE, ESG_NONE, ESG_NONE);
+                for (uint32_t i = lane; i < vis.hsize / 4; i += 32)
+                    h4[i] = make_uint4(ESG_NONE, ESG_NONE, ESG_NONE, ESG_NONE);
             }
             if (lane == 0) { w.hcount[0] = 0; w.hcount[1] = 0; }
             __syncwarp();
-            bool used_g = false;
+            vis.tag = (uint32_t)item + 1u;
             const uint32_t *adj = a.adj + (size_t)a.row_off[pc.depth] * a.R;
             // entry points: into P, and into Q when in range
             {
@@ -463,7 +480,7 @@ search_kernel(SearchArgs a) {
                     const int32_t v = a.entries[(size_t)pc.heap * a.E + lane];
                     if (v >= 0 && v < a.n) e = (uint32_t)v;
                 }
-                const bool nw = e != ESG_NONE && visit(vis, e, &saturated, &used_g);
+                const bool nw = e != ESG_NONE && visit(vis, e, &saturated);
                 const unsigned bal = __ballot_sync(0xffffffffu, nw);
                 if (nw) w.nbuf[__popc(bal & ((1u << lane) - 1))] = e;
                 const int m = __popc(bal);
@@ -475,7 +492,7 @@ search_kernel(SearchArgs a) {
                     else n_oor += (w.batch[j].id < pl || w.batch[j].id > pr);
                 }
                 __syncwarp();
-                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status);
+                admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, cap, pl, pr, status);
             }
             // all items before `hint` are expanded
             int hint = st.first < 0 ? st.len : st.first;
@@ -525,8 +542,8 @@ search_kernel(SearchArgs a) {
                         uint32_t v1 = c64 + lane + 32 < a.R ? __ldg(row + c64 + lane + 32) : ESG_NONE;
                         if (v0 >= (uint64_t)a.n) v0 = ESG_NONE;   // malformed imported graph: ignore
                         if (v1 >= (uint64_t)a.n) v1 = ESG_NONE;
-                        const bool n0 = v0 != ESG_NONE && visit(vis, v0, &saturated, &used_g);
-                        const bool n1 = v1 != ESG_NONE && visit(vis, v1, &saturated, &used_g);
+                        const bool n0 = v0 != ESG_NONE && visit(vis, v0, &saturated);
+                        const bool n1 = v1 != ESG_NONE && visit(vis, v1, &saturated);
                         const unsigned b0 = __ballot_sync(0xffffffffu, n0);
                         const unsigned b1 = __ballot_sync(0xffffffffu, n1);
                         const int c0 = __popc(b0);
@@ -556,15 +573,10 @@ search_kernel(SearchArgs a) {
                     if (!keep) w.batch[j] = Cand{INFINITY, ESG_NONE};
                 }
                 __syncwarp();
-                if (admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, a.C, pl, pr, status))
+                if (admit_batch(w.batch, a.BB, cbuf, list, w.nbuf, st, ef, cap, pl, pr, status))
                     hint = st.first < 0 ? st.len : st.first;
             }
             if (__any_sync(0xffffffffu, saturated)) status |= ESG_Q_OVERFLOW;
-            if (__any_sync(0xffffffffu, used_g)) {
-                // leave the overflow table clean for the warp's next item
-                for (int i = lane; i < a.G; i += 32) vis.hg[i] = ESG_NONE;
-                __syncwarp();
-            }
         }
         // FP32 re-rank of the final in-range candidates found on low-precision
         // rows, in place: the first ef in-range items are moved to the front
@@ -636,7 +648,8 @@ search_kernel(SearchArgs a) {
 
 namespace esg_sk {
 typedef void (*SearchFn)(SearchArgs);
-SearchFn pick_f32(int vpl);
-SearchFn pick_bf16(int vpl);
-SearchFn pick_fp8(int vpl);
+// occ5: the variant compiled for 5 blocks per SM (nullptr where none exists)
+SearchFn pick_f32(int vpl, bool occ5 = false);
+SearchFn pick_bf16(int vpl, bool occ5 = false);
+SearchFn pick_fp8(int vpl, bool occ5 = false);
 }  // namespace esg_sk

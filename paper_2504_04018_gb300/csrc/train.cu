@@ -197,10 +197,10 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     ESG_CUDA_TRY(cudaMemcpyAsync(params.data(), p_b.p, sizeof(float) * P, cudaMemcpyDeviceToHost, stream));
     ESG_CUDA_TRY(cudaStreamSynchronize(stream));
     // 5. calibrate the ef margin on the held-out split (bisection in log2
-    // units), first one margin for all queries, then an offset per class of
-    // k (floor(log2 k)) so that each class reaches the target on its own:
-    // the classes with large k dominate the pooled recall, and one margin
-    // set by them widens the beams of the small-k queries for nothing
+    // units): one margin for all queries against their pooled recall, then,
+    // if asked, an offset per class of k (floor(log2 k)) so that each class
+    // reaches the target on its own (the pooled recall weighs a query by its
+    // k, so one margin leaves the small-k classes below the target)
     const int KB = ESG_MLP_KBUCKETS;
     std::vector<float> blob(esg_mlp_blob_floats(), 0.f);
     std::memcpy(blob.data(), params.data(), sizeof(float) * P);
@@ -279,7 +279,7 @@ extern "C" esg_status esg_train_predictor(esg_index *ix, const float *queries, i
     std::vector<float> olo(KB, -4.f), ohi(KB, 4.f);
     bool any = false;
     for (int b = 0; b < KB; ++b) if (nv_b[b] >= kMinClass) any = true;
-    if (any) {
+    if (any && tp.per_k_class) {
         for (int it = 0; it < 10; ++it) {
             for (int b = 0; b < KB; ++b) margins[2 + b] = nv_b[b] >= kMinClass ? 0.5f * (olo[b] + ohi[b]) : 0.f;
             double rec = 0, cost = 0;

@@ -119,3 +119,66 @@ def test_budget_classes_do_not_change_results(monkeypatch):
     assert np.any(ef_q <= 64) and np.any(ef_q > 64)          # both classes are used
     assert np.array_equal(ia[ok], ib[ok]) and np.array_equal(ca[ok], cb[ok])
     assert np.array_equal(ta[ok, :5], tb[ok, :5])
+
+
+@pytest.fixture(scope="module")
+def lowp_setup():
+    w = synthetic.small_mixture(12000, 96, 400, n_comp=16, seed=17, M=12, leaf_size=64)
+    gix = E.esg_build(w.base, w.attr, M=w.M, leaf_size=w.leaf_size, n_entries=8, storage="bf16")
+    E.esg_index_add_storage(gix, "fp8")
+    dev = torch.device("cuda:0")
+    t = {"q": torch.as_tensor(w.queries, device=dev), "l": torch.as_tensor(w.l, device=dev),
+         "r": torch.as_tensor(w.r, device=dev)}
+    return w, gix, t
+
+
+@pytest.mark.parametrize("trav", ["bf16", "fp8"])
+def test_register_builds_do_not_change_results(lowp_setup, trav):
+    """The 96-register builds (BF16 rows of 3 or 6 vectors per lane, FP8 rows
+    of 1 or 3) return what the 128-register builds return; other splits and
+    FP32 rows refuse 96 registers."""
+    w, gix, t = lowp_setup
+    for lpr in (0, 1, 2, 4):
+        try:
+            ref = _search(gix, t, E.search_params(ef=48, traversal=trav, lanes_per_row=lpr, max_registers=128))
+        except E.EsgError as e:
+            assert "unsupported" in str(e)
+            continue
+        for mr in (0, 96):
+            try:
+                got = _search(gix, t, E.search_params(ef=48, traversal=trav, lanes_per_row=lpr, max_registers=mr))
+            except E.EsgError as e:
+                assert mr == 96 and "unsupported" in str(e)
+                continue
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[2], ref[2])
+            assert np.array_equal(got[1], ref[1])
+    with pytest.raises(E.EsgError):
+        _search(gix, t, E.search_params(ef=48, max_registers=96))     # FP32 rows: no 96-register build
+    with pytest.raises(E.EsgError):
+        _search(gix, t, E.search_params(ef=48, max_registers=64))
+
+
+def test_list_and_table_split_per_item(lowp_setup):
+    """One batch mixing k = 10 and k = 300 (beam widths 48 and 300): each item
+    sizes its candidate list for its own beam and gives the rest of the arena
+    to its visited table, so a k = 10 query returns exactly what it returns
+    in a batch of k = 10 queries alone (same list capacity, different table
+    sizes), whatever the table size asked for."""
+    w, gix, t = lowp_setup
+    nq = len(w.queries)
+    kk = np.where(np.arange(nq) % 3 == 0, 300, 10).astype(np.int32)
+    kd = torch.as_tensor(kk, device="cuda:0")
+    for hs in (0, 1024, 4096):
+        p = E.search_params(ef=48, traversal="bf16", hash_slots=hs)
+        ids, dist, cnt = E.esg_search_batch(gix, t["q"], t["l"], t["r"], kd, 300, params=p)[:3]
+        torch.cuda.synchronize()
+        ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
+        for k_only in (10, 300):
+            sel = np.nonzero(kk == k_only)[0]
+            st = torch.as_tensor(sel, device="cuda:0")
+            a = E.esg_search_batch(gix, t["q"][st], t["l"][st], t["r"][st], None, k_only, params=p)[:3]
+            torch.cuda.synchronize()
+            a = [x.cpu().numpy() for x in a]
+            assert np.array_equal(a[2], cnt[sel])
+            assert np.array_equal(a[0], ids[sel, :k_only])
+            assert np.array_equal(a[1], dist[sel, :k_only])

@@ -198,3 +198,46 @@ def test_constant_predictor_equals_fixed_ef(learned_setup):
         assert torch.equal(a[4][:, :5], b[4][:, :5])
     finally:
         E.esg_predictor_set(gix, *saved)
+
+
+def test_per_k_class_offsets(learned_setup):
+    """Mixed k (1 and 10): one pooled margin leaves the k = 1 class, which the
+    pooled recall weighs a tenth of a k = 10 query, below the target; with
+    per_k_class each class of k gets its own offset and reaches about the
+    target on unseen queries. Without it the offsets stay zero."""
+    w, gix, X, ent, perm, q, l, r, gt, gc = learned_setup
+    saved = E.esg_predictor_get(gix)
+    ks = np.where(np.arange(len(w.l)) % 2 == 0, 1, 10).astype(np.int32)
+    kd = _t(ks)
+    ntr = 4000
+    nparam, F = E.esg_mlp_num_params(), E.esg_mlp_num_features()
+    gtt, gct = gt[ntr:].cpu().numpy(), gc[ntr:].cpu().numpy()
+
+    def class_recall():
+        ids, _, cnt, _, _ = E.esg_search_batch(gix, q[ntr:], l[ntr:], r[ntr:], kd[ntr:], 10, ef=128,
+                                               use_learned=1)
+        torch.cuda.synchronize()
+        ids, cnt = ids.cpu().numpy(), cnt.cpu().numpy()
+        out = {}
+        for kk in (1, 10):
+            sel = np.nonzero(ks[ntr:] == kk)[0]
+            hits = sum(len(set(ids[i, :cnt[i]].tolist()) & set(gtt[i, :min(kk, gct[i])].tolist())) for i in sel)
+            out[kk] = hits / sum(min(kk, gct[i]) for i in sel)
+        return out
+
+    try:
+        for per_class in (0, 1):
+            E.esg_train_predictor(gix, q[:ntr], l[:ntr], r[:ntr], gt[:ntr], gc[:ntr], k_max=10, k=kd[:ntr],
+                                  target_recall=0.95, epochs=80, ef_lo=8, ef_hi=128, per_k_class=per_class)
+            blob, _, _ = E.esg_predictor_get(gix)
+            offs = blob[nparam + 2 * F + 2:]
+            rec = class_recall()
+            print(f"per_k_class={per_class}: offsets {offs[:4]}, recall by k {rec}")
+            if per_class:
+                assert offs[0] != 0.0 and offs[3] != 0.0
+                assert np.all(offs[[1, 2] + list(range(4, len(offs)))] == 0.0)
+                assert rec[1] >= 0.93 and rec[10] >= 0.93
+            else:
+                assert np.all(offs == 0.0)
+    finally:
+        E.esg_predictor_set(gix, *saved)
