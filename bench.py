@@ -23,8 +23,9 @@ Arms, each at the smallest setting whose recall reaches 0.95:
   learned  per-query ef and expansion budget from the trained predictor,
            BF16 rows + FP32 re-rank, launch shape from the autotuner, the
            whole batch replayed as one CUDA graph (the headline).
-Recall is checked against the exact answers of every query (GPU brute force,
-itself checked against the float64 oracle on a sample): recall@k over all
+Recall is checked against the exact answers of every query (GPU brute force;
+the CPU leg checks it, and every arm's returned distances, against the float64
+oracle on a sample): recall@k over all
 queries (hits among each query's first min(k, width) exact ids, summed, over
 the summed denominators) and recall@10 over the queries with k >= 10; an arm
 qualifies when both reach 0.95.
@@ -280,7 +281,40 @@ def qualifies(rec):
 
 # ---------------------------------------------------------------- CPU baseline
 
-def cpu_baseline(E, O, ix, w, Xr_host, ef, seconds, gt, gc, mem_budget=24 << 30):
+def oracle_checks(w, Xr_host, perm, gt, gc, sample, arm_samples, n_gt=24):
+    """CPU leg, float64 oracle: the GPU ground truth of `n_gt` sampled queries
+    against the oracle's exact answers (identical id lists, largest relative
+    distance error), and for each arm the largest relative error of the
+    distances it returned for the `sample` queries against float64 distances
+    of the same ids (relative to max(|d|, 1 % of the query's largest))."""
+    import oracle as O
+    inv = np.empty(w.n, np.int64)
+    inv[perm] = np.arange(w.n)
+    rng = np.random.default_rng(7)
+    chk = rng.choice(len(w.l), min(n_gt, len(w.l)), replace=False)
+    same, max_rel = 0, 0.0
+    for i in chk:
+        ranks, dd = fp64_exact(O, Xr_host, w.queries[i], int(w.l[i]), int(w.r[i]), int(w.k[i]), w.metric)
+        c = int(gc[i])
+        same += inv[gt[i, :c]].tolist() == ranks.tolist()
+        got = O.distances(Xr_host[inv[gt[i, :c]]], w.queries[i], w.metric)
+        max_rel = max(max_rel, float(np.max(np.abs(got - dd[:c]) / np.maximum(np.abs(dd[:c]), 1e-2 * np.abs(dd).max()))))
+    gt_check = {"sampled": int(len(chk)), "identical_id_lists": int(same), "max_rel_dist_err": max_rel}
+    errs = {}
+    for name, (ids, dist, cnt) in arm_samples.items():
+        e = 0.0
+        for j, i in enumerate(sample):
+            c = int(cnt[j])
+            if c == 0:
+                continue
+            ref = O.distances(Xr_host[inv[ids[j, :c]]], w.queries[i], w.metric)
+            scale = np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max())
+            e = max(e, float(np.max(np.abs(dist[j, :c].astype(np.float64) - ref) / scale)))
+        errs[name] = e
+    return gt_check, errs
+
+
+def cpu_baseline(E, ix, w, Xr_host, ef, seconds, gt, gc, mem_budget=24 << 30):
     """The oracle's ESG search (Algorithm 4 + Algorithm 1 in plain C, float64)
     on the GPU index's own graph at the plain arm's ef, on the first queries of
     the workload (all widths): one host thread, then all host cores (a thread
@@ -292,6 +326,7 @@ def cpu_baseline(E, O, ix, w, Xr_host, ef, seconds, gt, gc, mem_budget=24 << 30)
     exported rows, each wave timed on one thread and on all cores. The sample
     size is set from a probe to about `seconds` of one-thread search. Also
     returns the oracle's recall on the sample against the exact answers."""
+    import oracle as O
     X64 = Xr_host.astype(np.float64)
     ent_all = E.esg_index_export_entries(ix)
     perm = perm_of(ix, E)
@@ -442,7 +477,6 @@ def run_bruteforce_only(args, local):
 def run_ours(args, rank, world, local):
     import torch
     import paper_2504_04018_gb300 as E
-    import oracle as O
     from paper_2504_04018_gb300 import replicas as RP
 
     spec = WORKLOADS[args.workload]
@@ -487,20 +521,8 @@ def run_ours(args, rank, world, local):
     t0 = time.perf_counter()
     gt, gc = ground_truth(w.queries, w.l, w.r, w.k)
     gt_s = time.perf_counter() - t0
-    # the GPU ground truth against the float64 oracle on sampled queries
-    rng = np.random.default_rng(7)
-    chk = rng.choice(nq, min(24, nq), replace=False)
-    same = 0
-    max_rel = 0.0
-    inv = np.empty(w.n, np.int64)
-    inv[perm] = np.arange(w.n)
-    for i in chk:
-        ranks, dd = fp64_exact(O, Xr_host, w.queries[i], int(w.l[i]), int(w.r[i]), int(w.k[i]), w.metric)
-        c = int(gc[i])
-        same += inv[gt[i, :c]].tolist() == ranks.tolist()
-        got = O.distances(Xr_host[inv[gt[i, :c]]], w.queries[i], w.metric)
-        max_rel = max(max_rel, float(np.max(np.abs(got - dd[:c]) / np.maximum(np.abs(dd[:c]), 1e-2 * np.abs(dd).max()))))
-    gt_check = {"sampled": int(len(chk)), "identical_id_lists": int(same), "max_rel_dist_err": max_rel}
+    # queries whose returned distances the CPU leg checks against float64
+    dist_sample = np.random.default_rng(11).choice(nq, min(256, nq), replace=False)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -554,6 +576,7 @@ def run_ours(args, rank, world, local):
         one parameter setting with direct esg_search_batch calls."""
         ids, cnt, stats = search_once(params)
         status = outs[3].cpu().numpy()
+        sample = (ids[dist_sample], outs[1].cpu().numpy()[dist_sample], cnt[dist_sample])
         rec = recall(ids, cnt, gt, gc, w.k)
         alg_bytes = float(stats[:, 1].sum() * ix.d * ESIZE[trav] + stats[:, 0].sum() * ix.R * 4
                           + stats[:, 3].sum() * ix.d * 4)
@@ -581,7 +604,7 @@ def run_ours(args, rank, world, local):
                 "evals_per_query": float(stats[:, 1].mean()),
                 "expansions_per_query": float(stats[:, 0].mean()),
                 "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "by_k": by_k(stats, status)}
+                "by_k": by_k(stats, status), "_sample": sample}
 
     def sweep_arm(name, trav, width=1):
         sweep, chosen = [], None
@@ -648,7 +671,9 @@ def run_ours(args, rank, world, local):
         total_ms = timed(graph_step, name + "-graph")
         ids = b.view("ids", (nq, k_max), torch.int64).cpu().numpy()
         cnt = b.view("count", (nq,), torch.int32).cpu().numpy()
+        dist = b.view("dist", (nq, k_max), torch.float32).cpu().numpy()
         g = dict(results[name])
+        g["_sample"] = (ids[dist_sample], dist[dist_sample], cnt[dist_sample])
         rec = recall(ids, cnt, gt, gc, w.k)
         g.update({"recall_at_k": round(rec[0], 5),
                   "recall_at_10_k_ge_10": None if rec[1] is None else round(rec[1], 5),
@@ -717,15 +742,23 @@ def run_ours(args, rank, world, local):
                 "kernel_ms_per_call": round(head["kernel_ms"], 4),
                 "algorithmic_bytes_per_call": head["alg_bytes"],
                 "peak_source": "measured" if "hbm_gbs" in pk else "fallback"}
+    if args.workload == "scale" and rank == 0:
+        bf_details = bruteforce_timing(E, torch, Xr, Q, L, Rr, w)
+    cpu, gt_check = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the CPU leg: the oracle's own search on the same graph, and the
+        # float64 checks of the GPU ground truth and of every arm's distances
+        gt_check, dist_err = oracle_checks(w, Xr_host, perm, gt, gc, dist_sample,
+                                           {k: v["_sample"] for k, v in results.items()})
+        for k, v in dist_err.items():
+            results[k]["max_rel_dist_err"] = v
+        cpu = cpu_baseline(E, ix, w, Xr_host, results["plain"]["params"]["ef"], args.cpu_seconds, gt, gc)
     details = {"variants": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()
-                                if kk != "alg_bytes"} for k, v in results.items()},
+                                if kk not in ("alg_bytes", "_sample")} for k, v in results.items()},
                "learned": learned_info, "gen_s": round(gen_s, 1), "build_s": round(build_s, 1),
                "ground_truth_s": round(gt_s, 1), "ground_truth_check": gt_check}
     if args.workload == "scale" and rank == 0:
-        details["bruteforce"] = bruteforce_timing(E, torch, Xr, Q, L, Rr, w)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(E, O, ix, w, Xr_host, results["plain"]["params"]["ef"], args.cpu_seconds, gt, gc)
+        details["bruteforce"] = bf_details
     plain = results["plain"]
     line = {"metric": METRIC_NAME, "value": head["qps"], "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -740,6 +773,8 @@ def run_ours(args, rank, world, local):
         line["cpu_baseline"] = cpu
     # the comparison the metric names, last so that it survives a cut tail
     line.update({"build_s": round(build_s, 1), "ground_truth_check": gt_check,
+                 "arms": {k: {"qps": round(v["qps"]), "recall_at_k": v["recall_at_k"],
+                              "max_rel_dist_err": v.get("max_rel_dist_err")} for k, v in results.items()},
                  "latency_us": head["latency_us"], "params": head["params"],
                  "recall_at_k": head["recall_at_k"], "recall_at_10_k_ge_10": head["recall_at_10_k_ge_10"],
                  "plain_fp32": {"qps": plain["qps"], "ef": plain["params"]["ef"],

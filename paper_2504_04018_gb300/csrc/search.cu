@@ -232,7 +232,7 @@ esg_status make_plan(int d, int R, int efk, int64_t n_items, int st, int width, 
     pl.G = 16384;
     while (pl.G < 256 * efk && pl.G < (1 << 20)) pl.G <<= 1;
     pl.wpb = wpb_req > 0 ? wpb_req : 2;
-    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 8 + (size_t)pl.BB * 12 + 32 * 8 + 16 +
+    pl.smem = ((size_t)pl.H * 4 + (size_t)pl.C * 8 + (size_t)pl.BB * 12 + 32 * 8 + 16 + 128 +
                (((size_t)d * 4 + 15) & ~(size_t)15)) * pl.wpb;
     int dev = 0, sms = 0, per_sm = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));

@@ -27,7 +27,10 @@ __device__ __forceinline__ uint32_t hash_mix(uint32_t x) {
 // being stored (`saturated`; the list de-duplication then catches repeats).
 // A global slot holds (tag << 32 | id), the tag being the work item's index
 // + 1: a slot with another tag is free for this item, so the table is zeroed
-// once per launch and never cleared between the items a warp runs.
+// once per launch and never cleared between the items a warp runs. Its slots
+// form buckets of 4 (one 32-byte sector); an id's probe sequence starts at
+// the first slot of its bucket and runs on slot by slot, and slots are never
+// freed within an item, so an id is either in its bucket or its bucket is full.
 struct Visited {
     uint32_t *hs;   // shared table, hsize slots (a multiple of 4)
     uint32_t hsize;
@@ -38,26 +41,37 @@ struct Visited {
     uint32_t tag;             // this item's tag (>= 1)
     int *gcount;
     int glimit;
+    uint32_t *bm;             // per-warp shared bitmap of the buckets written in a pass (32 words)
 };
 
-__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated) {
+__device__ __forceinline__ uint32_t global_bucket(const Visited &v, uint32_t id) {
+    return hash_mix(id ^ 0x9e3779b9u) & (v.gmask >> 2);
+}
+
+// Shared-table part of a visit: 0 = visited, 1 = new (stored here), 2 = not
+// here and the table is at its limit (continue in the global table).
+__device__ __forceinline__ int visit_shared(const Visited &v, uint32_t id) {
     // first slot by multiply-shift range reduction (any table size)
     uint32_t slot = __umulhi(hash_mix(id), v.hsize);
     for (uint32_t probe = 0; probe < v.hsize; ++probe, slot = slot + 1 == v.hsize ? 0 : slot + 1) {
         const uint32_t cur = v.hs[slot];
-        if (cur == id) return false;
+        if (cur == id) return 0;
         if (cur == ESG_NONE) {
-            if (*(volatile int *)v.hcount >= v.hlimit) break;   // continue in the global table
+            if (*(volatile int *)v.hcount >= v.hlimit) return 2;
             const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
-            if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return true; }
-            if (prev == id) return false;
+            if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return 1; }
+            if (prev == id) return 0;
         }
     }
-    if (v.hg == nullptr) { *saturated = true; return true; }
+    return 2;
+}
+
+// Global-table visit by one lane, probing slot by slot from `start`: the
+// swap resolves races between lanes. Returns true iff `id` is new.
+__device__ __forceinline__ bool visit_global_from(const Visited &v, uint32_t id, uint32_t start, bool *saturated) {
     const unsigned long long mine = ((unsigned long long)v.tag << 32) | id;
-    const uint32_t h = hash_mix(id ^ 0x9e3779b9u) & v.gmask;
     for (uint32_t probe = 0; probe <= v.gmask; ++probe) {
-        const uint32_t slot = (h + probe) & v.gmask;
+        const uint32_t slot = (start + probe) & v.gmask;
         const unsigned long long cur = *(volatile unsigned long long *)&v.hg[slot];
         if ((uint32_t)(cur >> 32) == v.tag) {   // taken by this item
             if ((uint32_t)cur == id) return false;
@@ -72,6 +86,134 @@ __device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *satur
     }
     *saturated = true;
     return true;
+}
+
+// One lane's visit (the entry points). Returns true iff `id` is new.
+__device__ __forceinline__ bool visit(const Visited &v, uint32_t id, bool *saturated) {
+    const int r = visit_shared(v, id);
+    if (r < 2) return r == 1;
+    if (v.hg == nullptr) { *saturated = true; return true; }
+    return visit_global_from(v, id, global_bucket(v, id) << 2, saturated);
+}
+
+// A loaded bucket (slots pa, pb) for `id`: whether it holds `id`, and the
+// mask of its slots free for this item.
+__device__ __forceinline__ void scan_bucket(const Visited &v, uint32_t id, ulonglong2 pa, ulonglong2 pb,
+                                            bool &found, unsigned &freem) {
+    const unsigned long long mine = ((unsigned long long)v.tag << 32) | id;
+    const unsigned long long sl[4] = {pa.x, pa.y, pb.x, pb.y};
+    found = false;
+    freem = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        found |= sl[k] == mine;
+        if ((uint32_t)(sl[k] >> 32) != v.tag) freem |= 1u << k;
+    }
+}
+
+// One pass of the warp's global visits from bucket snapshots: `g` lanes have
+// looked `id` up in bucket `b` (found, free slots); the lanes that insert
+// into one bucket take its free slots in lane order (a second lane with the
+// same id reports it visited) and store without a swap, since no other lane
+// writes the table during the pass. Sets `n` (new) for `g` lanes; returns
+// true where the bucket was full (the caller continues slot by slot).
+__device__ __forceinline__ bool global_pass(const Visited &v, bool g, uint32_t id, uint32_t b, bool found,
+                                            unsigned freem, bool &n, bool *saturated) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long mine = ((unsigned long long)v.tag << 32) | id;
+    bool want = g && !found;
+    if (g && found) n = false;
+    if (want && *(volatile int *)v.gcount >= v.glimit) { *saturated = true; n = true; want = false; }
+    const unsigned grp = __match_any_sync(0xffffffffu, want ? b : (0x80000000u | (unsigned)lane));
+    bool dup = false;
+    if (__any_sync(0xffffffffu, want && __popc(grp) > 1)) {
+        const unsigned below = grp & ((1u << lane) - 1);
+#pragma unroll 1
+        for (int src = 0; src < 32; ++src) {
+            const uint32_t oid = __shfl_sync(0xffffffffu, id, src);
+            if (want && ((below >> src) & 1u) && oid == id) dup = true;
+        }
+    }
+    const unsigned ins = __ballot_sync(0xffffffffu, want && !dup) & grp;
+    bool full = false;
+    if (want) {
+        if (dup) {
+            n = false;   // the lowest lane with this id stores it
+        } else {
+            const int k = __popc(ins & ((1u << lane) - 1));
+            if (k < __popc(freem)) {
+                unsigned f = freem;
+                for (int t = 0; t < k; ++t) f &= f - 1;
+                __stcg(v.hg + ((size_t)b << 2) + (__ffs(f) - 1), mine);
+                atomicOr(&v.bm[(b >> 5) & 31], 1u << (b & 31));
+                n = true;
+            } else {
+                full = true;
+            }
+        }
+    }
+    const int added = __popc(__ballot_sync(0xffffffffu, want && !dup && !full));
+    if (lane == 0 && added) atomicAdd(v.gcount, added);
+    return full;
+}
+
+// The global-table part of visit_pair for the lanes with g0 / g1 set.
+__device__ __forceinline__ void visit_pair_global_body(const Visited &v, uint32_t v0, uint32_t v1, bool g0,
+                                                       bool g1, bool &n0, bool &n1, bool *saturated) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t b0 = g0 ? global_bucket(v, v0) : 0u, b1 = g1 ? global_bucket(v, v1) : 0u;
+    const ulonglong2 *q0 = reinterpret_cast<const ulonglong2 *>(v.hg + ((size_t)b0 << 2));
+    const ulonglong2 *q1 = reinterpret_cast<const ulonglong2 *>(v.hg + ((size_t)b1 << 2));
+    bool fd0 = false, fd1 = false;
+    unsigned fm0 = 0, fm1 = 0;
+    {   // both buckets' loads in flight together
+        ulonglong2 p0a{0, 0}, p0b{0, 0}, p1a{0, 0}, p1b{0, 0};
+        if (g0) { p0a = __ldcg(q0); p0b = __ldcg(q0 + 1); }
+        if (g1) { p1a = __ldcg(q1); p1b = __ldcg(q1 + 1); }
+        if (g0) scan_bucket(v, v0, p0a, p0b, fd0, fm0);
+        if (g1) scan_bucket(v, v1, p1a, p1b, fd1, fm1);
+    }
+    const bool f0 = global_pass(v, g0, v0, b0, fd0, fm0, n0, saturated);
+    __syncwarp();
+    if (g1 && ((v.bm[(b1 >> 5) & 31] >> (b1 & 31)) & 1u))
+        scan_bucket(v, v1, __ldcg(q1), __ldcg(q1 + 1), fd1, fm1);
+    const bool f1 = global_pass(v, g1, v1, b1, fd1, fm1, n1, saturated);
+    __syncwarp();
+    if (f0) n0 = visit_global_from(v, v0, (b0 + 1) << 2, saturated);
+    if (f1) n1 = visit_global_from(v, v1, (b1 + 1) << 2, saturated);
+    v.bm[lane] = 0u;
+    __syncwarp();
+}
+
+// Out-of-line copy for the FP32 kernels: inlined, its state competes for
+// registers with the whole expansion loop, and those kernels spill more.
+static __device__ __noinline__ void visit_pair_global_call(const Visited &v, uint32_t v0, uint32_t v1, bool g0, bool g1,
+                                                    bool &n0, bool &n1, bool *saturated) {
+    visit_pair_global_body(v, v0, v1, g0, g1, n0, n1, saturated);
+}
+
+// Visits of the two neighbours v0, v1 of each lane (ESG_NONE: none): the
+// shared table first; then, for the ids that go on to the global table, both
+// buckets are loaded at once, the v0 pass stores, the v1 lanes whose bucket
+// the v0 pass wrote load it again, and the v1 pass stores; ids whose bucket
+// was full probe on slot by slot with swaps. All lanes call it.
+template <bool OUTLINE>
+__device__ __forceinline__ void visit_pair(const Visited &v, uint32_t v0, uint32_t v1, bool &n0, bool &n1,
+                                           bool *saturated) {
+    const int r0 = v0 != ESG_NONE ? visit_shared(v, v0) : 0;
+    const int r1 = v1 != ESG_NONE ? visit_shared(v, v1) : 0;
+    n0 = r0 == 1;
+    n1 = r1 == 1;
+    const bool g0 = r0 == 2, g1 = r1 == 2;
+    if (!__any_sync(0xffffffffu, g0 || g1)) return;
+    if (v.hg == nullptr) {
+        if (g0 || g1) *saturated = true;
+        n0 |= g0;
+        n1 |= g1;
+        return;
+    }
+    if (OUTLINE) visit_pair_global_call(v, v0, v1, g0, g1, n0, n1, saturated);
+    else visit_pair_global_body(v, v0, v1, g0, g1, n0, n1, saturated);
 }
 
 // Storage types of the traversal rows (esg_dtype): elements per 16-byte vector.
@@ -378,7 +520,7 @@ search_kernel(SearchArgs a) {
     const int wpb = blockDim.x >> 5;
     const size_t qbytes = ((size_t)a.d * 4 + 15) & ~(size_t)15;
     const size_t per_warp = (size_t)a.H * 4 + (size_t)a.C * 8 + (size_t)a.BB * 12 + 32 * 8 +
-                            16 + qbytes;
+                            16 + 128 + qbytes;
     unsigned char *base = smem_raw + per_warp * wib;
     WarpSmem w;
     size_t off = 0;
@@ -386,6 +528,8 @@ search_kernel(SearchArgs a) {
     Cand *cbuf = (Cand *)(base + off); off += 32 * 8;
     w.nbuf = (uint32_t *)(base + off); off += (size_t)a.BB * 4;
     w.hcount = (int *)(base + off); off += 16;
+    uint32_t *gbits = (uint32_t *)(base + off); off += 128;
+    gbits[lane] = 0u;
     float *qs = (float *)(base + off); off += qbytes;
     const int gwarp = blockIdx.x * wpb + wib;
     // the arena of C list items and H table slots is split per item: the
@@ -397,7 +541,8 @@ search_kernel(SearchArgs a) {
     vis.gmask = (uint32_t)a.G - 1;
     vis.tag = 0;
     vis.gcount = w.hcount + 1;
-    vis.glimit = (a.G * 3) / 4;
+    vis.glimit = a.G / 2;   // buckets of 4 slots at most half full on average
+    vis.bm = gbits;
 
     const int64_t first = a.range ? (int64_t)a.range[0] : 0;
     const int64_t count = a.range ? (int64_t)a.range[1] - first : a.n_items;
@@ -542,8 +687,8 @@ search_kernel(SearchArgs a) {
                         uint32_t v1 = c64 + lane + 32 < a.R ? __ldg(row + c64 + lane + 32) : ESG_NONE;
                         if (v0 >= (uint64_t)a.n) v0 = ESG_NONE;   // malformed imported graph: ignore
                         if (v1 >= (uint64_t)a.n) v1 = ESG_NONE;
-                        const bool n0 = v0 != ESG_NONE && visit(vis, v0, &saturated);
-                        const bool n1 = v1 != ESG_NONE && visit(vis, v1, &saturated);
+                        bool n0, n1;
+                        visit_pair<ST == ESG_F32>(vis, v0, v1, n0, n1, &saturated);
                         const unsigned b0 = __ballot_sync(0xffffffffu, n0);
                         const unsigned b1 = __ballot_sync(0xffffffffu, n1);
                         const int c0 = __popc(b0);
