@@ -48,22 +48,46 @@ __device__ __forceinline__ uint32_t global_bucket(const Visited &v, uint32_t id)
     return hash_mix(id ^ 0x9e3779b9u) & (v.gmask >> 2);
 }
 
-// Shared-table part of a visit: 0 = visited, 1 = new (stored here), 2 = not
-// here and the table is at its limit (continue in the global table).
+// The shared table's slots form buckets of 4 (16 bytes). An id has two
+// buckets, from two hashes by multiply-shift range reduction (any table
+// size), and is stored in the one with more free slots, lowest free slot
+// first, so a bucket's used slots are a prefix. An id is in one of its two
+// buckets, or both were full when it came and it went to the global table:
+// as slots are never freed within an item, an id found in neither bucket is
+// new if either has a free slot, and looked up globally if both are full.
+__device__ __forceinline__ void shared_buckets(const Visited &v, uint32_t id, uint32_t &b1, uint32_t &b2) {
+    const uint32_t h = hash_mix(id);
+    b1 = __umulhi(h, v.hsize >> 2);
+    b2 = __umulhi(hash_mix(h ^ 0x5bd1e995u), v.hsize >> 2);
+}
+
+__device__ __forceinline__ unsigned free_slots(uint4 s4) {
+    return (s4.x == ESG_NONE ? 1u : 0u) | (s4.y == ESG_NONE ? 2u : 0u) | (s4.z == ESG_NONE ? 4u : 0u) |
+           (s4.w == ESG_NONE ? 8u : 0u);
+}
+
+__device__ __forceinline__ bool holds(uint4 s4, uint32_t id) {
+    return s4.x == id || s4.y == id || s4.z == id || s4.w == id;
+}
+
+// Shared-table part of one lane's visit: 0 = visited, 1 = new (stored here),
+// 2 = not here and both buckets are full or the table is at its limit
+// (continue in the global table).
 __device__ __forceinline__ int visit_shared(const Visited &v, uint32_t id) {
-    // first slot by multiply-shift range reduction (any table size)
-    uint32_t slot = __umulhi(hash_mix(id), v.hsize);
-    for (uint32_t probe = 0; probe < v.hsize; ++probe, slot = slot + 1 == v.hsize ? 0 : slot + 1) {
-        const uint32_t cur = v.hs[slot];
-        if (cur == id) return 0;
-        if (cur == ESG_NONE) {
-            if (*(volatile int *)v.hcount >= v.hlimit) return 2;
-            const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
-            if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return 1; }
-            if (prev == id) return 0;
-        }
+    uint32_t b1, b2;
+    shared_buckets(v, id, b1, b2);
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(v.hs);
+    for (;;) {
+        const uint4 s1 = h4[b1], s2 = h4[b2];
+        if (holds(s1, id) || holds(s2, id)) return 0;
+        const unsigned f1 = free_slots(s1), f2 = free_slots(s2);
+        if ((f1 | f2) == 0u || *(volatile int *)v.hcount >= v.hlimit) return 2;
+        const bool first = __popc(f1) >= __popc(f2);
+        const uint32_t slot = ((first ? b1 : b2) << 2) + (__ffs(first ? f1 : f2) - 1);
+        const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
+        if (prev == ESG_NONE) { atomicAdd(v.hcount, 1); return 1; }
+        if (prev == id) return 0;
     }
-    return 2;
 }
 
 // Global-table visit by one lane, probing slot by slot from `start`: the
@@ -185,23 +209,109 @@ __device__ __forceinline__ void visit_pair_global_body(const Visited &v, uint32_
     __syncwarp();
 }
 
-// Out-of-line copy for the FP32 kernels: inlined, its state competes for
-// registers with the whole expansion loop, and those kernels spill more.
-static __device__ __noinline__ void visit_pair_global_call(const Visited &v, uint32_t v0, uint32_t v1, bool g0, bool g1,
-                                                    bool &n0, bool &n1, bool *saturated) {
+// One pass of the warp's shared-table visits: pending lanes have loaded
+// the two buckets of `id` (s1, s2). Found: visited. Both full, or the table
+// at its limit (`room` false): on to the global table. Otherwise the lanes
+// inserting into one bucket (each the one of its two with more free slots)
+// take its free slots lowest first in lane order (a second lane with the same
+// id reports it visited); a lane left without a slot loads again and retries.
+// Returns whether it stored.
+__device__ __forceinline__ bool shared_pass(const Visited &v, bool &pend, uint32_t id, uint32_t b1, uint32_t b2,
+                                            uint4 s1, uint4 s2, int &r, bool room) {
+    const int lane = threadIdx.x & 31;
+    bool want = false;
+    uint32_t bk = 0;
+    unsigned freem = 0;
+    if (pend) {
+        if (holds(s1, id) || holds(s2, id)) {
+            r = 0;
+            pend = false;
+        } else {
+            const unsigned f1 = free_slots(s1), f2 = free_slots(s2);
+            if ((f1 | f2) == 0u || !room) {
+                r = 2;
+                pend = false;
+            } else {
+                const bool first = __popc(f1) >= __popc(f2);
+                bk = first ? b1 : b2;
+                freem = first ? f1 : f2;
+                want = true;
+            }
+        }
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, want ? bk : (0x80000000u | (unsigned)lane));
+    bool dup = false;
+    if (__any_sync(0xffffffffu, want && __popc(grp) > 1)) {
+        const unsigned below = grp & ((1u << lane) - 1);
+#pragma unroll 1
+        for (int src = 0; src < 32; ++src) {
+            const uint32_t oid = __shfl_sync(0xffffffffu, id, src);
+            if (want && ((below >> src) & 1u) && oid == id) dup = true;
+        }
+    }
+    const unsigned ins = __ballot_sync(0xffffffffu, want && !dup) & grp;
+    bool stored = false;
+    if (want) {
+        if (dup) {
+            r = 0;   // the lowest lane with this id stores it
+            pend = false;
+        } else {
+            const int k = __popc(ins & ((1u << lane) - 1));
+            if (k < __popc(freem)) {
+                unsigned f = freem;
+                for (int t = 0; t < k; ++t) f &= f - 1;
+                v.hs[(bk << 2) + (__ffs(f) - 1)] = id;
+                r = 1;
+                pend = false;
+                stored = true;
+            }
+        }
+    }
+    return stored;
+}
+
+// Visits of the two neighbours v0, v1 of each lane (ESG_NONE: none). The
+// shared table first, in passes over both ids' loaded buckets (the v1 pass
+// after the v0 pass's stores, reloading its bucket if that pass stored).
+// Then, for the ids that go on to the global table, both buckets are loaded
+// at once, the v0 pass stores, the v1 lanes whose bucket the v0 pass wrote
+// load it again, and the v1 pass stores; ids whose bucket was full probe on
+// slot by slot with swaps. All lanes call it.
+// Out-of-line copy of the global part for the FP32 kernels: inlined, its
+// state competes for registers with the whole expansion loop, and those
+// kernels spill more.
+static __device__ __noinline__ void visit_pair_global_call(const Visited &v, uint32_t v0, uint32_t v1, bool g0,
+                                                           bool g1, bool &n0, bool &n1, bool *saturated) {
     visit_pair_global_body(v, v0, v1, g0, g1, n0, n1, saturated);
 }
 
-// Visits of the two neighbours v0, v1 of each lane (ESG_NONE: none): the
-// shared table first; then, for the ids that go on to the global table, both
-// buckets are loaded at once, the v0 pass stores, the v1 lanes whose bucket
-// the v0 pass wrote load it again, and the v1 pass stores; ids whose bucket
-// was full probe on slot by slot with swaps. All lanes call it.
 template <bool OUTLINE>
 __device__ __forceinline__ void visit_pair(const Visited &v, uint32_t v0, uint32_t v1, bool &n0, bool &n1,
                                            bool *saturated) {
-    const int r0 = v0 != ESG_NONE ? visit_shared(v, v0) : 0;
-    const int r1 = v1 != ESG_NONE ? visit_shared(v, v1) : 0;
+    const int lane = threadIdx.x & 31;
+    int r0 = 0, r1 = 0;
+    {   // shared table: all four buckets of the two ids loaded together
+        bool p0 = v0 != ESG_NONE, p1 = v1 != ESG_NONE;
+        uint32_t a0 = 0, a1 = 0, c0 = 0, c1 = 0;
+        if (p0) shared_buckets(v, v0, a0, a1);
+        if (p1) shared_buckets(v, v1, c0, c1);
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(v.hs);
+        while (__any_sync(0xffffffffu, p0 || p1)) {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            uint4 s0a = z, s0b = z, s1a = z, s1b = z;
+            if (p0) { s0a = h4[a0]; s0b = h4[a1]; }
+            if (p1) { s1a = h4[c0]; s1b = h4[c1]; }
+            const bool st0 = shared_pass(v, p0, v0, a0, a1, s0a, s0b, r0, *(volatile int *)v.hcount < v.hlimit);
+            const int n_st0 = __popc(__ballot_sync(0xffffffffu, st0));
+            if (lane == 0 && n_st0) *v.hcount += n_st0;
+            __syncwarp();
+            if (n_st0 && p1) { s1a = h4[c0]; s1b = h4[c1]; }   // the v0 pass may have filled them
+            const bool st1 = shared_pass(v, p1, v1, c0, c1, s1a, s1b, r1, *(volatile int *)v.hcount < v.hlimit);
+            const int n_st1 = __popc(__ballot_sync(0xffffffffu, st1));
+            if (lane == 0 && n_st1) *v.hcount += n_st1;
+            __syncwarp();
+        }
+    }
     n0 = r0 == 1;
     n1 = r1 == 1;
     const bool g0 = r0 == 2, g1 = r1 == 2;
@@ -215,6 +325,7 @@ __device__ __forceinline__ void visit_pair(const Visited &v, uint32_t v0, uint32
     if (OUTLINE) visit_pair_global_call(v, v0, v1, g0, g1, n0, n1, saturated);
     else visit_pair_global_body(v, v0, v1, g0, g1, n0, n1, saturated);
 }
+
 
 // Storage types of the traversal rows (esg_dtype): elements per 16-byte vector.
 template <int ST> struct Store;
