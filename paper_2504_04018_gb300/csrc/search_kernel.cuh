@@ -209,74 +209,31 @@ __device__ __forceinline__ void visit_pair_global_body(const Visited &v, uint32_
     __syncwarp();
 }
 
-// One pass of the warp's shared-table visits: pending lanes have loaded
-// the two buckets of `id` (s1, s2). Found: visited. Both full, or the table
-// at its limit (`room` false): on to the global table. Otherwise the lanes
-// inserting into one bucket (each the one of its two with more free slots)
-// take its free slots lowest first in lane order (a second lane with the same
-// id reports it visited); a lane left without a slot loads again and retries.
-// Returns whether it stored.
-__device__ __forceinline__ bool shared_pass(const Visited &v, bool &pend, uint32_t id, uint32_t b1, uint32_t b2,
-                                            uint4 s1, uint4 s2, int &r, bool room) {
-    const int lane = threadIdx.x & 31;
-    bool want = false;
-    uint32_t bk = 0;
-    unsigned freem = 0;
-    if (pend) {
-        if (holds(s1, id) || holds(s2, id)) {
-            r = 0;
-            pend = false;
-        } else {
-            const unsigned f1 = free_slots(s1), f2 = free_slots(s2);
-            if ((f1 | f2) == 0u || !room) {
-                r = 2;
-                pend = false;
-            } else {
-                const bool first = __popc(f1) >= __popc(f2);
-                bk = first ? b1 : b2;
-                freem = first ? f1 : f2;
-                want = true;
-            }
-        }
-    }
-    const unsigned grp = __match_any_sync(0xffffffffu, want ? bk : (0x80000000u | (unsigned)lane));
-    bool dup = false;
-    if (__any_sync(0xffffffffu, want && __popc(grp) > 1)) {
-        const unsigned below = grp & ((1u << lane) - 1);
-#pragma unroll 1
-        for (int src = 0; src < 32; ++src) {
-            const uint32_t oid = __shfl_sync(0xffffffffu, id, src);
-            if (want && ((below >> src) & 1u) && oid == id) dup = true;
-        }
-    }
-    const unsigned ins = __ballot_sync(0xffffffffu, want && !dup) & grp;
-    bool stored = false;
-    if (want) {
-        if (dup) {
-            r = 0;   // the lowest lane with this id stores it
-            pend = false;
-        } else {
-            const int k = __popc(ins & ((1u << lane) - 1));
-            if (k < __popc(freem)) {
-                unsigned f = freem;
-                for (int t = 0; t < k; ++t) f &= f - 1;
-                v.hs[(bk << 2) + (__ffs(f) - 1)] = id;
-                r = 1;
-                pend = false;
-                stored = true;
-            }
-        }
-    }
-    return stored;
+// One try of a lane's shared-table visit from its two loaded buckets (s1,
+// s2): found: visited; both full, or the table at its limit (`room` false):
+// on to the global table (r = 2); else a swap into the lowest free slot of the
+// bucket with more free slots: stored (new), or the same id stored there by
+// another lane (visited), or another id took the slot (still pending: the
+// caller loads the buckets again).
+__device__ __forceinline__ void shared_try(const Visited &v, uint32_t id, uint32_t b1, uint32_t b2, uint4 s1,
+                                           uint4 s2, bool room, bool &pend, int &r, bool &stored) {
+    if (holds(s1, id) || holds(s2, id)) { r = 0; pend = false; return; }
+    const unsigned f1 = free_slots(s1), f2 = free_slots(s2);
+    if ((f1 | f2) == 0u || !room) { r = 2; pend = false; return; }
+    const bool first = __popc(f1) >= __popc(f2);
+    const uint32_t slot = ((first ? b1 : b2) << 2) + (__ffs(first ? f1 : f2) - 1);
+    const uint32_t prev = atomicCAS(&v.hs[slot], ESG_NONE, id);
+    if (prev == ESG_NONE) { r = 1; pend = false; stored = true; }
+    else if (prev == id) { r = 0; pend = false; }
 }
 
 // Visits of the two neighbours v0, v1 of each lane (ESG_NONE: none). The
-// shared table first, in passes over both ids' loaded buckets (the v1 pass
-// after the v0 pass's stores, reloading its bucket if that pass stored).
-// Then, for the ids that go on to the global table, both buckets are loaded
-// at once, the v0 pass stores, the v1 lanes whose bucket the v0 pass wrote
-// load it again, and the v1 pass stores; ids whose bucket was full probe on
-// slot by slot with swaps. All lanes call it.
+// shared table first: all four buckets of the two ids loaded together,
+// inserts by swap (a lane whose slot another id took loads again). Then, for
+// the ids that go on to the global table, both buckets are loaded at once,
+// the v0 pass stores, the v1 lanes whose bucket the v0 pass wrote load it
+// again, and the v1 pass stores; ids whose bucket was full probe on slot by
+// slot with swaps. All lanes call it.
 // Out-of-line copy of the global part for the FP32 kernels: inlined, its
 // state competes for registers with the whole expansion loop, and those
 // kernels spill more.
@@ -290,25 +247,24 @@ __device__ __forceinline__ void visit_pair(const Visited &v, uint32_t v0, uint32
                                            bool *saturated) {
     const int lane = threadIdx.x & 31;
     int r0 = 0, r1 = 0;
-    {   // shared table: all four buckets of the two ids loaded together
+    {   // shared table: all four buckets of the two ids loaded together,
+        // inserts by swap; a lane whose slot another id took loads again
         bool p0 = v0 != ESG_NONE, p1 = v1 != ESG_NONE;
         uint32_t a0 = 0, a1 = 0, c0 = 0, c1 = 0;
         if (p0) shared_buckets(v, v0, a0, a1);
         if (p1) shared_buckets(v, v1, c0, c1);
         const uint4 *h4 = reinterpret_cast<const uint4 *>(v.hs);
         while (__any_sync(0xffffffffu, p0 || p1)) {
+            const bool room = *(volatile int *)v.hcount < v.hlimit;
             const uint4 z = make_uint4(0, 0, 0, 0);
             uint4 s0a = z, s0b = z, s1a = z, s1b = z;
             if (p0) { s0a = h4[a0]; s0b = h4[a1]; }
             if (p1) { s1a = h4[c0]; s1b = h4[c1]; }
-            const bool st0 = shared_pass(v, p0, v0, a0, a1, s0a, s0b, r0, *(volatile int *)v.hcount < v.hlimit);
-            const int n_st0 = __popc(__ballot_sync(0xffffffffu, st0));
-            if (lane == 0 && n_st0) *v.hcount += n_st0;
-            __syncwarp();
-            if (n_st0 && p1) { s1a = h4[c0]; s1b = h4[c1]; }   // the v0 pass may have filled them
-            const bool st1 = shared_pass(v, p1, v1, c0, c1, s1a, s1b, r1, *(volatile int *)v.hcount < v.hlimit);
-            const int n_st1 = __popc(__ballot_sync(0xffffffffu, st1));
-            if (lane == 0 && n_st1) *v.hcount += n_st1;
+            bool st0 = false, st1 = false;
+            if (p0) shared_try(v, v0, a0, a1, s0a, s0b, room, p0, r0, st0);
+            if (p1) shared_try(v, v1, c0, c1, s1a, s1b, room, p1, r1, st1);
+            const int n_st = __popc(__ballot_sync(0xffffffffu, st0)) + __popc(__ballot_sync(0xffffffffu, st1));
+            if (lane == 0 && n_st) *v.hcount += n_st;
             __syncwarp();
         }
     }
