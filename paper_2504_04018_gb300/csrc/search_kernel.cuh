@@ -498,8 +498,9 @@ __device__ __forceinline__ void truncate_list(const Cand *list, ListState &st, i
 
 // Admitted candidates sit in batch[0..BB) (BB a multiple of 64 and a power
 // of two; rejected slots hold +inf). Sort them and merge them into `list` in
-// place (nbuf, BB entries, is scratch), then truncate. Batches of at most 32
-// are sorted in registers. Returns false when nothing was admitted.
+// place (nbuf, BB entries, is scratch), then truncate. Batches of at most 16
+// are ordered by counting ranks, of at most 32 sorted in registers. Returns
+// false when nothing was admitted.
 __device__ __forceinline__ bool admit_batch(Cand *batch, int BB, Cand *cbuf, Cand *list, uint32_t *nbuf,
                                             ListState &st, int ef, int C, uint32_t pl, uint32_t pr,
                                             int &status) {
@@ -522,8 +523,22 @@ __device__ __forceinline__ bool admit_batch(Cand *batch, int BB, Cand *cbuf, Can
         float d = lane < b ? cbuf[lane].d : INFINITY;
         uint32_t id = lane < b ? cbuf[lane].id : ESG_NONE;
         __syncwarp();
-        warp_sort32_reg(d, id);
-        cbuf[lane] = Cand{d, id};
+        if (b <= 16) {
+            // few candidates (the common case once the beam has settled):
+            // each lane's rank among them by counting, cheaper than a sort
+            // network over 32 lanes (ties, which visited ids rule out, by lane)
+            int rank = 0;
+#pragma unroll 4
+            for (int j = 0; j < b; ++j) {
+                const float dj = __shfl_sync(0xffffffffu, d, j);
+                const uint32_t ij = __shfl_sync(0xffffffffu, id, j);
+                rank += (cand_less(dj, ij, d, id) || (j < lane && cand_eq(Cand{dj, ij}, Cand{d, id}))) ? 1 : 0;
+            }
+            if (lane < b) cbuf[rank] = Cand{d, id};
+        } else {
+            warp_sort32_reg(d, id);
+            cbuf[lane] = Cand{d, id};
+        }
         __syncwarp();
         B = cbuf;
     } else {
