@@ -890,9 +890,11 @@ __global__ void scatter_subset_kernel(const int64_t *idx, int64_t m, int k, cons
     if (threadIdx.x == 0) cnt[q] = cnt_g[i];
 }
 
+struct Bf2Plan;
 static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
                               const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
-                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream);
+                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream,
+                              Bf2Plan *given = nullptr);
 
 // Queries whose list of K1 candidates could not be certified run again with
 // the longest list that fits the kernel (their own plan, a few query tiles), and
@@ -1195,9 +1197,11 @@ static esg_status bf2_plan(const int64_t *hl, const int64_t *hr, int64_t nq, int
     return ESG_OK;
 }
 
+// `given`: a plan already made for these ranges (it is consumed), or null.
 static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
                               const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
-                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream) {
+                              int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream,
+                              Bf2Plan *given) {
     if (nq == 0) return ESG_OK;
     const int nk = (d + TK - 1) / TK;
     int dev = 0, max_smem = 0, sms = 0, S = 0, stream_a = 0;
@@ -1208,13 +1212,17 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
     if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
 
     // ---- host plan
-    std::vector<int64_t> hl(nq), hr(nq);
-    ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
-    ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
-    ESG_CUDA_TRY(cudaStreamSynchronize(stream));
     Bf2Plan P;
-    const esg_status pst = bf2_plan(hl.data(), hr.data(), nq, n, d, sms, P);
-    if (pst != ESG_OK) return pst;
+    if (given) {
+        P = std::move(*given);
+    } else {
+        std::vector<int64_t> hl(nq), hr(nq);
+        ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+        ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+        ESG_CUDA_TRY(cudaStreamSynchronize(stream));
+        const esg_status pst = bf2_plan(hl.data(), hr.data(), nq, n, d, sms, P);
+        if (pst != ESG_OK) return pst;
+    }
     const std::vector<int32_t> &order = P.order, &tiles = P.tiles, &item_begin = P.item_begin,
                                &cta_first = P.cta_first;
     const std::vector<WorkItem> &items = P.items;
@@ -1328,6 +1336,14 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     if (nq == 0) return ESG_OK;
     const int nk = (d + TK - 1) / TK;
     const int64_t xt = (n + TN - 1) / TN;
+    // the ranges come to the host first, so that the host plan is made while
+    // the GPU splits and swizzles the point matrix
+    int sms = 0;
+    ESG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<int64_t> hl(nq), hr(nq);
+    ESG_CUDA_TRY(cudaMemcpyAsync(hl.data(), l, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaMemcpyAsync(hr.data(), r, sizeof(int64_t) * nq, cudaMemcpyDeviceToHost, stream));
+    ESG_CUDA_TRY(cudaStreamSynchronize(stream));
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t bytes = al((size_t)xt * nk * STAGE) + 2 * al(sizeof(float) * n) + al(sizeof(float) * 4);
     unsigned char *scratch = nullptr;
@@ -1346,9 +1362,11 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    Bf2Plan P;
+    if (st == ESG_OK) st = bf2_plan(hl.data(), hr.data(), nq, n, d, sms, P);
     if (st == ESG_OK) {
         const PreparedX X{xs, xnorm, xrow, xmax};
-        st = bf2_queries(X, base, n, d, metric, queries, nq, l, r, k, K1, out_ids, out_dist, out_count, stream);
+        st = bf2_queries(X, base, n, d, metric, queries, nq, l, r, k, K1, out_ids, out_dist, out_count, stream, &P);
     }
     cudaFreeAsync(scratch, stream);
     return st;
