@@ -408,3 +408,47 @@ def test_bruteforce_tensor_core_vs_oracle(dev, metric, d, k, monkeypatch):
     assert np.array_equal(count, count2.cpu().numpy())
     fin = np.isfinite(dist)
     assert np.allclose(dist[fin], dist2.cpu().numpy()[fin], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("hash_slots", [1024, 16384])
+def test_visited_tables_under_pressure(dev, tiny_oracle_index, hash_slots):
+    """ef 800 with the smallest shared visited table (1,024 slots, 768 before
+    it counts as full) sends much of a search's visits (about 2,000 per query)
+    to the global table, and rows that repeat a neighbour
+    id test the de-duplication of both tables (within a lane pair and across
+    lanes). On that graph the GPU's Algorithm 1 matches the oracle's, returns
+    no id twice, and returns the same results whatever the table size."""
+    import dataclasses
+    w, idx = tiny_oracle_index
+    adj = idx.adj.copy()
+    none = np.uint32(0xFFFFFFFF)
+    both = (adj[..., 0] != none) & (adj[..., 1] != none)
+    adj[..., 1] = np.where(both, adj[..., 0], adj[..., 1])          # lanes 0 and 1 of one pass
+    far = (adj[..., 0] != none) & (adj[..., -1] != none)
+    adj[..., -1] = np.where(far, adj[..., 0], adj[..., -1])         # v0 of lane 0, v1 of the last lane
+    didx = dataclasses.replace(idx, adj=adj)
+    gix = E.esg_index_import(w.base[idx.perm], idx.perm, idx.metric, idx.leaf_size, adj, idx.entries)
+    k, ef = 10, 800
+    ids, dist, count, status, stats = _gpu_search(gix, w.queries, w.l, w.r, None, k, ef, dev,
+                                                  params=E.search_params(ef=ef, hash_slots=hash_slots))
+    ref = _gpu_search(gix, w.queries, w.l, w.r, None, k, ef, dev,
+                      params=E.search_params(ef=ef, hash_slots=16384))
+    assert np.array_equal(ids, ref[0]) and np.array_equal(count, ref[2])
+    inv = np.empty(idx.n, np.int64)
+    inv[idx.perm] = np.arange(idx.n)
+    found_gpu, found_cpu, truth = [], [], []
+    same = 0
+    for i in range(len(w.queries)):
+        l, r = int(w.l[i]), int(w.r[i])
+        ranks = inv[ids[i, :count[i]]]
+        assert np.all((ranks >= l) & (ranks <= r)) and len(set(ranks.tolist())) == len(ranks)
+        cpu, _ = O.search(didx, w.queries[i], l, r, k, ef)
+        gt, _ = O.bruteforce(idx.X, w.queries[i], l, r, k, w.metric)
+        found_gpu.append(ranks); found_cpu.append(cpu); truth.append(gt)
+        same += ranks.tolist() == cpu.tolist()
+    rg, rc = O.recall_at_k(found_gpu, truth), O.recall_at_k(found_cpu, truth)
+    print(f"hash_slots {hash_slots}: recall GPU {rg:.4f} oracle {rc:.4f}, identical {same}/{len(w.queries)}, "
+          f"evaluations per query {stats[:, 1].mean():.0f}")
+    assert stats[:, 1].mean() > 2 * 768                     # the shared table overflowed
+    assert abs(rg - rc) <= 0.005, (rg, rc)
+    assert same >= 0.95 * len(w.queries)
