@@ -74,6 +74,34 @@ uint32_t crc32_update(uint32_t crc, const void *data, size_t len) {
 
 void esg_set_error(const std::string &msg) { g_last_error = msg; }
 
+cudaMemPool_t esg_scratch_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    static bool tried[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            const char *keep = getenv("ESG_POOL_KEEP_MB");
+            const long long mb = keep && *keep ? atoll(keep) : 8192;
+            uint64_t bytes = (uint64_t)(mb > 0 ? mb : 0) << 20;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &bytes);
+            pools[dev] = pool;
+        } else {
+            cudaGetLastError();   // clear it: the default pool serves instead
+        }
+    }
+    return pools[dev];
+}
+
 bool esg_fault_alloc() {
     static std::mutex mu;
     static std::string seen;

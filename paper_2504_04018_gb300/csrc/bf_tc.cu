@@ -19,6 +19,7 @@
 #include "esg_internal.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -890,6 +891,15 @@ __global__ void scatter_subset_kernel(const int64_t *idx, int64_t m, int k, cons
     if (threadIdx.x == 0) cnt[q] = cnt_g[i];
 }
 
+// Host clock (ms) for the ESG_BF_STATS=1 phase report.
+static double bf_host_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+static bool bf_stats() {
+    const char *dbg = getenv("ESG_BF_STATS");
+    return dbg && *dbg == '1';
+}
+
 struct Bf2Plan;
 static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, int32_t d, int metric,
                               const float *queries, int64_t nq, const int64_t *l, const int64_t *r, int32_t k,
@@ -1203,6 +1213,7 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
                               int K1, int64_t *out_ids, float *out_dist, int32_t *out_count, cudaStream_t stream,
                               Bf2Plan *given) {
     if (nq == 0) return ESG_OK;
+    const double h0 = bf_stats() ? bf_host_ms() : 0.0;
     const int nk = (d + TK - 1) / TK;
     int dev = 0, max_smem = 0, sms = 0, S = 0, stream_a = 0;
     size_t smem = 0;
@@ -1308,12 +1319,17 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
                 (long long)nqt, (long long)total_tiles, (long long)n_items, (long long)CH, S,
                 stream_a ? " (query tile streamed)" : "");
     std::vector<int64_t> left;
+    const double h1 = bf_stats() ? bf_host_ms() : 0.0;
     if (st == ESG_OK)
         st = certify_and_redo(base, n, d, metric, queries, nq, l, r, k, K1, cand_d, cand_i, cand_n, qrow, X.xmax,
                               redo, err, out_ids, out_dist, out_count, stream, &left);
     cudaFreeAsync(scratch, stream);
+    const double h2 = bf_stats() ? bf_host_ms() : 0.0;
     if (st == ESG_OK && !left.empty())
         st = bf2_escalate(X, base, n, d, metric, queries, nq, l, r, k, K1, left, out_ids, out_dist, out_count, stream);
+    if (bf_stats())
+        fprintf(stderr, "tensor-core brute force, host ms: plan + uploads + launches %.3f, until certified %.3f, "
+                        "escalation %.3f\n", h1 - h0, h2 - h1, bf_host_ms() - h2);
     return st;
 }
 
@@ -1334,6 +1350,7 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
     if (nq == 0) return ESG_OK;
+    const double t0 = bf_stats() ? bf_host_ms() : 0.0;
     const int nk = (d + TK - 1) / TK;
     const int64_t xt = (n + TN - 1) / TN;
     // the ranges come to the host first, so that the host plan is made while
@@ -1362,8 +1379,11 @@ static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int 
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) { esg_set_error(cudaGetErrorString(ce)); st = ESG_ERR_CUDA; }
+    const double t1 = bf_stats() ? bf_host_ms() : 0.0;
     Bf2Plan P;
     if (st == ESG_OK) st = bf2_plan(hl.data(), hr.data(), nq, n, d, sms, P);
+    if (bf_stats()) fprintf(stderr, "tensor-core brute force, host ms: ranges + point prep queued %.3f, plan %.3f\n",
+                            t1 - t0, bf_host_ms() - t1);
     if (st == ESG_OK) {
         const PreparedX X{xs, xnorm, xrow, xmax};
         st = bf2_queries(X, base, n, d, metric, queries, nq, l, r, k, K1, out_ids, out_dist, out_count, stream, &P);

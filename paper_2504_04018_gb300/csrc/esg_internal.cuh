@@ -40,9 +40,16 @@ inline cudaError_t esg_malloc(void **p, size_t bytes) {
     if (esg_fault_alloc()) { *p = nullptr; return cudaErrorMemoryAllocation; }
     return cudaMalloc(p, bytes);
 }
+// Stream-ordered scratch comes from the library's own memory pool on the
+// current device, which keeps up to ESG_POOL_KEEP_MB (default 8192) MiB of
+// freed memory mapped between calls (the default pool returns it at every
+// synchronisation, and mapping hundreds of MB again costs a call a fraction
+// of a millisecond); null if the pool could not be made (then the default pool).
+cudaMemPool_t esg_scratch_pool();
 inline cudaError_t esg_malloc_async(void **p, size_t bytes, cudaStream_t stream) {
     if (esg_fault_alloc()) { *p = nullptr; return cudaErrorMemoryAllocation; }
-    return cudaMallocAsync(p, bytes, stream);
+    cudaMemPool_t pool = esg_scratch_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
 }
 
 #define ESG_CUDA_TRY(expr)                                                                 \
