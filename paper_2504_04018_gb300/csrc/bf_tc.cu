@@ -1335,20 +1335,29 @@ static esg_status bf2_queries(const PreparedX &X, const float *base, int64_t n, 
 
 // Pipelined tensor-core path; ESG_ERR_UNSUPPORTED when the shape does not fit
 // (k > 56, or shared memory for fewer than two stages). Each list keeps
-// K1 = k + 8 approximate candidates: the certificate needs the exact k-th
+// K1 = k + 12 approximate candidates (k + 8 where the longer list does not
+// fit in shared memory): the certificate needs the exact k-th
 // distance below the approximate K1-th minus the error bound, which holds for
 // nearly every query, and a short list makes the epilogue's filter sharp; the
 // few queries left uncertified run again with 64 candidates.
 static esg_status bruteforce_tc_v2(const float *base, int64_t n, int32_t d, int metric, const float *queries,
                                    int64_t nq, const int64_t *l, const int64_t *r, int32_t k, int64_t *out_ids,
                                    float *out_dist, int32_t *out_count, cudaStream_t stream) {
-    const int K1 = k + 8;
-    if (k < 1 || K1 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
+    // k + 12 candidates, at least k + 8 (the longest list the kernel holds
+    // caps it): at 1M x 128, 10k queries, k = 10, lists of k + 8 left 2 queries
+    // uncertified and their second pass cost 0.75 ms of a 5.90 ms call; k + 12
+    // certified all (5.52 ms), k + 16 and k + 24 made the epilogue slower
+    // (5.83, 6.56 ms)
+    if (k < 1 || k + 8 > kMaxK1v2 || n >= ((int64_t)1 << 31) || d < 1) return ESG_ERR_UNSUPPORTED;
+    int K1 = std::min(k + 12, kMaxK1v2);
     int dev = 0, max_smem = 0, S = 0, stream_a = 0;
     size_t smem = 0;
     ESG_CUDA_TRY(cudaGetDevice(&dev));
     ESG_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+    if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) {
+        K1 = k + 8;
+        if (bf2_smem(d, K1, max_smem, &S, &smem, &stream_a) != ESG_OK) return ESG_ERR_UNSUPPORTED;
+    }
     if (nq == 0) return ESG_OK;
     const double t0 = bf_stats() ? bf_host_ms() : 0.0;
     const int nk = (d + TK - 1) / TK;

@@ -386,7 +386,7 @@ def test_search_width_keeps_recall(dev, tiny_oracle_index, width):
 def test_bruteforce_tensor_core_vs_oracle(dev, metric, d, k, monkeypatch):
     """Shapes that take the tcgen05 path: query tile resident (d <= 192) or
     streamed with the point chunks (d = 320, 768), d padded to a multiple
-    of 64, lists of k + 8: split BF16 MMAs, certified FP32 re-rank,
+    of 64, lists of k + 12: split BF16 MMAs, certified FP32 re-rank,
     escalation and SIMT redo of uncertified queries."""
     w = synthetic.small_mixture(5000, d, 300, n_comp=16, seed=17 + d + k, metric=metric,
                                 normalise=(metric == "ip"))
