@@ -38,6 +38,10 @@ def test_defaults_and_status_strings():
     assert (b.M, b.leaf_size, b.n_entries) == (16, 256, 16)
     s = lib.esg_search_params_default()
     assert s.ef == 64 and s.use_learned == 0
+    assert (s.post_root, s.max_registers) == (0, 0)
+    t = lib.esg_train_params_default()
+    # the last fields: a mismatch of layout between header and binding would garble them
+    assert (t.ef_lo, t.ef_hi, t.per_k_class, t.seed) == (8, 128, 0, 4005)
     assert lib.esg_status_str(0) == b"ok"
     assert lib.esg_status_str(7) == b"unsupported"
 
@@ -75,3 +79,24 @@ def test_load_missing_and_corrupt_files(tmp_path):
     bad = tmp_path / "bad.esg"
     bad.write_bytes(b"\x00" * 64)
     assert lib.esg_load(str(bad).encode(), ctypes.byref(h)) == 5                     # CORRUPT
+
+
+def test_binding_structs_follow_the_header():
+    """The ctypes records of the binding list the header's struct fields in
+    the header's order (names, and 32/64-bit widths)."""
+    hdr = open(os.path.join(ROOT, "include", "esg.h")).read()
+    for cname, pyname in (("esg_build_params", "_BuildParams"), ("esg_search_params", "_SearchParams"),
+                          ("esg_train_params", "_TrainParams")):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + cname + r";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, names = decl.split(None, 1)
+            for nm in names.split(","):
+                fields.append((nm.strip(), 8 if typ in ("uint64_t", "int64_t", "double") else 4))
+        py = getattr(E, pyname)._fields_
+        assert [f for f, _ in py] == [f for f, _ in fields], cname
+        assert [ctypes.sizeof(t) for _, t in py] == [w for _, w in fields], cname
