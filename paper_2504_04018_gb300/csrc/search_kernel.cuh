@@ -671,7 +671,7 @@ search_kernel(SearchArgs a) {
         w.hash = reinterpret_cast<uint32_t *>(arena + (size_t)cap * 8);
         vis.hs = w.hash;
         vis.hsize = (uint32_t)(a.H + 2 * (a.C - cap));
-        vis.hlimit = (int)(vis.hsize / 4) * 3;
+        vis.hlimit = (int)(vis.hsize / 8) * 7;   // two-choice buckets stay short up to 7/8
         bool saturated = false;
 
         if (!is_graph) {
