@@ -158,10 +158,13 @@ typedef struct {
  *                  visit order);
  *  warps_per_block, hash_slots, lanes_per_row
  *                  launch shape knobs that do not change results: warps per
- *                  CTA (1, 2 or 4), shared visited-table slots (power of two,
- *                  1024..16384) and lanes that share one row gather (1..32,
- *                  a power of two dividing the row's 16-byte vectors); 0 =
- *                  automatic. esg_autotune picks them;
+ *                  CTA (1, 2 or 4), shared visited-table slots of a search
+ *                  whose candidate list is the smallest, 256 items (power of
+ *                  two, 1024..16384; a search with a wider beam has two fewer
+ *                  per list item above 256, at least 1,024) and lanes that
+ *                  share one row gather (1..32, a power of two dividing the
+ *                  row's 16-byte vectors); 0 = automatic (2,048 slots).
+ *                  esg_autotune picks them;
  *  post_root       0 = the elastic decomposition of the index's layout;
  *                  1 = every query is one piece: POST on the root graph alone
  *                  (a scan when the root is a leaf), the baseline the elastic
